@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Throughput of the box-stencil sweeps on GB300: GPoints/s and roofline.
+
+Workload (one step): one radius-1 (27-point) and one radius-2 (125-point) box
+sweep of a 512^3 FP32 interior plus halo, coefficients ~ N(0, 1/npts), input
+U[-1, 1], through the library's AUTO path (the fastest path that meets FP32
+accuracy).  Inputs (550 MB each) and outputs (537 MB each) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank sweeps its own independent grids (weak
+scaling, no collective on the data path); `value` counts the points of all
+ranks over the slowest rank's time.  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "GPoints/s & % roofline per sweep; TC split-precision vs FP32 CUDA-core at ≤1e-5"
+N = 512
+RADII = (1, 2)
+FLOP_PER_PT = {1: 2 * 27, 2: 2 * 125}
+WORKLOAD = "box stencil sweeps r=1 (27 pt) + r=2 (125 pt), 512^3 FP32 interior + halo"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 1900.0, 2070.0, "fallback"
+
+
+def fp32_alu_peak_tflops(n_sm: int, mhz: float) -> float:
+    # 128 FP32 lanes per SM, one FMA (2 flop) per lane per clock.
+    return n_sm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(planes: int, salt: int = 0):
+    """Oracle on the first `planes` output planes of both sweeps; returns
+    (points, seconds, threads)."""
+    import oracle
+    pts, secs = 0, 0.0
+    for r in RADII:
+        c = workloads.normal_coeffs("box", r, workload=2, salt=r)
+        g = workloads.rng(2, 50 + r + 100 * salt)
+        sub = g.uniform(-1, 1, size=(planes + 2 * r, N + 2 * r, N + 2 * r)).astype(np.float32)
+        sub = sub.astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.stencil("box", r, c, sub)
+        secs += time.perf_counter() - t0
+        pts += planes * N * N
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return pts, secs, threads
+
+
+def calibrate_planes(budget_s: float) -> int:
+    pts, secs, _ = oracle_sample(2)
+    per_plane = secs / 2
+    return max(2, min(N, int(budget_s / max(per_plane, 1e-6))))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    budget = float(os.environ.get("MMS_REF_STEP_SECONDS", "6"))
+    planes = calibrate_planes(budget)
+    for _ in range(args.warmup):
+        oracle_sample(max(1, planes // 8))
+    total_pts, total_s = 0, 0.0
+    threads = 1
+    for k in range(args.steps):
+        p, s, threads = oracle_sample(planes, salt=k)
+        total_pts += p
+        total_s += s
+    value = total_pts / total_s / 1e9
+    sample = (f"FP64 oracle, box r=1 and r=2 on the first {planes} of 512 output planes of a "
+              f"512^2 x {planes} slab per sweep, per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GPoints/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GPoints/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GPoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--path", default="auto")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2507_11067_gb300 as mms
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mms.build()
+    mms.load()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    hbm_peak, bf16_peak, sm_max_mhz, peak_src = peaks()
+
+    # ---- inputs (seeded per rank), resident in HBM before timing
+    coeffs, inputs, outputs, hosts = {}, {}, {}, {}
+    for r in RADII:
+        coeffs[r] = workloads.normal_coeffs("box", r, workload=2, salt=r)
+        grid = workloads.uniform_grid(N, N, N, r, workload=2, salt=r + 100 * rank)
+        hosts[r] = torch.from_numpy(grid).pin_memory()
+        inputs[r] = mms.padded_empty(N, N, N, r, device=dev, zero=False)
+        inputs[r].copy_(hosts[r])
+        outputs[r] = torch.empty((N, N, N), device=dev)
+        del grid
+    host_out = {r: torch.empty((N, N, N), pin_memory=True) for r in RADII}
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for r in RADII:
+            mms.apply("box", r, coeffs[r], inputs[r], outputs[r], path=args.path)
+
+    # ---- device-resident timing
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
+    kernel_ms = {r: [] for r in RADII}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        e0, e1, e2 = ev[2 * k], ev[2 * k + 1], torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mms.apply("box", 1, coeffs[1], inputs[1], outputs[1], path=args.path)
+        e1.record(stream)
+        mms.apply("box", 2, coeffs[2], inputs[2], outputs[2], path=args.path)
+        e2.record(stream)
+        kernel_ms[1].append((e0, e1))
+        kernel_ms[2].append((e1, e2))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    pts_step = len(RADII) * N ** 3
+    value = world * pts_step * args.steps / elapsed / 1e9
+    kms = {r: statistics.mean(a.elapsed_time(b) for a, b in kernel_ms[r]) for r in RADII}
+
+    # ---- end to end through the public API: host in, host out, every step
+    for _ in range(2):
+        for r in RADII:
+            inputs[r].copy_(hosts[r], non_blocking=True)
+            mms.apply("box", r, coeffs[r], inputs[r], outputs[r], path=args.path)
+            host_out[r].copy_(outputs[r], non_blocking=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_s.record(stream)
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        for r in RADII:
+            inputs[r].copy_(hosts[r], non_blocking=True)
+            mms.apply("box", r, coeffs[r], inputs[r], outputs[r], path=args.path)
+            host_out[r].copy_(outputs[r], non_blocking=True)
+    e_e.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e_s.elapsed_time(e_e) / 1e3
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(hosts[r].numel() * 4 for r in RADII)
+    d2h = sum(host_out[r].numel() * 4 for r in RADII)
+    e2e_value = world * pts_step * e2e_steps / e2e_s / 1e9
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- dominant kernel roofline: the 125-point sweep on FP32 ALUs
+    path_used = args.path
+    dom_r = max(RADII, key=lambda r: kms[r])
+    flops = FLOP_PER_PT[dom_r] * N ** 3
+    achieved_tf = flops / (kms[dom_r] / 1e3) / 1e12
+    alu_peak = fp32_alu_peak_tflops(n_sm, sm_max_mhz)
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / alu_peak, "traffic": None,
+                "kernel": f"box r={dom_r} sweep ({path_used})",
+                "peak_note": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz (max SM clock)"}
+
+    sweeps = {}
+    for r in RADII:
+        bytes_alg = 4 * ((N + 2 * r) ** 3 + N ** 3)
+        sweeps[f"box_r{r}"] = {"ms": kms[r], "gpts": N ** 3 / (kms[r] / 1e3) / 1e9,
+                               "hbm_gbs": bytes_alg / (kms[r] / 1e3) / 1e9,
+                               "hbm_frac": bytes_alg / (kms[r] / 1e3) / 1e9 / hbm_peak,
+                               "tflops": FLOP_PER_PT[r] * N ** 3 / (kms[r] / 1e3) / 1e12,
+                               "alu_frac": FLOP_PER_PT[r] * N ** 3 / (kms[r] / 1e3) / 1e12 / alu_peak}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        planes = calibrate_planes(5.0)
+        p, s, threads = oracle_sample(planes)
+        cpu = {"value": p / s / 1e9, "unit": "GPoints/s", "cores": threads, "kind": "oracle",
+               "sample": f"FP64 oracle, box r=1 and r=2, first {planes} of 512 output planes each"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GPoints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "path": path_used, "radii": list(RADII), "n": N,
+                   "l2": "inputs and outputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "GPoints/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": len(RADII) * args.steps,
+        "clocks": clk, "peaks": {"hbm_gbs": hbm_peak, "bf16_tflops": bf16_peak, "source": peak_src},
+        "sweeps": sweeps,
+    }
+    if not args.no_extras:
+        line["extras"] = extras(mms, torch, dev, hbm_peak, alu_peak)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _time(fn, reps=5):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def extras(mms, torch, dev, hbm_peak, alu_peak):
+    """Per-path timings outside the timed region: every sweep path on the
+    box workload, and the 1024^3 star r=4 against the HBM roofline."""
+    out = {}
+    for r in RADII:
+        c = workloads.normal_coeffs("box", r, workload=2, salt=r)
+        g = torch.Generator(device=dev).manual_seed(1000 + r)
+        inp = mms.padded_empty(N, N, N, r, device=dev, zero=False)
+        inp.uniform_(-1, 1, generator=g)
+        o = torch.empty((N, N, N), device=dev)
+        for path in ("cuda_core", "naive", "tf32", "3xtf32", "bf16x3"):
+            if mms.num_variants("box", r, path) == 0:
+                continue
+            ms = _time(lambda: mms.apply("box", r, c, inp, o, path=path))
+            out[f"box_r{r}_{path}"] = {"ms": ms, "gpts": N ** 3 / ms / 1e6}
+        del inp, o
+    n = 1024
+    inp = mms.padded_empty(n, n, n, 4, device=dev, zero=False)
+    inp.uniform_(-1, 1, generator=torch.Generator(device=dev).manual_seed(7))
+    o = torch.empty((n, n, n), device=dev)
+    c = workloads.fd8_star_coeffs()
+    ms = _time(lambda: mms.apply("star", 4, c, inp, o, path="cuda_core"))
+    bytes_alg = 4 * ((n + 8) ** 3 + n ** 3)
+    out["star_r4_1024_cuda_core"] = {"ms": ms, "gpts": n ** 3 / ms / 1e6,
+                                     "hbm_gbs": bytes_alg / ms / 1e6,
+                                     "hbm_frac": bytes_alg / ms / 1e6 / hbm_peak}
+    del inp, o
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * mms.h -- C ABI of the GB300 (sm_103a) stencil-as-matrix-product library.
+ *
+ * All entry points are plain C: pointers, sizes and enums, no C++ or torch
+ * types.  Device pointers are CUDA global-memory addresses of the calling
+ * thread's current device; host pointers are ordinary process memory.
+ * `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ * stream).  Every call is asynchronous on `stream` unless stated otherwise.
+ *
+ * Ownership: the caller owns every buffer.  Host arrays (coefficients,
+ * source positions, descriptors) are read before the call returns and may be
+ * freed right after.  Device buffers must stay valid until the work queued
+ * on `stream` has finished.  The library keeps only caches keyed by value
+ * (prepared coefficient bands, tensor maps) and one device error word.
+ *
+ * Errors: arguments are validated before anything is queued.  A non-OK
+ * status means nothing was queued by that call (MMS_E_CUDA: a launch was
+ * refused by the runtime); mms_last_error() returns a thread-local message.
+ * Device-side faults of the library's own checks (a bounded wait that ran
+ * out, an index check in a debug build) set a device error word that
+ * mms_check_device() reads and clears; no kernel traps.
+ *
+ * Grid conventions (paper Sec. 1, Fig. 1 and Sec. 4.1): the interior has
+ * nx*ny*nz points, x fastest.  A stencil of radius r reads a grid padded by
+ * r on every face: padded element (X,Y,Z), 0 <= X < nx+2r etc., lives at
+ * in[Z*in_pitch_z + Y*in_pitch_y + X].  Output point (x,y,z) lives at
+ * out[z*out_pitch_z + y*out_pitch_y + x] and is
+ *     out(x,y,z) = sum_d c_d * in(x+r+dx, y+r+dy, z+r+dz)
+ * over the stencil's offsets d.  Pitches are in elements; 0 selects the
+ * dense value (in: nx+2r and (ny+2r)*pitch_y; out: nx and ny*pitch_y).
+ */
+#ifndef MMS_H
+#define MMS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MMS_OK = 0,
+    MMS_E_ARG = 1,          /* invalid argument (radius, sizes, null or overlapping buffers) */
+    MMS_E_UNSUPPORTED = 2,  /* valid request that this build does not implement */
+    MMS_E_ALIGN = 3,        /* a pitch or address that the forced path cannot use */
+    MMS_E_CUDA = 4,         /* the CUDA runtime refused a call or launch */
+    MMS_E_TIMEOUT = 5,      /* a bounded device-side wait ran out (from mms_check_device) */
+    MMS_E_DEVICE = 6,       /* a device-side check failed (from mms_check_device) */
+    MMS_E_NOMEM = 7         /* host-side allocation of a cache entry failed */
+} mms_status;
+
+/* Stencil shapes (paper Sec. 1, Fig. 1). */
+typedef enum {
+    MMS_STAR = 0,  /* axis neighbours only: 6r+1 points */
+    MMS_BOX = 1    /* full (2r+1)^3 cube */
+} mms_shape;
+
+/* Computation paths of a sweep. */
+typedef enum {
+    MMS_PATH_AUTO = 0,       /* library choice (the fastest path meeting FP32-level accuracy) */
+    MMS_PATH_CUDA_CORE = 1,  /* FP32 FMA on CUDA cores, TMA-staged plane tiles */
+    MMS_PATH_TF32 = 2,       /* tensor cores, one TF32 product (reduced accuracy) */
+    MMS_PATH_3XTF32 = 3,     /* tensor cores, TF32 hi/lo split, 3 products, FP32 accumulate */
+    MMS_PATH_BF16X3 = 4,     /* tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
+    MMS_PATH_NAIVE = 5       /* one thread per point, global loads (any pitch) */
+} mms_path;
+
+/*
+ * Coefficient layouts (host, float32):
+ *   star: 3*(2r+1) values, c[axis*(2r+1) + d+r] for axis 0=x, 1=y, 2=z and
+ *         d = -r..r; the applied centre weight is cx[0]+cy[0]+cz[0];
+ *   box:  (2r+1)^3 values, c[((dz+r)*(2r+1) + dy+r)*(2r+1) + dx+r].
+ * The paper's Sec. 4.1 turns each axis's 1D weights into a banded coefficient
+ * matrix; the library builds those bands from these arrays.
+ */
+
+/*
+ * One stencil sweep with dense layouts (pitches 0) and the AUTO path.
+ * shape: MMS_STAR or MMS_BOX; radius: 1..4; coeffs: host, layout above;
+ * in: device, (nz+2r)(ny+2r)(nx+2r) floats; out: device, nz*ny*nx floats;
+ * in and out must not overlap.  nx, ny, nz >= 0 (an empty interior queues
+ * nothing and returns MMS_OK).
+ * Defined by: paper Sec. 1 (star and box stencils, Fig. 1) and Sec. 4.1
+ * (stencil as banded matrix products, halo of width r).
+ */
+mms_status mms_stencil_apply(int shape, int radius, const float *coeffs, const float *in,
+                             float *out, int64_t nx, int64_t ny, int64_t nz, void *stream);
+
+/* Full description of a sweep: shape, radius, sizes, pitches, path and an
+ * optional tile-configuration index (variant; -1 = library choice, see
+ * mms_num_variants). */
+typedef struct {
+    int32_t shape;
+    int32_t radius;
+    const float *coeffs;   /* host */
+    int64_t nx, ny, nz;
+    int64_t in_pitch_y, in_pitch_z;    /* elements, 0 = dense */
+    int64_t out_pitch_y, out_pitch_z;  /* elements, 0 = dense */
+    int32_t path;          /* mms_path */
+    int32_t variant;       /* -1 = library choice */
+} mms_stencil_desc;
+
+/*
+ * The sweep of mms_stencil_apply with explicit pitches, path and tile
+ * variant.  The TMA-staged paths need in_pitch_y*4 and in_pitch_z*4 to be
+ * multiples of 16 bytes and `in` 16-byte aligned; with MMS_PATH_AUTO an
+ * input that breaks this runs on MMS_PATH_NAIVE, with a forced TMA path it
+ * returns MMS_E_ALIGN.  Tensor-core paths support the box shape with
+ * radius 1..4 and the star shape (as three per-axis banded passes) and
+ * return MMS_E_UNSUPPORTED otherwise.
+ * Defined by: paper Sec. 1, Sec. 4.1 (banded products), Sec. 4.3 (box as
+ * 2r+1 shifted 1D stencils per plane).
+ */
+mms_status mms_stencil_apply_ex(const mms_stencil_desc *desc, const float *in, float *out,
+                                void *stream);
+
+/* Number of tile variants of (shape, radius, path); variant indices run
+ * 0..n-1.  Returns 0 for an unsupported combination.  Host only. */
+int32_t mms_num_variants(int shape, int radius, int path);
+
+/* Library choice of variant for (shape, radius, path, nx, ny, nz), after any
+ * mms_set_variant override.  Host only. */
+int32_t mms_default_variant(int shape, int radius, int path, int64_t nx, int64_t ny, int64_t nz);
+
+/* Record a tuned variant for (shape, radius, path); used by MMS_PATH_AUTO
+ * and variant -1 from then on in this process.  variant -1 clears it. */
+mms_status mms_set_variant(int shape, int radius, int path, int32_t variant);
+
+/* ------------------------------------------------------- acoustic wave */
+
+/*
+ * Geometry of the damped acoustic wave step used for reverse time migration
+ * (paper Sec. 2.1 names RTM with radius-4 stencils; Sec. 5.5 runs it).  The
+ * paper prints no discretisation; the step is
+ *     a^{n+1} = G*( (2 + m*L) a^n - G*a^{n-1} + s^n )
+ * with L the star stencil of `radius` (unscaled weights), m = v^2 dt^2/h^2,
+ * G = g(x) g(y) g(z) the Cerjan sponge g(d) = exp(-(a (w-d))^2) for the
+ * cell at distance d < w from the nearest face (1 otherwise), and s^n the
+ * source value at one point per shot.  Fields are padded by `radius` with a
+ * zero halo that the library never writes; shots are stacked at
+ * `shot_stride` elements.
+ */
+typedef struct {
+    int64_t nx, ny, nz;        /* interior */
+    int32_t radius;            /* 1..4 */
+    int32_t nshots;            /* >= 1 */
+    int64_t pitch_y, pitch_z;  /* padded field pitches (elements), 0 = dense */
+    int64_t shot_stride;       /* elements between shots, 0 = pitch_z*(nz+2r) */
+    int32_t sponge_width;      /* w >= 0 (0 = no sponge) */
+    float sponge_a;            /* a */
+    int32_t rec_z;             /* receiver plane (interior z), -1 = no records */
+    const int32_t *src_xyz;    /* host, 3*nshots interior (x,y,z); x < 0 = no source */
+} mms_wave_desc;
+
+/*
+ * One forward step for all shots.
+ * coeffs: host 3*(2r+1) star weights; m: device padded field (one, shared by
+ * all shots; its halo is never read); p_cur: device a^n (nshots stacked);
+ * p_prev: device, in a^{n-1}, out a^{n+1} (in place); src_amp: device,
+ * nshots floats s^n; rec: device nshots*ny*nx floats receiving R a^{n+1}
+ * (NULL = none).  Receivers are the plane z = rec_z.
+ */
+mms_status mms_wave_step(const mms_wave_desc *desc, const float *coeffs, const float *m,
+                         const float *p_cur, float *p_prev, const float *src_amp, float *rec,
+                         void *stream);
+
+/* Flags of mms_wave_forward. */
+#define MMS_WAVE_GRAPH 1u  /* capture the step sequence once into a CUDA graph and replay it */
+
+/*
+ * nsteps forward steps from the states in p0 (a^{n-1}) and p1 (a^n); on
+ * return p0/p1 hold the last two states (p1 = newest when nsteps is even,
+ * p0 when odd: the buffers alternate).  amps: device nsteps*nshots source
+ * values; rec_all: device nsteps*nshots*ny*nx (NULL = none), row n = R a^{n+1}.
+ * ckpt: device buffer of (nsteps/ckpt_every) checkpoints, each 2 stacked
+ * shot sets (a^{k}, a^{k-1} at k = j*ckpt_every, j = 0..), NULL = none.
+ */
+mms_status mms_wave_forward(const mms_wave_desc *desc, const float *coeffs, const float *m,
+                            const float *amps, int32_t nsteps, float *p0, float *p1,
+                            float *rec_all, float *ckpt, int32_t ckpt_every, uint32_t flags,
+                            void *stream);
+
+/*
+ * One step of the discrete adjoint of mms_wave_step for all shots:
+ *     lam^n = R^T r^n + (2 + L m) G lam^{n+1} - G^2 lam^{n+2}
+ *     grad_m += sum_shots G lam^{n+1} (L a^n)          (FP64)
+ * lam_cur: device lam^{n+1} (padded, zero halo); lam_prev: device, in
+ * lam^{n+2}, out lam^n; resid: device nshots*ny*nx r^n on the receiver plane
+ * (NULL = none); a_n: device forward state a^n (NULL = no gradient term);
+ * grad_m: device nz*ny*nx doubles (dense), accumulated.  m must be padded
+ * (its halo values are multiplied by the zero halo of lam).
+ */
+mms_status mms_wave_adjoint(const mms_wave_desc *desc, const float *coeffs, const float *m,
+                            const float *lam_cur, float *lam_prev, const float *resid,
+                            const float *a_n, double *grad_m, void *stream);
+
+/* m = v^2 dt^2 / h^2 into a padded field (halo set to 0); v dense nz*ny*nx. */
+mms_status mms_model_from_velocity(const mms_wave_desc *desc, const float *v, float *m,
+                                   float dt, float h, void *stream);
+
+/* grad_v = grad_m * 2 v dt^2 / h^2 (chain rule of m = v^2 dt^2/h^2), n values. */
+mms_status mms_grad_to_velocity(const double *grad_m, const float *v, double *grad_v, int64_t n,
+                                float dt, float h, void *stream);
+
+/* result[0] = sum_i a[i]*b[i] in FP64 over n floats (device in, device out). */
+mms_status mms_dot_f64(const float *a, const float *b, int64_t n, double *result, void *stream);
+
+/* ------------------------------------------------------------ status */
+
+/* Thread-local message of the last non-OK status of this thread. */
+const char *mms_last_error(void);
+
+/* Synchronises `stream`, reads and clears the device error word of the
+ * current device: MMS_OK, MMS_E_TIMEOUT or MMS_E_DEVICE (or MMS_E_CUDA if
+ * the synchronisation itself failed). */
+mms_status mms_check_device(void *stream);
+
+/* Library version string. */
+const char *mms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMS_H */

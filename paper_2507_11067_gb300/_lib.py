@@ -1,0 +1,275 @@
+"""ctypes binding of libmms.so (include/mms.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  torch tensors provide device memory and the current stream.  If
+the shared library has not been built, loading fails with an explicit error;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+STAR, BOX = 0, 1
+SHAPES = {"star": STAR, "box": BOX, STAR: STAR, BOX: BOX}
+PATHS = {"auto": 0, "cuda_core": 1, "tf32": 2, "3xtf32": 3, "bf16x3": 4, "naive": 5}
+PATH_NAMES = {v: k for k, v in PATHS.items()}
+STATUS = {0: "MMS_OK", 1: "MMS_E_ARG", 2: "MMS_E_UNSUPPORTED", 3: "MMS_E_ALIGN", 4: "MMS_E_CUDA",
+          5: "MMS_E_TIMEOUT", 6: "MMS_E_DEVICE", 7: "MMS_E_NOMEM"}
+WAVE_GRAPH = 1
+
+# Every symbol include/mms.h declares (checked by the CPU test suite).
+EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_num_variants", "mms_default_variant",
+           "mms_set_variant", "mms_wave_step", "mms_wave_forward", "mms_wave_adjoint",
+           "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
+           "mms_check_device", "mms_version"]
+
+
+class MMSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class StencilDesc(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("coeffs", ctypes.c_void_p), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("nz", ctypes.c_int64), ("in_pitch_y", ctypes.c_int64),
+                ("in_pitch_z", ctypes.c_int64), ("out_pitch_y", ctypes.c_int64),
+                ("out_pitch_z", ctypes.c_int64), ("path", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
+
+
+class WaveDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("radius", ctypes.c_int32), ("nshots", ctypes.c_int32),
+                ("pitch_y", ctypes.c_int64), ("pitch_z", ctypes.c_int64),
+                ("shot_stride", ctypes.c_int64), ("sponge_width", ctypes.c_int32),
+                ("sponge_a", ctypes.c_float), ("rec_z", ctypes.c_int32),
+                ("src_xyz", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libmms.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: run "
+                               "paper_2507_11067_gb300.build.build() (or __graft_entry__.build()) first")
+        lib = ctypes.CDLL(path)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        sig = {
+            "mms_stencil_apply": [i32, i32, P, P, P, i64, i64, i64, P],
+            "mms_stencil_apply_ex": [ctypes.POINTER(StencilDesc), P, P, P],
+            "mms_num_variants": [i32, i32, i32],
+            "mms_default_variant": [i32, i32, i32, i64, i64, i64],
+            "mms_set_variant": [i32, i32, i32, i32],
+            "mms_wave_step": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P],
+            "mms_wave_forward": [ctypes.POINTER(WaveDesc), P, P, P, i32, P, P, P, P, i32,
+                                 ctypes.c_uint32, P],
+            "mms_wave_adjoint": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
+            "mms_model_from_velocity": [ctypes.POINTER(WaveDesc), P, P, ctypes.c_float,
+                                        ctypes.c_float, P],
+            "mms_grad_to_velocity": [P, P, P, i64, ctypes.c_float, ctypes.c_float, P],
+            "mms_dot_f64": [P, P, i64, P, P],
+            "mms_last_error": [],
+            "mms_check_device": [P],
+            "mms_version": [],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int32
+        lib.mms_last_error.restype = ctypes.c_char_p
+        lib.mms_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def check(status: int):
+    if status != 0:
+        raise MMSError(status, load().mms_last_error().decode())
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(None)
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _host_coeffs(coeffs) -> np.ndarray:
+    c = coeffs
+    if hasattr(c, "detach"):
+        c = c.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(c, dtype=np.float32).reshape(-1))
+
+
+# ------------------------------------------------------------ allocation
+
+def padded_empty(nx, ny, nz, r, device="cuda", align=32, nshots=None, dtype=None, zero=True):
+    """A padded grid view (nz+2r, ny+2r, nx+2r) over storage whose row pitch
+    is rounded up to `align` elements (the TMA paths need 16-byte pitches);
+    with nshots, a (nshots, ...) stack.  The halo (and pad) start at zero."""
+    import torch
+    dtype = dtype or torch.float32
+    X, Y, Z = nx + 2 * r, ny + 2 * r, nz + 2 * r
+    py = -(-X // align) * align
+    shape = (Z, Y, py) if nshots is None else (nshots, Z, Y, py)
+    base = (torch.zeros if zero else torch.empty)(shape, device=device, dtype=dtype)
+    return base[..., :X]
+
+
+def pitches(t):
+    """(pitch_y, pitch_z) in elements of a 3D (z, y, x) view with unit x stride."""
+    if t.dim() != 3 or t.stride(2) != 1:
+        raise ValueError("expected a 3D (z, y, x) tensor with unit x stride")
+    return t.stride(1), t.stride(0)
+
+
+def to_padded_device(grid: np.ndarray, r: int, device="cuda", align=32):
+    """Copy a host padded grid (nz+2r, ny+2r, nx+2r) into a pitched device view."""
+    import torch
+    Z, Y, X = grid.shape
+    t = padded_empty(X - 2 * r, Y - 2 * r, Z - 2 * r, r, device=device, align=align, zero=False)
+    t.copy_(torch.from_numpy(np.ascontiguousarray(grid, dtype=np.float32)))
+    return t
+
+
+# ---------------------------------------------------------------- sweeps
+
+def apply(shape, r, coeffs, inp, out=None, path="auto", variant=-1, stream=None):
+    """One stencil sweep: out(x,y,z) = sum_d c_d in(x+r+dx, ...) (mms_stencil_apply_ex).
+
+    inp: CUDA float32 (nz+2r, ny+2r, nx+2r) view with unit x stride (any
+    pitches); out: (nz, ny, nx) view or None (allocated).  Returns out.
+    """
+    import torch
+    if not inp.is_cuda or inp.dtype != torch.float32:
+        raise ValueError("input must be a CUDA float32 tensor")
+    Z, Y, X = inp.shape
+    nx, ny, nz = X - 2 * r, Y - 2 * r, Z - 2 * r
+    if out is None:
+        out = torch.empty((nz, ny, nx), device=inp.device, dtype=torch.float32)
+    ipy, ipz = pitches(inp)
+    opy, opz = pitches(out)
+    c = _host_coeffs(coeffs)
+    d = StencilDesc(SHAPES[shape], r, c.ctypes.data, nx, ny, nz, ipy, ipz, opy, opz,
+                    PATHS[path] if isinstance(path, str) else int(path), int(variant))
+    check(load().mms_stencil_apply_ex(ctypes.byref(d), _ptr(inp), _ptr(out), _stream(stream)))
+    return out
+
+
+def apply_dense(shape, r, coeffs, inp, out, stream=None):
+    """mms_stencil_apply on dense contiguous tensors (AUTO path)."""
+    c = _host_coeffs(coeffs)
+    Z, Y, X = inp.shape
+    check(load().mms_stencil_apply(SHAPES[shape], r, c.ctypes.data_as(ctypes.c_void_p), _ptr(inp),
+                                   _ptr(out), X - 2 * r, Y - 2 * r, Z - 2 * r, _stream(stream)))
+    return out
+
+
+def num_variants(shape, r, path) -> int:
+    return load().mms_num_variants(SHAPES[shape], r, PATHS[path])
+
+
+def default_variant(shape, r, path, nx=0, ny=0, nz=0) -> int:
+    return load().mms_default_variant(SHAPES[shape], r, PATHS[path], nx, ny, nz)
+
+
+def set_variant(shape, r, path, variant):
+    check(load().mms_set_variant(SHAPES[shape], r, PATHS[path], int(variant)))
+
+
+def check_device(stream=None):
+    check(load().mms_check_device(_stream(stream)))
+
+
+def version() -> str:
+    return load().mms_version().decode()
+
+
+# ------------------------------------------------------------------ wave
+
+def wave_desc(nx, ny, nz, r, nshots, pitch_y=0, pitch_z=0, shot_stride=0, sponge_width=0,
+              sponge_a=0.0, rec_z=-1, src=None):
+    """A WaveDesc plus the host source array it points to (keep both alive)."""
+    src_arr = None
+    if src is not None:
+        src_arr = np.ascontiguousarray(np.asarray(src, dtype=np.int32).reshape(-1))
+        if src_arr.size != 3 * nshots:
+            raise ValueError("src needs 3 coordinates per shot")
+    d = WaveDesc(nx, ny, nz, r, nshots, pitch_y, pitch_z, shot_stride, sponge_width,
+                 float(sponge_a), rec_z, None if src_arr is None else src_arr.ctypes.data)
+    return d, src_arr
+
+
+def field_geometry(fields):
+    """(pitch_y, pitch_z, shot_stride) of a (nshots, Z, Y, X) stacked view."""
+    if fields.dim() != 4 or fields.stride(3) != 1:
+        raise ValueError("expected a (nshots, z, y, x) view with unit x stride")
+    return fields.stride(2), fields.stride(1), fields.stride(0)
+
+
+def wave_step(desc, coeffs, m, p_cur, p_prev, src_amp, rec=None, stream=None):
+    c = _host_coeffs(coeffs)
+    check(load().mms_wave_step(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
+                               _ptr(p_cur), _ptr(p_prev), _ptr(src_amp), _ptr(rec),
+                               _stream(stream)))
+
+
+def wave_forward(desc, coeffs, m, amps, nsteps, p0, p1, rec_all=None, ckpt=None, ckpt_every=0,
+                 graph=False, stream=None):
+    c = _host_coeffs(coeffs)
+    check(load().mms_wave_forward(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
+                                  _ptr(amps), int(nsteps), _ptr(p0), _ptr(p1), _ptr(rec_all),
+                                  _ptr(ckpt), int(ckpt_every), WAVE_GRAPH if graph else 0,
+                                  _stream(stream)))
+
+
+def wave_adjoint(desc, coeffs, m, lam_cur, lam_prev, resid=None, a_n=None, grad_m=None,
+                 stream=None):
+    c = _host_coeffs(coeffs)
+    check(load().mms_wave_adjoint(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
+                                  _ptr(lam_cur), _ptr(lam_prev), _ptr(resid), _ptr(a_n),
+                                  _ptr(grad_m), _stream(stream)))
+
+
+def model_from_velocity(desc, v, m, dt, h, stream=None):
+    check(load().mms_model_from_velocity(ctypes.byref(desc), _ptr(v), _ptr(m), float(dt),
+                                         float(h), _stream(stream)))
+
+
+def grad_to_velocity(grad_m, v, grad_v, dt, h, stream=None):
+    check(load().mms_grad_to_velocity(_ptr(grad_m), _ptr(v), _ptr(grad_v), grad_m.numel(),
+                                      float(dt), float(h), _stream(stream)))
+
+
+def dot_f64(a, b, result, stream=None):
+    check(load().mms_dot_f64(_ptr(a), _ptr(b), a.numel(), _ptr(result), _stream(stream)))

@@ -1,0 +1,476 @@
+// abi.cu -- the C ABI of include/mms.h: argument validation, path and
+// variant choice, TMA descriptor encoding, error reporting.
+#include <cudaTypedefs.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+#include "wave.cuh"
+
+namespace mms {
+
+static thread_local std::string g_last_error;
+
+mms_status fail(mms_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+mms_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(MMS_E_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------- tensor maps
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+bool encode_tmap_3d(CUtensorMap *map, const float *base, int64_t X, int64_t Y, int64_t Z,
+                    int64_t py, int64_t pz, int bx, int by, int bz)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)Z};
+    cuuint64_t strides[2] = {(cuuint64_t)py * 4, (cuuint64_t)pz * 4};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool encode_tmap_4d(CUtensorMap *map, const float *base, int64_t X, int64_t Y, int64_t Z,
+                    int64_t W, int64_t py, int64_t pz, int64_t pw, int bx, int by, int bz)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)Z, (cuuint64_t)W};
+    cuuint64_t strides[3] = {(cuuint64_t)py * 4, (cuuint64_t)pz * 4, (cuuint64_t)pw * 4};
+    cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------- variant table
+static std::mutex g_var_mu;
+static int g_tuned[2][kMaxR + 1][8];
+static bool g_tuned_init = false;
+
+static int tuned_variant(int shape, int r, int path)
+{
+    std::lock_guard<std::mutex> lk(g_var_mu);
+    if (!g_tuned_init) {
+        for (auto &a : g_tuned)
+            for (auto &b : a)
+                for (int &c : b) c = -1;
+        g_tuned_init = true;
+    }
+    return g_tuned[shape][r][path];
+}
+
+static int num_variants(int shape, int r, int path)
+{
+    if (shape < 0 || shape > 1 || r < 1 || r > kMaxR) return 0;
+    switch (path) {
+        case MMS_PATH_CUDA_CORE: return shape == MMS_STAR ? star_cc_variants() : box_cc_variants();
+        case MMS_PATH_NAIVE: return 1;
+        case MMS_PATH_TF32:
+        case MMS_PATH_3XTF32:
+        case MMS_PATH_BF16X3: return band_tc_supported(shape, r, path) ? band_tc_variants(shape, r, path) : 0;
+        default: return 0;
+    }
+}
+
+static int default_variant(int shape, int r, int path, int64_t nx, int64_t ny, int64_t nz)
+{
+    const int t = tuned_variant(shape, r, path);
+    if (t >= 0 && t < num_variants(shape, r, path)) return t;
+    (void)nx; (void)ny; (void)nz;
+    if (path == MMS_PATH_CUDA_CORE) return 0;
+    return 0;
+}
+
+static bool tma_ok(const float *in, int64_t ipy, int64_t ipz)
+{
+    return (reinterpret_cast<uintptr_t>(in) % 16) == 0 && (ipy % 4) == 0 && (ipz % 4) == 0;
+}
+
+static bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + nb && b0 < a0 + na;
+}
+
+static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, void *stream)
+{
+    if (!d) return fail(MMS_E_ARG, "null descriptor");
+    const int shape = d->shape, r = d->radius;
+    if (shape != MMS_STAR && shape != MMS_BOX) return fail(MMS_E_ARG, "shape %d is not STAR or BOX", shape);
+    if (r < 1 || r > kMaxR) return fail(MMS_E_ARG, "radius %d outside 1..%d", r, kMaxR);
+    if (!d->coeffs) return fail(MMS_E_ARG, "null coefficient array");
+    if (d->nx < 0 || d->ny < 0 || d->nz < 0) return fail(MMS_E_ARG, "negative size");
+    if (d->nx >= (1ll << 30) || d->ny >= (1ll << 30) || d->nz >= (1ll << 30))
+        return fail(MMS_E_ARG, "size above 2^30");
+    if (d->path < MMS_PATH_AUTO || d->path > MMS_PATH_NAIVE) return fail(MMS_E_ARG, "unknown path %d", d->path);
+    if (d->nx == 0 || d->ny == 0 || d->nz == 0) return MMS_OK;
+    if (!in || !out) return fail(MMS_E_ARG, "null grid pointer");
+    const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * r;
+    const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
+    const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
+    const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
+    const int64_t opz = d->out_pitch_z ? d->out_pitch_z : d->ny * opy;
+    if (ipy < X || ipz < Y * ipy) return fail(MMS_E_ARG, "input pitches (%lld, %lld) below the padded extents", (long long)ipy, (long long)ipz);
+    if (opy < d->nx || opz < d->ny * opy) return fail(MMS_E_ARG, "output pitches (%lld, %lld) below the interior extents", (long long)opy, (long long)opz);
+    const size_t in_bytes = (size_t)((Z - 1) * ipz + (Y - 1) * ipy + X) * 4;
+    const size_t out_bytes = (size_t)((d->nz - 1) * opz + (d->ny - 1) * opy + d->nx) * 4;
+    if (overlaps(in, in_bytes, out, out_bytes)) return fail(MMS_E_ARG, "input and output overlap");
+    if (d->variant < -1) return fail(MMS_E_ARG, "variant %d", d->variant);
+
+    Sweep s{shape, r, d->nx, d->ny, d->nz, in, ipy, ipz, out, opy, opz, d->coeffs, d->variant,
+            reinterpret_cast<cudaStream_t>(stream)};
+    int path = d->path;
+    const bool aligned = tma_ok(in, ipy, ipz);
+    if (path == MMS_PATH_AUTO) {
+        path = aligned ? MMS_PATH_CUDA_CORE : MMS_PATH_NAIVE;
+        if (aligned && shape == MMS_BOX && r >= 2 && band_tc_supported(shape, r, MMS_PATH_BF16X3) &&
+            tuned_variant(shape, r, MMS_PATH_BF16X3) >= 0)
+            path = MMS_PATH_BF16X3;
+    }
+    if (path == MMS_PATH_NAIVE) {
+        cudaError_t e = launch_naive(s);
+        return e == cudaSuccess ? MMS_OK : cuda_fail(e, "naive sweep launch");
+    }
+    if (!aligned)
+        return fail(MMS_E_ALIGN, "TMA path needs a 16-byte aligned input and pitches that are multiples of 4 floats");
+    const int nvar = num_variants(shape, r, path);
+    if (nvar == 0) return fail(MMS_E_UNSUPPORTED, "path %d does not support shape %d radius %d", path, shape, r);
+    int v = d->variant >= 0 ? d->variant : default_variant(shape, r, path, d->nx, d->ny, d->nz);
+    if (v >= nvar) return fail(MMS_E_ARG, "variant %d of %d", v, nvar);
+    CUtensorMap map;
+    if (path == MMS_PATH_CUDA_CORE) {
+        int bx, by;
+        if (shape == MMS_STAR) star_cc_box(r, v, &bx, &by); else box_cc_box(r, v, &bx, &by);
+        if (!encode_tmap_3d(&map, in, X, Y, Z, ipy, ipz, bx, by, 1))
+            return fail(MMS_E_CUDA, "cuTensorMapEncodeTiled refused the input grid");
+        cudaError_t e = shape == MMS_STAR ? launch_star_cc(s, map, v) : launch_box_cc(s, map, v);
+        return e == cudaSuccess ? MMS_OK : cuda_fail(e, "CUDA-core sweep launch");
+    }
+    int bx, by, bz;
+    band_tc_box(shape, r, path, v, &bx, &by, &bz);
+    if (!encode_tmap_3d(&map, in, X, Y, Z, ipy, ipz, bx, by, bz))
+        return fail(MMS_E_CUDA, "cuTensorMapEncodeTiled refused the input grid");
+    cudaError_t e = launch_band_tc(s, path, map, v);
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "tensor-core sweep launch");
+}
+
+}  // namespace mms
+
+using namespace mms;
+
+extern "C" {
+
+mms_status mms_stencil_apply(int shape, int radius, const float *coeffs, const float *in, float *out,
+                             int64_t nx, int64_t ny, int64_t nz, void *stream)
+{
+    mms_stencil_desc d{};
+    d.shape = shape;
+    d.radius = radius;
+    d.coeffs = coeffs;
+    d.nx = nx;
+    d.ny = ny;
+    d.nz = nz;
+    d.path = MMS_PATH_AUTO;
+    d.variant = -1;
+    return apply(&d, in, out, stream);
+}
+
+mms_status mms_stencil_apply_ex(const mms_stencil_desc *desc, const float *in, float *out, void *stream)
+{
+    return apply(desc, in, out, stream);
+}
+
+int32_t mms_num_variants(int shape, int radius, int path) { return num_variants(shape, radius, path); }
+
+int32_t mms_default_variant(int shape, int radius, int path, int64_t nx, int64_t ny, int64_t nz)
+{
+    if (num_variants(shape, radius, path) == 0) return -1;
+    return default_variant(shape, radius, path, nx, ny, nz);
+}
+
+mms_status mms_set_variant(int shape, int radius, int path, int32_t variant)
+{
+    if (shape < 0 || shape > 1 || radius < 1 || radius > kMaxR || path < 0 || path > MMS_PATH_NAIVE)
+        return fail(MMS_E_ARG, "bad (shape, radius, path)");
+    if (variant < -1 || variant >= num_variants(shape, radius, path))
+        return fail(MMS_E_ARG, "variant %d out of range", variant);
+    tuned_variant(shape, radius, path);  // initialises the table
+    std::lock_guard<std::mutex> lk(g_var_mu);
+    g_tuned[shape][radius][path] = variant;
+    return MMS_OK;
+}
+
+const char *mms_last_error(void) { return g_last_error.c_str(); }
+
+const char *mms_version(void) { return "mms-gb300 0.1 (sm_103a)"; }
+
+mms_status mms_check_device(void *stream)
+{
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    unsigned *w = device_error_word();
+    if (!w) return fail(MMS_E_CUDA, "device error word unavailable");
+    unsigned h = 0;
+    e = cudaMemcpy(&h, w, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read device error word");
+    if (h) {
+        const unsigned z = 0;
+        cudaMemcpy(w, &z, sizeof z, cudaMemcpyHostToDevice);
+    }
+    if (h & kErrTimeout) return fail(MMS_E_TIMEOUT, "a bounded device-side wait ran out");
+    if (h & kErrIndex) return fail(MMS_E_DEVICE, "a device-side index check failed");
+    return MMS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ wave ABI
+namespace mms {
+
+static mms_status wave_geo(const mms_wave_desc *d, const float *coeffs, WaveGeo *g)
+{
+    if (!d) return fail(MMS_E_ARG, "null wave descriptor");
+    if (!coeffs) return fail(MMS_E_ARG, "null coefficient array");
+    if (d->radius < 1 || d->radius > kMaxR) return fail(MMS_E_ARG, "radius %d outside 1..%d", d->radius, kMaxR);
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nx >= (1ll << 30) || d->ny >= (1ll << 30) || d->nz >= (1ll << 30))
+        return fail(MMS_E_ARG, "interior sizes must be in 1..2^30");
+    if (d->nshots < 1 || d->nshots > kMaxShots) return fail(MMS_E_ARG, "nshots %d outside 1..%d", d->nshots, kMaxShots);
+    if (d->sponge_width < 0) return fail(MMS_E_ARG, "negative sponge width");
+    if (d->rec_z < -1 || d->rec_z >= d->nz) return fail(MMS_E_ARG, "receiver plane %d outside the interior", d->rec_z);
+    const int r = d->radius;
+    const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * r;
+    g->nx = (int)d->nx; g->ny = (int)d->ny; g->nz = (int)d->nz; g->r = r; g->nshots = d->nshots;
+    g->py = d->pitch_y ? d->pitch_y : X;
+    g->pz = d->pitch_z ? d->pitch_z : Y * g->py;
+    g->ss = d->shot_stride ? d->shot_stride : Z * g->pz;
+    if (g->py < X || g->pz < Y * g->py || g->ss < Z * g->pz) return fail(MMS_E_ARG, "field pitches below the padded extents");
+    if (g->py % 4 || g->pz % 4 || g->ss % 4)
+        return fail(MMS_E_ALIGN, "wave fields need pitches and shot stride that are multiples of 4 floats");
+    g->sponge_w = d->sponge_width;
+    g->sponge_a = d->sponge_a;
+    g->rec_z = d->rec_z;
+    for (int s = 0; s < d->nshots; ++s) {
+        int x = -1, y = -1, z = -1;
+        if (d->src_xyz) { x = d->src_xyz[3 * s]; y = d->src_xyz[3 * s + 1]; z = d->src_xyz[3 * s + 2]; }
+        if (x >= 0 && (x >= d->nx || y < 0 || y >= d->ny || z < 0 || z >= d->nz))
+            return fail(MMS_E_ARG, "source %d outside the interior", s);
+        if (x < 0) x = y = z = -1;
+        g->src[s][0] = x; g->src[s][1] = y; g->src[s][2] = z;
+    }
+    return MMS_OK;
+}
+
+static bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) % 16) == 0; }
+
+static size_t field_bytes(const WaveGeo &g) { return (size_t)g.nshots * g.ss * 4; }
+
+struct GraphEntry {
+    uint64_t key;
+    cudaGraphExec_t exec;
+};
+static std::mutex g_graph_mu;
+static GraphEntry g_graphs[16];
+static int g_ngraphs = 0;
+
+static uint64_t mix(uint64_t h, uint64_t v) { return (h ^ v) * 0x100000001b3ull + (h >> 29); }
+
+static uint64_t fbits(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+}  // namespace mms
+
+extern "C" {
+
+mms_status mms_wave_step(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *p_cur,
+                         float *p_prev, const float *src_amp, float *rec, void *stream)
+{
+    WaveGeo g;
+    mms_status st = wave_geo(desc, coeffs, &g);
+    if (st != MMS_OK) return st;
+    if (!m || !p_cur || !p_prev || !src_amp) return fail(MMS_E_ARG, "null field pointer");
+    if (!al16(m) || !al16(p_cur) || !al16(p_prev)) return fail(MMS_E_ALIGN, "wave fields must be 16-byte aligned");
+    if (overlaps(p_cur, field_bytes(g), p_prev, field_bytes(g))) return fail(MMS_E_ARG, "p_cur and p_prev overlap");
+    cudaError_t e = launch_wave_fwd(g, coeffs, m, p_cur, p_prev, src_amp, rec, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "wave step launch");
+}
+
+mms_status mms_wave_forward(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *amps,
+                            int32_t nsteps, float *p0, float *p1, float *rec_all, float *ckpt, int32_t ckpt_every,
+                            uint32_t flags, void *stream)
+{
+    WaveGeo g;
+    mms_status st = wave_geo(desc, coeffs, &g);
+    if (st != MMS_OK) return st;
+    if (nsteps < 0) return fail(MMS_E_ARG, "negative step count");
+    if (!m || !amps || !p0 || !p1) return fail(MMS_E_ARG, "null field pointer");
+    if (!al16(m) || !al16(p0) || !al16(p1)) return fail(MMS_E_ALIGN, "wave fields must be 16-byte aligned");
+    if (overlaps(p0, field_bytes(g), p1, field_bytes(g))) return fail(MMS_E_ARG, "p0 and p1 overlap");
+    if (ckpt && ckpt_every < 1) return fail(MMS_E_ARG, "checkpoint interval must be >= 1");
+    if (rec_all && g.rec_z < 0) return fail(MMS_E_ARG, "records requested without a receiver plane");
+    if (flags & ~MMS_WAVE_GRAPH) return fail(MMS_E_ARG, "unknown flags 0x%x", flags);
+    if (nsteps == 0) return MMS_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t fb = field_bytes(g);
+    const int64_t rec_step = (int64_t)g.nshots * g.ny * g.nx;
+
+    auto enqueue = [&]() -> mms_status {
+        float *bufs[2] = {p0, p1};
+        int c = 1;
+        for (int n = 0; n < nsteps; ++n) {
+            if (ckpt && n % ckpt_every == 0) {
+                const int j = n / ckpt_every;
+                char *slot = reinterpret_cast<char *>(ckpt) + (size_t)j * 2 * fb;
+                cudaError_t e = cudaMemcpyAsync(slot, bufs[c], fb, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(slot + fb, bufs[1 - c], fb, cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
+            }
+            cudaError_t e = launch_wave_fwd(g, coeffs, m, bufs[c], bufs[1 - c], amps + (int64_t)n * g.nshots,
+                                            rec_all ? rec_all + n * rec_step : nullptr, s);
+            if (e != cudaSuccess) return cuda_fail(e, "wave step launch");
+            c = 1 - c;
+        }
+        return MMS_OK;
+    };
+    if (!(flags & MMS_WAVE_GRAPH)) return enqueue();
+
+    // Key of the captured sequence: every argument that ends up in a node.
+    uint64_t key = 0xcbf29ce484222325ull;
+    const uint64_t vals[] = {(uint64_t)(uintptr_t)m, (uint64_t)(uintptr_t)amps, (uint64_t)nsteps,
+                             (uint64_t)(uintptr_t)p0, (uint64_t)(uintptr_t)p1, (uint64_t)(uintptr_t)rec_all,
+                             (uint64_t)(uintptr_t)ckpt, (uint64_t)ckpt_every, (uint64_t)g.nx, (uint64_t)g.ny,
+                             (uint64_t)g.nz, (uint64_t)g.r, (uint64_t)g.nshots, (uint64_t)g.py, (uint64_t)g.pz,
+                             (uint64_t)g.ss, (uint64_t)g.sponge_w, fbits(g.sponge_a),
+                             (uint64_t)(int64_t)g.rec_z};
+    for (uint64_t v : vals) key = mix(key, v);
+    for (int i = 0; i < 3 * (2 * g.r + 1); ++i) key = mix(key, fbits(coeffs[i]));
+    for (int i = 0; i < g.nshots; ++i)
+        key = mix(key, ((uint64_t)(uint32_t)g.src[i][0] << 40) ^ ((uint64_t)(uint32_t)g.src[i][1] << 20) ^
+                           (uint32_t)g.src[i][2]);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (int i = 0; i < g_ngraphs; ++i)
+        if (g_graphs[i].key == key) {
+            cudaError_t e = cudaGraphLaunch(g_graphs[i].exec, s);
+            return e == cudaSuccess ? MMS_OK : cuda_fail(e, "graph launch");
+        }
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cap); return cuda_fail(e, "begin capture"); }
+    cudaStream_t saved = s;
+    s = cap;
+    mms_status qs = enqueue();
+    s = saved;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (qs != MMS_OK) { if (graph) cudaGraphDestroy(graph); return qs; }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    if (g_ngraphs == 16) {
+        // Oldest entry out; a replay of it may still be running, so wait for
+        // the device before destroying it.
+        cudaDeviceSynchronize();
+        cudaGraphExecDestroy(g_graphs[0].exec);
+        for (int i = 1; i < 16; ++i) g_graphs[i - 1] = g_graphs[i];
+        g_ngraphs = 15;
+    }
+    g_graphs[g_ngraphs++] = {key, exec};
+    e = cudaGraphLaunch(exec, s);
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "graph launch");
+}
+
+mms_status mms_wave_adjoint(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *lam_cur,
+                            float *lam_prev, const float *resid, const float *a_n, double *grad_m, void *stream)
+{
+    WaveGeo g;
+    mms_status st = wave_geo(desc, coeffs, &g);
+    if (st != MMS_OK) return st;
+    if (!m || !lam_cur || !lam_prev) return fail(MMS_E_ARG, "null field pointer");
+    if (a_n && !grad_m) return fail(MMS_E_ARG, "a_n given without grad_m");
+    if (resid && g.rec_z < 0) return fail(MMS_E_ARG, "residual given without a receiver plane");
+    if (!al16(m) || !al16(lam_cur) || !al16(lam_prev) || (a_n && !al16(a_n)))
+        return fail(MMS_E_ALIGN, "wave fields must be 16-byte aligned");
+    if (overlaps(lam_cur, field_bytes(g), lam_prev, field_bytes(g))) return fail(MMS_E_ARG, "lam_cur and lam_prev overlap");
+    if (a_n && overlaps(a_n, field_bytes(g), lam_prev, field_bytes(g))) return fail(MMS_E_ARG, "a_n and lam_prev overlap");
+    cudaError_t e = launch_wave_adj(g, coeffs, m, lam_cur, lam_prev, resid, a_n, grad_m,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "adjoint step launch");
+}
+
+mms_status mms_model_from_velocity(const mms_wave_desc *desc, const float *v, float *m, float dt, float h,
+                                   void *stream)
+{
+    WaveGeo g;
+    static const float dummy[27] = {0};
+    mms_status st = wave_geo(desc, dummy, &g);
+    if (st != MMS_OK) return st;
+    if (!v || !m) return fail(MMS_E_ARG, "null pointer");
+    if (!(dt > 0.f) || !(h > 0.f)) return fail(MMS_E_ARG, "dt and h must be positive");
+    cudaError_t e = launch_model_from_velocity(g, v, m, dt, h, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "model kernel launch");
+}
+
+mms_status mms_grad_to_velocity(const double *grad_m, const float *v, double *grad_v, int64_t n, float dt, float h,
+                                void *stream)
+{
+    if (n < 0) return fail(MMS_E_ARG, "negative length");
+    if (n == 0) return MMS_OK;
+    if (!grad_m || !v || !grad_v) return fail(MMS_E_ARG, "null pointer");
+    if (!(dt > 0.f) || !(h > 0.f)) return fail(MMS_E_ARG, "dt and h must be positive");
+    cudaError_t e = launch_grad_to_velocity(grad_m, v, grad_v, n, dt, h, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "chain-rule kernel launch");
+}
+
+mms_status mms_dot_f64(const float *a, const float *b, int64_t n, double *result, void *stream)
+{
+    if (n < 0) return fail(MMS_E_ARG, "negative length");
+    if (!result) return fail(MMS_E_ARG, "null result pointer");
+    if (n > 0 && (!a || !b)) return fail(MMS_E_ARG, "null input pointer");
+    cudaError_t e = launch_dot_f64(a, b, n, result, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "dot kernel launch");
+}
+
+}  // extern "C"

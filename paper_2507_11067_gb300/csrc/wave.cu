@@ -1,0 +1,472 @@
+// wave.cu -- fused acoustic wave step, its discrete adjoint, and the small
+// pointwise kernels around them (model, chain rule, FP64 dot product).
+//
+// The forward kernel is the star sweep of sweep_cc.cu with the leapfrog
+// update fused into its epilogue: the Laplacian of a^n never leaves
+// registers, so one step moves 16 bytes per point (read a^n, a^{n-1}, m;
+// write a^{n+1}) plus the L2-served halos.  Shots are independent and run
+// as separate grid slices of the same launch.
+//
+// The adjoint kernel computes, per point and shot,
+//   lam^n = R^T r^n + 2 g lam^{n+1} + L(m g lam^{n+1}) - g^2 lam^{n+2}
+//   grad += g lam^{n+1} (L a^n)     (FP64, all shots)
+// staging lam^{n+1}, m and a^n planes with TMA; the stencil input
+// q = m g lam^{n+1} is formed plane by plane in shared memory.
+#include "common.cuh"
+#include "tile.cuh"
+#include "wave.cuh"
+
+namespace mms {
+
+__device__ unsigned g_error_word = 0;
+
+unsigned *device_error_word()
+{
+    static unsigned *addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return nullptr;
+        addr[dev] = static_cast<unsigned *>(p);
+    }
+    return addr[dev];
+}
+
+namespace {
+
+// Cerjan sponge factor of cell i of n (distance d to the nearest face).
+__device__ __forceinline__ float sponge(int i, int n, int w, float a)
+{
+    const int d = min(i, n - 1 - i);
+    if (d < w) {
+        const float t = a * (float)(w - d);
+        return expf(-t * t);
+    }
+    return 1.f;
+}
+
+template <int R, int TX, int TY, int PY, int S>
+__global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
+    wave_fwd_kernel(const __grid_constant__ CUtensorMap tcur, const __grid_constant__ StarCoef cf,
+                    const __grid_constant__ WaveGeo geo, const float *__restrict__ m,
+                    float *__restrict__ pprev, const float *__restrict__ amp,
+                    float *__restrict__ rec, int tz, int nzc, int vec, unsigned *err)
+{
+    using G = Geom<R, TX, TY, PY, S>;
+    constexpr int W = G::W;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *planes = reinterpret_cast<float *>(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * G::PLANE * sizeof(float));
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % G::NTX, ty = tid / G::NTX;
+    const int sh = blockIdx.z / nzc, zc = blockIdx.z % nzc;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, zb = zc * tz;
+    const int nzt = min(tz, geo.nz - zb);
+    const int P = nzt + 2 * R;
+    const int ry0 = ty * PY;
+    const int gx = x0 + 4 * tx;
+    const int sx = geo.src[sh][0], sy = geo.src[sh][1], sz = geo.src[sh][2];
+
+    if (tid == 0) {
+        ptx::prefetch_tmap(&tcur);
+#pragma unroll
+        for (int s = 0; s < S; ++s) ptx::mbar_init(&full[s], 1);
+        ptx::fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int j = 0; j < S && j < P; ++j) {
+            ptx::mbar_arrive_expect_tx(&full[j], G::PLANE * sizeof(float));
+            ptx::tma_load_4d(planes + j * G::PLANE, &tcur, x0, y0, zb + j, sh, &full[j]);
+        }
+    }
+    float gxs[4], gys[PY];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gxs[k] = sponge(gx + k, geo.nx, geo.sponge_w, geo.sponge_a);
+#pragma unroll
+    for (int i = 0; i < PY; ++i) gys[i] = sponge(y0 + ry0 + i, geo.ny, geo.sponge_w, geo.sponge_a);
+
+    float acc[W][PY][4], ctr[R + 1][PY][4];
+#pragma unroll
+    for (int kk = 0; kk < W; ++kk)
+#pragma unroll
+        for (int i = 0; i < PY; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[kk][i][k] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk <= R; ++kk)
+#pragma unroll
+        for (int i = 0; i < PY; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ctr[kk][i][k] = 0.f;
+
+    const float samp = amp[sh];
+    const int64_t shot_off = (int64_t)sh * geo.ss;
+    for (int j = 0; j < P; ++j) {
+        const int s = j % S;
+        if (ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err)) {
+            star_plane<R, PY, G::BX, G::NV>(planes + s * G::PLANE, cf, acc, ctr[R], tx, ry0);
+        } else {
+            abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) return;
+        if (tid == 0 && j + S < P) {
+            ptx::mbar_arrive_expect_tx(&full[s], G::PLANE * sizeof(float));
+            ptx::tma_load_4d(planes + s * G::PLANE, &tcur, x0, y0, zb + j + S, sh, &full[s]);
+        }
+        const int zo = j - 2 * R;
+        if (zo >= 0) {
+            const int z = zb + zo;
+            const float gzv = sponge(z, geo.nz, geo.sponge_w, geo.sponge_a);
+#pragma unroll
+            for (int i = 0; i < PY; ++i) {
+                const int y = y0 + ry0 + i;
+                if (y >= geo.ny || gx >= geo.nx) continue;
+                const int64_t mp = (int64_t)(z + R) * geo.pz + (int64_t)(y + R) * geo.py + (gx + R);
+                float *pp = pprev + shot_off + mp;
+                const float *mm = m + mp;
+                float mv[4], pv[4], res[4];
+                const bool full4 = vec && gx + 3 < geo.nx;
+                if (full4) {
+                    const float4 a = *reinterpret_cast<const float4 *>(mm);
+                    const float4 b = *reinterpret_cast<const float4 *>(pp);
+                    mv[0] = a.x; mv[1] = a.y; mv[2] = a.z; mv[3] = a.w;
+                    pv[0] = b.x; pv[1] = b.y; pv[2] = b.z; pv[3] = b.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        mv[k] = gx + k < geo.nx ? mm[k] : 0.f;
+                        pv[k] = gx + k < geo.nx ? pp[k] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float g = gxs[k] * gys[i] * gzv;
+                    float v = 2.f * ctr[0][i][k] + mv[k] * acc[0][i][k] - g * pv[k];
+                    if (gx + k == sx && y == sy && z == sz) v += samp;
+                    res[k] = g * v;
+                }
+                if (full4) {
+                    *reinterpret_cast<float4 *>(pp) = make_float4(res[0], res[1], res[2], res[3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (gx + k < geo.nx) pp[k] = res[k];
+                }
+                if (rec && z == geo.rec_z) {
+                    float *rp = rec + ((int64_t)sh * geo.ny + y) * geo.nx + gx;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (gx + k < geo.nx) rp[k] = res[k];
+                }
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < W - 1; ++kk)
+#pragma unroll
+            for (int i = 0; i < PY; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[kk][i][k] = acc[kk + 1][i][k];
+#pragma unroll
+        for (int i = 0; i < PY; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[W - 1][i][k] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < R; ++kk)
+#pragma unroll
+            for (int i = 0; i < PY; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ctr[kk][i][k] = ctr[kk + 1][i][k];
+    }
+}
+
+// Adjoint step.  Ring stage s holds three planes: lam^{n+1}, m, a^n.
+template <int R, int TX, int TY, int S>
+__global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
+    wave_adj_kernel(const __grid_constant__ CUtensorMap tlam, const __grid_constant__ CUtensorMap tm,
+                    const __grid_constant__ CUtensorMap ta, const __grid_constant__ StarCoef cf,
+                    const __grid_constant__ WaveGeo geo, float *__restrict__ lprev,
+                    const float *__restrict__ resid, double *__restrict__ grad, int has_a, int tz,
+                    int nzc, unsigned *err)
+{
+    constexpr int PY = 1;
+    using G = Geom<R, TX, TY, PY, S>;
+    constexpr int W = G::W;
+    constexpr int NPL = 3;  // planes per stage
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *planes = reinterpret_cast<float *>(smem_raw);
+    float *qbuf = planes + (size_t)S * NPL * G::PLANE;
+    float *gxt = qbuf + G::PLANE;
+    float *gyt = gxt + G::BX;
+    uint64_t *full = reinterpret_cast<uint64_t *>(gyt + ((G::BY + 3) & ~3));
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % G::NTX, ty = tid / G::NTX;
+    const int sh = blockIdx.z / nzc, zc = blockIdx.z % nzc;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, zb = zc * tz;
+    const int nzt = min(tz, geo.nz - zb);
+    const int P = nzt + 2 * R;
+    const int ry0 = ty * PY;
+    const int gx = x0 + 4 * tx;
+    const uint32_t stage_bytes = (has_a ? 3u : 2u) * G::PLANE * sizeof(float);
+
+    for (int c = tid; c < G::BX; c += G::NT) gxt[c] = sponge(x0 + c - R, geo.nx, geo.sponge_w, geo.sponge_a);
+    for (int rr = tid; rr < G::BY; rr += G::NT) gyt[rr] = sponge(y0 + rr - R, geo.ny, geo.sponge_w, geo.sponge_a);
+    if (tid == 0) {
+        ptx::prefetch_tmap(&tlam);
+        ptx::prefetch_tmap(&tm);
+        if (has_a) ptx::prefetch_tmap(&ta);
+#pragma unroll
+        for (int s = 0; s < S; ++s) ptx::mbar_init(&full[s], 1);
+        ptx::fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int j, int s) {
+        float *st = planes + (size_t)s * NPL * G::PLANE;
+        ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
+        ptx::tma_load_4d(st, &tlam, x0, y0, zb + j, sh, &full[s]);
+        ptx::tma_load_3d(st + G::PLANE, &tm, x0, y0, zb + j, &full[s]);
+        if (has_a) ptx::tma_load_4d(st + 2 * G::PLANE, &ta, x0, y0, zb + j, sh, &full[s]);
+    };
+    if (tid == 0)
+        for (int j = 0; j < S && j < P; ++j) issue(j, j);
+
+    float accq[W][PY][4], acca[W][PY][4], ctr[R + 1][PY][4];
+#pragma unroll
+    for (int kk = 0; kk < W; ++kk)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) accq[kk][0][k] = acca[kk][0][k] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk <= R; ++kk)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ctr[kk][0][k] = 0.f;
+    float gxs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gxs[k] = gxt[4 * tx + R + k];
+    const float gys0 = gyt[ry0 + R];
+    const int64_t shot_off = (int64_t)sh * geo.ss;
+
+    for (int j = 0; j < P; ++j) {
+        const int s = j % S;
+        const float *st = planes + (size_t)s * NPL * G::PLANE;
+        const bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err);
+        if (ok) {
+            // q = m * g * lam^{n+1} over the whole staged plane
+            const float gzp = sponge(zb + j - R, geo.nz, geo.sponge_w, geo.sponge_a);
+            for (int e = tid; e < G::PLANE; e += G::NT) {
+                const int c = e % G::BX, rr = e / G::BX;
+                qbuf[e] = st[G::PLANE + e] * (gxt[c] * gyt[rr] * gzp) * st[e];
+            }
+        } else {
+            abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) return;
+        {
+            float dummy[PY][4];
+            star_plane<R, PY, G::BX, G::NV>(qbuf, cf, accq, dummy, tx, ry0);
+            if (has_a) star_plane<R, PY, G::BX, G::NV>(st + 2 * G::PLANE, cf, acca, dummy, tx, ry0);
+            float lc[4];
+            load_center<R>(st + (ry0 + R) * G::BX + 4 * tx, lc);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ctr[R][0][k] = lc[k];
+        }
+        __syncthreads();
+        if (tid == 0 && j + S < P) issue(j + S, s);
+        const int zo = j - 2 * R;
+        if (zo >= 0) {
+            const int z = zb + zo;
+            const int y = y0 + ry0;
+            if (y < geo.ny && gx < geo.nx) {
+                const float gzv = sponge(z, geo.nz, geo.sponge_w, geo.sponge_a);
+                const int64_t mp = (int64_t)(z + R) * geo.pz + (int64_t)(y + R) * geo.py + (gx + R);
+                float *lp = lprev + shot_off + mp;
+                const int64_t gi = ((int64_t)z * geo.ny + y) * geo.nx + gx;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (gx + k >= geo.nx) break;
+                    const float g = gxs[k] * gys0 * gzv;
+                    const float l1 = ctr[0][0][k];
+                    float v = 2.f * g * l1 + accq[0][0][k] - g * g * lp[k];
+                    if (resid && z == geo.rec_z) v += resid[((int64_t)sh * geo.ny + y) * geo.nx + gx + k];
+                    lp[k] = v;
+                    if (has_a) atomicAdd(grad + gi + k, (double)g * (double)l1 * (double)acca[0][0][k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < W - 1; ++kk)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                accq[kk][0][k] = accq[kk + 1][0][k];
+                acca[kk][0][k] = acca[kk + 1][0][k];
+            }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) accq[W - 1][0][k] = acca[W - 1][0][k] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < R; ++kk)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ctr[kk][0][k] = ctr[kk + 1][0][k];
+    }
+}
+
+__global__ void model_kernel(WaveGeo geo, const float *__restrict__ v, float *__restrict__ m, float s)
+{
+    const int r = geo.r;
+    const int64_t X = geo.nx + 2 * r, Y = geo.ny + 2 * r, Z = geo.nz + 2 * r;
+    const int64_t total = X * Y * Z;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t xx = i % X, yy = (i / X) % Y, zz = i / (X * Y);
+        const int64_t x = xx - r, y = yy - r, z = zz - r;
+        float val = 0.f;
+        if (x >= 0 && x < geo.nx && y >= 0 && y < geo.ny && z >= 0 && z < geo.nz) {
+            const float vv = v[(z * geo.ny + y) * geo.nx + x];
+            val = vv * vv * s;
+        }
+        m[zz * geo.pz + yy * geo.py + xx] = val;
+    }
+}
+
+__global__ void chain_kernel(const double *__restrict__ gm, const float *__restrict__ v,
+                             double *__restrict__ gv, int64_t n, double s)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        gv[i] = gm[i] * 2.0 * (double)v[i] * s;
+}
+
+__global__ void dot_kernel(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
+                           double *__restrict__ res)
+{
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < blockDim.x / 32 ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(res, acc);
+    }
+}
+
+constexpr int kFwdTX = 64, kFwdTY = 16, kFwdPY = 2, kFwdS = 4, kFwdTZ = 64;
+constexpr int kAdjTX = 64, kAdjTY = 16, kAdjS = 2, kAdjTZ = 64;
+
+template <int R>
+cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const float *p_cur,
+                  float *p_prev, const float *amp, float *rec, cudaStream_t st)
+{
+    using G = Geom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
+    CUtensorMap map;
+    if (!encode_tmap_4d(&map, p_cur, g.nx + 2 * R, g.ny + 2 * R, g.nz + 2 * R, g.nshots, g.py, g.pz, g.ss,
+                        G::BX, G::BY, 1))
+        return cudaErrorInvalidValue;
+    auto kern = wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    const int nzc = (g.nz + kFwdTZ - 1) / kFwdTZ;
+    const dim3 grid((g.nx + kFwdTX - 1) / kFwdTX, (g.ny + kFwdTY - 1) / kFwdTY, nzc * g.nshots);
+    const int vec = (R % 4 == 0) && g.py % 4 == 0 && g.pz % 4 == 0 && g.ss % 4 == 0 &&
+                    reinterpret_cast<uintptr_t>(m) % 16 == 0 &&
+                    reinterpret_cast<uintptr_t>(p_prev) % 16 == 0;
+    kern<<<grid, G::NT, G::SMEM, st>>>(map, cf, g, m, p_prev, amp, rec, kFwdTZ, nzc, vec,
+                                       device_error_word());
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t adj_r(const WaveGeo &g, const StarCoef &cf, const float *m, const float *lam_cur,
+                  float *lam_prev, const float *resid, const float *a_n, double *grad, cudaStream_t st)
+{
+    using G = Geom<R, kAdjTX, kAdjTY, 1, kAdjS>;
+    CUtensorMap ml, mm, ma;
+    const int X = g.nx + 2 * R, Y = g.ny + 2 * R, Z = g.nz + 2 * R;
+    if (!encode_tmap_4d(&ml, lam_cur, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1) ||
+        !encode_tmap_3d(&mm, m, X, Y, Z, g.py, g.pz, G::BX, G::BY, 1))
+        return cudaErrorInvalidValue;
+    if (a_n) {
+        if (!encode_tmap_4d(&ma, a_n, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1))
+            return cudaErrorInvalidValue;
+    } else {
+        ma = ml;
+    }
+    auto kern = wave_adj_kernel<R, kAdjTX, kAdjTY, kAdjS>;
+    const size_t smem = (size_t)kAdjS * 3 * G::PLANE * 4 + (size_t)G::PLANE * 4 + G::BX * 4 +
+                        ((G::BY + 3) & ~3) * 4 + kAdjS * 8;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nzc = (g.nz + kAdjTZ - 1) / kAdjTZ;
+    const dim3 grid((g.nx + kAdjTX - 1) / kAdjTX, (g.ny + kAdjTY - 1) / kAdjTY, nzc * g.nshots);
+    kern<<<grid, G::NT, smem, st>>>(ml, mm, ma, cf, g, lam_prev, resid, grad, a_n ? 1 : 0, kAdjTZ, nzc,
+                                    device_error_word());
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_wave_fwd(const WaveGeo &g, const float *coeffs, const float *m, const float *p_cur,
+                            float *p_prev, const float *src_amp, float *rec, cudaStream_t st)
+{
+    StarCoef cf{};
+    for (int i = 0; i < 3 * (2 * g.r + 1); ++i) cf.c[i] = coeffs[i];
+    switch (g.r) {
+        case 1: return fwd_r<1>(g, cf, m, p_cur, p_prev, src_amp, rec, st);
+        case 2: return fwd_r<2>(g, cf, m, p_cur, p_prev, src_amp, rec, st);
+        case 3: return fwd_r<3>(g, cf, m, p_cur, p_prev, src_amp, rec, st);
+        case 4: return fwd_r<4>(g, cf, m, p_cur, p_prev, src_amp, rec, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_wave_adj(const WaveGeo &g, const float *coeffs, const float *m, const float *lam_cur,
+                            float *lam_prev, const float *resid, const float *a_n, double *grad,
+                            cudaStream_t st)
+{
+    StarCoef cf{};
+    for (int i = 0; i < 3 * (2 * g.r + 1); ++i) cf.c[i] = coeffs[i];
+    switch (g.r) {
+        case 1: return adj_r<1>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st);
+        case 2: return adj_r<2>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st);
+        case 3: return adj_r<3>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st);
+        case 4: return adj_r<4>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_model_from_velocity(const WaveGeo &g, const float *v, float *m, float dt, float h,
+                                       cudaStream_t st)
+{
+    const float s = (dt * dt) / (h * h);
+    model_kernel<<<152 * 8, 256, 0, st>>>(g, v, m, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_to_velocity(const double *gm, const float *v, double *gv, int64_t n, float dt,
+                                    float h, cudaStream_t st)
+{
+    const double s = ((double)dt * dt) / ((double)h * h);
+    chain_kernel<<<152 * 8, 256, 0, st>>>(gm, v, gv, n, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_f64(const float *a, const float *b, int64_t n, double *res, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(res, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    dot_kernel<<<152 * 4, 256, 0, st>>>(a, b, n, res);
+    return cudaGetLastError();
+}
+
+}  // namespace mms

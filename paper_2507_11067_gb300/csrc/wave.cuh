@@ -1,0 +1,34 @@
+// wave.cuh -- internal interface of the fused acoustic wave kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace mms {
+
+constexpr int kMaxShots = 64;
+
+// Geometry of a batched wave step, as validated by the ABI layer.
+struct WaveGeo {
+    int nx, ny, nz, r, nshots;
+    int64_t py, pz, ss;  // padded pitches and shot stride (elements)
+    int sponge_w;
+    float sponge_a;
+    int rec_z;
+    int src[kMaxShots][3];
+};
+
+cudaError_t launch_wave_fwd(const WaveGeo &g, const float *coeffs, const float *m, const float *p_cur,
+                            float *p_prev, const float *src_amp, float *rec, cudaStream_t st);
+cudaError_t launch_wave_adj(const WaveGeo &g, const float *coeffs, const float *m, const float *lam_cur,
+                            float *lam_prev, const float *resid, const float *a_n, double *grad,
+                            cudaStream_t st);
+cudaError_t launch_model_from_velocity(const WaveGeo &g, const float *v, float *m, float dt, float h,
+                                       cudaStream_t st);
+cudaError_t launch_grad_to_velocity(const double *gm, const float *v, double *gv, int64_t n, float dt,
+                                    float h, cudaStream_t st);
+cudaError_t launch_dot_f64(const float *a, const float *b, int64_t n, double *res, cudaStream_t st);
+
+mms_status fail(mms_status st, const char *fmt, ...);
+mms_status cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace mms

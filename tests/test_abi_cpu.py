@@ -1,0 +1,103 @@
+"""The C-ABI library on a machine without a GPU: it builds, loads, exports
+every symbol include/mms.h declares, and rejects bad arguments before it
+touches the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2507_11067_gb300 as mms
+from paper_2507_11067_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    mms.build()
+    return mms.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "mms.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mms_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_symbols() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_variants(lib):
+    assert "sm_103a" in mms.version()
+    assert mms.num_variants("star", 4, "cuda_core") >= 4
+    assert mms.num_variants("box", 2, "cuda_core") >= 4
+    assert mms.num_variants("star", 5, "cuda_core") == 0
+    assert mms.num_variants("box", 1, "naive") == 1
+
+
+def _desc(**kw):
+    c = np.ones(729, np.float32)
+    d = _lib.StencilDesc(kw.get("shape", 1), kw.get("radius", 2), c.ctypes.data, kw.get("nx", 8),
+                         kw.get("ny", 8), kw.get("nz", 8), kw.get("ipy", 0), kw.get("ipz", 0),
+                         kw.get("opy", 0), kw.get("opz", 0), kw.get("path", 0), kw.get("variant", -1))
+    return d, c
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(radius=0), 1), (dict(radius=5), 1), (dict(shape=2), 1), (dict(nx=-1), 1),
+    (dict(path=9), 1), (dict(ipy=3), 1), (dict(opy=2), 1), (dict(variant=-2), 1),
+])
+def test_argument_validation(lib, kw, status):
+    d, c = _desc(**kw)
+    buf_in = ctypes.create_string_buffer(64)
+    buf_out = ctypes.create_string_buffer(64)
+    st = lib.mms_stencil_apply_ex(ctypes.byref(d), buf_in, buf_out, None)
+    assert st == status
+    assert lib.mms_last_error()
+
+
+def test_null_grid_and_overlap_rejected(lib):
+    d, c = _desc()
+    assert lib.mms_stencil_apply_ex(ctypes.byref(d), None, None, None) == 1
+    buf = ctypes.create_string_buffer(1 << 16)
+    assert lib.mms_stencil_apply_ex(ctypes.byref(d), buf, buf, None) == 1
+    assert b"overlap" in lib.mms_last_error()
+
+
+def test_empty_interior_is_a_no_op(lib):
+    d, c = _desc(nx=0)
+    assert lib.mms_stencil_apply_ex(ctypes.byref(d), None, None, None) == 0
+
+
+def test_wave_validation(lib):
+    d, src = mms.wave_desc(8, 8, 8, 4, 0)
+    c = np.zeros(27, np.float32)
+    assert lib.mms_wave_step(ctypes.byref(d), c.ctypes.data, None, None, None, None, None, None) == 1
+    d, src = mms.wave_desc(8, 8, 8, 4, 1, src=[(9, 0, 0)])
+    assert lib.mms_wave_step(ctypes.byref(d), c.ctypes.data, None, None, None, None, None, None) == 1
+    assert b"source" in lib.mms_last_error()
+    d, src = mms.wave_desc(8, 8, 8, 4, 1, pitch_y=17)
+    assert lib.mms_wave_step(ctypes.byref(d), c.ctypes.data, None, None, None, None, None, None) == 3
+
+
+def test_set_variant_range(lib):
+    assert lib.mms_set_variant(1, 2, 1, 99) == 1
+    assert lib.mms_set_variant(1, 2, 1, 1) == 0
+    assert mms.default_variant("box", 2, "cuda_core") == 1
+    assert lib.mms_set_variant(1, 2, 1, -1) == 0
+    assert mms.default_variant("box", 2, "cuda_core") == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib._build, "LIB", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.load()

@@ -1,0 +1,178 @@
+"""GPU parity of the stencil sweeps against the FP64 oracle.
+
+Bar (spec tolerance for the FP32 CUDA-core and split paths):
+max|gpu - oracle| / max|oracle| <= 1e-5, element by element on grids the
+oracle finishes in seconds (several tiles plus ragged tails), and on sampled
+points at the full 512^3 / 1024^3 sizes in the launch configuration the
+benchmark uses.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_11067_gb300 as mms
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    mms.build()
+    mms.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def rel(g, o):
+    return float(np.abs(np.asarray(g, np.float64) - o).max() / max(np.abs(o).max(), 1e-300))
+
+
+def run(shape, r, c, grid, path, variant=-1, align=32):
+    inp = mms.to_padded_device(grid, r, align=align)
+    out = mms.apply(shape, r, c, inp, path=path, variant=variant)
+    torch.cuda.synchronize()
+    mms.check_device()
+    return out.cpu().numpy()
+
+
+def small_case(shape, r, n, seed):
+    nx, ny, nz = n
+    grid = workloads.uniform_grid(nx, ny, nz, r, workload=2, salt=seed)
+    c = workloads.normal_coeffs(shape, r, workload=2, salt=seed)
+    return grid, c
+
+
+SIZES = [(37, 29, 23), (64, 17, 70), (5, 3, 2), (130, 33, 9)]
+
+
+@pytest.mark.parametrize("shape", ["star", "box"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_naive_matches_oracle(shape, r):
+    for k, n in enumerate(SIZES[:3]):
+        grid, c = small_case(shape, r, n, 10 * r + k)
+        ref = oracle.stencil(shape, r, c, grid)
+        assert rel(run(shape, r, c, grid, "naive"), ref) <= TOL
+
+
+@pytest.mark.parametrize("shape", ["star", "box"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_cuda_core_every_variant_matches_oracle(shape, r):
+    nv = mms.num_variants(shape, r, "cuda_core")
+    assert nv >= 1
+    for k, n in enumerate(SIZES):
+        grid, c = small_case(shape, r, n, 100 + 10 * r + k)
+        ref = oracle.stencil(shape, r, c, grid)
+        for v in range(nv):
+            err = rel(run(shape, r, c, grid, "cuda_core", variant=v), ref)
+            assert err <= TOL, (n, v, err)
+
+
+def test_star_r4_fd8_64cubed():
+    # 64^3 interior + 4-cell halo, FD8 weights, U[-1,1] input.
+    grid = workloads.uniform_grid(64, 64, 64, 4, workload=1)
+    c = workloads.fd8_star_coeffs()
+    ref = oracle.stencil("star", 4, c, grid)
+    for path in ("cuda_core", "naive", "auto"):
+        assert rel(run("star", 4, c, grid, path), ref) <= TOL
+
+
+def test_fourier_symbol_on_gpu():
+    # cos(k.x + phi) input: the exact output is Re(sigma(k) e^{i(k.x+phi)}).
+    r, n = 3, (70, 45, 40)
+    g = np.random.default_rng(1)
+    k = g.uniform(0, np.pi, 3)
+    c = workloads.normal_coeffs("box", r, workload=2, salt=4)
+    Z, Y, X = np.meshgrid(*(np.arange(s + 2 * r) for s in n[::-1]), indexing="ij")
+    grid = np.cos(k[0] * X + k[1] * Y + k[2] * Z + 0.3).astype(np.float32)
+    d = np.arange(-r, r + 1)
+    DZ, DY, DX = np.meshgrid(d, d, d, indexing="ij")
+    sigma = np.sum(c.reshape(2 * r + 1, 2 * r + 1, 2 * r + 1).astype(np.float64)
+                   * np.exp(1j * (k[0] * DX + k[1] * DY + k[2] * DZ)))
+    expect = np.real(sigma * np.exp(1j * (k[0] * X + k[1] * Y + k[2] * Z + 0.3)))[r:-r, r:-r, r:-r]
+    out = run("box", r, c, grid, "cuda_core")
+    # the input itself is rounded to FP32: allow that rounding, scaled by sum|c|
+    bound = 1e-6 * np.sum(np.abs(c)) / np.abs(expect).max() + TOL
+    assert rel(out, expect) <= bound
+
+
+def test_dense_api_unaligned_pitch_uses_naive():
+    r = 1
+    grid, c = small_case("box", r, (13, 11, 9), 5)   # nx+2r = 15: not a 16-byte pitch
+    ref = oracle.stencil("box", r, c, grid)
+    inp = torch.from_numpy(grid).cuda()
+    out = torch.empty((9, 11, 13), device="cuda")
+    mms.apply_dense("box", r, c, inp, out)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), ref) <= TOL
+    with pytest.raises(mms.MMSError, match="E_ALIGN"):
+        mms.apply("box", r, c, inp, path="cuda_core")
+
+
+def test_overlap_and_bad_variant_rejected():
+    grid, c = small_case("star", 2, (16, 16, 16), 6)
+    inp = mms.to_padded_device(grid, 2)
+    with pytest.raises(mms.MMSError, match="E_ARG"):
+        mms.apply("star", 2, c, inp, out=inp[2:-2, 2:-2, 2:-2])
+    with pytest.raises(mms.MMSError, match="E_ARG"):
+        mms.apply("star", 2, c, inp, path="cuda_core", variant=99)
+
+
+def test_output_pitch_and_canary():
+    # A pitched output view: values land inside the view, the pad is untouched.
+    r = 2
+    grid, c = small_case("box", r, (50, 20, 12), 8)
+    ref = oracle.stencil("box", r, c, grid)
+    inp = mms.to_padded_device(grid, r)
+    base = torch.full((12, 20, 64), 7.25, device="cuda")
+    out = base[:, :, :50]
+    mms.apply("box", r, c, inp, out=out, path="cuda_core")
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), ref) <= TOL
+    assert torch.all(base[:, :, 50:] == 7.25)
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_box_512_sampled(r):
+    # Full 512^3 box in the benchmark's launch configuration (default variant).
+    n = 512
+    grid = workloads.uniform_grid(n, n, n, r, workload=2, salt=r)
+    c = workloads.normal_coeffs("box", r, workload=2, salt=r)
+    pts = workloads.sample_points(n, n, n, 3000, workload=2)
+    ref = oracle.stencil_points("box", r, c, grid, pts)
+    inp = mms.to_padded_device(grid, r)
+    del grid
+    for path in ("cuda_core", "auto"):
+        out = mms.apply("box", r, c, inp, path=path)
+        torch.cuda.synchronize()
+        mms.check_device()
+        got = out[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()
+        assert rel(got, ref) <= TOL
+
+
+def test_star_1024_sampled_all_radii():
+    # 1024^3 stars r = 1..4 on 16 sinusoids + 1e-3 noise; the radius-r input
+    # is the radius-4 grid with its outer 4-r layers cropped.
+    n = 1024
+    grid4 = workloads.sinusoid_grid(n, n, n, 4)
+    inp4 = mms.to_padded_device(grid4, 4)
+    pts = workloads.sample_points(n, n, n, 2000, workload=3)
+    for r in (1, 2, 3, 4):
+        c = workloads.star_coeffs(r)
+        o = 4 - r
+        crop = (slice(o, grid4.shape[0] - o), slice(o, grid4.shape[1] - o), slice(o, grid4.shape[2] - o))
+        ref = oracle.stencil_points("star", r, c, np.ascontiguousarray(grid4[crop]), pts)
+        if o == 0:
+            inp = inp4
+        else:
+            # a cropped view starts off the 16-byte grid: re-pitch it on the device
+            inp = mms.padded_empty(n, n, n, r, zero=False)
+            inp.copy_(inp4[crop])
+        out = mms.apply("star", r, c, inp, path="cuda_core")
+        torch.cuda.synchronize()
+        mms.check_device()
+        got = out[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()
+        assert rel(got, ref) <= TOL, r
+        del out, inp

@@ -1,0 +1,195 @@
+"""GPU parity of the fused wave step and its adjoint against the FP64 oracle.
+
+Teacher-forced: the oracle takes the GPU's FP32 state and does one FP64
+step; the bar is max|gpu - oracle| / max|oracle| <= 1e-5.  The adjoint is
+also checked against the GPU forward by dot-product tests (FP64 inner
+products), which bind its transpose structure independently of the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_11067_gb300 as mms
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+R = 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    mms.build()
+    mms.load()
+    assert torch.cuda.is_available()
+
+
+def rel(g, o):
+    return float(np.abs(np.asarray(g, np.float64) - o).max() / max(np.abs(o).max(), 1e-300))
+
+
+class Setup:
+    def __init__(self, nx=45, ny=38, nz=41, nshots=3, nsteps=30, sponge=6, seed=0):
+        self.nx, self.ny, self.nz, self.ns = nx, ny, nz, nshots
+        self.w = workloads.WaveInputs(nx, ny, nz, nshots=nshots, nsteps=nsteps, sponge=sponge,
+                                      salt=seed)
+        self.cf = workloads.fd8_star_coeffs()
+        self.m = mms.padded_empty(nx, ny, nz, R)
+        self.fields = [mms.padded_empty(nx, ny, nz, R, nshots=nshots) for _ in range(4)]
+        py, pz, ss = mms.field_geometry(self.fields[0])
+        self.desc, self._src = mms.wave_desc(nx, ny, nz, R, nshots, py, pz, ss, self.w.sponge,
+                                             self.w.sponge_a, self.w.zrec, self.w.src)
+        self.v = torch.from_numpy(self.w.v).cuda()
+        mms.model_from_velocity(self.desc, self.v, self.m, self.w.dt, self.w.h)
+        self.amps = torch.from_numpy(self.w.amp).cuda().contiguous()
+        self.prob = oracle.WaveProblem(R, self.cf, oracle.model_m(self.w.v, self.w.dt, self.w.h),
+                                       (self.w.sponge, self.w.sponge_a), self.w.src, self.w.amp,
+                                       self.w.zrec)
+
+    def fill(self, f, seed):
+        g = np.random.default_rng(seed)
+        f[:, R:-R, R:-R, R:-R] = torch.from_numpy(
+            g.uniform(-1, 1, (self.ns, self.nz, self.ny, self.nx)).astype(np.float32))
+
+    def host(self, f):
+        return f.cpu().numpy().astype(np.float64)
+
+
+def test_model_from_velocity():
+    s = Setup()
+    m = s.m.cpu().numpy()
+    ref = oracle.model_m(s.w.v, s.w.dt, s.w.h)
+    assert rel(m[R:-R, R:-R, R:-R], ref) <= 1e-6
+    assert np.all(m[:R] == 0) and np.all(m[:, :, :R] == 0)
+
+
+def test_teacher_forced_step():
+    s = Setup()
+    cur, prev = s.fields[0], s.fields[1]
+    s.fill(cur, 1)
+    s.fill(prev, 2)
+    c0, p0 = s.host(cur), s.host(prev)
+    rec = torch.zeros((s.ns, s.ny, s.nx), device="cuda")
+    n = 3
+    mms.wave_step(s.desc, s.cf, s.m, cur, prev, s.amps[n], rec)
+    torch.cuda.synchronize()
+    mms.check_device()
+    got = prev.cpu().numpy()
+    for sh in range(s.ns):
+        ref = s.prob.step(c0[sh], p0[sh], sh, n)
+        assert rel(got[sh], ref) <= TOL
+        assert np.array_equal(rec[sh].cpu().numpy(), got[sh, R + s.w.zrec, R:-R, R:-R])
+        # the zero halo is never written
+        assert np.all(got[sh, :R] == 0) and np.all(got[sh, :, :, -R:] == 0)
+
+
+def test_source_only_step_is_exact_at_source():
+    # From zero states the first step is G s at the source point only.
+    s = Setup(nshots=2)
+    cur, prev = s.fields[0], s.fields[1]
+    amp = torch.tensor([0.5, -2.0], device="cuda")
+    mms.wave_step(s.desc, s.cf, s.m, cur, prev, amp)
+    torch.cuda.synchronize()
+    got = prev.cpu().numpy()
+    for sh, (x, y, z) in enumerate(s.w.src):
+        nz_idx = np.argwhere(got[sh] != 0)
+        assert len(nz_idx) == 1 and tuple(nz_idx[0]) == (z + R, y + R, x + R)
+        g = s.prob.gx[x] * s.prob.gy[y] * s.prob.gz[z]
+        assert got[sh, z + R, y + R, x + R] == pytest.approx(g * amp[sh].item(), rel=1e-6)
+
+
+def test_trajectory_against_oracle():
+    # 60 steps from rest: FP32 drift against the FP64 oracle stays small.
+    nsteps = 60
+    s = Setup(nshots=2, nsteps=nsteps)
+    rec = torch.zeros((nsteps, s.ns, s.ny, s.nx), device="cuda")
+    mms.wave_forward(s.desc, s.cf, s.m, s.amps, nsteps, s.fields[0], s.fields[1], rec)
+    torch.cuda.synchronize()
+    mms.check_device()
+    ref, _ = s.prob.forward(nsteps)
+    err = rel(rec.cpu().numpy(), ref)
+    assert err <= 1e-4, err
+
+
+def _flat(f):
+    """The whole storage of a (pitched) field view, as one flat float view."""
+    return torch.as_strided(f, (f.untyped_storage().nbytes() // 4,), (1,), 0)
+
+
+def test_forward_graph_matches_steps_and_checkpoints():
+    nsteps, every = 25, 10
+    s = Setup(nshots=2, nsteps=nsteps)
+    a0, a1, b0, b1 = s.fields
+    rec_a = torch.zeros((nsteps, s.ns, s.ny, s.nx), device="cuda")
+    rec_b = torch.zeros_like(rec_a)
+    fb = a0.untyped_storage().nbytes() // 4
+    ckpt = torch.zeros((3, 2, fb), device="cuda")
+    saved = {}
+    for k in range(nsteps):
+        cur, prev = (a1, a0) if k % 2 == 0 else (a0, a1)
+        if k % every == 0:
+            saved[k // every] = (_flat(cur).clone(), _flat(prev).clone())
+        mms.wave_step(s.desc, s.cf, s.m, cur, prev, s.amps[k], rec_a[k])
+    mms.wave_forward(s.desc, s.cf, s.m, s.amps, nsteps, b0, b1, rec_b, ckpt, every, graph=True)
+    torch.cuda.synchronize()
+    mms.check_device()
+    assert torch.equal(rec_a, rec_b)
+    assert torch.equal(a0, b0) and torch.equal(a1, b1)
+    for j in range(3):   # checkpoint j holds (a^{10 j}, a^{10 j - 1})
+        assert torch.equal(ckpt[j, 0], saved[j][0]) and torch.equal(ckpt[j, 1], saved[j][1])
+    # a replay of the cached graph gives the same records again
+    rec_b.zero_()
+    b0.zero_()
+    b1.zero_()
+    mms.wave_forward(s.desc, s.cf, s.m, s.amps, nsteps, b0, b1, rec_b, ckpt, every, graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(rec_a, rec_b)
+
+
+def test_teacher_forced_adjoint_step():
+    s = Setup(nshots=2)
+    lam1, lam2, a_n = s.fields[0], s.fields[1], s.fields[2]
+    for f, sd in ((lam1, 3), (lam2, 4), (a_n, 5)):
+        s.fill(f, sd)
+    l1, l2, an = s.host(lam1), s.host(lam2), s.host(a_n)
+    g = np.random.default_rng(9)
+    resid = torch.from_numpy(g.normal(size=(s.ns, s.ny, s.nx)).astype(np.float32)).cuda()
+    grad = torch.zeros((s.nz, s.ny, s.nx), device="cuda", dtype=torch.float64)
+    mms.wave_adjoint(s.desc, s.cf, s.m, lam1, lam2, resid, a_n, grad)
+    torch.cuda.synchronize()
+    mms.check_device()
+    got = lam2.cpu().numpy()
+    gref = np.zeros((s.nz, s.ny, s.nx))
+    rh = resid.cpu().numpy().astype(np.float64)
+    for sh in range(s.ns):
+        ref = s.prob.adjoint_step(l1[sh], l2[sh], rh[sh], an[sh], gref)
+        assert rel(got[sh], ref) <= TOL
+    assert rel(grad.cpu().numpy(), gref) <= TOL
+
+
+def _dot(a, b):
+    out = torch.zeros(1, device="cuda", dtype=torch.float64)
+    mms.dot_f64(a, b, out)
+    return out.item()
+
+
+def test_gpu_dot_product_one_step():
+    # <T(u, w), lam> = <u, (2 + L m) G lam> + <w, -G^2 lam>, all on the GPU.
+    s = Setup(nshots=1)
+    u, w, lam, t = s.fields
+    for f, sd in ((u, 11), (w, 12), (lam, 13)):
+        s.fill(f, sd)
+    t.copy_(w)
+    mms.wave_step(s.desc, s.cf, s.m, u, t, torch.zeros(1, device="cuda"))   # t = T(u, w)
+    zero = mms.padded_empty(s.nx, s.ny, s.nz, R, nshots=1)
+    tu = mms.padded_empty(s.nx, s.ny, s.nz, R, nshots=1)
+    mms.wave_adjoint(s.desc, s.cf, s.m, lam, tu)          # lam^{n+2} = 0: (2 + L m) G lam
+    tw = mms.padded_empty(s.nx, s.ny, s.nz, R, nshots=1)
+    tw.copy_(lam)
+    mms.wave_adjoint(s.desc, s.cf, s.m, zero, tw)         # lam^{n+1} = 0: -G^2 lam
+    torch.cuda.synchronize()
+    lhs = _dot(_flat(t), _flat(lam))
+    rhs = _dot(_flat(u), _flat(tu)) + _dot(_flat(w), _flat(tw))
+    assert abs(lhs - rhs) <= 1e-6 * (abs(lhs) + abs(rhs))
