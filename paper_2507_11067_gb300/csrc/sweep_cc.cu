@@ -67,9 +67,10 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     using G = Geom<R, TX, TY, PY, S>;
     constexpr int W = G::W;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *planes = reinterpret_cast<float *>(smem_raw);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * G::PLANE * sizeof(float));
-    __shared__ int abort_flag;
+    unsigned char *smem = smem_align128(smem_raw);
+    float *planes = reinterpret_cast<float *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * G::STAGE * sizeof(float));
+    int &abort_flag = *reinterpret_cast<int *>(full + S);
 
     const int tid = threadIdx.x;
     const int tx = tid % G::NTX, ty = tid / G::NTX;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     if (tid == 0) {
         for (int j = 0; j < S && j < P; ++j) {
             ptx::mbar_arrive_expect_tx(&full[j], G::PLANE * sizeof(float));
-            ptx::tma_load_3d(planes + j * G::PLANE, &tmap, x0, y0, zb + j, &full[j]);
+            ptx::tma_load_3d(planes + j * G::STAGE, &tmap, x0, y0, zb + j, &full[j]);
         }
     }
 
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     for (int j = 0; j < P; ++j) {
         const int s = j % S;
         if (ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err)) {
-            const float *pl = planes + s * G::PLANE;
+            const float *pl = planes + s * G::STAGE;
             if constexpr (BOX)
                 box_plane<R, PY, G::BX, G::NV>(pl, cf, acc, tx, ry0);
             else {
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
         if (abort_flag) return;
         if (tid == 0 && j + S < P) {
             ptx::mbar_arrive_expect_tx(&full[s], G::PLANE * sizeof(float));
-            ptx::tma_load_3d(planes + s * G::PLANE, &tmap, x0, y0, zb + j + S, &full[s]);
+            ptx::tma_load_3d(planes + s * G::STAGE, &tmap, x0, y0, zb + j + S, &full[s]);
         }
         const int zo = j - 2 * R;  // output plane completed by plane j
         if (zo >= 0) {

@@ -7,16 +7,27 @@
 
 namespace mms {
 
+// The dynamic shared-memory base rounded up to 128 bytes (TMA destinations
+// need 128-byte alignment; the launch adds 128 bytes of slack for this).
+__device__ __forceinline__ unsigned char *smem_align128(unsigned char *p)
+{
+    const uint32_t a = ptx::smem_u32(p);  // offset in the shared window
+    return p + ((128u - (a & 127u)) & 127u);
+}
+
 template <int R, int TX, int TY, int PY, int S>
 struct Geom {
     static constexpr int W = 2 * R + 1;
     static constexpr int BX = (TX + 2 * R + 3) & ~3;  // TMA box x: a 16-byte multiple
     static constexpr int BY = TY + 2 * R;
-    static constexpr int PLANE = BX * BY;             // floats per ring stage
+    static constexpr int PLANE = BX * BY;             // floats one TMA box writes
+    static constexpr int STAGE = (PLANE + 31) & ~31;  // ring stride: 128-byte multiple
     static constexpr int NTX = TX / 4;                // threads along x (4 points each)
     static constexpr int NT = NTX * (TY / PY);
     static constexpr int NV = (4 + 2 * R + 3) / 4;    // float4 per window row
-    static constexpr size_t SMEM = (size_t)S * PLANE * sizeof(float) + S * sizeof(uint64_t);
+    // 128 bytes of slack to align the dynamic base, the ring, its barriers
+    // and the CTA's abort flag.
+    static constexpr size_t SMEM = 128 + (size_t)S * STAGE * sizeof(float) + S * sizeof(uint64_t) + 16;
     static_assert(TX % 4 == 0 && TY % PY == 0, "tile");
     static_assert(BX <= 256 && BY <= 256, "TMA box dims are at most 256");
     static_assert(4 * (NTX - 1) + 4 * NV <= BX, "window inside the staged row");

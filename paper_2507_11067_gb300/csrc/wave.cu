@@ -56,9 +56,10 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     using G = Geom<R, TX, TY, PY, S>;
     constexpr int W = G::W;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *planes = reinterpret_cast<float *>(smem_raw);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * G::PLANE * sizeof(float));
-    __shared__ int abort_flag;
+    unsigned char *smem = smem_align128(smem_raw);
+    float *planes = reinterpret_cast<float *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * G::STAGE * sizeof(float));
+    int &abort_flag = *reinterpret_cast<int *>(full + S);
 
     const int tid = threadIdx.x;
     const int tx = tid % G::NTX, ty = tid / G::NTX;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     if (tid == 0) {
         for (int j = 0; j < S && j < P; ++j) {
             ptx::mbar_arrive_expect_tx(&full[j], G::PLANE * sizeof(float));
-            ptx::tma_load_4d(planes + j * G::PLANE, &tcur, x0, y0, zb + j, sh, &full[j]);
+            ptx::tma_load_4d(planes + j * G::STAGE, &tcur, x0, y0, zb + j, sh, &full[j]);
         }
     }
     float gxs[4], gys[PY];
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     for (int j = 0; j < P; ++j) {
         const int s = j % S;
         if (ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err)) {
-            star_plane<R, PY, G::BX, G::NV>(planes + s * G::PLANE, cf, acc, ctr[R], tx, ry0);
+            star_plane<R, PY, G::BX, G::NV>(planes + s * G::STAGE, cf, acc, ctr[R], tx, ry0);
         } else {
             abort_flag = 1;
         }
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
         if (abort_flag) return;
         if (tid == 0 && j + S < P) {
             ptx::mbar_arrive_expect_tx(&full[s], G::PLANE * sizeof(float));
-            ptx::tma_load_4d(planes + s * G::PLANE, &tcur, x0, y0, zb + j + S, sh, &full[s]);
+            ptx::tma_load_4d(planes + s * G::STAGE, &tcur, x0, y0, zb + j + S, sh, &full[s]);
         }
         const int zo = j - 2 * R;
         if (zo >= 0) {
@@ -199,12 +200,12 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
     constexpr int W = G::W;
     constexpr int NPL = 3;  // planes per stage
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *planes = reinterpret_cast<float *>(smem_raw);
-    float *qbuf = planes + (size_t)S * NPL * G::PLANE;
-    float *gxt = qbuf + G::PLANE;
+    float *planes = reinterpret_cast<float *>(smem_align128(smem_raw));
+    float *qbuf = planes + (size_t)S * NPL * G::STAGE;
+    float *gxt = qbuf + G::STAGE;
     float *gyt = gxt + G::BX;
     uint64_t *full = reinterpret_cast<uint64_t *>(gyt + ((G::BY + 3) & ~3));
-    __shared__ int abort_flag;
+    int &abort_flag = *reinterpret_cast<int *>(full + S);
 
     const int tid = threadIdx.x;
     const int tx = tid % G::NTX, ty = tid / G::NTX;
@@ -229,11 +230,11 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
     }
     __syncthreads();
     auto issue = [&](int j, int s) {
-        float *st = planes + (size_t)s * NPL * G::PLANE;
+        float *st = planes + (size_t)s * NPL * G::STAGE;
         ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
         ptx::tma_load_4d(st, &tlam, x0, y0, zb + j, sh, &full[s]);
-        ptx::tma_load_3d(st + G::PLANE, &tm, x0, y0, zb + j, &full[s]);
-        if (has_a) ptx::tma_load_4d(st + 2 * G::PLANE, &ta, x0, y0, zb + j, sh, &full[s]);
+        ptx::tma_load_3d(st + G::STAGE, &tm, x0, y0, zb + j, &full[s]);
+        if (has_a) ptx::tma_load_4d(st + 2 * G::STAGE, &ta, x0, y0, zb + j, sh, &full[s]);
     };
     if (tid == 0)
         for (int j = 0; j < S && j < P; ++j) issue(j, j);
@@ -255,14 +256,14 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
 
     for (int j = 0; j < P; ++j) {
         const int s = j % S;
-        const float *st = planes + (size_t)s * NPL * G::PLANE;
+        const float *st = planes + (size_t)s * NPL * G::STAGE;
         const bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err);
         if (ok) {
             // q = m * g * lam^{n+1} over the whole staged plane
             const float gzp = sponge(zb + j - R, geo.nz, geo.sponge_w, geo.sponge_a);
             for (int e = tid; e < G::PLANE; e += G::NT) {
                 const int c = e % G::BX, rr = e / G::BX;
-                qbuf[e] = st[G::PLANE + e] * (gxt[c] * gyt[rr] * gzp) * st[e];
+                qbuf[e] = st[G::STAGE + e] * (gxt[c] * gyt[rr] * gzp) * st[e];
             }
         } else {
             abort_flag = 1;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
         {
             float dummy[PY][4];
             star_plane<R, PY, G::BX, G::NV>(qbuf, cf, accq, dummy, tx, ry0);
-            if (has_a) star_plane<R, PY, G::BX, G::NV>(st + 2 * G::PLANE, cf, acca, dummy, tx, ry0);
+            if (has_a) star_plane<R, PY, G::BX, G::NV>(st + 2 * G::STAGE, cf, acca, dummy, tx, ry0);
             float lc[4];
             load_center<R>(st + (ry0 + R) * G::BX + 4 * tx, lc);
 #pragma unroll
@@ -403,8 +404,8 @@ cudaError_t adj_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
         ma = ml;
     }
     auto kern = wave_adj_kernel<R, kAdjTX, kAdjTY, kAdjS>;
-    const size_t smem = (size_t)kAdjS * 3 * G::PLANE * 4 + (size_t)G::PLANE * 4 + G::BX * 4 +
-                        ((G::BY + 3) & ~3) * 4 + kAdjS * 8;
+    const size_t smem = 128 + (size_t)kAdjS * 3 * G::STAGE * 4 + (size_t)G::STAGE * 4 + G::BX * 4 +
+                        ((G::BY + 3) & ~3) * 4 + kAdjS * 8 + 16;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nzc = (g.nz + kAdjTZ - 1) / kAdjTZ;
