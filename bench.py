@@ -37,6 +37,36 @@ RADII = (1, 2)
 FLOP_PER_PT = {1: 2 * 27, 2: 2 * 125}
 WORKLOAD = "box stencil sweeps r=1 (27 pt) + r=2 (125 pt), 512^3 FP32 interior + halo"
 
+# Sweeps of one step, per workload: (shape, radius, n, coefficient recipe).
+WORKLOADS = {
+    "box512": [("box", 1, 512), ("box", 2, 512)],
+    "star1024": [("star", 4, 1024)],
+    "star512": [("star", 4, 512)],
+}
+WORKLOAD_NAMES = {
+    "box512": WORKLOAD,
+    "star1024": "star stencil sweep r=4 (25 pt, FD8 weights), 1024^3 FP32 interior + halo, "
+                "16 sinusoids + 1e-3 noise",
+    "star512": "star stencil sweep r=4 (25 pt, FD8 weights), 512^3 FP32 interior + halo, "
+               "16 sinusoids + 1e-3 noise (profiling size)",
+}
+
+
+def sweep_coeffs(shape, r):
+    if shape == "star":
+        return workloads.star_coeffs(r)
+    return workloads.normal_coeffs("box", r, workload=2, salt=r)
+
+
+def sweep_input(shape, r, n, rank):
+    if shape == "star":
+        return workloads.sinusoid_grid(n, n, n, r, workload=3, salt=rank)
+    return workloads.uniform_grid(n, n, n, r, workload=2, salt=r + 100 * rank)
+
+
+def flop_per_pt(shape, r):
+    return 2 * (6 * r + 1 if shape == "star" else (2 * r + 1) ** 3)
+
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -44,6 +74,24 @@ def peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("sm_max_mhz", 2070.0), "measured"
     return 6800.0, 1900.0, 2070.0, "fallback"
+
+
+def captured_traffic(key: str, points: int):
+    """DRAM bytes of one launch from the committed ncu capture of this kernel
+    (profiles/traffic.json), scaled by points; None when the kernel's sources
+    changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(key)
+    if not rec:
+        return None
+    for f, h in rec["sources"].items():
+        path = os.path.join(ROOT, "paper_2507_11067_gb300", "csrc", f)
+        if not os.path.exists(path) or hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] != h:
+            return None
+    return rec["dram_bytes_per_point"] * points
 
 
 def fp32_alu_peak_tflops(n_sm: int, mhz: float) -> float:
@@ -131,6 +179,7 @@ def run_reference(args):
         oracle_sample(max(1, planes // 8))
     total_pts, total_s = 0, 0.0
     threads = 1
+    args.steps = args.steps or 3
     for k in range(args.steps):
         p, s, threads = oracle_sample(planes, salt=k)
         total_pts += p
@@ -155,8 +204,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=0, help="0 = about 2 s of timed sweeps")
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="box512", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="auto")
     ap.add_argument("--no-extras", action="store_true")
@@ -185,43 +235,50 @@ def main():
     hbm_peak, bf16_peak, sm_max_mhz, peak_src = peaks()
 
     # ---- inputs (seeded per rank), resident in HBM before timing
-    coeffs, inputs, outputs, hosts = {}, {}, {}, {}
-    for r in RADII:
-        coeffs[r] = workloads.normal_coeffs("box", r, workload=2, salt=r)
-        grid = workloads.uniform_grid(N, N, N, r, workload=2, salt=r + 100 * rank)
-        hosts[r] = torch.from_numpy(grid).pin_memory()
-        inputs[r] = mms.padded_empty(N, N, N, r, device=dev, zero=False)
-        inputs[r].copy_(hosts[r])
-        outputs[r] = torch.empty((N, N, N), device=dev)
+    from paper_2507_11067_gb300 import tune
+    tune.load_table()
+    plan = WORKLOADS[args.workload]
+    coeffs, inputs, outputs, hosts, host_out = [], [], [], [], []
+    for (shape, r, n) in plan:
+        coeffs.append(sweep_coeffs(shape, r))
+        grid = sweep_input(shape, r, n, rank)
+        # host buffer pinned with the device pitch, so each copy is one memcpy
+        hp = mms.padded_empty(n, n, n, r, device="cpu", zero=False)
+        hp = torch.as_strided(torch.empty(hp.untyped_storage().nbytes() // 4, pin_memory=True),
+                              hp.shape, hp.stride())
+        hp.copy_(torch.from_numpy(grid))
+        hosts.append(hp)
+        inputs.append(mms.padded_empty(n, n, n, r, device=dev, zero=False))
+        inputs[-1].copy_(hosts[-1])
+        outputs.append(torch.empty((n, n, n), device=dev))
+        host_out.append(torch.empty((n, n, n), pin_memory=True))
         del grid
-    host_out = {r: torch.empty((N, N, N), pin_memory=True) for r in RADII}
     stream = torch.cuda.current_stream(dev)
+    steps = args.steps or max(20, int(2000 / max(1, sum(n ** 3 for _, _, n in plan) / 2.7e8)))
 
-    def step():
-        for r in RADII:
-            mms.apply("box", r, coeffs[r], inputs[r], outputs[r], path=args.path)
+    def sweep(i):
+        shape, r, _ = plan[i]
+        mms.apply(shape, r, coeffs[i], inputs[i], outputs[i], path=args.path)
 
     # ---- device-resident timing
     for _ in range(args.warmup):
-        step()
+        for i in range(len(plan)):
+            sweep(i)
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
-    kernel_ms = {r: [] for r in RADII}
+    kernel_ev = [[] for _ in plan]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for k in range(args.steps):
-        e0, e1, e2 = ev[2 * k], ev[2 * k + 1], torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        mms.apply("box", 1, coeffs[1], inputs[1], outputs[1], path=args.path)
-        e1.record(stream)
-        mms.apply("box", 2, coeffs[2], inputs[2], outputs[2], path=args.path)
-        e2.record(stream)
-        kernel_ms[1].append((e0, e1))
-        kernel_ms[2].append((e1, e2))
+    for k in range(steps):
+        for i in range(len(plan)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sweep(i)
+            b.record(stream)
+            kernel_ev[i].append((a, b))
     t_end.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -232,27 +289,29 @@ def main():
         t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t.item())
-    pts_step = len(RADII) * N ** 3
-    value = world * pts_step * args.steps / elapsed / 1e9
-    kms = {r: statistics.mean(a.elapsed_time(b) for a, b in kernel_ms[r]) for r in RADII}
+    pts_step = sum(n ** 3 for _, _, n in plan)
+    value = world * pts_step * steps / elapsed / 1e9
+    kms = [statistics.mean(a.elapsed_time(b) for a, b in ev) for ev in kernel_ev]
 
     # ---- end to end through the public API: host in, host out, every step
+    def storage(t):
+        return torch.as_strided(t, (t.untyped_storage().nbytes() // 4,), (1,), 0)
+
+    def e2e_step():
+        for i in range(len(plan)):
+            storage(inputs[i]).copy_(storage(hosts[i]), non_blocking=True)
+            sweep(i)
+            host_out[i].copy_(outputs[i], non_blocking=True)
     for _ in range(2):
-        for r in RADII:
-            inputs[r].copy_(hosts[r], non_blocking=True)
-            mms.apply("box", r, coeffs[r], inputs[r], outputs[r], path=args.path)
-            host_out[r].copy_(outputs[r], non_blocking=True)
+        e2e_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_s.record(stream)
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(3, min(50, steps // 4))
     for _ in range(e2e_steps):
-        for r in RADII:
-            inputs[r].copy_(hosts[r], non_blocking=True)
-            mms.apply("box", r, coeffs[r], inputs[r], outputs[r], path=args.path)
-            host_out[r].copy_(outputs[r], non_blocking=True)
+        e2e_step()
     e_e.record(stream)
     torch.cuda.synchronize()
     e2e_s = e_s.elapsed_time(e_e) / 1e3
@@ -260,8 +319,8 @@ def main():
         t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    h2d = sum(hosts[r].numel() * 4 for r in RADII)
-    d2h = sum(host_out[r].numel() * 4 for r in RADII)
+    h2d = sum(h.untyped_storage().nbytes() for h in hosts)
+    d2h = sum(h.numel() * 4 for h in host_out)
     e2e_value = world * pts_step * e2e_steps / e2e_s / 1e9
 
     if rank != 0:
@@ -269,28 +328,43 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    # ---- dominant kernel roofline: the 125-point sweep on FP32 ALUs
+    # ---- dominant kernel roofline
     path_used = args.path
-    dom_r = max(RADII, key=lambda r: kms[r])
-    flops = FLOP_PER_PT[dom_r] * N ** 3
-    achieved_tf = flops / (kms[dom_r] / 1e3) / 1e12
     alu_peak = fp32_alu_peak_tflops(n_sm, sm_max_mhz)
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / alu_peak, "traffic": None,
-                "kernel": f"box r={dom_r} sweep ({path_used})",
-                "peak_note": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz (max SM clock)"}
+    di = max(range(len(plan)), key=lambda i: kms[i])
+    shape, r, n = plan[di]
+    sec = kms[di] / 1e3
+    bytes_alg = 4 * ((n + 2 * r) ** 3 + n ** 3)
+    flops = flop_per_pt(shape, r) * n ** 3
+    if flops / bytes_alg > alu_peak * 1e12 / (hbm_peak * 1e9):
+        roofline = {"bound": "alu", "achieved": flops / sec / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": flops / sec / 1e12 / alu_peak, "traffic": None,
+                    "peak_note": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz "
+                                 "(max SM clock)"}
+    else:
+        roofline = {"bound": "hbm", "achieved": bytes_alg / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": bytes_alg / sec / 1e9 / hbm_peak, "traffic": None,
+                    "peak_note": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+    resolved = mms.auto_path(shape, r) if path_used == "auto" else path_used
+    var = mms.default_variant(shape, r, resolved, n, n, n)
+    roofline["kernel"] = f"{shape} r={r} {n}^3 sweep ({resolved}, variant {var})"
+    roofline["ms"] = kms[di]
+    tr = captured_traffic(f"{resolved} {shape} r={r} v{var}", n ** 3)
+    roofline["traffic"] = tr
+    if tr:
+        roofline["traffic_over_algorithmic"] = tr / bytes_alg
 
     sweeps = {}
-    for r in RADII:
-        bytes_alg = 4 * ((N + 2 * r) ** 3 + N ** 3)
-        sweeps[f"box_r{r}"] = {"ms": kms[r], "gpts": N ** 3 / (kms[r] / 1e3) / 1e9,
-                               "hbm_gbs": bytes_alg / (kms[r] / 1e3) / 1e9,
-                               "hbm_frac": bytes_alg / (kms[r] / 1e3) / 1e9 / hbm_peak,
-                               "tflops": FLOP_PER_PT[r] * N ** 3 / (kms[r] / 1e3) / 1e12,
-                               "alu_frac": FLOP_PER_PT[r] * N ** 3 / (kms[r] / 1e3) / 1e12 / alu_peak}
+    for i, (shape, r, n) in enumerate(plan):
+        sec = kms[i] / 1e3
+        b = 4 * ((n + 2 * r) ** 3 + n ** 3)
+        f = flop_per_pt(shape, r) * n ** 3
+        sweeps[f"{shape}_r{r}_{n}"] = {"ms": kms[i], "gpts": n ** 3 / sec / 1e9,
+                                       "hbm_gbs": b / sec / 1e9, "hbm_frac": b / sec / 1e9 / hbm_peak,
+                                       "tflops": f / sec / 1e12, "alu_frac": f / sec / 1e12 / alu_peak}
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.workload == "box512":
         import oracle
         oracle.build()
         planes = calibrate_planes(5.0)
@@ -300,16 +374,17 @@ def main():
 
     line = {
         "metric": METRIC, "value": value, "unit": "GPoints/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path": path_used, "radii": list(RADII), "n": N,
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "path": path_used,
+                   "sweeps": [f"{sh} r={r} {n}^3" for sh, r, n in plan],
                    "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GPoints/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": len(RADII) * args.steps,
+        "gpu_launches": len(plan) * steps,
         "clocks": clk, "peaks": {"hbm_gbs": hbm_peak, "bf16_tflops": bf16_peak, "source": peak_src},
         "sweeps": sweeps,
     }

@@ -114,6 +114,11 @@ typedef struct {
 mms_status mms_stencil_apply_ex(const mms_stencil_desc *desc, const float *in, float *out,
                                 void *stream);
 
+/* The path MMS_PATH_AUTO takes for (shape, radius) on an input that does
+ * (tma_aligned = 1) or does not (0) meet the TMA alignment rule above;
+ * -1 for an invalid shape or radius.  Host only. */
+int32_t mms_auto_path(int shape, int radius, int tma_aligned);
+
 /* Number of tile variants of (shape, radius, path); variant indices run
  * 0..n-1.  Returns 0 for an unsupported combination.  Host only. */
 int32_t mms_num_variants(int shape, int radius, int path);

@@ -24,7 +24,8 @@ STATUS = {0: "MMS_OK", 1: "MMS_E_ARG", 2: "MMS_E_UNSUPPORTED", 3: "MMS_E_ALIGN",
 WAVE_GRAPH = 1
 
 # Every symbol include/mms.h declares (checked by the CPU test suite).
-EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_num_variants", "mms_default_variant",
+EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_num_variants",
+           "mms_default_variant",
            "mms_set_variant", "mms_wave_step", "mms_wave_forward", "mms_wave_adjoint",
            "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
            "mms_check_device", "mms_version"]
@@ -80,6 +81,7 @@ def load():
             "mms_stencil_apply": [i32, i32, P, P, P, i64, i64, i64, P],
             "mms_stencil_apply_ex": [ctypes.POINTER(StencilDesc), P, P, P],
             "mms_num_variants": [i32, i32, i32],
+            "mms_auto_path": [i32, i32, i32],
             "mms_default_variant": [i32, i32, i32, i64, i64, i64],
             "mms_set_variant": [i32, i32, i32, i32],
             "mms_wave_step": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P],
@@ -197,6 +199,11 @@ def apply_dense(shape, r, coeffs, inp, out, stream=None):
 
 def num_variants(shape, r, path) -> int:
     return load().mms_num_variants(SHAPES[shape], r, PATHS[path])
+
+
+def auto_path(shape, r, tma_aligned=True) -> str:
+    """Name of the path MMS_PATH_AUTO takes for (shape, r)."""
+    return PATH_NAMES[load().mms_auto_path(SHAPES[shape], r, 1 if tma_aligned else 0)]
 
 
 def default_variant(shape, r, path, nx=0, ny=0, nz=0) -> int:

@@ -121,6 +121,17 @@ static bool tma_ok(const float *in, int64_t ipy, int64_t ipz)
     return (reinterpret_cast<uintptr_t>(in) % 16) == 0 && (ipy % 4) == 0 && (ipz % 4) == 0;
 }
 
+// AUTO: the tensor-core BF16x3 box path once a tuned variant for it is
+// registered (the autotuner does so only where it beats the CUDA-core path),
+// else the TMA CUDA-core path, else the naive path for unaligned pitches.
+static int auto_path(int shape, int r, bool aligned)
+{
+    if (!aligned) return MMS_PATH_NAIVE;
+    if (band_tc_supported(shape, r, MMS_PATH_BF16X3) && tuned_variant(shape, r, MMS_PATH_BF16X3) >= 0)
+        return MMS_PATH_BF16X3;
+    return MMS_PATH_CUDA_CORE;
+}
+
 static bool overlaps(const void *a, size_t na, const void *b, size_t nb)
 {
     const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
@@ -156,12 +167,7 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
             reinterpret_cast<cudaStream_t>(stream)};
     int path = d->path;
     const bool aligned = tma_ok(in, ipy, ipz);
-    if (path == MMS_PATH_AUTO) {
-        path = aligned ? MMS_PATH_CUDA_CORE : MMS_PATH_NAIVE;
-        if (aligned && shape == MMS_BOX && r >= 2 && band_tc_supported(shape, r, MMS_PATH_BF16X3) &&
-            tuned_variant(shape, r, MMS_PATH_BF16X3) >= 0)
-            path = MMS_PATH_BF16X3;
-    }
+    if (path == MMS_PATH_AUTO) path = auto_path(shape, r, aligned);
     if (path == MMS_PATH_NAIVE) {
         cudaError_t e = launch_naive(s);
         return e == cudaSuccess ? MMS_OK : cuda_fail(e, "naive sweep launch");
@@ -216,6 +222,12 @@ mms_status mms_stencil_apply_ex(const mms_stencil_desc *desc, const float *in, f
 }
 
 int32_t mms_num_variants(int shape, int radius, int path) { return num_variants(shape, radius, path); }
+
+int32_t mms_auto_path(int shape, int radius, int tma_aligned)
+{
+    if ((shape != MMS_STAR && shape != MMS_BOX) || radius < 1 || radius > kMaxR) return -1;
+    return auto_path(shape, radius, tma_aligned != 0);
+}
 
 int32_t mms_default_variant(int shape, int radius, int path, int64_t nx, int64_t ny, int64_t nz)
 {
