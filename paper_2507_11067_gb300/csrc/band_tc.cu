@@ -22,9 +22,11 @@
 // Split precision (3 products hi*hi + hi*lo + lo*hi, FP32 accumulation)
 // recovers FP32-level accuracy from BF16 or TF32 operands.
 //
-// Pipeline (persistent CTAs, one per SM, 128 threads): TMA stages the FP32
-// box of group i+2 while group i is converted and its MMAs run; the
-// epilogue of group i-1 drains the other TMEM accumulator meanwhile.
+// Pipeline (persistent CTAs, one per SM, 16 warps in four roles, double
+// buffers handed over by mbarriers): TMA stages the FP32 box of group i+1
+// while converter warps turn group i into operand parts, one thread issues
+// the MMAs of group i-1 and the epilogue warps drain the TMEM accumulator
+// of group i-2.
 #include <cuda_bf16.h>
 #include <stdio.h>
 
@@ -65,16 +67,17 @@ struct Cfg {
     static constexpr int STG_BYTES = NL * K * 4;     // FP32 TMA staging
     static constexpr int PART_BYTES = NL * K * ELT;  // one converted operand part
     static constexpr int CONV_BYTES = PART_BYTES * NPARTS;
-    static constexpr int DSM_LD = 33;                // epilogue row stride (floats)
-    static constexpr int DSM_BYTES = 128 * DSM_LD * 4;
-    static constexpr int NT = 128;
+    static constexpr int NT = 512;                   // 16 warps, 4 per TMEM lane quarter
+    static constexpr int DSM_LD = 132;               // epilogue: [row y][lane] floats, two planes
+    static constexpr int DSM_PLANE = YP * DSM_LD;
+    static constexpr int DSM_BYTES = 2 * DSM_PLANE * 4;
     static constexpr int BAND_COL0 = 2 * N;          // TMEM: D0 | D1 | bands
     static constexpr uint32_t IDESC = tc::instr_desc(BF ? 1u : 2u, 128, N);
     // shared memory: [stg0 stg1 | conv0 conv1 | dsm | barriers, tmem slot, flag]
     static constexpr size_t OFF_CONV = 2 * (size_t)STG_BYTES;
     static constexpr size_t OFF_DSM = OFF_CONV + 2 * (size_t)CONV_BYTES;
     static constexpr size_t OFF_BAR = OFF_DSM + DSM_BYTES;
-    static constexpr size_t SMEM = 128 + OFF_BAR + 64;
+    static constexpr size_t SMEM = 128 + OFF_BAR + 128;
     static_assert(N % 16 == 0 && N <= 256, "MMA N");
     static_assert(STG_BYTES % 128 == 0 && CONV_BYTES % 128 == 0 && PART_BYTES % 16 == 0, "align");
 };
@@ -114,12 +117,24 @@ struct TcArgs {
     float *out;
     int64_t opy, opz;
     int nx, ny, nz;
+    int vec;                      // 16-byte output rows: float4 stores
     int tiles_x, tiles_y, tiles;  // tiles = tiles_x * tiles_y * zchunks
     int groups;                   // groups (of NZ planes) per tile
 };
 
+// Warp roles (16 warps): 0 = TMA producer, 1 = MMA issuer (and TMEM owner),
+// 2..7 = converters (FP32 box -> operand parts), 8..15 = epilogue (two per
+// TMEM lane quarter).  Roles hand buffers to each other through mbarriers,
+// so TMA, conversion, MMA and epilogue of different groups overlap.
+constexpr int kConvWarps = 6, kConvWarp0 = 2, kEpiWarps = 8, kEpiWarp0 = 8;
+
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 template <int R, int PREC>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(512, 1)
     box_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BoxCoef cf,
                   const __grid_constant__ TcArgs a, unsigned *err)
 {
@@ -130,35 +145,45 @@ __global__ void __launch_bounds__(128, 1)
     float *stg = reinterpret_cast<float *>(smem);
     unsigned char *conv = smem + C::OFF_CONV;
     float *dsm = reinterpret_cast<float *>(smem + C::OFF_DSM);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);  // [2]
-    uint64_t *mmad = full + 2;                                         // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mmad + 2);
-    int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+    uint64_t *full_stg = bar, *empty_stg = bar + 2, *full_conv = bar + 4, *empty_conv = bar + 6;
+    uint64_t *full_d = bar + 8, *empty_d = bar + 10;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 12);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *epi_fail = abort_flag + 1, *epi_stop = abort_flag + 2;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int my_tiles = a.tiles > (int)blockIdx.x ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int ng = my_tiles * a.groups;
 
-    if (warp == 0) {
+    if (warp == 1) {
         tc::tmem_alloc(tmem_slot, 512);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
-            ptx::mbar_init(&full[b], 1);
-            ptx::mbar_init(&mmad[b], 1);
+            ptx::mbar_init(&full_stg[b], 1);
+            ptx::mbar_init(&empty_stg[b], kConvWarps * 32);
+            ptx::mbar_init(&full_conv[b], kConvWarps * 32);
+            ptx::mbar_init(&empty_conv[b], 1);
+            ptx::mbar_init(&full_d[b], 1);
+            ptx::mbar_init(&empty_d[b], kEpiWarps);
         }
         ptx::fence_mbar_init();
         *abort_flag = 0;
+        *epi_fail = 0;
+        *epi_stop = 0;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *tmem_slot;
 
-    // Banded coefficient operand: lane (dy, x) of part p for plane offset dz.
-    {
-        const int l = warp * 32 + lane;
+    // Banded coefficient operand, written once by the first warp of each lane
+    // quarter: lane (dy, x) of part p for plane offset dz.
+    if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4) {
+        const int q = warp & 3;
+        const int l = q * 32 + lane;
         const bool used = l < C::LANES;
         const int dyi = used ? l / C::TXO : 0, xo = used ? l % C::TXO : 0;
         for (int dzi = 0; dzi < W; ++dzi)
@@ -185,10 +210,13 @@ __global__ void __launch_bounds__(128, 1)
                         v[j] = word;
                     }
                     const uint32_t col = C::BAND_COL0 + (dzi * C::NPARTS + p) * C::BANDCOLS + c0;
-                    tc::tmem_st_32x32b_x8(tbase + ((uint32_t)(warp * 32) << 16) + col, v);
+                    tc::tmem_st_32x32b_x8(tbase + ((uint32_t)(q * 32) << 16) + col, v);
                 }
         tc::tmem_wait_st();
     }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
 
     // group i -> (tile origin, first output plane)
     auto group_origin = [&](int i, int &x0, int &y0, int &z0) {
@@ -199,141 +227,196 @@ __global__ void __launch_bounds__(128, 1)
         y0 = yt * C::TY;
         z0 = (zc * a.groups + g) * C::NZ;
     };
-    auto issue_tma = [&](int i) {
-        int x0, y0, z0;
-        group_origin(i, x0, y0, z0);
-        ptx::mbar_arrive_expect_tx(&full[i & 1], C::STG_BYTES);
-        ptx::tma_load_3d(stg + (size_t)(i & 1) * (C::STG_BYTES / 4), &tmap, x0, y0, z0, &full[i & 1]);
-    };
-    if (tid == 0) {
-        ptx::prefetch_tmap(&tmap);
-        for (int i = 0; i < 2 && i < ng; ++i) issue_tma(i);
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-
-    int issued = 0, drained = 0;  // MMA groups issued by thread 0 / drained by the epilogue
-
-    auto epilogue = [&](int j) -> bool {
-        const bool ok = ptx::mbar_wait_bounded(&mmad[j & 1], (uint32_t)(j >> 1) & 1u, err);
-        if (!ok) *abort_flag = 1;
-        __syncthreads();
+    // Bounded wait; on expiry raise the CTA-wide abort flag.
+    auto wait = [&](uint64_t *b, uint32_t parity) -> bool {
         if (*abort_flag) return false;
-        tc::fence_after_sync();
-        ++drained;
-        int x0, y0, z0;
-        group_origin(j, x0, y0, z0);
-        for (int zl = 0; zl < C::NZ; ++zl) {
-            uint32_t r[32];
-            tc::tmem_ld_32x32b_x32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)((j & 1) * C::N + zl * C::YP), r);
-            tc::tmem_wait_ld();
-            float *row = dsm + (warp * 32 + lane) * C::DSM_LD;
+        if (ptx::mbar_wait_bounded(b, parity, err)) return true;
+        *abort_flag = 1;
+        return false;
+    };
+
+    if (warp == 0) {
+        // ---------------------------------------------------- TMA producer
+        if (lane == 0) {
+            ptx::prefetch_tmap(&tmap);
+            for (int i = 0; i < ng; ++i) {
+                const int s = i & 1;
+                if (!wait(&empty_stg[s], ((uint32_t)(i >> 1) & 1u) ^ 1u)) break;
+                int x0, y0, z0;
+                group_origin(i, x0, y0, z0);
+                ptx::mbar_arrive_expect_tx(&full_stg[s], C::STG_BYTES);
+                ptx::tma_load_3d(stg + (size_t)s * (C::STG_BYTES / 4), &tmap, x0, y0, z0, &full_stg[s]);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            for (int i = 0; i < ng; ++i) {
+                const int s = i & 1;
+                const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+                if (!wait(&full_conv[s], ph)) break;
+                if (!wait(&empty_d[s], ph ^ 1u)) break;
+                tc::fence_after_sync();
+                const uint32_t dcol = tbase + (uint32_t)(s * C::N);
+                const uint32_t cbase = ptx::smem_u32(conv + (size_t)s * C::CONV_BYTES);
+                uint32_t acc = 0;
+                for (int dzi = 0; dzi < W; ++dzi) {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) row[c] = __uint_as_float(r[c]);
-            __syncthreads();
-            const int z = z0 + zl;
-            if (z < a.nz) {
-                for (int it = tid; it < C::TXO * C::TY; it += C::NT) {
-                    const int xl = it % C::TXO, yl = it / C::TXO;
-                    const int x = x0 + xl, y = y0 + yl;
-                    if (x < a.nx && y < a.ny) {
-                        float s = 0.f;
+                    for (int pr = 0; pr < C::NPROD; ++pr) {
+                        const int pa = pr == 2 ? 1 : 0;  // band part
+                        const int pb = pr == 1 ? 1 : 0;  // data part
 #pragma unroll
-                        for (int dyi = 0; dyi < W; ++dyi) s += dsm[(dyi * C::TXO + xl) * C::DSM_LD + yl + dyi];
-                        a.out[(int64_t)z * a.opz + (int64_t)y * a.opy + x] = s;
+                        for (int kk = 0; kk < C::K / C::KSTEP; ++kk) {
+                            const uint32_t acol = tbase + C::BAND_COL0 + (dzi * C::NPARTS + pa) * C::BANDCOLS +
+                                                  kk * (C::KSTEP * C::ELT / 4);
+                            const uint32_t baddr = cbase + pb * C::PART_BYTES + (dzi * C::YP) * 16 +
+                                                   kk * (C::KSTEP / C::KC) * C::NL * 16;
+                            const uint64_t bdesc = tc::smem_desc(baddr, C::NL * 16, 128);
+                            if constexpr (C::BF)
+                                tc::mma_bf16_ts(dcol, acol, bdesc, C::IDESC, acc);
+                            else
+                                tc::mma_tf32_ts(dcol, acol, bdesc, C::IDESC, acc);
+                            acc = 1;
+                        }
                     }
                 }
+                tc::mma_commit(&full_d[s]);      // accumulator ready for the epilogue
+                tc::mma_commit(&empty_conv[s]);  // operand stage may be refilled
             }
-            __syncthreads();
+            // every issued MMA completes before TMEM is freed at teardown
+            if (ng > 0) ptx::mbar_wait_bounded(&empty_conv[(ng - 1) & 1], (uint32_t)((ng - 1) >> 1) & 1u, err);
         }
-        tc::fence_before_sync();
-        return true;
-    };
-
-    bool alive = true;
-    for (int i = 0; i < ng && alive; ++i) {
-        const int s = i & 1;
-        // 1. the FP32 box of group i has landed
-        if (!ptx::mbar_wait_bounded(&full[s], (uint32_t)(i >> 1) & 1u, err)) *abort_flag = 1;
-        // 2. convert it to the K-major operand parts (hi, lo)
-        if (!*abort_flag) {
+    } else if (warp < kConvWarp0 + kConvWarps) {
+        // -------------------------------------------------------- converters
+        const int ct = tid - kConvWarp0 * 32;
+        constexpr int CT = kConvWarps * 32;
+        for (int i = 0; i < ng; ++i) {
+            const int s = i & 1;
+            const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+            // decisions stay warp-uniform: a failed wait in any lane stops the warp
+            bool ok = ptx::mbar_wait_bounded(&full_stg[s], ph, err) &&
+                      ptx::mbar_wait_bounded(&empty_conv[s], ph ^ 1u, err);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                *abort_flag = 1;
+                break;
+            }
             const float *src = stg + (size_t)s * (C::STG_BYTES / 4);
             unsigned char *dst = conv + (size_t)s * C::CONV_BYTES;
             constexpr int NCH = C::K / C::KC;  // 16-byte chunks per line
-            for (int it = tid; it < C::NL * NCH; it += C::NT) {
+            for (int it = ct; it < C::NL * NCH; it += CT) {
                 const int kc = it % NCH, n = it / NCH;
                 const float *p = src + n * C::K + kc * C::KC;
-                float v[8];
-                const float4 q0 = *reinterpret_cast<const float4 *>(p);
-                v[0] = q0.x; v[1] = q0.y; v[2] = q0.z; v[3] = q0.w;
-                if constexpr (C::KC == 8) {
+                unsigned char *d0 = dst + ((size_t)kc * C::NL + n) * 16;
+                if constexpr (C::BF) {
+                    const float4 q0 = *reinterpret_cast<const float4 *>(p);
                     const float4 q1 = *reinterpret_cast<const float4 *>(p + 4);
-                    v[4] = q1.x; v[5] = q1.y; v[6] = q1.z; v[7] = q1.w;
-                }
+                    const float v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+                    uint32_t hi[4], lo[4];
 #pragma unroll
-                for (int part = 0; part < C::NPARTS; ++part) {
-                    uint4 o;
-                    if constexpr (C::BF) {
-                        uint32_t w4[4];
-#pragma unroll
-                        for (int h = 0; h < 4; ++h)
-                            w4[h] = split_part<PREC>(v[2 * h], part) | (split_part<PREC>(v[2 * h + 1], part) << 16);
-                        o = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                    } else {
-                        o = make_uint4(split_part<PREC>(v[0], part), split_part<PREC>(v[1], part),
-                                       split_part<PREC>(v[2], part), split_part<PREC>(v[3], part));
+                    for (int h = 0; h < 4; ++h) {
+                        // one cvt packs the pair (even k in the low half)
+                        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+                        hi[h] = *reinterpret_cast<const uint32_t *>(&b);
+                        const float h0 = __uint_as_float(hi[h] << 16), h1 = __uint_as_float(hi[h] & 0xffff0000u);
+                        const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * h] - h0, v[2 * h + 1] - h1);
+                        lo[h] = *reinterpret_cast<const uint32_t *>(&l);
                     }
-                    *reinterpret_cast<uint4 *>(dst + (size_t)part * C::PART_BYTES + ((size_t)kc * C::NL + n) * 16) = o;
+                    *reinterpret_cast<uint4 *>(d0) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4 *>(d0 + C::PART_BYTES) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                } else {
+                    const float4 q = *reinterpret_cast<const float4 *>(p);
+                    const uint32_t h0 = tf32_rna(q.x), h1 = tf32_rna(q.y), h2 = tf32_rna(q.z), h3 = tf32_rna(q.w);
+                    *reinterpret_cast<uint4 *>(d0) = make_uint4(h0, h1, h2, h3);
+                    if constexpr (C::NPARTS == 2)
+                        *reinterpret_cast<uint4 *>(d0 + C::PART_BYTES) =
+                            make_uint4(tf32_rna(q.x - __uint_as_float(h0)), tf32_rna(q.y - __uint_as_float(h1)),
+                                       tf32_rna(q.z - __uint_as_float(h2)), tf32_rna(q.w - __uint_as_float(h3)));
                 }
             }
             ptx::fence_proxy_async_smem();  // generic writes -> tensor-core reads
+            ptx::mbar_arrive(&full_conv[s]);
+            ptx::mbar_arrive(&empty_stg[s]);
         }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (*abort_flag) { alive = false; break; }
-        // 3. thread 0: refill the staging buffer, issue group i's MMAs
-        if (tid == 0) {
-            if (i + 2 < ng) issue_tma(i + 2);
-            const uint32_t dcol = tbase + (uint32_t)(s * C::N);
-            const uint32_t cbase = ptx::smem_u32(conv + (size_t)s * C::CONV_BYTES);
-            uint32_t acc = 0;
-            for (int dzi = 0; dzi < W; ++dzi) {
+    } else {
+        // ---------------------------------------------------------- epilogue
+        // TMEM -> registers -> shared memory, the sum over the 2r+1 lanes
+        // (dy, x) with rows shifted by dy, float4 stores.  Lane (dy, x) of
+        // column c feeds output row y = c - dy, so it is stored at [y][lane]
+        // and the reduction reads four x positions per load.
+        const int q = warp & 3, half = (warp - kEpiWarp0) >> 2;
+        const int my_lane = q * 32 + lane;
+        const int my_dyi = my_lane < C::LANES ? my_lane / C::TXO : 0;
+        const int et = tid - kEpiWarp0 * 32;
+        constexpr int ET = kEpiWarps * 32;
+        constexpr int XQ = C::TXO / 4;
+        int plane_ctr = 0;
+        for (int i = 0; i < ng; ++i) {
+            const int s = i & 1;
+            // the epilogue warps share named barriers: they stop together
+            if (!ptx::mbar_wait_bounded(&full_d[s], (uint32_t)(i >> 1) & 1u, err)) *epi_fail = 1;
+            named_sync(1, ET);
+            if (et == 0) *epi_stop = (*epi_fail || *abort_flag) ? 1 : 0;
+            named_sync(1, ET);
+            if (*epi_stop) {
+                *abort_flag = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            int x0, y0, z0;
+            group_origin(i, x0, y0, z0);
+            for (int zl = 0; zl < C::NZ; ++zl, ++plane_ctr) {
+                float *dbuf = dsm + (plane_ctr & 1) * C::DSM_PLANE;
+                uint32_t r[16];
+                tc::tmem_ld_32x32b_x16(tbase + ((uint32_t)(q * 32) << 16) +
+                                           (uint32_t)(s * C::N + zl * C::YP + half * 16),
+                                       r);
+                tc::tmem_wait_ld();
+                if (my_lane < C::LANES) {
+                    float *dst = dbuf + my_lane;
 #pragma unroll
-                for (int pr = 0; pr < C::NPROD; ++pr) {
-                    const int pa = pr == 2 ? 1 : 0;  // band part
-                    const int pb = pr == 1 ? 1 : 0;  // data part
+                    for (int c = 0; c < 16; ++c) {
+                        const int y = half * 16 + c - my_dyi;
+                        if (y >= 0 && y < C::TY) dst[y * C::DSM_LD] = __uint_as_float(r[c]);
+                    }
+                }
+                if (zl == C::NZ - 1) {
+                    // all TMEM reads of this accumulator are done: hand it back
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&empty_d[s]);
+                }
+                named_sync(1, ET);
+                const int z = z0 + zl;
+                if (z < a.nz) {
+                    for (int it = et; it < C::TY * XQ; it += ET) {
+                        const int xq = it % XQ, yl = it / XQ;
+                        const int y = y0 + yl, x = x0 + 4 * xq;
+                        if (y >= a.ny || x >= a.nx) continue;
+                        const float *src = dbuf + yl * C::DSM_LD + 4 * xq;
+                        float4 acc = *reinterpret_cast<const float4 *>(src);
 #pragma unroll
-                    for (int kk = 0; kk < C::K / C::KSTEP; ++kk) {
-                        const uint32_t acol = tbase + C::BAND_COL0 + (dzi * C::NPARTS + pa) * C::BANDCOLS +
-                                              kk * (C::KSTEP * C::ELT / 4);
-                        const uint32_t baddr = cbase + pb * C::PART_BYTES + (dzi * C::YP) * 16 +
-                                               kk * (C::KSTEP / C::KC) * C::NL * 16;
-                        const uint64_t bdesc = tc::smem_desc(baddr, C::NL * 16, 128);
-                        if constexpr (C::BF)
-                            tc::mma_bf16_ts(dcol, acol, bdesc, C::IDESC, acc);
-                        else
-                            tc::mma_tf32_ts(dcol, acol, bdesc, C::IDESC, acc);
-                        acc = 1;
+                        for (int dyi = 1; dyi < W; ++dyi) {
+                            const float4 t = *reinterpret_cast<const float4 *>(src + dyi * C::TXO);
+                            acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
+                        }
+                        float *o = a.out + (int64_t)z * a.opz + (int64_t)y * a.opy + x;
+                        if (a.vec && x + 3 < a.nx) {
+                            *reinterpret_cast<float4 *>(o) = acc;
+                        } else {
+                            const float v4[4] = {acc.x, acc.y, acc.z, acc.w};
+                            for (int k = 0; k < 4 && x + k < a.nx; ++k) o[k] = v4[k];
+                        }
                     }
                 }
             }
-            tc::mma_commit(&mmad[s]);
-            ++issued;
         }
-        // 4. drain the previous group's accumulator
-        if (i >= 1 && !epilogue(i - 1)) { alive = false; break; }
     }
-    if (alive && ng >= 1) epilogue(ng - 1);
 
-    // teardown: no MMA may still write TMEM when it is freed
-    if (tid == 0 && issued > drained) {
-        for (int j = drained; j < issued; ++j) ptx::mbar_wait_bounded(&mmad[j & 1], (uint32_t)(j >> 1) & 1u, err);
-    }
+    __syncwarp();  // the single-lane roles reconverge their warps first
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tbase, 512);
     }
@@ -369,6 +452,7 @@ cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int groups)
         a.nx = (int)s.nx;
         a.ny = (int)s.ny;
         a.nz = (int)s.nz;
+        a.vec = (s.opy % 4 == 0 && s.opz % 4 == 0 && reinterpret_cast<uintptr_t>(s.out) % 16 == 0) ? 1 : 0;
         a.tiles_x = (int)((s.nx + C::TXO - 1) / C::TXO);
         a.tiles_y = (int)((s.ny + C::TY - 1) / C::TY);
         const int zgroups = (int)((s.nz + C::NZ - 1) / C::NZ);
