@@ -42,6 +42,8 @@ WORKLOADS = {
     "box512": [("box", 1, 512), ("box", 2, 512)],
     "star1024": [("star", 4, 1024)],
     "star512": [("star", 4, 512)],
+    "rtm512": None,    # acoustic forward: 8 shots x 512^3, 500 steps (see run_wave)
+    "grad256": None,   # adjoint gradient: 2 shots x 256^3, 200 steps, checkpoint 20
 }
 WORKLOAD_NAMES = {
     "box512": WORKLOAD,
@@ -49,6 +51,10 @@ WORKLOAD_NAMES = {
                 "16 sinusoids + 1e-3 noise",
     "star512": "star stencil sweep r=4 (25 pt, FD8 weights), 512^3 FP32 interior + halo, "
                "16 sinusoids + 1e-3 noise (profiling size)",
+    "rtm512": "batched acoustic forward, 8 shots x 512^3, r=4 FD8 star, 20-cell sponge, h=10 m, "
+              "CFL 0.4, 15 Hz Ricker, one CUDA graph per run",
+    "grad256": "adjoint gradient of 0.5|d - d_obs|^2 wrt velocity, 2 shots x 256^3, 200 steps, "
+               "checkpoint every 20 with recompute, FP64 accumulation",
 }
 
 
@@ -216,6 +222,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("rtm512", "grad256"):
+        return run_wave(args)
 
     import torch
     import paper_2507_11067_gb300 as mms
@@ -391,6 +399,131 @@ def main():
     if not args.no_extras:
         line["extras"] = extras(mms, torch, dev, hbm_peak, alu_peak)
     print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_wave(args):
+    """The acoustic workloads on one GPU (shots are independent: under
+    torchrun each rank runs its own shots, weak scaling)."""
+    import torch
+    import paper_2507_11067_gb300 as mms
+    from paper_2507_11067_gb300.wave import WaveFunction, WavePropagator
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mms.build()
+    mms.load()
+    hbm_peak, _, _, peak_src = peaks()
+    if args.workload == "rtm512":
+        n, nshots, nsteps, every = 512, 8, 500, 0
+    else:
+        n, nshots, nsteps, every = 256, 2, 200, 20
+    wi = workloads.WaveInputs(n, n, n, nshots=nshots, nsteps=nsteps, workload=4 if n == 512 else 5,
+                              noise=True, salt=rank)
+    prop = WavePropagator(n, n, n, wi.src, wi.zrec, wi.h, wi.dt, sponge_width=wi.sponge,
+                          sponge_a=wi.sponge_a, device=dev)
+    v_host = torch.from_numpy(wi.v).pin_memory()
+    amps_host = torch.from_numpy(wi.amp).pin_memory()
+    v = v_host.to(dev)
+    amps = amps_host.to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    if args.workload == "rtm512":
+        steps = args.steps or nsteps
+
+        def run():
+            rec, _ = prop.forward(v, amps[:steps], steps, graph=True)
+            return rec
+        launches = steps
+    else:
+        steps = args.steps or 1
+        w0 = workloads.WaveInputs(n, n, n, nshots=nshots, nsteps=nsteps, workload=5, noise=False, salt=rank)
+        with torch.no_grad():
+            obs, _ = prop.forward(v, amps, nsteps)
+        v0 = torch.from_numpy(w0.v).to(dev)
+
+        def run():
+            vv = v0.clone().requires_grad_(True)
+            rec = WaveFunction.apply(vv, prop, amps, nsteps, every)
+            loss = 0.5 * ((rec - obs) ** 2).sum()
+            loss.backward()
+            return vv.grad
+        # forward + per segment recompute + adjoint, plus the copies of the recompute
+        launches = nsteps + 2 * nsteps + 2
+
+    for _ in range(max(1, args.warmup // 3)):
+        run()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 1 if args.workload == "rtm512" else steps
+    t0.record(stream)
+    for _ in range(reps):
+        out = run()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    pts = nshots * n ** 3
+    if args.workload == "rtm512":
+        units = world * pts * steps
+        bytes_alg = 16.0 * pts * steps
+        # end to end: velocity and wavelet in from pinned host memory, records out
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vv = v_host.to(dev, non_blocking=True)
+        aa = amps_host.to(dev, non_blocking=True)
+        rec, _ = prop.forward(vv, aa[:steps], steps, graph=True)
+        rec_host = rec.to("cpu")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_s = e0.elapsed_time(e1) / 1e3
+        h2d = v_host.numel() * 4 + amps_host.numel() * 4
+        d2h = rec_host.numel() * 4
+        value = units / elapsed / 1e9
+        e2e = {"value": units / e2e_s / 1e9, "unit": "GPoint-steps/s", "h2d_bytes_per_step": h2d / steps,
+               "d2h_bytes_per_step": d2h / steps}
+        roof = {"bound": "hbm", "achieved": bytes_alg / elapsed / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": bytes_alg / elapsed / 1e9 / hbm_peak, "traffic": None,
+                "kernel": "wave_fwd_kernel (fused star r=4 + leapfrog + sponge + source + receivers)",
+                "bytes_per_point_step": 16}
+        unit = "GPoint-steps/s"
+    else:
+        units = world * pts * nsteps * steps
+        value = units / elapsed / 1e9
+        e2e = {"value": value, "unit": "GPoint-steps/s (forward + gradient)", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": 0}
+        # forward 16 B + recompute 16 B (+8 B copy) + adjoint 20 B + FP64 gradient RMW 16 B per point-step
+        bytes_alg = 76.0 * pts * nsteps * steps
+        roof = {"bound": "hbm", "achieved": bytes_alg / elapsed / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": bytes_alg / elapsed / 1e9 / hbm_peak, "traffic": None,
+                "kernel": "forward + recompute + wave_adj_kernel",
+                "bytes_per_point_step": 76}
+        unit = "GPoint-steps/s"
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / (steps if args.workload == "rtm512" else reps),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": {"workload": WORKLOAD_NAMES[args.workload], "shots": nshots,
+                                                "n": n, "time_steps": nsteps if args.workload != "rtm512" else steps},
+                "roofline": roof, "cpu_baseline": None, "e2e": e2e,
+                "gpu_launches": launches * reps, "clocks": clk,
+                "peaks": {"hbm_gbs": hbm_peak, "source": peak_src}}
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0

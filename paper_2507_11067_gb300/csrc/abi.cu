@@ -48,7 +48,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 }
 
 bool encode_tmap_3d(CUtensorMap *map, const float *base, int64_t X, int64_t Y, int64_t Z,
-                    int64_t py, int64_t pz, int bx, int by, int bz)
+                    int64_t py, int64_t pz, int bx, int by, int bz, bool swizzle128)
 {
     auto enc = get_encode();
     if (!enc) return false;
@@ -57,7 +57,8 @@ bool encode_tmap_3d(CUtensorMap *map, const float *base, int64_t X, int64_t Y, i
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -187,9 +188,9 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
         cudaError_t e = shape == MMS_STAR ? launch_star_cc(s, map, v) : launch_box_cc(s, map, v);
         return e == cudaSuccess ? MMS_OK : cuda_fail(e, "CUDA-core sweep launch");
     }
-    int bx, by, bz;
-    band_tc_box(shape, r, path, v, &bx, &by, &bz);
-    if (!encode_tmap_3d(&map, in, X, Y, Z, ipy, ipz, bx, by, bz))
+    int bx, by, bz, swz;
+    band_tc_box(shape, r, path, v, &bx, &by, &bz, &swz);
+    if (!encode_tmap_3d(&map, in, X, Y, Z, ipy, ipz, bx, by, bz, swz != 0))
         return fail(MMS_E_CUDA, "cuTensorMapEncodeTiled refused the input grid");
     cudaError_t e = launch_band_tc(s, path, map, v);
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "tensor-core sweep launch");

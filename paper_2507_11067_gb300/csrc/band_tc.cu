@@ -34,6 +34,33 @@
 #include "tc.cuh"
 
 namespace mms {
+
+#ifdef MMS_ROLE_TRACE
+// Role trace (debug builds only, -DMMS_ROLE_TRACE): cycles each role of the
+// first eight CTAs spends waiting on its barriers and in total, summed.
+//   [0] producer: wait empty staging, total
+//   [1] MMA: wait operands, total, wait accumulator, issuing
+//   [2] converter (first lane): wait staging, total, wait operand slot
+//   [3] epilogue (first lane): wait accumulator, total, group barriers
+__device__ unsigned long long g_role_trace[4][4];
+#define MMS_TRACE_ADD(role, slot, v) \
+    do { if (blockIdx.x < 8) atomicAdd(&g_role_trace[role][slot], (unsigned long long)(v)); } while (0)
+#define MMS_CLOCK() clock64()
+extern "C" int mms_role_trace_read(unsigned long long *host, int reset)
+{
+    if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+    if (cudaMemcpyFromSymbol(host, g_role_trace, sizeof(g_role_trace)) != cudaSuccess) return 1;
+    if (reset) {
+        unsigned long long z[4][4] = {};
+        cudaMemcpyToSymbol(g_role_trace, z, sizeof(z));
+    }
+    return 0;
+}
+#else
+#define MMS_TRACE_ADD(role, slot, v) do { } while (0)
+#define MMS_CLOCK() 0ull
+#endif
+
 namespace {
 
 enum { P_TF32 = 0, P_3XTF32 = 1, P_BF16X3 = 2 };
@@ -60,26 +87,62 @@ struct Cfg {
                               : (2 * 3 * YP + BAND_TOTAL <= 512) ? 3
                               : (2 * 2 * YP + BAND_TOTAL <= 512) ? 2
                                                                  : 1;
-    static constexpr bool OK = 2 * NZ * YP + BAND_TOTAL <= 512 && LANES <= 128;
+    static constexpr bool FITS_TMEM = 2 * NZ * YP + BAND_TOTAL <= 512 && LANES <= 128;
     static constexpr int N = NZ * YP;                // MMA N (lines per group)
-    static constexpr int ZS = NZ + 2 * R;            // staged planes per group
-    static constexpr int NL = ZS * YP;               // staged lines per group
-    static constexpr int STG_BYTES = NL * K * 4;     // FP32 TMA staging
-    static constexpr int PART_BYTES = NL * K * ELT;  // one converted operand part
+    // Planes are staged and converted once, in chunks of NZ planes.  Group g
+    // of a tile reads planes [g NZ, g NZ + NZ + 2R) = chunks g .. g + H; the
+    // converted chunks live in a ring of CR slots plus H duplicate slots (a
+    // chunk in slot s < H is also written to slot CR + s), so every window of
+    // H + 1 consecutive chunks is contiguous and one descriptor spans it.
+    static constexpr int H = (2 * R + NZ - 1) / NZ;
+    static constexpr int CR = H + 2;
+    static constexpr int CHUNK_LINES = NZ * YP;
+    static constexpr int RING_LINES = (CR + H) * CHUNK_LINES;
+    static constexpr int PART_BYTES = RING_LINES * K * ELT;  // one operand part, whole ring
     static constexpr int CONV_BYTES = PART_BYTES * NPARTS;
-    static constexpr int NT = 512;                   // 16 warps, 4 per TMEM lane quarter
-    static constexpr int DSM_LD = 132;               // epilogue: [row y][lane] floats, two planes
-    static constexpr int DSM_PLANE = YP * DSM_LD;
-    static constexpr int DSM_BYTES = 2 * DSM_PLANE * 4;
+    static constexpr int STG_BYTES = CHUNK_LINES * K * 4;     // FP32 TMA staging of one chunk
+    // epilogue: one [row y + 2R][lane] float tile per epilogue warp group.
+    // A row stride of 0 mod 32 words puts lane l in bank l whatever its row,
+    // so the scattered stores are conflict-free; 2R spare rows take the
+    // values that fall outside the tile, so every store is unconditional; the
+    // reduction pads its x quads to a multiple of 8 so that 8 consecutive
+    // items read 8 different bank groups.
+    static constexpr int DSM_LD = 128;
+    static constexpr int XQ = TXO / 4, XQP = (XQ + 7) / 8 * 8;
+    static constexpr int DSM_ROWS = YP + 2 * R;
+    static constexpr int DSM_GROUP = DSM_ROWS * DSM_LD;  // floats per epilogue group
     static constexpr int BAND_COL0 = 2 * N;          // TMEM: D0 | D1 | bands
     static constexpr uint32_t IDESC = tc::instr_desc(BF ? 1u : 2u, 128, N);
-    // shared memory: [stg0 stg1 | conv0 conv1 | dsm | barriers, tmem slot, flag]
-    static constexpr size_t OFF_CONV = 2 * (size_t)STG_BYTES;
-    static constexpr size_t OFF_DSM = OFF_CONV + 2 * (size_t)CONV_BYTES;
-    static constexpr size_t OFF_BAR = OFF_DSM + DSM_BYTES;
-    static constexpr size_t SMEM = 128 + OFF_BAR + 128;
+    // shared memory: [conv ring | dsm | staging ring | barriers, tmem slot, flags]
+    static constexpr size_t BUDGET = 227 * 1024;
+    static constexpr size_t BASE = (size_t)CONV_BYTES + 1024 + 512;
+    static constexpr size_t GRP = (size_t)DSM_GROUP * 4;
+    // epilogue warp groups (4 warps, one per TMEM lane quarter, each owns whole
+    // planes of the accumulator): as many as the planes and shared memory allow
+    static constexpr int EGF = BASE + 4 * GRP + 2 * (size_t)STG_BYTES <= BUDGET   ? 4
+                               : BASE + 3 * GRP + 2 * (size_t)STG_BYTES <= BUDGET ? 3
+                               : BASE + 2 * GRP + 2 * (size_t)STG_BYTES <= BUDGET ? 2
+                                                                                 : 1;
+    static constexpr int EG = EGF < NZ ? EGF : NZ;
+    static constexpr int DSM_BYTES = EG * DSM_GROUP * 4;
+    static constexpr int NCONV = 4;                  // converter warps: 2, 3 and the last two
+    static constexpr int NWARPS = 4 + 4 * EG + 2;
+    static constexpr int NT = 32 * NWARPS;
+    static constexpr size_t FIXED = BASE + DSM_BYTES;
+    static constexpr int NST = FIXED + 4 * (size_t)STG_BYTES <= BUDGET   ? 4
+                               : FIXED + 3 * (size_t)STG_BYTES <= BUDGET ? 3
+                                                                         : 2;
+    static constexpr size_t OFF_DSM = CONV_BYTES;
+    static constexpr size_t OFF_STG = OFF_DSM + DSM_BYTES;
+    static constexpr size_t OFF_BAR = OFF_STG + (size_t)NST * STG_BYTES;
+    static constexpr size_t SMEM = 1024 + OFF_BAR + 512;
+    static constexpr bool OK = FITS_TMEM && SMEM <= BUDGET && RING_LINES * 16 < (1 << 18);
+    // FP32 staging rows of exactly 128 bytes are loaded with the TMA 128-byte
+    // swizzle: 16-byte chunk q of line n sits at chunk q ^ (n & 7), so the
+    // converters' column reads across 8 lines hit 8 different bank groups.
+    static constexpr bool SWZ = K * 4 == 128;
     static_assert(N % 16 == 0 && N <= 256, "MMA N");
-    static_assert(STG_BYTES % 128 == 0 && CONV_BYTES % 128 == 0 && PART_BYTES % 16 == 0, "align");
+    static_assert(STG_BYTES % 1024 == 0 && CONV_BYTES % 1024 == 0 && PART_BYTES % 16 == 0, "align");
 };
 
 __device__ __forceinline__ uint32_t bf16_bits(float v)
@@ -122,11 +185,12 @@ struct TcArgs {
     int groups;                   // groups (of NZ planes) per tile
 };
 
-// Warp roles (16 warps): 0 = TMA producer, 1 = MMA issuer (and TMEM owner),
-// 2..7 = converters (FP32 box -> operand parts), 8..15 = epilogue (two per
-// TMEM lane quarter).  Roles hand buffers to each other through mbarriers,
-// so TMA, conversion, MMA and epilogue of different groups overlap.
-constexpr int kConvWarps = 6, kConvWarp0 = 2, kEpiWarps = 8, kEpiWarp0 = 8;
+// Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2, 3 and
+// the last two warps = converters (FP32 box -> operand parts), 4 .. 4+4EG-1 =
+// epilogue, EG groups of four warps (warp w reaches TMEM lane quarter w % 4);
+// group e drains planes e, e+EG, ... of each accumulator.  Roles hand buffers
+// to each other through mbarriers, so TMA, conversion, MMA and epilogue of
+// different groups overlap.
 
 __device__ __forceinline__ void named_sync(int id, int nthreads)
 {
@@ -134,45 +198,53 @@ __device__ __forceinline__ void named_sync(int id, int nthreads)
 }
 
 template <int R, int PREC>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
     box_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BoxCoef cf,
                   const __grid_constant__ TcArgs a, unsigned *err)
 {
     using C = Cfg<R, PREC>;
     constexpr int W = C::W;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char *smem = smem_raw + ((128u - (ptx::smem_u32(smem_raw) & 127u)) & 127u);
-    float *stg = reinterpret_cast<float *>(smem);
-    unsigned char *conv = smem + C::OFF_CONV;
+    // 1024-byte alignment: the TMA swizzle pattern repeats every 1024 bytes
+    unsigned char *smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char *conv = smem;
     float *dsm = reinterpret_cast<float *>(smem + C::OFF_DSM);
+    float *stg = reinterpret_cast<float *>(smem + C::OFF_STG);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
-    uint64_t *full_stg = bar, *empty_stg = bar + 2, *full_conv = bar + 4, *empty_conv = bar + 6;
-    uint64_t *full_d = bar + 8, *empty_d = bar + 10;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 12);
+    uint64_t *full_stg = bar, *empty_stg = bar + C::NST;
+    uint64_t *full_conv = bar + 2 * C::NST, *empty_conv = full_conv + C::CR;
+    uint64_t *full_d = empty_conv + C::CR, *empty_d = full_d + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty_d + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    volatile int *epi_fail = abort_flag + 1, *epi_stop = abort_flag + 2;
+    volatile int *epi_fail = abort_flag + 1;  // [EG][2], by epilogue group and accumulator parity
+    constexpr int CT = C::NCONV * 32;           // converter threads
+    constexpr int NEPI = 4 * C::EG;             // epilogue warps
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int my_tiles = a.tiles > (int)blockIdx.x ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int ng = my_tiles * a.groups;
+    const int G = a.groups, CPT = a.groups + C::H;  // groups and chunks per tile
+    const int ng = my_tiles * G, nch = my_tiles * CPT;
 
     if (warp == 1) {
         tc::tmem_alloc(tmem_slot, 512);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < C::NST; ++b) {
             ptx::mbar_init(&full_stg[b], 1);
-            ptx::mbar_init(&empty_stg[b], kConvWarps * 32);
-            ptx::mbar_init(&full_conv[b], kConvWarps * 32);
+            ptx::mbar_init(&empty_stg[b], CT);
+        }
+        for (int b = 0; b < C::CR; ++b) {
+            ptx::mbar_init(&full_conv[b], CT);
             ptx::mbar_init(&empty_conv[b], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&full_d[b], 1);
-            ptx::mbar_init(&empty_d[b], kEpiWarps);
+            ptx::mbar_init(&empty_d[b], NEPI);
         }
         ptx::fence_mbar_init();
         *abort_flag = 0;
-        *epi_fail = 0;
-        *epi_stop = 0;
+        for (int e = 0; e < 2 * C::EG; ++e) epi_fail[e] = 0;
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -181,7 +253,7 @@ __global__ void __launch_bounds__(512, 1)
 
     // Banded coefficient operand, written once by the first warp of each lane
     // quarter: lane (dy, x) of part p for plane offset dz.
-    if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4) {
+    if (warp >= 4 && warp < 8) {
         const int q = warp & 3;
         const int l = q * 32 + lane;
         const bool used = l < C::LANES;
@@ -218,48 +290,67 @@ __global__ void __launch_bounds__(512, 1)
     __syncthreads();
     tc::fence_after_sync();
 
-    // group i -> (tile origin, first output plane)
-    auto group_origin = [&](int i, int &x0, int &y0, int &z0) {
-        const int t = (int)blockIdx.x + (i / a.groups) * (int)gridDim.x;
-        const int g = i % a.groups;
+    // tile (per CTA, tl-th) -> column origin and first plane of its z chunk
+    auto tile_origin = [&](int tl, int &x0, int &y0, int &zt) {
+        const int t = (int)blockIdx.x + tl * (int)gridDim.x;
         const int xt = t % a.tiles_x, yt = (t / a.tiles_x) % a.tiles_y, zc = t / (a.tiles_x * a.tiles_y);
         x0 = xt * C::TXO;
         y0 = yt * C::TY;
-        z0 = (zc * a.groups + g) * C::NZ;
+        zt = zc * G * C::NZ;
     };
-    // Bounded wait; on expiry raise the CTA-wide abort flag.
+    // Bounded wait for the single-thread roles; on expiry raise the abort flag.
+    unsigned long long waited = 0;  // role trace only
     auto wait = [&](uint64_t *b, uint32_t parity) -> bool {
         if (*abort_flag) return false;
-        if (ptx::mbar_wait_bounded(b, parity, err)) return true;
+        const unsigned long long t0 = MMS_CLOCK();
+        const bool done = ptx::mbar_wait_bounded(b, parity, err);
+        waited += MMS_CLOCK() - t0;
+        if (done) return true;
         *abort_flag = 1;
         return false;
     };
 
     if (warp == 0) {
-        // ---------------------------------------------------- TMA producer
+        // ------------------------------------------- TMA producer: chunk k
         if (lane == 0) {
+            const unsigned long long tstart = MMS_CLOCK();
             ptx::prefetch_tmap(&tmap);
-            for (int i = 0; i < ng; ++i) {
-                const int s = i & 1;
-                if (!wait(&empty_stg[s], ((uint32_t)(i >> 1) & 1u) ^ 1u)) break;
-                int x0, y0, z0;
-                group_origin(i, x0, y0, z0);
-                ptx::mbar_arrive_expect_tx(&full_stg[s], C::STG_BYTES);
-                ptx::tma_load_3d(stg + (size_t)s * (C::STG_BYTES / 4), &tmap, x0, y0, z0, &full_stg[s]);
+            for (int k = 0; k < nch; ++k) {
+                const int st = k % C::NST;
+                if (!wait(&empty_stg[st], ((uint32_t)(k / C::NST) & 1u) ^ 1u)) break;
+                int x0, y0, zt;
+                tile_origin(k / CPT, x0, y0, zt);
+                ptx::mbar_arrive_expect_tx(&full_stg[st], C::STG_BYTES);
+                ptx::tma_load_3d(stg + (size_t)st * (C::STG_BYTES / 4), &tmap, x0, y0,
+                                 zt + (k % CPT) * C::NZ, &full_stg[st]);
             }
+            MMS_TRACE_ADD(0, 0, waited);
+            MMS_TRACE_ADD(0, 1, MMS_CLOCK() - tstart);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
+            const unsigned long long tstart = MMS_CLOCK();
+            unsigned long long wconv = 0, wacc = 0, tissue = 0;
             for (int i = 0; i < ng; ++i) {
-                const int s = i & 1;
-                const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-                if (!wait(&full_conv[s], ph)) break;
-                if (!wait(&empty_d[s], ph ^ 1u)) break;
+                const int s = i & 1, g = i % G;
+                const int kg = (i / G) * CPT + g;  // first chunk of this group's window
+                bool ok = true;
+                unsigned long long w0 = waited;
+                for (int h = 0; h <= C::H && ok; ++h)
+                    ok = wait(&full_conv[(kg + h) % C::CR], (uint32_t)((kg + h) / C::CR) & 1u);
+                wconv += waited - w0;
+                w0 = waited;
+                if (!ok || !wait(&empty_d[s], ((uint32_t)(i >> 1) & 1u) ^ 1u)) break;
+                wacc += waited - w0;
+                const unsigned long long ti = MMS_CLOCK();
                 tc::fence_after_sync();
                 const uint32_t dcol = tbase + (uint32_t)(s * C::N);
-                const uint32_t cbase = ptx::smem_u32(conv + (size_t)s * C::CONV_BYTES);
-                uint32_t acc = 0;
+                const uint32_t cbase = ptx::smem_u32(conv) + (uint32_t)((kg % C::CR) * C::CHUNK_LINES * 16);
+                // one descriptor per group; each MMA adds a constant (>> 4) to its start field
+                const uint64_t d0 = tc::smem_desc(cbase, C::RING_LINES * 16, 128);
+                const uint32_t a0 = tbase + C::BAND_COL0;
+#pragma unroll
                 for (int dzi = 0; dzi < W; ++dzi) {
 #pragma unroll
                     for (int pr = 0; pr < C::NPROD; ++pr) {
@@ -267,50 +358,67 @@ __global__ void __launch_bounds__(512, 1)
                         const int pb = pr == 1 ? 1 : 0;  // data part
 #pragma unroll
                         for (int kk = 0; kk < C::K / C::KSTEP; ++kk) {
-                            const uint32_t acol = tbase + C::BAND_COL0 + (dzi * C::NPARTS + pa) * C::BANDCOLS +
-                                                  kk * (C::KSTEP * C::ELT / 4);
-                            const uint32_t baddr = cbase + pb * C::PART_BYTES + (dzi * C::YP) * 16 +
-                                                   kk * (C::KSTEP / C::KC) * C::NL * 16;
-                            const uint64_t bdesc = tc::smem_desc(baddr, C::NL * 16, 128);
+                            const uint32_t acol = a0 + (dzi * C::NPARTS + pa) * C::BANDCOLS + kk * (C::KSTEP * C::ELT / 4);
+                            const uint64_t bdesc = d0 + (uint64_t)((pb * C::PART_BYTES + (dzi * C::YP) * 16 +
+                                                                    kk * (C::KSTEP / C::KC) * C::RING_LINES * 16) >> 4);
+                            const uint32_t acc = (dzi | pr | kk) ? 1u : 0u;
                             if constexpr (C::BF)
                                 tc::mma_bf16_ts(dcol, acol, bdesc, C::IDESC, acc);
                             else
                                 tc::mma_tf32_ts(dcol, acol, bdesc, C::IDESC, acc);
-                            acc = 1;
                         }
                     }
                 }
-                tc::mma_commit(&full_d[s]);      // accumulator ready for the epilogue
-                tc::mma_commit(&empty_conv[s]);  // operand stage may be refilled
+                tissue += MMS_CLOCK() - ti;
+                tc::mma_commit(&full_d[s]);                 // accumulator ready for the epilogue
+                tc::mma_commit(&empty_conv[kg % C::CR]);    // chunk kg has no later reader
+                if (g == G - 1)                             // the tile's tail chunks neither
+                    for (int h = 1; h <= C::H; ++h) tc::mma_commit(&empty_conv[(kg + h) % C::CR]);
             }
             // every issued MMA completes before TMEM is freed at teardown
-            if (ng > 0) ptx::mbar_wait_bounded(&empty_conv[(ng - 1) & 1], (uint32_t)((ng - 1) >> 1) & 1u, err);
+            if (ng > 0) ptx::mbar_wait_bounded(&full_d[(ng - 1) & 1], (uint32_t)((ng - 1) >> 1) & 1u, err);
+            MMS_TRACE_ADD(1, 0, wconv);
+            MMS_TRACE_ADD(1, 1, MMS_CLOCK() - tstart);
+            MMS_TRACE_ADD(1, 2, wacc);
+            MMS_TRACE_ADD(1, 3, tissue);
         }
-    } else if (warp < kConvWarp0 + kConvWarps) {
-        // -------------------------------------------------------- converters
-        const int ct = tid - kConvWarp0 * 32;
-        constexpr int CT = kConvWarps * 32;
-        for (int i = 0; i < ng; ++i) {
-            const int s = i & 1;
-            const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+    } else if (warp < 4 || warp >= 4 + NEPI) {
+        // -------------------------------------------- converters: chunk k
+        const int ct = (warp < 4 ? warp - 2 : warp - 2 - NEPI) * 32 + lane;
+        constexpr int NCH = C::K / C::KC;  // 16-byte operand chunks per line
+        const unsigned long long tstart = MMS_CLOCK();
+        unsigned long long wstg = 0, wslot = 0;
+        for (int k = 0; k < nch; ++k) {
+            const int st = k % C::NST, sl = k % C::CR;
             // decisions stay warp-uniform: a failed wait in any lane stops the warp
-            bool ok = ptx::mbar_wait_bounded(&full_stg[s], ph, err) &&
-                      ptx::mbar_wait_bounded(&empty_conv[s], ph ^ 1u, err);
+            const unsigned long long t0 = MMS_CLOCK();
+            bool ok = ptx::mbar_wait_bounded(&full_stg[st], (uint32_t)(k / C::NST) & 1u, err);
+            const unsigned long long t1 = MMS_CLOCK();
+            ok = ok && ptx::mbar_wait_bounded(&empty_conv[sl], ((uint32_t)(k / C::CR) & 1u) ^ 1u, err);
+            wstg += t1 - t0;
+            wslot += MMS_CLOCK() - t1;
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 *abort_flag = 1;
                 break;
             }
-            const float *src = stg + (size_t)s * (C::STG_BYTES / 4);
-            unsigned char *dst = conv + (size_t)s * C::CONV_BYTES;
-            constexpr int NCH = C::K / C::KC;  // 16-byte chunks per line
-            for (int it = ct; it < C::NL * NCH; it += CT) {
-                const int kc = it % NCH, n = it / NCH;
-                const float *p = src + n * C::K + kc * C::KC;
-                unsigned char *d0 = dst + ((size_t)kc * C::NL + n) * 16;
+            const float *src = stg + (size_t)st * (C::STG_BYTES / 4);
+            const int line0 = sl * C::CHUNK_LINES;
+            const bool dup = sl < C::H;
+            // lines fastest: a warp converts one 16-byte chunk column of 32
+            // consecutive lines, so its stores are contiguous
+            for (int it = ct; it < C::CHUNK_LINES * NCH; it += CT) {
+                const int n = it % C::CHUNK_LINES, kc = it / C::CHUNK_LINES;
+                unsigned char *d0 = conv + ((size_t)kc * C::RING_LINES + line0 + n) * 16;
+                const float *line = src + n * C::K;
+                // 16-byte FP32 chunk j of this line (swizzled staging: chunk j ^ (n & 7))
+                auto chunk = [&](int j) {
+                    const int pj = C::SWZ ? (j ^ (n & 7)) : j;
+                    return *reinterpret_cast<const float4 *>(line + 4 * pj);
+                };
+                uint4 o[2];
                 if constexpr (C::BF) {
-                    const float4 q0 = *reinterpret_cast<const float4 *>(p);
-                    const float4 q1 = *reinterpret_cast<const float4 *>(p + 4);
+                    const float4 q0 = chunk(2 * kc), q1 = chunk(2 * kc + 1);
                     const float v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
                     uint32_t hi[4], lo[4];
 #pragma unroll
@@ -322,78 +430,89 @@ __global__ void __launch_bounds__(512, 1)
                         const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * h] - h0, v[2 * h + 1] - h1);
                         lo[h] = *reinterpret_cast<const uint32_t *>(&l);
                     }
-                    *reinterpret_cast<uint4 *>(d0) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    *reinterpret_cast<uint4 *>(d0 + C::PART_BYTES) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    o[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    o[1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                 } else {
-                    const float4 q = *reinterpret_cast<const float4 *>(p);
+                    const float4 q = chunk(kc);
                     const uint32_t h0 = tf32_rna(q.x), h1 = tf32_rna(q.y), h2 = tf32_rna(q.z), h3 = tf32_rna(q.w);
-                    *reinterpret_cast<uint4 *>(d0) = make_uint4(h0, h1, h2, h3);
+                    o[0] = make_uint4(h0, h1, h2, h3);
                     if constexpr (C::NPARTS == 2)
-                        *reinterpret_cast<uint4 *>(d0 + C::PART_BYTES) =
-                            make_uint4(tf32_rna(q.x - __uint_as_float(h0)), tf32_rna(q.y - __uint_as_float(h1)),
-                                       tf32_rna(q.z - __uint_as_float(h2)), tf32_rna(q.w - __uint_as_float(h3)));
+                        o[1] = make_uint4(tf32_rna(q.x - __uint_as_float(h0)), tf32_rna(q.y - __uint_as_float(h1)),
+                                          tf32_rna(q.z - __uint_as_float(h2)), tf32_rna(q.w - __uint_as_float(h3)));
+                }
+#pragma unroll
+                for (int part = 0; part < C::NPARTS; ++part) {
+                    *reinterpret_cast<uint4 *>(d0 + (size_t)part * C::PART_BYTES) = o[part];
+                    if (dup)
+                        *reinterpret_cast<uint4 *>(d0 + (size_t)part * C::PART_BYTES +
+                                                   (size_t)C::CR * C::CHUNK_LINES * 16) = o[part];
                 }
             }
             ptx::fence_proxy_async_smem();  // generic writes -> tensor-core reads
-            ptx::mbar_arrive(&full_conv[s]);
-            ptx::mbar_arrive(&empty_stg[s]);
+            ptx::mbar_arrive(&full_conv[sl]);
+            ptx::mbar_arrive(&empty_stg[st]);
+        }
+        if (ct == 0) {
+            MMS_TRACE_ADD(2, 0, wstg);
+            MMS_TRACE_ADD(2, 1, MMS_CLOCK() - tstart);
+            MMS_TRACE_ADD(2, 2, wslot);
         }
     } else {
         // ---------------------------------------------------------- epilogue
         // TMEM -> registers -> shared memory, the sum over the 2r+1 lanes
         // (dy, x) with rows shifted by dy, float4 stores.  Lane (dy, x) of
-        // column c feeds output row y = c - dy, so it is stored at [y][lane]
-        // and the reduction reads four x positions per load.
-        const int q = warp & 3, half = (warp - kEpiWarp0) >> 2;
+        // column c feeds output row y = c - dy, so it is stored at
+        // [y + 2R][lane] and the reduction reads four x positions per load.
+        const int eg = (warp - 4) >> 2, q = warp & 3;
         const int my_lane = q * 32 + lane;
         const int my_dyi = my_lane < C::LANES ? my_lane / C::TXO : 0;
-        const int et = tid - kEpiWarp0 * 32;
-        constexpr int ET = kEpiWarps * 32;
-        constexpr int XQ = C::TXO / 4;
-        int plane_ctr = 0;
-        for (int i = 0; i < ng; ++i) {
+        const int et = (warp & 3) * 32 + lane;  // thread index within the group
+        float *gbuf = dsm + eg * C::DSM_GROUP;
+        float *st_base = gbuf + (2 * R - my_dyi) * C::DSM_LD + my_lane;
+        volatile int *fail = epi_fail + 2 * eg;
+        bool stop = false;
+        const unsigned long long tstart = MMS_CLOCK();
+        unsigned long long wacc = 0, wbar = 0;
+        for (int i = 0; i < ng && !stop; ++i) {
             const int s = i & 1;
-            // the epilogue warps share named barriers: they stop together
-            if (!ptx::mbar_wait_bounded(&full_d[s], (uint32_t)(i >> 1) & 1u, err)) *epi_fail = 1;
-            named_sync(1, ET);
-            if (et == 0) *epi_stop = (*epi_fail || *abort_flag) ? 1 : 0;
-            named_sync(1, ET);
-            if (*epi_stop) {
-                *abort_flag = 1;
-                break;
-            }
+            const unsigned long long t0 = MMS_CLOCK();
+            if (!ptx::mbar_wait_bounded(&full_d[s], (uint32_t)(i >> 1) & 1u, err)) fail[s] = 1;
+            wacc += MMS_CLOCK() - t0;
             tc::fence_after_sync();
-            int x0, y0, z0;
-            group_origin(i, x0, y0, z0);
-            for (int zl = 0; zl < C::NZ; ++zl, ++plane_ctr) {
-                float *dbuf = dsm + (plane_ctr & 1) * C::DSM_PLANE;
-                uint32_t r[16];
-                tc::tmem_ld_32x32b_x16(tbase + ((uint32_t)(q * 32) << 16) +
-                                           (uint32_t)(s * C::N + zl * C::YP + half * 16),
-                                       r);
+            int x0, y0, zt;
+            tile_origin(i / G, x0, y0, zt);
+            const int z0 = zt + (i % G) * C::NZ;
+            for (int zl = eg; zl < C::NZ; zl += C::EG) {
+                uint32_t r[32];
+                tc::tmem_ld_32x32b_x32(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * C::N + zl * C::YP), r);
                 tc::tmem_wait_ld();
-                if (my_lane < C::LANES) {
-                    float *dst = dbuf + my_lane;
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const int y = half * 16 + c - my_dyi;
-                        if (y >= 0 && y < C::TY) dst[y * C::DSM_LD] = __uint_as_float(r[c]);
-                    }
-                }
-                if (zl == C::NZ - 1) {
-                    // all TMEM reads of this accumulator are done: hand it back
+                if (zl + C::EG >= C::NZ) {
+                    // this warp's last read of the accumulator: hand it back
                     tc::fence_before_sync();
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&empty_d[s]);
                 }
-                named_sync(1, ET);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) st_base[c * C::DSM_LD] = __uint_as_float(r[c]);
+                const unsigned long long tb = MMS_CLOCK();
+                named_sync(1 + eg, 128);
+                wbar += MMS_CLOCK() - tb;
+                // a timed-out wait (any thread of the group) was recorded before
+                // the group's first barrier, in the flag of this accumulator
+                // parity, which no thread writes again before all have read it:
+                // the four warps take the same decision and stop together
+                if (zl == eg && fail[s]) {
+                    stop = true;
+                    *abort_flag = 1;
+                    break;
+                }
                 const int z = z0 + zl;
                 if (z < a.nz) {
-                    for (int it = et; it < C::TY * XQ; it += ET) {
-                        const int xq = it % XQ, yl = it / XQ;
+                    for (int it = et; it < C::TY * C::XQP; it += 128) {
+                        const int xq = it % C::XQP, yl = it / C::XQP;
                         const int y = y0 + yl, x = x0 + 4 * xq;
-                        if (y >= a.ny || x >= a.nx) continue;
-                        const float *src = dbuf + yl * C::DSM_LD + 4 * xq;
+                        if (xq >= C::XQ || y >= a.ny || x >= a.nx) continue;
+                        const float *src = gbuf + (2 * R + yl) * C::DSM_LD + 4 * xq;
                         float4 acc = *reinterpret_cast<const float4 *>(src);
 #pragma unroll
                         for (int dyi = 1; dyi < W; ++dyi) {
@@ -409,7 +528,13 @@ __global__ void __launch_bounds__(512, 1)
                         }
                     }
                 }
+                named_sync(1 + eg, 128);  // the tile is free for the next plane
             }
+        }
+        if (warp == 4 && lane == 0) {
+            MMS_TRACE_ADD(3, 0, wacc);
+            MMS_TRACE_ADD(3, 1, MMS_CLOCK() - tstart);
+            MMS_TRACE_ADD(3, 2, wbar);
         }
     }
 
@@ -486,20 +611,21 @@ cudaError_t launch_prec(const Sweep &s, const CUtensorMap &map, int v)
 }
 
 template <int PREC>
-void box_dims(int r, int *bx, int *by, int *bz)
+void box_dims(int r, int *bx, int *by, int *bz, int *swz)
 {
 #define MMS_DIMS(RR)                                  \
     case RR:                                          \
         *bx = Cfg<RR, PREC>::K;                       \
         *by = Cfg<RR, PREC>::YP;                      \
-        *bz = Cfg<RR, PREC>::ZS;                      \
+        *bz = Cfg<RR, PREC>::NZ;                      \
+        *swz = Cfg<RR, PREC>::SWZ ? 1 : 0;            \
         return;
     switch (r) {
         MMS_DIMS(1)
         MMS_DIMS(2)
         MMS_DIMS(3)
         MMS_DIMS(4)
-        default: *bx = *by = *bz = 0;
+        default: *bx = *by = *bz = *swz = 0;
     }
 #undef MMS_DIMS
 }
@@ -541,15 +667,15 @@ int band_tc_supported(int shape, int r, int path)
 
 int band_tc_variants(int shape, int r, int path) { return band_tc_supported(shape, r, path) ? kNumVariants : 0; }
 
-void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz)
+void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz, int *swz)
 {
     (void)shape;
     (void)v;
     switch (prec_of(path)) {
-        case P_TF32: box_dims<P_TF32>(r, bx, by, bz); return;
-        case P_3XTF32: box_dims<P_3XTF32>(r, bx, by, bz); return;
-        case P_BF16X3: box_dims<P_BF16X3>(r, bx, by, bz); return;
-        default: *bx = *by = *bz = 0;
+        case P_TF32: box_dims<P_TF32>(r, bx, by, bz, swz); return;
+        case P_3XTF32: box_dims<P_3XTF32>(r, bx, by, bz, swz); return;
+        case P_BF16X3: box_dims<P_BF16X3>(r, bx, by, bz, swz); return;
+        default: *bx = *by = *bz = *swz = 0;
     }
 }
 

@@ -54,7 +54,7 @@ void box_cc_box(int r, int v, int *bx, int *by);
 // Tensor-core banded sweeps (band_tc.cu).
 int band_tc_supported(int shape, int r, int path);
 cudaError_t launch_band_tc(const Sweep &s, int path, const CUtensorMap &tmap, int variant);
-void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz);
+void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz, int *swz);
 int band_tc_variants(int shape, int r, int path);
 
 // Error word helpers (wave.cu owns the symbol).
@@ -63,7 +63,7 @@ unsigned *device_error_word();
 // Encodes a 3D FP32 tensor map over a padded grid (x extent X, pitches in
 // elements) with box (bx, by, bz); returns false when the driver refuses.
 bool encode_tmap_3d(CUtensorMap *map, const float *base, int64_t X, int64_t Y, int64_t Z,
-                    int64_t py, int64_t pz, int bx, int by, int bz);
+                    int64_t py, int64_t pz, int bx, int by, int bz, bool swizzle128 = false);
 // The same over nw stacked grids `pw` elements apart, box depth 1 in w.
 bool encode_tmap_4d(CUtensorMap *map, const float *base, int64_t X, int64_t Y, int64_t Z,
                     int64_t W, int64_t py, int64_t pz, int64_t pw, int bx, int by, int bz);
