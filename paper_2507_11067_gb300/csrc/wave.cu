@@ -46,19 +46,49 @@ __device__ __forceinline__ float sponge(int i, int n, int w, float a)
     return 1.f;
 }
 
+// Interior tile (TX x TY) of m or a^{n-1} that completes with output plane
+// zo: TMA box x start rounded down to a 16-byte boundary, OFF columns in.
+template <int R, int TX>
+struct Interior {
+    static constexpr int OFF = R % 4;                   // column of output x0 inside the box
+    static constexpr int BXI = OFF == 0 ? TX : TX + 4;  // box width (16-byte multiple)
+};
+
+// Ring stage s: [a^n plane + halo | m tile | a^{n-1} tile | a^n tile].  The
+// interior tiles of output plane zo = j - 2R (m, a^{n-1} and the centre
+// values of a^n) ride in the stage of input plane j, the plane that completes
+// zo, so every operand arrives asynchronously and no register queue of
+// centre values is needed.
+template <int R, int TX, int TY, int PY, int S>
+struct FwdGeom {
+    using G = Geom<R, TX, TY, PY, S>;
+    using I = Interior<R, TX>;
+    static constexpr int MT = I::BXI * TY;                  // floats of one interior tile
+    // sub-tile offsets rounded to 32 floats: every TMA destination is 128-byte aligned
+    static constexpr int OFF_M = (G::PLANE + 31) & ~31;
+    static constexpr int OFF_P = OFF_M + ((MT + 31) & ~31);
+    static constexpr int OFF_C = OFF_P + ((MT + 31) & ~31);
+    static constexpr int STAGE = OFF_C + ((MT + 31) & ~31);
+    static constexpr size_t SMEM = 128 + (size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16;
+};
+
 template <int R, int TX, int TY, int PY, int S>
 __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
-    wave_fwd_kernel(const __grid_constant__ CUtensorMap tcur, const __grid_constant__ StarCoef cf,
-                    const __grid_constant__ WaveGeo geo, const float *__restrict__ m,
-                    float *__restrict__ pprev, const float *__restrict__ amp,
-                    float *__restrict__ rec, int tz, int nzc, int vec, unsigned *err)
+    wave_fwd_kernel(const __grid_constant__ CUtensorMap tcur, const __grid_constant__ CUtensorMap tm,
+                    const __grid_constant__ CUtensorMap tprev, const __grid_constant__ CUtensorMap tctr,
+                    const __grid_constant__ StarCoef cf,
+                    const __grid_constant__ WaveGeo geo, float *__restrict__ pprev,
+                    const float *__restrict__ amp, float *__restrict__ rec, int tz, int nzc, int vec,
+                    unsigned *err)
 {
     using G = Geom<R, TX, TY, PY, S>;
+    using F = FwdGeom<R, TX, TY, PY, S>;
+    using I = Interior<R, TX>;
     constexpr int W = G::W;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_align128(smem_raw);
-    float *planes = reinterpret_cast<float *>(smem);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * G::STAGE * sizeof(float));
+    float *stages = reinterpret_cast<float *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * F::STAGE * sizeof(float));
     int &abort_flag = *reinterpret_cast<int *>(full + S);
 
     const int tid = threadIdx.x;
@@ -71,56 +101,71 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     const int gx = x0 + 4 * tx;
     const int sx = geo.src[sh][0], sy = geo.src[sh][1], sz = geo.src[sh][2];
 
+    auto issue = [&](int j, int s) {
+        float *st = stages + (size_t)s * F::STAGE;
+        const bool inner = j >= 2 * R;  // this plane completes output plane j - 2R
+        ptx::mbar_arrive_expect_tx(&full[s], (G::PLANE + (inner ? 3 * F::MT : 0)) * sizeof(float));
+        ptx::tma_load_4d(st, &tcur, x0, y0, zb + j, sh, &full[s]);
+        if (inner) {
+            const int zp = zb + j - R;  // padded plane of output zo = j - 2R
+            const int xs = x0 + (R & ~3);
+            ptx::tma_load_3d(st + F::OFF_M, &tm, xs, y0 + R, zp, &full[s]);
+            ptx::tma_load_4d(st + F::OFF_P, &tprev, xs, y0 + R, zp, sh, &full[s]);
+            ptx::tma_load_4d(st + F::OFF_C, &tctr, xs, y0 + R, zp, sh, &full[s]);
+        }
+    };
     if (tid == 0) {
         ptx::prefetch_tmap(&tcur);
+        ptx::prefetch_tmap(&tm);
+        ptx::prefetch_tmap(&tprev);
+        ptx::prefetch_tmap(&tctr);
 #pragma unroll
         for (int s = 0; s < S; ++s) ptx::mbar_init(&full[s], 1);
         ptx::fence_mbar_init();
         abort_flag = 0;
     }
     __syncthreads();
-    if (tid == 0) {
-        for (int j = 0; j < S && j < P; ++j) {
-            ptx::mbar_arrive_expect_tx(&full[j], G::PLANE * sizeof(float));
-            ptx::tma_load_4d(planes + j * G::STAGE, &tcur, x0, y0, zb + j, sh, &full[j]);
-        }
-    }
+    if (tid == 0)
+        for (int j = 0; j < S && j < P; ++j) issue(j, j);
     float gxs[4], gys[PY];
 #pragma unroll
     for (int k = 0; k < 4; ++k) gxs[k] = sponge(gx + k, geo.nx, geo.sponge_w, geo.sponge_a);
 #pragma unroll
     for (int i = 0; i < PY; ++i) gys[i] = sponge(y0 + ry0 + i, geo.ny, geo.sponge_w, geo.sponge_a);
 
-    float acc[W][PY][4], ctr[R + 1][PY][4];
+    float acc[W][PY][4];
 #pragma unroll
     for (int kk = 0; kk < W; ++kk)
 #pragma unroll
         for (int i = 0; i < PY; ++i)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[kk][i][k] = 0.f;
-#pragma unroll
-    for (int kk = 0; kk <= R; ++kk)
-#pragma unroll
-        for (int i = 0; i < PY; ++i)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) ctr[kk][i][k] = 0.f;
 
     const float samp = amp[sh];
     const int64_t shot_off = (int64_t)sh * geo.ss;
     for (int j = 0; j < P; ++j) {
         const int s = j % S;
+        const float *st = stages + (size_t)s * F::STAGE;
+        const int zo = j - 2 * R;  // output plane completed by plane j
+        float mv[PY][4], pv[PY][4], cv[PY][4];
         if (ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err)) {
-            star_plane<R, PY, G::BX, G::NV>(planes + s * G::STAGE, cf, acc, ctr[R], tx, ry0);
+            float unused[PY][4];
+            star_plane<R, PY, G::BX, G::NV>(st, cf, acc, unused, tx, ry0);
+            if (zo >= 0) {
+#pragma unroll
+                for (int i = 0; i < PY; ++i) {
+                    // interior tiles: row ry0+i, columns 4tx+OFF .. +3
+                    load_center<I::OFF>(st + F::OFF_M + (ry0 + i) * I::BXI + 4 * tx, mv[i]);
+                    load_center<I::OFF>(st + F::OFF_P + (ry0 + i) * I::BXI + 4 * tx, pv[i]);
+                    load_center<I::OFF>(st + F::OFF_C + (ry0 + i) * I::BXI + 4 * tx, cv[i]);
+                }
+            }
         } else {
             abort_flag = 1;
         }
         __syncthreads();
         if (abort_flag) return;
-        if (tid == 0 && j + S < P) {
-            ptx::mbar_arrive_expect_tx(&full[s], G::PLANE * sizeof(float));
-            ptx::tma_load_4d(planes + s * G::STAGE, &tcur, x0, y0, zb + j + S, sh, &full[s]);
-        }
-        const int zo = j - 2 * R;
+        if (tid == 0 && j + S < P) issue(j + S, s);
         if (zo >= 0) {
             const int z = zb + zo;
             const float gzv = sponge(z, geo.nz, geo.sponge_w, geo.sponge_a);
@@ -130,29 +175,15 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                 if (y >= geo.ny || gx >= geo.nx) continue;
                 const int64_t mp = (int64_t)(z + R) * geo.pz + (int64_t)(y + R) * geo.py + (gx + R);
                 float *pp = pprev + shot_off + mp;
-                const float *mm = m + mp;
-                float mv[4], pv[4], res[4];
-                const bool full4 = vec && gx + 3 < geo.nx;
-                if (full4) {
-                    const float4 a = *reinterpret_cast<const float4 *>(mm);
-                    const float4 b = *reinterpret_cast<const float4 *>(pp);
-                    mv[0] = a.x; mv[1] = a.y; mv[2] = a.z; mv[3] = a.w;
-                    pv[0] = b.x; pv[1] = b.y; pv[2] = b.z; pv[3] = b.w;
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        mv[k] = gx + k < geo.nx ? mm[k] : 0.f;
-                        pv[k] = gx + k < geo.nx ? pp[k] : 0.f;
-                    }
-                }
+                float res[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float g = gxs[k] * gys[i] * gzv;
-                    float v = 2.f * ctr[0][i][k] + mv[k] * acc[0][i][k] - g * pv[k];
+                    float v = 2.f * cv[i][k] + mv[i][k] * acc[0][i][k] - g * pv[i][k];
                     if (gx + k == sx && y == sy && z == sz) v += samp;
                     res[k] = g * v;
                 }
-                if (full4) {
+                if (vec && gx + 3 < geo.nx) {
                     *reinterpret_cast<float4 *>(pp) = make_float4(res[0], res[1], res[2], res[3]);
                 } else {
 #pragma unroll
@@ -177,12 +208,6 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
         for (int i = 0; i < PY; ++i)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[W - 1][i][k] = 0.f;
-#pragma unroll
-        for (int kk = 0; kk < R; ++kk)
-#pragma unroll
-            for (int i = 0; i < PY; ++i)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) ctr[kk][i][k] = ctr[kk + 1][i][k];
     }
 }
 
@@ -362,7 +387,7 @@ __global__ void dot_kernel(const float *__restrict__ a, const float *__restrict_
     }
 }
 
-constexpr int kFwdTX = 64, kFwdTY = 16, kFwdPY = 2, kFwdS = 4, kFwdTZ = 64;
+constexpr int kFwdTX = 64, kFwdTY = 16, kFwdPY = 1, kFwdS = 3, kFwdTZ = 128;
 constexpr int kAdjTX = 64, kAdjTY = 16, kAdjS = 2, kAdjTZ = 64;
 
 template <int R>
@@ -370,19 +395,23 @@ cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
                   float *p_prev, const float *amp, float *rec, cudaStream_t st)
 {
     using G = Geom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
-    CUtensorMap map;
-    if (!encode_tmap_4d(&map, p_cur, g.nx + 2 * R, g.ny + 2 * R, g.nz + 2 * R, g.nshots, g.py, g.pz, g.ss,
-                        G::BX, G::BY, 1))
+    using F = FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
+    using I = Interior<R, kFwdTX>;
+    const int X = g.nx + 2 * R, Y = g.ny + 2 * R, Z = g.nz + 2 * R;
+    CUtensorMap mcur, mm, mprev, mctr;
+    if (!encode_tmap_4d(&mcur, p_cur, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1) ||
+        !encode_tmap_3d(&mm, m, X, Y, Z, g.py, g.pz, I::BXI, kFwdTY, 1) ||
+        !encode_tmap_4d(&mprev, p_prev, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kFwdTY, 1) ||
+        !encode_tmap_4d(&mctr, p_cur, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kFwdTY, 1))
         return cudaErrorInvalidValue;
     auto kern = wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
     if (e != cudaSuccess) return e;
     const int nzc = (g.nz + kFwdTZ - 1) / kFwdTZ;
     const dim3 grid((g.nx + kFwdTX - 1) / kFwdTX, (g.ny + kFwdTY - 1) / kFwdTY, nzc * g.nshots);
     const int vec = (R % 4 == 0) && g.py % 4 == 0 && g.pz % 4 == 0 && g.ss % 4 == 0 &&
-                    reinterpret_cast<uintptr_t>(m) % 16 == 0 &&
                     reinterpret_cast<uintptr_t>(p_prev) % 16 == 0;
-    kern<<<grid, G::NT, G::SMEM, st>>>(map, cf, g, m, p_prev, amp, rec, kFwdTZ, nzc, vec,
+    kern<<<grid, G::NT, F::SMEM, st>>>(mcur, mm, mprev, mctr, cf, g, p_prev, amp, rec, kFwdTZ, nzc, vec,
                                        device_error_word());
     return cudaGetLastError();
 }
