@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
         zt = zc * G * C::NZ;
     };
     // Bounded wait for the single-thread roles; on expiry raise the abort flag.
-    unsigned long long waited = 0;  // role trace only
+    [[maybe_unused]] unsigned long long waited = 0;  // role trace only
     auto wait = [&](uint64_t *b, uint32_t parity) -> bool {
         if (*abort_flag) return false;
         const unsigned long long t0 = MMS_CLOCK();
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
     if (warp == 0) {
         // ------------------------------------------- TMA producer: chunk k
         if (lane == 0) {
-            const unsigned long long tstart = MMS_CLOCK();
+            [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
             ptx::prefetch_tmap(&tmap);
             for (int k = 0; k < nch; ++k) {
                 const int st = k % C::NST;
@@ -330,8 +330,8 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const unsigned long long tstart = MMS_CLOCK();
-            unsigned long long wconv = 0, wacc = 0, tissue = 0;
+            [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
+            [[maybe_unused]] unsigned long long wconv = 0, wacc = 0, tissue = 0;
             for (int i = 0; i < ng; ++i) {
                 const int s = i & 1, g = i % G;
                 const int kg = (i / G) * CPT + g;  // first chunk of this group's window
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
                 w0 = waited;
                 if (!ok || !wait(&empty_d[s], ((uint32_t)(i >> 1) & 1u) ^ 1u)) break;
                 wacc += waited - w0;
-                const unsigned long long ti = MMS_CLOCK();
+                [[maybe_unused]] const unsigned long long ti = MMS_CLOCK();
                 tc::fence_after_sync();
                 const uint32_t dcol = tbase + (uint32_t)(s * C::N);
                 const uint32_t cbase = ptx::smem_u32(conv) + (uint32_t)((kg % C::CR) * C::CHUNK_LINES * 16);
@@ -386,8 +386,8 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
         // -------------------------------------------- converters: chunk k
         const int ct = (warp < 4 ? warp - 2 : warp - 2 - NEPI) * 32 + lane;
         constexpr int NCH = C::K / C::KC;  // 16-byte operand chunks per line
-        const unsigned long long tstart = MMS_CLOCK();
-        unsigned long long wstg = 0, wslot = 0;
+        [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
+        [[maybe_unused]] unsigned long long wstg = 0, wslot = 0;
         for (int k = 0; k < nch; ++k) {
             const int st = k % C::NST, sl = k % C::CR;
             // decisions stay warp-uniform: a failed wait in any lane stops the warp
@@ -471,8 +471,8 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
         float *st_base = gbuf + (2 * R - my_dyi) * C::DSM_LD + my_lane;
         volatile int *fail = epi_fail + 2 * eg;
         bool stop = false;
-        const unsigned long long tstart = MMS_CLOCK();
-        unsigned long long wacc = 0, wbar = 0;
+        [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
+        [[maybe_unused]] unsigned long long wacc = 0, wbar = 0;
         for (int i = 0; i < ng && !stop; ++i) {
             const int s = i & 1;
             const unsigned long long t0 = MMS_CLOCK();
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
                 }
 #pragma unroll
                 for (int c = 0; c < 32; ++c) st_base[c * C::DSM_LD] = __uint_as_float(r[c]);
-                const unsigned long long tb = MMS_CLOCK();
+                [[maybe_unused]] const unsigned long long tb = MMS_CLOCK();
                 named_sync(1 + eg, 128);
                 wbar += MMS_CLOCK() - tb;
                 // a timed-out wait (any thread of the group) was recorded before

@@ -159,11 +159,11 @@ struct Variant { int tx, ty, py, s, tz; };
 // Tile variants (TX, TY, PY, stages, TZ) of the CUDA-core sweeps.
 constexpr Variant kStarVariants[] = {
     {64, 32, 2, 4, 128}, {64, 16, 2, 4, 128}, {128, 16, 2, 4, 128}, {64, 32, 4, 3, 128},
-    {64, 32, 2, 4, 64},  {128, 32, 2, 3, 64},
+    {64, 32, 2, 4, 64},  {128, 32, 2, 3, 64}, {64, 16, 1, 3, 128}, {64, 16, 1, 4, 256},
 };
 constexpr Variant kBoxVariants[] = {
     {64, 16, 2, 3, 64}, {64, 32, 2, 3, 64}, {32, 16, 2, 3, 64}, {64, 16, 4, 3, 64},
-    {64, 8, 2, 3, 128}, {128, 16, 2, 3, 32},
+    {64, 8, 2, 3, 128}, {128, 16, 2, 3, 32}, {64, 16, 1, 3, 128}, {64, 8, 1, 3, 128},
 };
 constexpr int kNumStar = sizeof(kStarVariants) / sizeof(Variant);
 constexpr int kNumBox = sizeof(kBoxVariants) / sizeof(Variant);
@@ -207,6 +207,8 @@ cudaError_t dispatch_variant(const Sweep &sw, const CUtensorMap &tmap, const Coe
         MMS_CASE(3)
         MMS_CASE(4)
         MMS_CASE(5)
+        MMS_CASE(6)
+        MMS_CASE(7)
         default: return cudaErrorInvalidValue;
     }
 #undef MMS_CASE

@@ -211,25 +211,45 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     }
 }
 
-// Adjoint step.  Ring stage s holds three planes: lam^{n+1}, m, a^n.
+// Adjoint step.  Ring stage s holds the planes lam^{n+1}, m, a^n (with halo)
+// of input plane j and the interior tiles lam^{n+2} and lam^{n+1} of the
+// output plane zo = j - 2R that plane j completes.
 template <int R, int TX, int TY, int S>
-__global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
+struct AdjGeom {
+    using G = Geom<R, TX, TY, 1, S>;
+    using I = Interior<R, TX>;
+    static constexpr int PL = (G::PLANE + 31) & ~31;   // padded plane stride
+    static constexpr int MT = (I::BXI * TY + 31) & ~31;
+    static constexpr int OFF_L2 = 3 * PL, OFF_L1 = OFF_L2 + MT;
+    static constexpr int STAGE = OFF_L1 + MT;
+    // [ring | q plane | sponge tables | barriers | abort flag]
+    static constexpr size_t OFF_Q = (size_t)S * STAGE;
+    static constexpr size_t OFF_GX = OFF_Q + PL;
+    static constexpr size_t OFF_GY = OFF_GX + ((G::BX + 3) & ~3);
+    static constexpr size_t OFF_BAR = OFF_GY + ((G::BY + 3) & ~3);
+    static constexpr size_t SMEM = 128 + OFF_BAR * 4 + S * 8 + 16;
+};
+
+template <int R, int TX, int TY, int S>
+__global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
     wave_adj_kernel(const __grid_constant__ CUtensorMap tlam, const __grid_constant__ CUtensorMap tm,
-                    const __grid_constant__ CUtensorMap ta, const __grid_constant__ StarCoef cf,
+                    const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tl2,
+                    const __grid_constant__ CUtensorMap tl1, const __grid_constant__ StarCoef cf,
                     const __grid_constant__ WaveGeo geo, float *__restrict__ lprev,
                     const float *__restrict__ resid, double *__restrict__ grad, int has_a, int tz,
                     int nzc, unsigned *err)
 {
     constexpr int PY = 1;
     using G = Geom<R, TX, TY, PY, S>;
+    using A = AdjGeom<R, TX, TY, S>;
+    using I = Interior<R, TX>;
     constexpr int W = G::W;
-    constexpr int NPL = 3;  // planes per stage
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *planes = reinterpret_cast<float *>(smem_align128(smem_raw));
-    float *qbuf = planes + (size_t)S * NPL * G::STAGE;
-    float *gxt = qbuf + G::STAGE;
-    float *gyt = gxt + G::BX;
-    uint64_t *full = reinterpret_cast<uint64_t *>(gyt + ((G::BY + 3) & ~3));
+    float *base = reinterpret_cast<float *>(smem_align128(smem_raw));
+    float *qbuf = base + A::OFF_Q;
+    float *gxt = base + A::OFF_GX;
+    float *gyt = base + A::OFF_GY;
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + A::OFF_BAR);
     int &abort_flag = *reinterpret_cast<int *>(full + S);
 
     const int tid = threadIdx.x;
@@ -240,13 +260,15 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
     const int P = nzt + 2 * R;
     const int ry0 = ty * PY;
     const int gx = x0 + 4 * tx;
-    const uint32_t stage_bytes = (has_a ? 3u : 2u) * G::PLANE * sizeof(float);
+    const uint32_t plane_bytes = (has_a ? 3u : 2u) * G::PLANE * sizeof(float);
 
     for (int c = tid; c < G::BX; c += G::NT) gxt[c] = sponge(x0 + c - R, geo.nx, geo.sponge_w, geo.sponge_a);
     for (int rr = tid; rr < G::BY; rr += G::NT) gyt[rr] = sponge(y0 + rr - R, geo.ny, geo.sponge_w, geo.sponge_a);
     if (tid == 0) {
         ptx::prefetch_tmap(&tlam);
         ptx::prefetch_tmap(&tm);
+        ptx::prefetch_tmap(&tl2);
+        ptx::prefetch_tmap(&tl1);
         if (has_a) ptx::prefetch_tmap(&ta);
 #pragma unroll
         for (int s = 0; s < S; ++s) ptx::mbar_init(&full[s], 1);
@@ -255,24 +277,27 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
     }
     __syncthreads();
     auto issue = [&](int j, int s) {
-        float *st = planes + (size_t)s * NPL * G::STAGE;
-        ptx::mbar_arrive_expect_tx(&full[s], stage_bytes);
+        float *st = base + (size_t)s * A::STAGE;
+        const bool inner = j >= 2 * R;
+        ptx::mbar_arrive_expect_tx(&full[s], plane_bytes + (inner ? 2u * I::BXI * TY * 4u : 0u));
         ptx::tma_load_4d(st, &tlam, x0, y0, zb + j, sh, &full[s]);
-        ptx::tma_load_3d(st + G::STAGE, &tm, x0, y0, zb + j, &full[s]);
-        if (has_a) ptx::tma_load_4d(st + 2 * G::STAGE, &ta, x0, y0, zb + j, sh, &full[s]);
+        ptx::tma_load_3d(st + A::PL, &tm, x0, y0, zb + j, &full[s]);
+        if (has_a) ptx::tma_load_4d(st + 2 * A::PL, &ta, x0, y0, zb + j, sh, &full[s]);
+        if (inner) {
+            const int zp = zb + j - R;
+            const int xs = x0 + (R & ~3);
+            ptx::tma_load_4d(st + A::OFF_L2, &tl2, xs, y0 + R, zp, sh, &full[s]);
+            ptx::tma_load_4d(st + A::OFF_L1, &tl1, xs, y0 + R, zp, sh, &full[s]);
+        }
     };
     if (tid == 0)
         for (int j = 0; j < S && j < P; ++j) issue(j, j);
 
-    float accq[W][PY][4], acca[W][PY][4], ctr[R + 1][PY][4];
+    float accq[W][PY][4], acca[W][PY][4];
 #pragma unroll
     for (int kk = 0; kk < W; ++kk)
 #pragma unroll
         for (int k = 0; k < 4; ++k) accq[kk][0][k] = acca[kk][0][k] = 0.f;
-#pragma unroll
-    for (int kk = 0; kk <= R; ++kk)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) ctr[kk][0][k] = 0.f;
     float gxs[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) gxs[k] = gxt[4 * tx + R + k];
@@ -281,32 +306,33 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
 
     for (int j = 0; j < P; ++j) {
         const int s = j % S;
-        const float *st = planes + (size_t)s * NPL * G::STAGE;
+        const float *st = base + (size_t)s * A::STAGE;
+        const int zo = j - 2 * R;
         const bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err);
         if (ok) {
             // q = m * g * lam^{n+1} over the whole staged plane
             const float gzp = sponge(zb + j - R, geo.nz, geo.sponge_w, geo.sponge_a);
             for (int e = tid; e < G::PLANE; e += G::NT) {
                 const int c = e % G::BX, rr = e / G::BX;
-                qbuf[e] = st[G::STAGE + e] * (gxt[c] * gyt[rr] * gzp) * st[e];
+                qbuf[e] = st[A::PL + e] * (gxt[c] * gyt[rr] * gzp) * st[e];
             }
         } else {
             abort_flag = 1;
         }
         __syncthreads();
         if (abort_flag) return;
+        float l2v[4], l1v[4];
         {
-            float dummy[PY][4];
-            star_plane<R, PY, G::BX, G::NV>(qbuf, cf, accq, dummy, tx, ry0);
-            if (has_a) star_plane<R, PY, G::BX, G::NV>(st + 2 * G::STAGE, cf, acca, dummy, tx, ry0);
-            float lc[4];
-            load_center<R>(st + (ry0 + R) * G::BX + 4 * tx, lc);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) ctr[R][0][k] = lc[k];
+            float unused[PY][4];
+            star_plane<R, PY, G::BX, G::NV>(qbuf, cf, accq, unused, tx, ry0);
+            if (has_a) star_plane<R, PY, G::BX, G::NV>(st + 2 * A::PL, cf, acca, unused, tx, ry0);
+            if (zo >= 0) {
+                load_center<I::OFF>(st + A::OFF_L2 + ry0 * I::BXI + 4 * tx, l2v);
+                load_center<I::OFF>(st + A::OFF_L1 + ry0 * I::BXI + 4 * tx, l1v);
+            }
         }
         __syncthreads();
         if (tid == 0 && j + S < P) issue(j + S, s);
-        const int zo = j - 2 * R;
         if (zo >= 0) {
             const int z = zb + zo;
             const int y = y0 + ry0;
@@ -315,15 +341,15 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
                 const int64_t mp = (int64_t)(z + R) * geo.pz + (int64_t)(y + R) * geo.py + (gx + R);
                 float *lp = lprev + shot_off + mp;
                 const int64_t gi = ((int64_t)z * geo.ny + y) * geo.nx + gx;
+                const bool at_rec = resid && z == geo.rec_z;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     if (gx + k >= geo.nx) break;
                     const float g = gxs[k] * gys0 * gzv;
-                    const float l1 = ctr[0][0][k];
-                    float v = 2.f * g * l1 + accq[0][0][k] - g * g * lp[k];
-                    if (resid && z == geo.rec_z) v += resid[((int64_t)sh * geo.ny + y) * geo.nx + gx + k];
+                    float v = 2.f * g * l1v[k] + accq[0][0][k] - g * g * l2v[k];
+                    if (at_rec) v += resid[((int64_t)sh * geo.ny + y) * geo.nx + gx + k];
                     lp[k] = v;
-                    if (has_a) atomicAdd(grad + gi + k, (double)g * (double)l1 * (double)acca[0][0][k]);
+                    if (has_a) atomicAdd(grad + gi + k, (double)g * (double)l1v[k] * (double)acca[0][0][k]);
                 }
             }
         }
@@ -336,10 +362,6 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT)
             }
 #pragma unroll
         for (int k = 0; k < 4; ++k) accq[W - 1][0][k] = acca[W - 1][0][k] = 0.f;
-#pragma unroll
-        for (int kk = 0; kk < R; ++kk)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) ctr[kk][0][k] = ctr[kk + 1][0][k];
     }
 }
 
@@ -388,7 +410,7 @@ __global__ void dot_kernel(const float *__restrict__ a, const float *__restrict_
 }
 
 constexpr int kFwdTX = 64, kFwdTY = 16, kFwdPY = 1, kFwdS = 3, kFwdTZ = 128;
-constexpr int kAdjTX = 64, kAdjTY = 16, kAdjS = 2, kAdjTZ = 64;
+constexpr int kAdjTX = 64, kAdjTY = 16, kAdjS = 2, kAdjTZ = 128;
 
 template <int R>
 cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const float *p_cur,
@@ -421,10 +443,14 @@ cudaError_t adj_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
                   float *lam_prev, const float *resid, const float *a_n, double *grad, cudaStream_t st)
 {
     using G = Geom<R, kAdjTX, kAdjTY, 1, kAdjS>;
-    CUtensorMap ml, mm, ma;
+    using A = AdjGeom<R, kAdjTX, kAdjTY, kAdjS>;
+    using I = Interior<R, kAdjTX>;
+    CUtensorMap ml, mm, ma, m2, m1;
     const int X = g.nx + 2 * R, Y = g.ny + 2 * R, Z = g.nz + 2 * R;
     if (!encode_tmap_4d(&ml, lam_cur, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1) ||
-        !encode_tmap_3d(&mm, m, X, Y, Z, g.py, g.pz, G::BX, G::BY, 1))
+        !encode_tmap_3d(&mm, m, X, Y, Z, g.py, g.pz, G::BX, G::BY, 1) ||
+        !encode_tmap_4d(&m2, lam_prev, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kAdjTY, 1) ||
+        !encode_tmap_4d(&m1, lam_cur, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kAdjTY, 1))
         return cudaErrorInvalidValue;
     if (a_n) {
         if (!encode_tmap_4d(&ma, a_n, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1))
@@ -433,14 +459,12 @@ cudaError_t adj_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
         ma = ml;
     }
     auto kern = wave_adj_kernel<R, kAdjTX, kAdjTY, kAdjS>;
-    const size_t smem = 128 + (size_t)kAdjS * 3 * G::STAGE * 4 + (size_t)G::STAGE * 4 + G::BX * 4 +
-                        ((G::BY + 3) & ~3) * 4 + kAdjS * 8 + 16;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A::SMEM);
     if (e != cudaSuccess) return e;
     const int nzc = (g.nz + kAdjTZ - 1) / kAdjTZ;
     const dim3 grid((g.nx + kAdjTX - 1) / kAdjTX, (g.ny + kAdjTY - 1) / kAdjTY, nzc * g.nshots);
-    kern<<<grid, G::NT, smem, st>>>(ml, mm, ma, cf, g, lam_prev, resid, grad, a_n ? 1 : 0, kAdjTZ, nzc,
-                                    device_error_word());
+    kern<<<grid, G::NT, A::SMEM, st>>>(ml, mm, ma, m2, m1, cf, g, lam_prev, resid, grad, a_n ? 1 : 0,
+                                       kAdjTZ, nzc, device_error_word());
     return cudaGetLastError();
 }
 
