@@ -63,6 +63,30 @@ def tune(shape, r, path, nx, ny, nz, coeffs=None, reps=10, table=TABLE, write=Tr
     return best, ms
 
 
+def tune_auto(shape, r, nx, ny, nz, reps=10, table=TABLE, seed=0):
+    """Tune the CUDA-core path and, where built, the BF16x3 tensor-core path
+    (FP32-level accuracy) for (shape, r); the tensor-core variant is recorded
+    (and so chosen by MMS_PATH_AUTO) only if it is faster."""
+    import torch
+    best_cc, ms_cc = tune(shape, r, "cuda_core", nx, ny, nz, reps=reps, table=table, seed=seed)
+    out = {"cuda_core": (best_cc, ms_cc)}
+    if _lib.num_variants(shape, r, "bf16x3"):
+        best_tc, ms_tc = tune(shape, r, "bf16x3", nx, ny, nz, reps=reps, table=table, write=False,
+                              seed=seed)
+        out["bf16x3"] = (best_tc, ms_tc)
+        gpu = torch.cuda.get_device_name(torch.cuda.current_device())
+        data = json.load(open(table)) if os.path.exists(table) else {}
+        key = _key(gpu, shape, r, "bf16x3", (nx, ny, nz))
+        if min(ms_tc) < min(ms_cc):
+            data[key] = {"variant": best_tc, "ms": ms_tc, "beats_cuda_core_ms": min(ms_cc)}
+        else:
+            data.pop(key, None)
+            _lib.set_variant(shape, r, "bf16x3", -1)
+        with open(table, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+    return out
+
+
 def load_table(table=TABLE, n=None):
     """Register the recorded best variants for this GPU (largest grid wins
     when several sizes were tuned, unless n = (nx, ny, nz) picks one)."""
