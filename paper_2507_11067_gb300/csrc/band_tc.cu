@@ -67,8 +67,10 @@ enum { P_TF32 = 0, P_3XTF32 = 1, P_BF16X3 = 2 };
 
 constexpr int roundup(int a, int b) { return (a + b - 1) / b * b; }
 
-template <int R, int PREC>
+template <int R, int PREC, bool LDG = false>
 struct Cfg {
+    // LDG: converter warps read the FP32 input from global memory themselves
+    // (no TMA staging ring); otherwise a producer warp stages it with TMA.
     static constexpr bool BF = PREC == P_BF16X3;
     static constexpr int ELT = BF ? 2 : 4;           // operand bytes
     static constexpr int KSTEP = BF ? 16 : 8;        // K of one MMA instruction
@@ -119,17 +121,19 @@ struct Cfg {
     static constexpr size_t GRP = (size_t)DSM_GROUP * 4;
     // epilogue warp groups (4 warps, one per TMEM lane quarter, each owns whole
     // planes of the accumulator): as many as the planes and shared memory allow
-    static constexpr int EGF = BASE + 4 * GRP + 2 * (size_t)STG_BYTES <= BUDGET   ? 4
-                               : BASE + 3 * GRP + 2 * (size_t)STG_BYTES <= BUDGET ? 3
-                               : BASE + 2 * GRP + 2 * (size_t)STG_BYTES <= BUDGET ? 2
-                                                                                 : 1;
+    static constexpr size_t STG_MIN = LDG ? 0 : 2 * (size_t)STG_BYTES;
+    static constexpr int EGF = BASE + 4 * GRP + STG_MIN <= BUDGET   ? 4
+                               : BASE + 3 * GRP + STG_MIN <= BUDGET ? 3
+                               : BASE + 2 * GRP + STG_MIN <= BUDGET ? 2
+                                                                   : 1;
     static constexpr int EG = EGF < NZ ? EGF : NZ;
     static constexpr int DSM_BYTES = EG * DSM_GROUP * 4;
-    static constexpr int NCONV = 4;                  // converter warps: 2, 3 and the last two
+    static constexpr int NCONV = LDG ? 5 : 4;        // converter warps: (0,) 2, 3 and the last two
     static constexpr int NWARPS = 4 + 4 * EG + 2;
     static constexpr int NT = 32 * NWARPS;
     static constexpr size_t FIXED = BASE + DSM_BYTES;
-    static constexpr int NST = FIXED + 4 * (size_t)STG_BYTES <= BUDGET   ? 4
+    static constexpr int NST = LDG                                           ? 0
+                               : FIXED + 4 * (size_t)STG_BYTES <= BUDGET   ? 4
                                : FIXED + 3 * (size_t)STG_BYTES <= BUDGET ? 3
                                                                          : 2;
     static constexpr size_t OFF_DSM = CONV_BYTES;
@@ -177,6 +181,9 @@ __device__ __forceinline__ uint32_t split_part(float v, int p)
 }
 
 struct TcArgs {
+    const float *in;              // padded input (read directly by LDG converters)
+    int64_t ipy, ipz;
+    int X, Y, Z;                  // padded extents
     float *out;
     int64_t opy, opz;
     int nx, ny, nz;
@@ -197,12 +204,25 @@ __device__ __forceinline__ void named_sync(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <int R, int PREC>
-__global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
+// 16 bytes of the padded input at (xi, yi, zi), zero outside the grid.
+__device__ __forceinline__ float4 load_in4(const TcArgs &a, int xi, int yi, int zi)
+{
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (yi >= a.Y || zi >= a.Z || xi >= a.X) return v;
+    const float *p = a.in + (int64_t)zi * a.ipz + (int64_t)yi * a.ipy + xi;
+    if (xi + 3 < a.X) return __ldg(reinterpret_cast<const float4 *>(p));
+    v.x = __ldg(p);
+    if (xi + 1 < a.X) v.y = __ldg(p + 1);
+    if (xi + 2 < a.X) v.z = __ldg(p + 2);
+    return v;
+}
+
+template <int R, int PREC, bool LDG>
+__global__ void __launch_bounds__(Cfg<R, PREC, LDG>::NT, 1)
     box_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BoxCoef cf,
                   const __grid_constant__ TcArgs a, unsigned *err)
 {
-    using C = Cfg<R, PREC>;
+    using C = Cfg<R, PREC, LDG>;
     constexpr int W = C::W;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 1024-byte alignment: the TMA swizzle pattern repeats every 1024 bytes
@@ -310,7 +330,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
         return false;
     };
 
-    if (warp == 0) {
+    if (warp == 0 && !LDG) {
         // ------------------------------------------- TMA producer: chunk k
         if (lane == 0) {
             [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
@@ -384,16 +404,38 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
         }
     } else if (warp < 4 || warp >= 4 + NEPI) {
         // -------------------------------------------- converters: chunk k
-        const int ct = (warp < 4 ? warp - 2 : warp - 2 - NEPI) * 32 + lane;
+        const int cw = warp == 0 ? C::NCONV - 1 : warp < 4 ? warp - 2 : warp - 2 - NEPI;
+        const int ct = cw * 32 + lane;
         constexpr int NCH = C::K / C::KC;  // 16-byte operand chunks per line
         [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
         [[maybe_unused]] unsigned long long wstg = 0, wslot = 0;
+        constexpr int NV4 = C::KC / 4;  // FP32 float4 per operand chunk (2 for BF16, 1 for TF32)
+        constexpr int IPT = (C::CHUNK_LINES * NCH + CT - 1) / CT;  // items per thread
         for (int k = 0; k < nch; ++k) {
-            const int st = k % C::NST, sl = k % C::CR;
+            const int sl = k % C::CR;
+            const int st = LDG ? 0 : k % C::NST;
+            // operand values of this thread's items, from global memory (LDG)
+            // or from the TMA staging ring
+            float4 in4[IPT][NV4];
+            if constexpr (LDG) {
+                int x0, y0, zt;
+                tile_origin(k / CPT, x0, y0, zt);
+                const int zc = zt + (k % CPT) * C::NZ;
+#pragma unroll
+                for (int t = 0; t < IPT; ++t) {
+                    const int it = ct + t * CT;
+                    const int n = it % C::CHUNK_LINES, kc = it / C::CHUNK_LINES;
+#pragma unroll
+                    for (int q = 0; q < NV4; ++q)
+                        in4[t][q] = it < C::CHUNK_LINES * NCH
+                                        ? load_in4(a, x0 + kc * C::KC + 4 * q, y0 + n % C::YP, zc + n / C::YP)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
             // decisions stay warp-uniform: a failed wait in any lane stops the warp
-            const unsigned long long t0 = MMS_CLOCK();
-            bool ok = ptx::mbar_wait_bounded(&full_stg[st], (uint32_t)(k / C::NST) & 1u, err);
-            const unsigned long long t1 = MMS_CLOCK();
+            [[maybe_unused]] const unsigned long long t0 = MMS_CLOCK();
+            bool ok = LDG ? true : ptx::mbar_wait_bounded(&full_stg[st], (uint32_t)(k / C::NST) & 1u, err);
+            [[maybe_unused]] const unsigned long long t1 = MMS_CLOCK();
             ok = ok && ptx::mbar_wait_bounded(&empty_conv[sl], ((uint32_t)(k / C::CR) & 1u) ^ 1u, err);
             wstg += t1 - t0;
             wslot += MMS_CLOCK() - t1;
@@ -407,18 +449,25 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
             const bool dup = sl < C::H;
             // lines fastest: a warp converts one 16-byte chunk column of 32
             // consecutive lines, so its stores are contiguous
-            for (int it = ct; it < C::CHUNK_LINES * NCH; it += CT) {
+#pragma unroll
+            for (int t = 0; t < IPT; ++t) {
+                const int it = ct + t * CT;
+                if (it >= C::CHUNK_LINES * NCH) break;
                 const int n = it % C::CHUNK_LINES, kc = it / C::CHUNK_LINES;
                 unsigned char *d0 = conv + ((size_t)kc * C::RING_LINES + line0 + n) * 16;
-                const float *line = src + n * C::K;
-                // 16-byte FP32 chunk j of this line (swizzled staging: chunk j ^ (n & 7))
-                auto chunk = [&](int j) {
-                    const int pj = C::SWZ ? (j ^ (n & 7)) : j;
-                    return *reinterpret_cast<const float4 *>(line + 4 * pj);
-                };
+                if constexpr (!LDG) {
+                    const float *line = src + n * C::K;
+#pragma unroll
+                    for (int q = 0; q < NV4; ++q) {
+                        // swizzled staging: 16-byte chunk j of line n sits at j ^ (n & 7)
+                        const int j = kc * NV4 + q;
+                        const int pj = C::SWZ ? (j ^ (n & 7)) : j;
+                        in4[t][q] = *reinterpret_cast<const float4 *>(line + 4 * pj);
+                    }
+                }
                 uint4 o[2];
                 if constexpr (C::BF) {
-                    const float4 q0 = chunk(2 * kc), q1 = chunk(2 * kc + 1);
+                    const float4 q0 = in4[t][0], q1 = in4[t][NV4 - 1];
                     const float v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
                     uint32_t hi[4], lo[4];
 #pragma unroll
@@ -433,7 +482,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
                     o[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
                     o[1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                 } else {
-                    const float4 q = chunk(kc);
+                    const float4 q = in4[t][0];
                     const uint32_t h0 = tf32_rna(q.x), h1 = tf32_rna(q.y), h2 = tf32_rna(q.z), h3 = tf32_rna(q.w);
                     o[0] = make_uint4(h0, h1, h2, h3);
                     if constexpr (C::NPARTS == 2)
@@ -450,7 +499,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC>::NT, 1)
             }
             ptx::fence_proxy_async_smem();  // generic writes -> tensor-core reads
             ptx::mbar_arrive(&full_conv[sl]);
-            ptx::mbar_arrive(&empty_stg[st]);
+            if (!LDG) ptx::mbar_arrive(&empty_stg[st]);
         }
         if (ct == 0) {
             MMS_TRACE_ADD(2, 0, wstg);
@@ -560,10 +609,10 @@ int num_sms()
     return g_num_sms;
 }
 
-template <int R, int PREC>
+template <int R, int PREC, bool LDG>
 cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int groups)
 {
-    using C = Cfg<R, PREC>;
+    using C = Cfg<R, PREC, LDG>;
     if constexpr (!C::OK) {
         return cudaErrorNotSupported;
     } else {
@@ -571,6 +620,12 @@ cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int groups)
         const int w = 2 * R + 1;
         for (int i = 0; i < w * w * w; ++i) cf.c[i] = s.coeffs[i];
         TcArgs a;
+        a.in = s.in;
+        a.ipy = s.ipy;
+        a.ipz = s.ipz;
+        a.X = (int)s.nx + 2 * R;
+        a.Y = (int)s.ny + 2 * R;
+        a.Z = (int)s.nz + 2 * R;
         a.out = s.out;
         a.opy = s.opy;
         a.opz = s.opz;
@@ -584,7 +639,7 @@ cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int groups)
         a.groups = groups < zgroups ? groups : zgroups;
         const int zchunks = (zgroups + a.groups - 1) / a.groups;
         a.tiles = a.tiles_x * a.tiles_y * zchunks;
-        auto kern = box_tc_kernel<R, PREC>;
+        auto kern = box_tc_kernel<R, PREC, LDG>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
         const int grid = a.tiles < num_sms() ? a.tiles : num_sms();
@@ -593,21 +648,29 @@ cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int groups)
     }
 }
 
-// Variants: z-groups per tile (the z extent of a tile is groups * NZ planes).
+// Variants: z-groups per tile (the z extent of a tile is groups * NZ planes)
+// times the feed of the converters (TMA staging ring, or direct loads).
 constexpr int kGroups[] = {16, 8, 32, 4};
-constexpr int kNumVariants = sizeof(kGroups) / sizeof(int);
+constexpr int kNumGroups = sizeof(kGroups) / sizeof(int);
+constexpr int kNumVariants = 2 * kNumGroups;
+
+template <int PREC, bool LDG>
+cudaError_t launch_feed(const Sweep &s, const CUtensorMap &map, int g)
+{
+    switch (s.r) {
+        case 1: return launch_r<1, PREC, LDG>(s, map, g);
+        case 2: return launch_r<2, PREC, LDG>(s, map, g);
+        case 3: return launch_r<3, PREC, LDG>(s, map, g);
+        case 4: return launch_r<4, PREC, LDG>(s, map, g);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 template <int PREC>
 cudaError_t launch_prec(const Sweep &s, const CUtensorMap &map, int v)
 {
-    const int g = kGroups[v];
-    switch (s.r) {
-        case 1: return launch_r<1, PREC>(s, map, g);
-        case 2: return launch_r<2, PREC>(s, map, g);
-        case 3: return launch_r<3, PREC>(s, map, g);
-        case 4: return launch_r<4, PREC>(s, map, g);
-        default: return cudaErrorInvalidValue;
-    }
+    const int g = kGroups[v % kNumGroups];
+    return v < kNumGroups ? launch_feed<PREC, false>(s, map, g) : launch_feed<PREC, true>(s, map, g);
 }
 
 template <int PREC>
@@ -634,10 +697,10 @@ template <int PREC>
 bool supported_r(int r)
 {
     switch (r) {
-        case 1: return Cfg<1, PREC>::OK;
-        case 2: return Cfg<2, PREC>::OK;
-        case 3: return Cfg<3, PREC>::OK;
-        case 4: return Cfg<4, PREC>::OK;
+        case 1: return Cfg<1, PREC>::OK && Cfg<1, PREC, true>::OK;
+        case 2: return Cfg<2, PREC>::OK && Cfg<2, PREC, true>::OK;
+        case 3: return Cfg<3, PREC>::OK && Cfg<3, PREC, true>::OK;
+        case 4: return Cfg<4, PREC>::OK && Cfg<4, PREC, true>::OK;
         default: return false;
     }
 }
