@@ -192,7 +192,19 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
     band_tc_box(shape, r, path, v, &bx, &by, &bz, &swz);
     if (!encode_tmap_3d(&map, in, X, Y, Z, ipy, ipz, bx, by, bz, swz != 0))
         return fail(MMS_E_CUDA, "cuTensorMapEncodeTiled refused the input grid");
-    cudaError_t e = launch_band_tc(s, path, map, v);
+    // The star's x/y partial sums go through a temporary grid (stream-ordered
+    // allocation from the device's default memory pool).
+    float *scratch = nullptr;
+    const size_t sb = band_tc_scratch_bytes(s);
+    if (sb) {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), sb, s.stream);
+        if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+    }
+    cudaError_t e = launch_band_tc(s, path, map, v, scratch);
+    if (scratch) {
+        cudaError_t f = cudaFreeAsync(scratch, s.stream);
+        if (e == cudaSuccess) e = f;
+    }
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "tensor-core sweep launch");
 }
 

@@ -67,10 +67,14 @@ enum { P_TF32 = 0, P_3XTF32 = 1, P_BF16X3 = 2 };
 
 constexpr int roundup(int a, int b) { return (a + b - 1) / b * b; }
 
-template <int R, int PREC, bool LDG = false>
+template <int R, int PREC, bool LDG = false, bool PLANAR = false>
 struct Cfg {
     // LDG: converter warps read the FP32 input from global memory themselves
     // (no TMA staging ring); otherwise a producer warp stages it with TMA.
+    // PLANAR: the stencil has no z extent (2D in each plane of the padded
+    // grid, coefficients [dy][dx]): the x/y pass of the star on tensor cores.
+    static constexpr int RZ = PLANAR ? 0 : R;
+    static constexpr int WZ = 2 * RZ + 1;
     static constexpr bool BF = PREC == P_BF16X3;
     static constexpr int ELT = BF ? 2 : 4;           // operand bytes
     static constexpr int KSTEP = BF ? 16 : 8;        // K of one MMA instruction
@@ -82,7 +86,7 @@ struct Cfg {
     static constexpr int NPARTS = PREC == P_TF32 ? 1 : 2;
     static constexpr int NPROD = PREC == P_TF32 ? 1 : 3;
     static constexpr int BANDCOLS = K * ELT / 4;     // 32-bit TMEM columns per band part
-    static constexpr int BAND_TOTAL = W * NPARTS * BANDCOLS;
+    static constexpr int BAND_TOTAL = WZ * NPARTS * BANDCOLS;
     static constexpr int YP = 32;                    // staged rows per plane
     static constexpr int TY = YP - 2 * R;            // output rows per tile
     static constexpr int NZ = (2 * 4 * YP + BAND_TOTAL <= 512)   ? 4
@@ -96,7 +100,7 @@ struct Cfg {
     // converted chunks live in a ring of CR slots plus H duplicate slots (a
     // chunk in slot s < H is also written to slot CR + s), so every window of
     // H + 1 consecutive chunks is contiguous and one descriptor spans it.
-    static constexpr int H = (2 * R + NZ - 1) / NZ;
+    static constexpr int H = (2 * RZ + NZ - 1) / NZ;
     static constexpr int CR = H + 2;
     static constexpr int CHUNK_LINES = NZ * YP;
     static constexpr int RING_LINES = (CR + H) * CHUNK_LINES;
@@ -145,7 +149,7 @@ struct Cfg {
     // swizzle: 16-byte chunk q of line n sits at chunk q ^ (n & 7), so the
     // converters' column reads across 8 lines hit 8 different bank groups.
     static constexpr bool SWZ = K * 4 == 128;
-    static_assert(N % 16 == 0 && N <= 256, "MMA N");
+    static_assert(SWZ == (K * 4 == 128) && N % 16 == 0 && N <= 256, "MMA N");
     static_assert(STG_BYTES % 1024 == 0 && CONV_BYTES % 1024 == 0 && PART_BYTES % 16 == 0, "align");
 };
 
@@ -217,13 +221,14 @@ __device__ __forceinline__ float4 load_in4(const TcArgs &a, int xi, int yi, int 
     return v;
 }
 
-template <int R, int PREC, bool LDG>
-__global__ void __launch_bounds__(Cfg<R, PREC, LDG>::NT, 1)
+template <int R, int PREC, bool LDG, bool PLANAR>
+__global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
     box_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BoxCoef cf,
                   const __grid_constant__ TcArgs a, unsigned *err)
 {
-    using C = Cfg<R, PREC, LDG>;
+    using C = Cfg<R, PREC, LDG, PLANAR>;
     constexpr int W = C::W;
+    constexpr int ZOFF = R - C::RZ;  // padded-plane offset of an output's centre plane
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 1024-byte alignment: the TMA swizzle pattern repeats every 1024 bytes
     unsigned char *smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG>::NT, 1)
         const int l = q * 32 + lane;
         const bool used = l < C::LANES;
         const int dyi = used ? l / C::TXO : 0, xo = used ? l % C::TXO : 0;
-        for (int dzi = 0; dzi < W; ++dzi)
+        for (int dzi = 0; dzi < C::WZ; ++dzi)
             for (int p = 0; p < C::NPARTS; ++p)
                 for (int c0 = 0; c0 < C::BANDCOLS; c0 += 8) {
                     uint32_t v[8];
@@ -336,13 +341,14 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG>::NT, 1)
             [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
             ptx::prefetch_tmap(&tmap);
             for (int k = 0; k < nch; ++k) {
-                const int st = k % C::NST;
-                if (!wait(&empty_stg[st], ((uint32_t)(k / C::NST) & 1u) ^ 1u)) break;
+                constexpr int NSTD = C::NST > 0 ? C::NST : 1;  // (this branch only runs with a ring)
+                const int st = k % NSTD;
+                if (!wait(&empty_stg[st], ((uint32_t)(k / NSTD) & 1u) ^ 1u)) break;
                 int x0, y0, zt;
                 tile_origin(k / CPT, x0, y0, zt);
                 ptx::mbar_arrive_expect_tx(&full_stg[st], C::STG_BYTES);
                 ptx::tma_load_3d(stg + (size_t)st * (C::STG_BYTES / 4), &tmap, x0, y0,
-                                 zt + (k % CPT) * C::NZ, &full_stg[st]);
+                                 zt + (k % CPT) * C::NZ + ZOFF, &full_stg[st]);
             }
             MMS_TRACE_ADD(0, 0, waited);
             MMS_TRACE_ADD(0, 1, MMS_CLOCK() - tstart);
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG>::NT, 1)
                 const uint64_t d0 = tc::smem_desc(cbase, C::RING_LINES * 16, 128);
                 const uint32_t a0 = tbase + C::BAND_COL0;
 #pragma unroll
-                for (int dzi = 0; dzi < W; ++dzi) {
+                for (int dzi = 0; dzi < C::WZ; ++dzi) {
 #pragma unroll
                     for (int pr = 0; pr < C::NPROD; ++pr) {
                         const int pa = pr == 2 ? 1 : 0;  // band part
@@ -413,14 +419,14 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG>::NT, 1)
         constexpr int IPT = (C::CHUNK_LINES * NCH + CT - 1) / CT;  // items per thread
         for (int k = 0; k < nch; ++k) {
             const int sl = k % C::CR;
-            const int st = LDG ? 0 : k % C::NST;
+            const int st = LDG ? 0 : k % (C::NST > 0 ? C::NST : 1);
             // operand values of this thread's items, from global memory (LDG)
             // or from the TMA staging ring
             float4 in4[IPT][NV4];
             if constexpr (LDG) {
                 int x0, y0, zt;
                 tile_origin(k / CPT, x0, y0, zt);
-                const int zc = zt + (k % CPT) * C::NZ;
+                const int zc = zt + (k % CPT) * C::NZ + ZOFF;
 #pragma unroll
                 for (int t = 0; t < IPT; ++t) {
                     const int it = ct + t * CT;
@@ -434,7 +440,8 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG>::NT, 1)
             }
             // decisions stay warp-uniform: a failed wait in any lane stops the warp
             [[maybe_unused]] const unsigned long long t0 = MMS_CLOCK();
-            bool ok = LDG ? true : ptx::mbar_wait_bounded(&full_stg[st], (uint32_t)(k / C::NST) & 1u, err);
+            constexpr int NSTD = C::NST > 0 ? C::NST : 1;
+            bool ok = LDG ? true : ptx::mbar_wait_bounded(&full_stg[st], (uint32_t)(k / NSTD) & 1u, err);
             [[maybe_unused]] const unsigned long long t1 = MMS_CLOCK();
             ok = ok && ptx::mbar_wait_bounded(&empty_conv[sl], ((uint32_t)(k / C::CR) & 1u) ^ 1u, err);
             wstg += t1 - t0;
@@ -609,16 +616,15 @@ int num_sms()
     return g_num_sms;
 }
 
-template <int R, int PREC, bool LDG>
+template <int R, int PREC, bool LDG, bool PLANAR = false>
 cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int groups)
 {
-    using C = Cfg<R, PREC, LDG>;
+    using C = Cfg<R, PREC, LDG, PLANAR>;
     if constexpr (!C::OK) {
         return cudaErrorNotSupported;
     } else {
         BoxCoef cf{};
-        const int w = 2 * R + 1;
-        for (int i = 0; i < w * w * w; ++i) cf.c[i] = s.coeffs[i];
+        for (int i = 0; i < C::WZ * C::W * C::W; ++i) cf.c[i] = s.coeffs[i];
         TcArgs a;
         a.in = s.in;
         a.ipy = s.ipy;
@@ -639,7 +645,7 @@ cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int groups)
         a.groups = groups < zgroups ? groups : zgroups;
         const int zchunks = (zgroups + a.groups - 1) / a.groups;
         a.tiles = a.tiles_x * a.tiles_y * zchunks;
-        auto kern = box_tc_kernel<R, PREC, LDG>;
+        auto kern = box_tc_kernel<R, PREC, LDG, PLANAR>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
         const int grid = a.tiles < num_sms() ? a.tiles : num_sms();
@@ -654,34 +660,35 @@ constexpr int kGroups[] = {16, 8, 32, 4};
 constexpr int kNumGroups = sizeof(kGroups) / sizeof(int);
 constexpr int kNumVariants = 2 * kNumGroups;
 
-template <int PREC, bool LDG>
+template <int PREC, bool LDG, bool PLANAR>
 cudaError_t launch_feed(const Sweep &s, const CUtensorMap &map, int g)
 {
     switch (s.r) {
-        case 1: return launch_r<1, PREC, LDG>(s, map, g);
-        case 2: return launch_r<2, PREC, LDG>(s, map, g);
-        case 3: return launch_r<3, PREC, LDG>(s, map, g);
-        case 4: return launch_r<4, PREC, LDG>(s, map, g);
+        case 1: return launch_r<1, PREC, LDG, PLANAR>(s, map, g);
+        case 2: return launch_r<2, PREC, LDG, PLANAR>(s, map, g);
+        case 3: return launch_r<3, PREC, LDG, PLANAR>(s, map, g);
+        case 4: return launch_r<4, PREC, LDG, PLANAR>(s, map, g);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int PREC>
+template <int PREC, bool PLANAR>
 cudaError_t launch_prec(const Sweep &s, const CUtensorMap &map, int v)
 {
     const int g = kGroups[v % kNumGroups];
-    return v < kNumGroups ? launch_feed<PREC, false>(s, map, g) : launch_feed<PREC, true>(s, map, g);
+    return v < kNumGroups ? launch_feed<PREC, false, PLANAR>(s, map, g)
+                          : launch_feed<PREC, true, PLANAR>(s, map, g);
 }
 
-template <int PREC>
+template <int PREC, bool PLANAR>
 void box_dims(int r, int *bx, int *by, int *bz, int *swz)
 {
-#define MMS_DIMS(RR)                                  \
-    case RR:                                          \
-        *bx = Cfg<RR, PREC>::K;                       \
-        *by = Cfg<RR, PREC>::YP;                      \
-        *bz = Cfg<RR, PREC>::NZ;                      \
-        *swz = Cfg<RR, PREC>::SWZ ? 1 : 0;            \
+#define MMS_DIMS(RR)                                          \
+    case RR:                                                  \
+        *bx = Cfg<RR, PREC, false, PLANAR>::K;                \
+        *by = Cfg<RR, PREC, false, PLANAR>::YP;               \
+        *bz = Cfg<RR, PREC, false, PLANAR>::NZ;               \
+        *swz = Cfg<RR, PREC, false, PLANAR>::SWZ ? 1 : 0;     \
         return;
     switch (r) {
         MMS_DIMS(1)
@@ -693,14 +700,14 @@ void box_dims(int r, int *bx, int *by, int *bz, int *swz)
 #undef MMS_DIMS
 }
 
-template <int PREC>
+template <int PREC, bool PLANAR>
 bool supported_r(int r)
 {
     switch (r) {
-        case 1: return Cfg<1, PREC>::OK && Cfg<1, PREC, true>::OK;
-        case 2: return Cfg<2, PREC>::OK && Cfg<2, PREC, true>::OK;
-        case 3: return Cfg<3, PREC>::OK && Cfg<3, PREC, true>::OK;
-        case 4: return Cfg<4, PREC>::OK && Cfg<4, PREC, true>::OK;
+        case 1: return Cfg<1, PREC, false, PLANAR>::OK && Cfg<1, PREC, true, PLANAR>::OK;
+        case 2: return Cfg<2, PREC, false, PLANAR>::OK && Cfg<2, PREC, true, PLANAR>::OK;
+        case 3: return Cfg<3, PREC, false, PLANAR>::OK && Cfg<3, PREC, true, PLANAR>::OK;
+        case 4: return Cfg<4, PREC, false, PLANAR>::OK && Cfg<4, PREC, true, PLANAR>::OK;
         default: return false;
     }
 }
@@ -715,40 +722,151 @@ int prec_of(int path)
     }
 }
 
+template <bool PLANAR>
+int supported(int r, int path)
+{
+    switch (prec_of(path)) {
+        case P_TF32: return supported_r<P_TF32, PLANAR>(r);
+        case P_3XTF32: return supported_r<P_3XTF32, PLANAR>(r);
+        case P_BF16X3: return supported_r<P_BF16X3, PLANAR>(r);
+        default: return 0;
+    }
+}
+
+template <bool PLANAR>
+cudaError_t launch_tc(const Sweep &s, int path, const CUtensorMap &map, int v)
+{
+    switch (prec_of(path)) {
+        case P_TF32: return launch_prec<P_TF32, PLANAR>(s, map, v);
+        case P_3XTF32: return launch_prec<P_3XTF32, PLANAR>(s, map, v);
+        case P_BF16X3: return launch_prec<P_BF16X3, PLANAR>(s, map, v);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// z part of the star after the tensor-core x/y pass:
+//   out(x,y,z) = T(x,y,z) + sum_{dz != 0} cz[dz] in(x+r, y+r, z+r+dz)
+// Each thread owns four x positions of one row and marches a z range with a
+// register queue of the 2r+1 centre values.
+struct ZCoef { float c[2 * kMaxR + 1]; };
+
+template <int R>
+__global__ void __launch_bounds__(256)
+    star_zpass_kernel(const float *__restrict__ in, int64_t ipy, int64_t ipz, const float *__restrict__ T,
+                      int64_t tpy, int64_t tpz, float *__restrict__ out, int64_t opy, int64_t opz, int nx,
+                      int ny, int nz, const __grid_constant__ ZCoef cz, int tz, int vec)
+{
+    constexpr int W = 2 * R + 1;
+    const int x = (blockIdx.x * 16 + (threadIdx.x & 15)) * 4;
+    const int y = blockIdx.y * 16 + (threadIdx.x >> 4);
+    const int zb = blockIdx.z * tz, ze = min(zb + tz, nz);
+    if (x >= nx || y >= ny) return;
+    const float *col = in + (int64_t)(y + R) * ipy + (x + R);
+    const bool full4 = x + 3 < nx;
+    auto load4 = [&](const float *p, float (&v)[4]) {
+        if (vec && full4 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+            const float4 t = *reinterpret_cast<const float4 *>(p);
+            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = x + k < nx ? p[k] : 0.f;
+        }
+    };
+    float q[W][4];
+#pragma unroll
+    for (int d = 0; d < W - 1; ++d) load4(col + (int64_t)(zb + d) * ipz, q[d + 1]);  // planes zb-R .. zb+R-1
+    for (int z = zb; z < ze; ++z) {
+#pragma unroll
+        for (int d = 0; d < W - 1; ++d)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[d][k] = q[d + 1][k];
+        load4(col + (int64_t)(z + 2 * R) * ipz, q[W - 1]);  // padded plane z + 2R = centre z + R, offset +R
+        float t[4], o[4];
+        load4(T + (int64_t)z * tpz + (int64_t)y * tpy + x, t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float acc = t[k];
+#pragma unroll
+            for (int d = 0; d < W; ++d)
+                if (d != R) acc = fmaf(cz.c[d], q[d][k], acc);
+            o[k] = acc;
+        }
+        float *op = out + (int64_t)z * opz + (int64_t)y * opy + x;
+        if (vec && full4 && (reinterpret_cast<uintptr_t>(op) & 15) == 0) {
+            *reinterpret_cast<float4 *>(op) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (x + k < nx) op[k] = o[k];
+        }
+    }
+}
+
+template <int R>
+cudaError_t launch_zpass(const Sweep &s, const float *T, int64_t tpy, int64_t tpz)
+{
+    ZCoef cz{};
+    for (int d = 0; d < 2 * R + 1; ++d) cz.c[d] = s.coeffs[2 * (2 * R + 1) + d];
+    const int tz = 64;
+    const dim3 grid((unsigned)((s.nx + 63) / 64), (unsigned)((s.ny + 15) / 16), (unsigned)((s.nz + tz - 1) / tz));
+    const int vec = (s.ipy % 4 == 0 && s.ipz % 4 == 0 && tpy % 4 == 0 && tpz % 4 == 0 && s.opy % 4 == 0 &&
+                     s.opz % 4 == 0)
+                        ? 1
+                        : 0;
+    star_zpass_kernel<R><<<grid, 256, 0, s.stream>>>(s.in, s.ipy, s.ipz, T, tpy, tpz, s.out, s.opy, s.opz,
+                                                     (int)s.nx, (int)s.ny, (int)s.nz, cz, tz, vec);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int band_tc_supported(int shape, int r, int path)
 {
-    if (shape != MMS_BOX) return 0;
-    switch (prec_of(path)) {
-        case P_TF32: return supported_r<P_TF32>(r);
-        case P_3XTF32: return supported_r<P_3XTF32>(r);
-        case P_BF16X3: return supported_r<P_BF16X3>(r);
-        default: return 0;
-    }
+    return shape == MMS_BOX ? supported<false>(r, path) : supported<true>(r, path);
 }
 
 int band_tc_variants(int shape, int r, int path) { return band_tc_supported(shape, r, path) ? kNumVariants : 0; }
 
 void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz, int *swz)
 {
-    (void)shape;
     (void)v;
+    const bool planar = shape == MMS_STAR;
     switch (prec_of(path)) {
-        case P_TF32: box_dims<P_TF32>(r, bx, by, bz, swz); return;
-        case P_3XTF32: box_dims<P_3XTF32>(r, bx, by, bz, swz); return;
-        case P_BF16X3: box_dims<P_BF16X3>(r, bx, by, bz, swz); return;
+        case P_TF32: planar ? box_dims<P_TF32, true>(r, bx, by, bz, swz) : box_dims<P_TF32, false>(r, bx, by, bz, swz); return;
+        case P_3XTF32: planar ? box_dims<P_3XTF32, true>(r, bx, by, bz, swz) : box_dims<P_3XTF32, false>(r, bx, by, bz, swz); return;
+        case P_BF16X3: planar ? box_dims<P_BF16X3, true>(r, bx, by, bz, swz) : box_dims<P_BF16X3, false>(r, bx, by, bz, swz); return;
         default: *bx = *by = *bz = *swz = 0;
     }
 }
 
-cudaError_t launch_band_tc(const Sweep &s, int path, const CUtensorMap &map, int v)
+size_t band_tc_scratch_bytes(const Sweep &s) { return s.shape == MMS_STAR ? (size_t)s.nx * s.ny * s.nz * 4 : 0; }
+
+cudaError_t launch_band_tc(const Sweep &s, int path, const CUtensorMap &map, int v, float *scratch)
 {
     if (v < 0 || v >= kNumVariants) return cudaErrorInvalidValue;
-    switch (prec_of(path)) {
-        case P_TF32: return launch_prec<P_TF32>(s, map, v);
-        case P_3XTF32: return launch_prec<P_3XTF32>(s, map, v);
-        case P_BF16X3: return launch_prec<P_BF16X3>(s, map, v);
+    if (s.shape == MMS_BOX) return launch_tc<false>(s, path, map, v);
+    // Star: the in-plane x/y part (with the three centre weights) as a planar
+    // banded pass on tensor cores into `scratch` (the paper's temporary buffer
+    // for x/y partial results, Sec. 4.3), then the z part on CUDA cores.
+    const int r = s.r, w = 2 * r + 1;
+    float c2[(2 * kMaxR + 1) * (2 * kMaxR + 1)] = {};
+    for (int d = -r; d <= r; ++d) {
+        c2[r * w + d + r] += s.coeffs[0 * w + d + r];  // x line (dy = 0)
+        c2[(d + r) * w + r] += s.coeffs[1 * w + d + r];  // y line (dx = 0)
+    }
+    c2[r * w + r] += s.coeffs[2 * w + r];  // z centre
+    Sweep p = s;
+    p.coeffs = c2;
+    p.out = scratch;
+    p.opy = s.nx;
+    p.opz = s.nx * s.ny;
+    cudaError_t e = launch_tc<true>(p, path, map, v);
+    if (e != cudaSuccess) return e;
+    switch (r) {
+        case 1: return launch_zpass<1>(s, scratch, p.opy, p.opz);
+        case 2: return launch_zpass<2>(s, scratch, p.opy, p.opz);
+        case 3: return launch_zpass<3>(s, scratch, p.opy, p.opz);
+        case 4: return launch_zpass<4>(s, scratch, p.opy, p.opz);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -53,7 +53,10 @@ void box_cc_box(int r, int v, int *bx, int *by);
 
 // Tensor-core banded sweeps (band_tc.cu).
 int band_tc_supported(int shape, int r, int path);
-cudaError_t launch_band_tc(const Sweep &s, int path, const CUtensorMap &tmap, int variant);
+// The star runs as a planar tensor-core pass into `scratch` (nx*ny*nz floats,
+// dense) followed by a CUDA-core z pass; the box needs no scratch.
+cudaError_t launch_band_tc(const Sweep &s, int path, const CUtensorMap &tmap, int variant, float *scratch);
+size_t band_tc_scratch_bytes(const Sweep &s);
 void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz, int *swz);
 int band_tc_variants(int shape, int r, int path);
 
