@@ -131,6 +131,36 @@ int32_t mms_default_variant(int shape, int radius, int path, int64_t nx, int64_t
  * and variant -1 from then on in this process.  variant -1 clears it. */
 mms_status mms_set_variant(int shape, int radius, int path, int32_t variant);
 
+/* Largest interior (nx*ny*nz points) of mms_stencil_apply_noalloc: its
+ * temporary grid is a fixed device array of this many floats (32 MiB). */
+#define MMS_NOALLOC_MAX_POINTS 8388608
+
+/*
+ * The star sweep on tensor cores (MMS_PATH_TF32, MMS_PATH_3XTF32 or
+ * MMS_PATH_BF16X3; MMS_PATH_AUTO means MMS_PATH_BF16X3) without any device
+ * allocation.  The paper has no counterpart: it is for callers that cannot
+ * call cudaMalloc or a stream-ordered allocator (a host whose device memory
+ * is all reserved for its own allocator, a plugin with a fixed footprint).
+ * mms_stencil_apply_ex takes the star's temporary grid of nx*ny*nz floats
+ * from the device's memory pool on each tensor-core call; this entry point
+ * uses a file-scope device array of MMS_NOALLOC_MAX_POINTS floats instead,
+ * which every GPU that loads the library holds until the process exits.
+ * Arguments, layouts and results are those of mms_stencil_apply_ex with
+ * shape MMS_STAR; the caller still passes the input and output.
+ * Set-up: the first call on each device (current device at the call) looks
+ * the array's device address up with cudaGetSymbolAddress; make that first
+ * call outside any stream capture.
+ * Errors: MMS_E_ARG for nx*ny*nz above MMS_NOALLOC_MAX_POINTS (and the
+ * checks of mms_stencil_apply_ex); MMS_E_UNSUPPORTED for the box shape or a
+ * non-tensor-core path; MMS_E_ALIGN as for the forced TMA paths.
+ * Sharing: every call on a device uses the same array and leaves its
+ * contents behind; nothing in it needs to start at zero (each call writes
+ * the part it reads).  Calls whose work overlaps on the GPU (other streams,
+ * other host threads) race on the array: serialise them, e.g. on one stream.
+ */
+mms_status mms_stencil_apply_noalloc(const mms_stencil_desc *desc, const float *in, float *out,
+                                     void *stream);
+
 /* ------------------------------------------------------- acoustic wave */
 
 /*

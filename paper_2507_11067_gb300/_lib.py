@@ -22,13 +22,14 @@ PATH_NAMES = {v: k for k, v in PATHS.items()}
 STATUS = {0: "MMS_OK", 1: "MMS_E_ARG", 2: "MMS_E_UNSUPPORTED", 3: "MMS_E_ALIGN", 4: "MMS_E_CUDA",
           5: "MMS_E_TIMEOUT", 6: "MMS_E_DEVICE", 7: "MMS_E_NOMEM"}
 WAVE_GRAPH = 1
+NOALLOC_MAX_POINTS = 8388608  # MMS_NOALLOC_MAX_POINTS of include/mms.h
 
 # Every symbol include/mms.h declares (checked by the CPU test suite).
 EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_num_variants",
            "mms_default_variant",
            "mms_set_variant", "mms_wave_step", "mms_wave_forward", "mms_wave_adjoint",
            "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
-           "mms_check_device", "mms_version"]
+           "mms_check_device", "mms_version", "mms_stencil_apply_noalloc"]
 
 
 class MMSError(RuntimeError):
@@ -80,6 +81,7 @@ def load():
         sig = {
             "mms_stencil_apply": [i32, i32, P, P, P, i64, i64, i64, P],
             "mms_stencil_apply_ex": [ctypes.POINTER(StencilDesc), P, P, P],
+            "mms_stencil_apply_noalloc": [ctypes.POINTER(StencilDesc), P, P, P],
             "mms_num_variants": [i32, i32, i32],
             "mms_auto_path": [i32, i32, i32],
             "mms_default_variant": [i32, i32, i32, i64, i64, i64],
@@ -185,6 +187,26 @@ def apply(shape, r, coeffs, inp, out=None, path="auto", variant=-1, stream=None)
     d = StencilDesc(SHAPES[shape], r, c.ctypes.data, nx, ny, nz, ipy, ipz, opy, opz,
                     PATHS[path] if isinstance(path, str) else int(path), int(variant))
     check(load().mms_stencil_apply_ex(ctypes.byref(d), _ptr(inp), _ptr(out), _stream(stream)))
+    return out
+
+
+def apply_noalloc(r, coeffs, inp, out=None, path="bf16x3", variant=-1, stream=None):
+    """The star sweep on tensor cores with no device allocation inside the
+    call (mms_stencil_apply_noalloc); same arguments as ``apply`` with
+    shape "star".  Interiors above NOALLOC_MAX_POINTS points are refused."""
+    import torch
+    if not inp.is_cuda or inp.dtype != torch.float32:
+        raise ValueError("input must be a CUDA float32 tensor")
+    Z, Y, X = inp.shape
+    nx, ny, nz = X - 2 * r, Y - 2 * r, Z - 2 * r
+    if out is None:
+        out = torch.empty((nz, ny, nx), device=inp.device, dtype=torch.float32)
+    ipy, ipz = pitches(inp)
+    opy, opz = pitches(out)
+    c = _host_coeffs(coeffs)
+    d = StencilDesc(SHAPES["star"], r, c.ctypes.data, nx, ny, nz, ipy, ipz, opy, opz,
+                    PATHS[path] if isinstance(path, str) else int(path), int(variant))
+    check(load().mms_stencil_apply_noalloc(ctypes.byref(d), _ptr(inp), _ptr(out), _stream(stream)))
     return out
 
 

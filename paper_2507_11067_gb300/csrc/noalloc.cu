@@ -1,0 +1,125 @@
+// noalloc.cu -- the star sweep on tensor cores for callers that cannot
+// allocate device memory (mms_stencil_apply_noalloc in include/mms.h).
+//
+// The star's tensor-core form needs a temporary grid of nx*ny*nz floats for
+// the in-plane partial sums.  mms_stencil_apply_ex takes it from the
+// device's stream-ordered memory pool on every call; some callers cannot
+// allow that: code whose memory is budgeted up front (a host that reserves
+// all device memory for its own allocator), code that may not call
+// cudaMalloc-family routines at all (a driver or plugin with a fixed
+// footprint).  Here the temporary grid is a file-scope device array of a
+// fixed size, part of the library's own module, so the call allocates
+// nothing.
+#include <mutex>
+
+#include "common.cuh"
+
+namespace mms {
+
+mms_status fail(mms_status st, const char *fmt, ...);
+mms_status cuda_fail(cudaError_t e, const char *what);
+
+namespace {
+
+// The temporary grid.  Every device that loads this module holds these
+// MMS_NOALLOC_MAX_POINTS floats (32 MiB) until the process exits.
+static __device__ __align__(256) float g_noalloc_scratch[MMS_NOALLOC_MAX_POINTS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+float *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device.  In host code the array's name only stands for the symbol.
+mms_status scratch_of_current_device(float **ptr)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(MMS_E_UNSUPPORTED, "device %d above %d", dev, kMaxDevices - 1);
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch");
+        g_scratch_ptr[dev] = static_cast<float *>(p);
+    }
+    *ptr = g_scratch_ptr[dev];
+    return MMS_OK;
+}
+
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + nb && b0 < a0 + na;
+}
+
+}  // namespace
+
+static mms_status apply_noalloc(const mms_stencil_desc *d, const float *in, float *out, void *stream)
+{
+    if (!d) return fail(MMS_E_ARG, "null descriptor");
+    const int r = d->radius;
+    if (d->shape != MMS_STAR) return fail(MMS_E_UNSUPPORTED, "the no-alloc sweep is the star shape only");
+    if (r < 1 || r > kMaxR) return fail(MMS_E_ARG, "radius %d outside 1..%d", r, kMaxR);
+    if (!d->coeffs) return fail(MMS_E_ARG, "null coefficient array");
+    if (d->nx < 0 || d->ny < 0 || d->nz < 0) return fail(MMS_E_ARG, "negative size");
+    if (d->nx >= (1ll << 30) || d->ny >= (1ll << 30) || d->nz >= (1ll << 30))
+        return fail(MMS_E_ARG, "size above 2^30");
+    int path = d->path == MMS_PATH_AUTO ? MMS_PATH_BF16X3 : d->path;
+    if (path != MMS_PATH_TF32 && path != MMS_PATH_3XTF32 && path != MMS_PATH_BF16X3)
+        return fail(MMS_E_UNSUPPORTED, "the no-alloc sweep runs on tensor-core paths only (path %d)", d->path);
+    if (d->variant < -1) return fail(MMS_E_ARG, "variant %d", d->variant);
+    if (d->nx == 0 || d->ny == 0 || d->nz == 0) return MMS_OK;
+    const int64_t points = d->nx * d->ny * d->nz;
+    if (points > (int64_t)MMS_NOALLOC_MAX_POINTS)
+        return fail(MMS_E_ARG,
+                    "interior of %lld x %lld x %lld = %lld points is above the no-alloc limit of %lld points",
+                    (long long)d->nx, (long long)d->ny, (long long)d->nz, (long long)points,
+                    (long long)MMS_NOALLOC_MAX_POINTS);
+    if (!in || !out) return fail(MMS_E_ARG, "null grid pointer");
+    const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * r;
+    const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
+    const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
+    const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
+    const int64_t opz = d->out_pitch_z ? d->out_pitch_z : d->ny * opy;
+    if (ipy < X || ipz < Y * ipy)
+        return fail(MMS_E_ARG, "input pitches (%lld, %lld) below the padded extents", (long long)ipy, (long long)ipz);
+    if (opy < d->nx || opz < d->ny * opy)
+        return fail(MMS_E_ARG, "output pitches (%lld, %lld) below the interior extents", (long long)opy,
+                    (long long)opz);
+    const size_t in_bytes = (size_t)((Z - 1) * ipz + (Y - 1) * ipy + X) * 4;
+    const size_t out_bytes = (size_t)((d->nz - 1) * opz + (d->ny - 1) * opy + d->nx) * 4;
+    if (ranges_overlap(in, in_bytes, out, out_bytes)) return fail(MMS_E_ARG, "input and output overlap");
+    if ((reinterpret_cast<uintptr_t>(in) % 16) != 0 || (ipy % 4) != 0 || (ipz % 4) != 0)
+        return fail(MMS_E_ALIGN, "TMA path needs a 16-byte aligned input and pitches that are multiples of 4 floats");
+    if (!band_tc_supported(MMS_STAR, r, path))
+        return fail(MMS_E_UNSUPPORTED, "path %d does not support the star of radius %d", path, r);
+    const int nvar = band_tc_variants(MMS_STAR, r, path);
+    const int v = d->variant >= 0 ? d->variant : mms_default_variant(MMS_STAR, r, path, d->nx, d->ny, d->nz);
+    if (v < 0 || v >= nvar) return fail(MMS_E_ARG, "variant %d of %d", v, nvar);
+
+    float *scratch = nullptr;
+    mms_status st = scratch_of_current_device(&scratch);
+    if (st != MMS_OK) return st;
+
+    Sweep s{MMS_STAR, r, d->nx, d->ny, d->nz, in, ipy, ipz, out, opy, opz, d->coeffs, v,
+            reinterpret_cast<cudaStream_t>(stream)};
+    int bx, by, bz, swz;
+    band_tc_box(MMS_STAR, r, path, v, &bx, &by, &bz, &swz);
+    CUtensorMap map;
+    if (!encode_tmap_3d(&map, in, X, Y, Z, ipy, ipz, bx, by, bz, swz != 0))
+        return fail(MMS_E_CUDA, "cuTensorMapEncodeTiled refused the input grid");
+    // The planar pass writes every element of the first nx*ny*nz floats of
+    // the array before the z pass reads it, so nothing needs clearing.
+    cudaError_t e = launch_band_tc(s, path, map, v, scratch);
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "no-alloc tensor-core star launch");
+}
+
+}  // namespace mms
+
+extern "C" mms_status mms_stencil_apply_noalloc(const mms_stencil_desc *desc, const float *in, float *out,
+                                                void *stream)
+{
+    return mms::apply_noalloc(desc, in, out, stream);
+}
