@@ -22,11 +22,11 @@
 // Split precision (3 products hi*hi + hi*lo + lo*hi, FP32 accumulation)
 // recovers FP32-level accuracy from BF16 or TF32 operands.
 //
-// Pipeline (persistent CTAs, one per SM, 16 warps in four roles, double
-// buffers handed over by mbarriers): TMA stages the FP32 box of group i+1
-// while converter warps turn group i into operand parts, one thread issues
-// the MMAs of group i-1 and the epilogue warps drain the TMEM accumulator
-// of group i-2.
+// Pipeline (persistent CTAs, one per SM, warps in four roles, buffers handed
+// over by mbarriers): TMA stages the FP32 planes of later groups while
+// converter warps turn them into operand parts, two issuer warps take turns
+// with the MMAs of groups i and i+1 (one TMEM accumulator each) and the
+// epilogue warps drain the accumulator of the group before.
 #include <cuda_bf16.h>
 #include <stdio.h>
 
@@ -133,7 +133,7 @@ struct Cfg {
     static constexpr int EG = EGF < NZ ? EGF : NZ;
     static constexpr int DSM_BYTES = EG * DSM_GROUP * 4;
     static constexpr int NCONV = LDG ? 5 : 4;        // converter warps: (0,) 2, 3 and the last two
-    static constexpr int NWARPS = 4 + 4 * EG + 2;
+    static constexpr int NWARPS = 4 + 4 * EG + 3;   // + the second MMA issuer (last warp)
     static constexpr int NT = 32 * NWARPS;
     static constexpr size_t FIXED = BASE + DSM_BYTES;
     static constexpr int NST = LDG                                           ? 0
@@ -196,12 +196,13 @@ struct TcArgs {
     int groups;                   // groups (of NZ planes) per tile
 };
 
-// Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2, 3 and
-// the last two warps = converters (FP32 box -> operand parts), 4 .. 4+4EG-1 =
-// epilogue, EG groups of four warps (warp w reaches TMEM lane quarter w % 4);
-// group e drains planes e, e+EG, ... of each accumulator.  Roles hand buffers
-// to each other through mbarriers, so TMA, conversion, MMA and epilogue of
-// different groups overlap.
+// Warp roles: 0 = TMA producer, 1 = MMA issuer of the even groups (and TMEM
+// owner), the last warp = MMA issuer of the odd groups, 2, 3 and the two
+// warps before the last = converters (FP32 box -> operand parts),
+// 4 .. 4+4EG-1 = epilogue, EG groups of four warps (warp w reaches TMEM lane
+// quarter w % 4); group e drains planes e, e+EG, ... of each accumulator.
+// Roles hand buffers to each other through mbarriers, so TMA, conversion,
+// MMA and epilogue of different groups overlap.
 
 __device__ __forceinline__ void named_sync(int id, int nthreads)
 {
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
         }
         for (int b = 0; b < C::CR; ++b) {
             ptx::mbar_init(&full_conv[b], CT);
-            ptx::mbar_init(&empty_conv[b], 1);
+            ptx::mbar_init(&empty_conv[b], C::H + 1);
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&full_d[b], 1);
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
         y0 = yt * C::TY;
         zt = zc * G * C::NZ;
     };
-    // Bounded wait for the single-thread roles; on expiry raise the abort flag.
+    // Bounded wait of the producer and MMA roles; on expiry raise the abort flag.
     [[maybe_unused]] unsigned long long waited = 0;  // role trace only
     auto wait = [&](uint64_t *b, uint32_t parity) -> bool {
         if (*abort_flag) return false;
@@ -337,40 +338,63 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
 
     if (warp == 0 && !LDG) {
         // ------------------------------------------- TMA producer: chunk k
-        if (lane == 0) {
-            [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
-            ptx::prefetch_tmap(&tmap);
-            for (int k = 0; k < nch; ++k) {
-                constexpr int NSTD = C::NST > 0 ? C::NST : 1;  // (this branch only runs with a ring)
-                const int st = k % NSTD;
-                if (!wait(&empty_stg[st], ((uint32_t)(k / NSTD) & 1u) ^ 1u)) break;
+        // (whole warp waits, one elected lane issues)
+        const bool leader = ptx::elect_one();
+        [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
+        if (leader) ptx::prefetch_tmap(&tmap);
+        for (int k = 0; k < nch; ++k) {
+            constexpr int NSTD = C::NST > 0 ? C::NST : 1;  // (this branch only runs with a ring)
+            const int st = k % NSTD;
+            const bool ok = wait(&empty_stg[st], ((uint32_t)(k / NSTD) & 1u) ^ 1u);
+            if (!__all_sync(0xffffffffu, ok)) {
+                *abort_flag = 1;
+                break;
+            }
+            if (leader) {
                 int x0, y0, zt;
                 tile_origin(k / CPT, x0, y0, zt);
                 ptx::mbar_arrive_expect_tx(&full_stg[st], C::STG_BYTES);
                 ptx::tma_load_3d(stg + (size_t)st * (C::STG_BYTES / 4), &tmap, x0, y0,
                                  zt + (k % CPT) * C::NZ + ZOFF, &full_stg[st]);
             }
+            __syncwarp();
+        }
+        if (lane == 0) {
             MMS_TRACE_ADD(0, 0, waited);
             MMS_TRACE_ADD(0, 1, MMS_CLOCK() - tstart);
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
-            [[maybe_unused]] unsigned long long wconv = 0, wacc = 0, tissue = 0;
-            for (int i = 0; i < ng; ++i) {
-                const int s = i & 1, g = i % G;
-                const int kg = (i / G) * CPT + g;  // first chunk of this group's window
-                bool ok = true;
-                unsigned long long w0 = waited;
-                for (int h = 0; h <= C::H && ok; ++h)
-                    ok = wait(&full_conv[(kg + h) % C::CR], (uint32_t)((kg + h) / C::CR) & 1u);
-                wconv += waited - w0;
-                w0 = waited;
-                if (!ok || !wait(&empty_d[s], ((uint32_t)(i >> 1) & 1u) ^ 1u)) break;
-                wacc += waited - w0;
-                [[maybe_unused]] const unsigned long long ti = MMS_CLOCK();
-                tc::fence_after_sync();
+    } else if (warp == 1 || warp == C::NWARPS - 1) {
+        // ----------------------------------------------------- MMA issuers
+        // Two warps alternate groups: warp 1 issues the even groups into
+        // accumulator 0, the last warp the odd ones into accumulator 1.  A
+        // warp's barrier polls wait behind its own MMAs still queued, so a
+        // single issuer leaves the tensor pipe idle at every group boundary;
+        // with two, one warp's queued MMAs cover the other's polls.  The
+        // whole warp runs the loop and waits; one elected lane issues.
+        const int s = warp == 1 ? 0 : 1;
+        const bool leader = ptx::elect_one();
+        [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
+        [[maybe_unused]] unsigned long long wconv = 0, wacc = 0, tissue = 0;
+        int last = -1;  // last group this warp issued
+        for (int i = s; i < ng; i += 2) {
+            const int g = i % G;
+            const int kg = (i / G) * CPT + g;  // first chunk of this group's window
+            bool ok = true;
+            unsigned long long w0 = waited;
+            for (int h = 0; h <= C::H && ok; ++h)
+                ok = wait(&full_conv[(kg + h) % C::CR], (uint32_t)((kg + h) / C::CR) & 1u);
+            wconv += waited - w0;
+            w0 = waited;
+            ok = ok && wait(&empty_d[s], ((uint32_t)(i >> 1) & 1u) ^ 1u);
+            wacc += waited - w0;
+            // every lane takes the same decision
+            if (!__all_sync(0xffffffffu, ok)) {
+                *abort_flag = 1;
+                break;
+            }
+            [[maybe_unused]] const unsigned long long ti = MMS_CLOCK();
+            tc::fence_after_sync();
+            if (leader) {
                 const uint32_t dcol = tbase + (uint32_t)(s * C::N);
                 const uint32_t cbase = ptx::smem_u32(conv) + (uint32_t)((kg % C::CR) * C::CHUNK_LINES * 16);
                 // one descriptor per group; each MMA adds a constant (>> 4) to its start field
@@ -395,14 +419,26 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
                         }
                     }
                 }
-                tissue += MMS_CLOCK() - ti;
-                tc::mma_commit(&full_d[s]);                 // accumulator ready for the epilogue
-                tc::mma_commit(&empty_conv[kg % C::CR]);    // chunk kg has no later reader
-                if (g == G - 1)                             // the tile's tail chunks neither
-                    for (int h = 1; h <= C::H; ++h) tc::mma_commit(&empty_conv[(kg + h) % C::CR]);
+                tc::mma_commit(&full_d[s]);  // accumulator ready for the epilogue
+                // A chunk slot is free again after H+1 arrivals: one from every
+                // group of the tile that reads the chunk, once its MMAs are
+                // done, and, for the chunks at the tile's ends that fewer
+                // groups read, the missing ones from their first reader.
+                for (int h = 0; h <= C::H; ++h) {
+                    const int c = g + h;  // tile-local chunk
+                    const int first = c - C::H > 0 ? c - C::H : 0;
+                    const int nread = (c < G - 1 ? c : G - 1) - first + 1;
+                    const int n = g == first ? C::H + 2 - nread : 1;
+                    for (int j = 0; j < n; ++j) tc::mma_commit(&empty_conv[(kg + h) % C::CR]);
+                }
             }
-            // every issued MMA completes before TMEM is freed at teardown
-            if (ng > 0) ptx::mbar_wait_bounded(&full_d[(ng - 1) & 1], (uint32_t)((ng - 1) >> 1) & 1u, err);
+            __syncwarp();
+            last = i;
+            tissue += MMS_CLOCK() - ti;
+        }
+        // every MMA this warp issued completes before TMEM is freed at teardown
+        if (last >= 0) ptx::mbar_wait_bounded(&full_d[s], (uint32_t)(last >> 1) & 1u, err);
+        if (lane == 0) {
             MMS_TRACE_ADD(1, 0, wconv);
             MMS_TRACE_ADD(1, 1, MMS_CLOCK() - tstart);
             MMS_TRACE_ADD(1, 2, wacc);
