@@ -82,6 +82,17 @@ def peaks():
     return 6800.0, 1900.0, 2070.0, "fallback"
 
 
+def bf16_sustained_peak():
+    """Measured BF16 dense peak of a seconds-long GEMM loop (the timed region
+    here is one), else the fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if "bf16_tflops_sustained" in d:
+            return d["bf16_tflops_sustained"], "measured sustained"
+    return 1700.0, "fallback sustained"
+
+
 def captured_traffic(key: str, points: int):
     """DRAM bytes of one launch from the committed ncu capture of this kernel
     (profiles/traffic.json), scaled by points; None when the kernel's sources
@@ -98,6 +109,21 @@ def captured_traffic(key: str, points: int):
         if not os.path.exists(path) or hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] != h:
             return None
     return rec["dram_bytes_per_point"] * points
+
+
+# x outputs per tile of the tensor-core box kernel by radius; its MMA K is
+# that plus 2r, rounded up to the instruction K (16 for BF16, 8 for TF32).
+TC_TXO = {1: 40, 2: 24, 3: 16, 4: 12}
+TC_PATHS = ("tf32", "3xtf32", "bf16x3")
+
+
+def tc_dense_flop_per_pt(path: str, r: int) -> int:
+    """Dense work the banded MMAs issue per output point (band zeros
+    included): 2 K_pad per (dz, dy) pass, (2r+1)^2 passes, times the split
+    products (3 for 3xTF32 / BF16x3, 1 for TF32)."""
+    step = 16 if path == "bf16x3" else 8
+    k_pad = -(-(TC_TXO[r] + 2 * r) // step) * step
+    return 2 * k_pad * (2 * r + 1) ** 2 * (1 if path == "tf32" else 3)
 
 
 def fp32_alu_peak_tflops(n_sm: int, mhz: float) -> float:
@@ -217,6 +243,8 @@ def main():
     ap.add_argument("--path", default="auto")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shots", type=int, default=0,
+                    help="shots of the wave workloads (0 = the workload's own: 8 for rtm512, 2 for grad256)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -344,7 +372,21 @@ def main():
     sec = kms[di] / 1e3
     bytes_alg = 4 * ((n + 2 * r) ** 3 + n ** 3)
     flops = flop_per_pt(shape, r) * n ** 3
-    if flops / bytes_alg > alu_peak * 1e12 / (hbm_peak * 1e9):
+    resolved = mms.auto_path(shape, r) if path_used == "auto" else path_used
+    if resolved in TC_PATHS and shape == "box":
+        # tensor pipe: the banded products' dense work against the BF16 peak
+        # (TF32 at the nominal TF32/BF16 ratio 1.1/2.25)
+        tpk, tsrc = bf16_sustained_peak()
+        if resolved != "bf16x3":
+            tpk, tsrc = tpk * 1.1 / 2.25, tsrc + " x 1.1/2.25 (TF32)"
+        dense = tc_dense_flop_per_pt(resolved, r) * n ** 3
+        roofline = {"bound": "tensor", "achieved": dense / sec / 1e12, "peak": tpk, "unit": "TFLOP/s",
+                    "frac": dense / sec / 1e12 / tpk, "traffic": None,
+                    "peak_note": f"MEASURED_PEAKS.json bf16 ({tsrc}); achieved counts the banded MMAs' "
+                                 f"dense work, {tc_dense_flop_per_pt(resolved, r)} flop/pt (band zeros "
+                                 f"included); the stencil's own {flop_per_pt(shape, r)} flop/pt run at "
+                                 f"{flops / sec / 1e12:.1f} TFLOP/s"}
+    elif flops / bytes_alg > alu_peak * 1e12 / (hbm_peak * 1e9):
         roofline = {"bound": "alu", "achieved": flops / sec / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": flops / sec / 1e12 / alu_peak, "traffic": None,
                     "peak_note": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz "
@@ -353,7 +395,6 @@ def main():
         roofline = {"bound": "hbm", "achieved": bytes_alg / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "frac": bytes_alg / sec / 1e9 / hbm_peak, "traffic": None,
                     "peak_note": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
-    resolved = mms.auto_path(shape, r) if path_used == "auto" else path_used
     var = mms.default_variant(shape, r, resolved, n, n, n)
     roofline["kernel"] = f"{shape} r={r} {n}^3 sweep ({resolved}, variant {var})"
     roofline["ms"] = kms[di]
@@ -426,6 +467,7 @@ def run_wave(args):
         n, nshots, nsteps, every = 512, 8, 500, 0
     else:
         n, nshots, nsteps, every = 256, 2, 200, 20
+    nshots = args.shots or nshots
     wi = workloads.WaveInputs(n, n, n, nshots=nshots, nsteps=nsteps, workload=4 if n == 512 else 5,
                               noise=True, salt=rank)
     prop = WavePropagator(n, n, n, wi.src, wi.zrec, wi.h, wi.dt, sponge_width=wi.sponge,
@@ -498,9 +540,12 @@ def run_wave(args):
         e2e = {"value": units / e2e_s / 1e9, "unit": "GPoint-steps/s", "h2d_bytes_per_step": h2d / steps,
                "d2h_bytes_per_step": d2h / steps}
         roof = {"bound": "hbm", "achieved": bytes_alg / elapsed / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "frac": bytes_alg / elapsed / 1e9 / hbm_peak, "traffic": None,
+                "frac": bytes_alg / elapsed / 1e9 / hbm_peak,
+                "traffic": captured_traffic("wave_fwd r=4", pts),
                 "kernel": "wave_fwd_kernel (fused star r=4 + leapfrog + sponge + source + receivers)",
                 "bytes_per_point_step": 16}
+        if roof["traffic"]:
+            roof["traffic_over_algorithmic"] = roof["traffic"] / (16.0 * pts)
         unit = "GPoint-steps/s"
     else:
         units = world * pts * nsteps * steps
