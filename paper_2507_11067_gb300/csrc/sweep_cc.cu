@@ -22,11 +22,13 @@
 // pitch and is the reference path of the library's own tests.
 #include <stdio.h>
 
-#include "common.cuh"
-#include "tile.cuh"
+#include "sweep_cc.cuh"
 
 namespace mms {
 namespace {
+
+using sweep::Variant;
+using sweep::launch_tiled;
 
 // ---------------------------------------------------------------- naive
 __global__ void naive_kernel(int shape, int r, const __grid_constant__ BoxCoef cf,
@@ -58,173 +60,17 @@ __global__ void naive_kernel(int shape, int r, const __grid_constant__ BoxCoef c
     }
 }
 
-template <int R, int TX, int TY, int PY, int S, bool BOX, typename Coef>
-__global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
-    sweep_cc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Coef cf,
-                    float *__restrict__ out, int nx, int ny, int nz, int64_t opy, int64_t opz,
-                    int tz, int vec_store, unsigned *err)
+using sweep::kBoxVariants;
+
+template <int R>
+cudaError_t dispatch_box(const Sweep &sw, const CUtensorMap &tmap, const BoxCoef &cf, int v)
 {
-    using G = Geom<R, TX, TY, PY, S>;
-    constexpr int W = G::W;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char *smem = smem_align128(smem_raw);
-    float *planes = reinterpret_cast<float *>(smem);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * G::STAGE * sizeof(float));
-    int &abort_flag = *reinterpret_cast<int *>(full + S);
-
-    const int tid = threadIdx.x;
-    const int tx = tid % G::NTX, ty = tid / G::NTX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, zb = blockIdx.z * tz;
-    const int nzt = min(tz, nz - zb);
-    const int P = nzt + 2 * R;  // padded planes this CTA consumes
-    const int ry0 = ty * PY;
-    const int gx = x0 + 4 * tx;
-
-    if (tid == 0) {
-        ptx::prefetch_tmap(&tmap);
-#pragma unroll
-        for (int s = 0; s < S; ++s) ptx::mbar_init(&full[s], 1);
-        ptx::fence_mbar_init();
-        abort_flag = 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int j = 0; j < S && j < P; ++j) {
-            ptx::mbar_arrive_expect_tx(&full[j], G::PLANE * sizeof(float));
-            ptx::tma_load_3d(planes + j * G::STAGE, &tmap, x0, y0, zb + j, &full[j]);
-        }
-    }
-
-    float acc[W][PY][4];
-#pragma unroll
-    for (int kk = 0; kk < W; ++kk)
-#pragma unroll
-        for (int i = 0; i < PY; ++i)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[kk][i][k] = 0.f;
-
-    for (int j = 0; j < P; ++j) {
-        const int s = j % S;
-        if (ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err)) {
-            const float *pl = planes + s * G::STAGE;
-            if constexpr (BOX)
-                box_plane<R, PY, G::BX, G::NV>(pl, cf, acc, tx, ry0);
-            else {
-                float ctr[PY][4];
-                star_plane<R, PY, G::BX, G::NV>(pl, cf, acc, ctr, tx, ry0);
-            }
-        } else {
-            abort_flag = 1;
-        }
-        __syncthreads();  // every thread is done with stage s
-        if (abort_flag) return;
-        if (tid == 0 && j + S < P) {
-            ptx::mbar_arrive_expect_tx(&full[s], G::PLANE * sizeof(float));
-            ptx::tma_load_3d(planes + s * G::STAGE, &tmap, x0, y0, zb + j + S, &full[s]);
-        }
-        const int zo = j - 2 * R;  // output plane completed by plane j
-        if (zo >= 0) {
-            const int64_t zoff = (int64_t)(zb + zo) * opz;
-#pragma unroll
-            for (int i = 0; i < PY; ++i) {
-                const int y = y0 + ry0 + i;
-                if (y < ny && gx < nx) {
-                    float *o = out + zoff + (int64_t)y * opy + gx;
-                    if (vec_store && gx + 3 < nx) {
-                        *reinterpret_cast<float4 *>(o) =
-                            make_float4(acc[0][i][0], acc[0][i][1], acc[0][i][2], acc[0][i][3]);
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if (gx + k < nx) o[k] = acc[0][i][k];
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int kk = 0; kk < W - 1; ++kk)
-#pragma unroll
-            for (int i = 0; i < PY; ++i)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc[kk][i][k] = acc[kk + 1][i][k];
-#pragma unroll
-        for (int i = 0; i < PY; ++i)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[W - 1][i][k] = 0.f;
-    }
-}
-
-struct Variant { int tx, ty, py, s, tz; };
-
-// Tile variants (TX, TY, PY, stages, TZ) of the CUDA-core sweeps.
-constexpr Variant kStarVariants[] = {
-    {64, 32, 2, 4, 128}, {64, 16, 2, 4, 128}, {128, 16, 2, 4, 128}, {64, 32, 4, 3, 128},
-    {64, 32, 2, 4, 64},  {128, 32, 2, 3, 64}, {64, 16, 1, 3, 128}, {64, 16, 1, 4, 256},
-};
-constexpr Variant kBoxVariants[] = {
-    {64, 16, 2, 3, 64}, {64, 32, 2, 3, 64}, {32, 16, 2, 3, 64}, {64, 16, 4, 3, 64},
-    {64, 8, 2, 3, 128}, {128, 16, 2, 3, 32}, {64, 16, 1, 3, 128}, {64, 8, 1, 3, 128},
-};
-constexpr int kNumStar = sizeof(kStarVariants) / sizeof(Variant);
-constexpr int kNumBox = sizeof(kBoxVariants) / sizeof(Variant);
-
-template <int R, int TX, int TY, int PY, int S, bool BOX, typename Coef>
-cudaError_t launch_tiled(const Sweep &sw, const CUtensorMap &tmap, const Coef &cf, int tz)
-{
-    using G = Geom<R, TX, TY, PY, S>;
-    auto kern = sweep_cc_kernel<R, TX, TY, PY, S, BOX, Coef>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((sw.nx + TX - 1) / TX), (unsigned)((sw.ny + TY - 1) / TY),
-                    (unsigned)((sw.nz + tz - 1) / tz));
-    const int vec = ((sw.opy % 4) == 0 && (sw.opz % 4) == 0 &&
-                     (reinterpret_cast<uintptr_t>(sw.out) % 16) == 0)
-                        ? 1
-                        : 0;
-    kern<<<grid, G::NT, G::SMEM, sw.stream>>>(tmap, cf, sw.out, (int)sw.nx, (int)sw.ny,
-                                               (int)sw.nz, sw.opy, sw.opz, tz, vec,
-                                               device_error_word());
-    return cudaGetLastError();
-}
-
-template <int R, bool BOX, typename Coef>
-cudaError_t dispatch_variant(const Sweep &sw, const CUtensorMap &tmap, const Coef &cf, int v)
-{
-    const Variant *tab = BOX ? kBoxVariants : kStarVariants;
-    const int tz = tab[v].tz;
-#define MMS_CASE(I)                                                                          \
-    case I:                                                                                  \
-        return launch_tiled<R, (BOX ? kBoxVariants : kStarVariants)[I].tx,                   \
-                            (BOX ? kBoxVariants : kStarVariants)[I].ty,                      \
-                            (BOX ? kBoxVariants : kStarVariants)[I].py,                      \
-                            (BOX ? kBoxVariants : kStarVariants)[I].s, BOX, Coef>(sw, tmap, cf, \
-                                                                                   tz);
-    switch (v) {
-        MMS_CASE(0)
-        MMS_CASE(1)
-        MMS_CASE(2)
-        MMS_CASE(3)
-        MMS_CASE(4)
-        MMS_CASE(5)
-        MMS_CASE(6)
-        MMS_CASE(7)
-        default: return cudaErrorInvalidValue;
-    }
-#undef MMS_CASE
+    MMS_SWEEP_DISPATCH(kBoxVariants, R, true, BoxCoef, sw, tmap, cf, v)
 }
 
 }  // namespace
 
-int star_cc_variants() { return kNumStar; }
-int box_cc_variants() { return kNumBox; }
-
-void star_cc_box(int r, int v, int *bx, int *by)
-{
-    const Variant &t = kStarVariants[v];
-    *bx = (t.tx + 2 * r + 3) & ~3;
-    *by = t.ty + 2 * r;
-}
+int box_cc_variants() { return sweep::kNumBox; }
 
 void box_cc_box(int r, int v, int *bx, int *by)
 {
@@ -248,30 +94,16 @@ cudaError_t launch_naive(const Sweep &s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_star_cc(const Sweep &s, const CUtensorMap &tmap, int v)
-{
-    StarCoef cf{};
-    const int w = 2 * s.r + 1;
-    for (int i = 0; i < 3 * w; ++i) cf.c[i] = s.coeffs[i];
-    switch (s.r) {
-        case 1: return dispatch_variant<1, false>(s, tmap, cf, v);
-        case 2: return dispatch_variant<2, false>(s, tmap, cf, v);
-        case 3: return dispatch_variant<3, false>(s, tmap, cf, v);
-        case 4: return dispatch_variant<4, false>(s, tmap, cf, v);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 cudaError_t launch_box_cc(const Sweep &s, const CUtensorMap &tmap, int v)
 {
     BoxCoef cf{};
     const int w = 2 * s.r + 1;
     for (int i = 0; i < w * w * w; ++i) cf.c[i] = s.coeffs[i];
     switch (s.r) {
-        case 1: return dispatch_variant<1, true>(s, tmap, cf, v);
-        case 2: return dispatch_variant<2, true>(s, tmap, cf, v);
-        case 3: return dispatch_variant<3, true>(s, tmap, cf, v);
-        case 4: return dispatch_variant<4, true>(s, tmap, cf, v);
+        case 1: return dispatch_box<1>(s, tmap, cf, v);
+        case 2: return dispatch_box<2>(s, tmap, cf, v);
+        case 3:
+        case 4: return sweep::launch_box_cc_high(s, tmap, cf, v);
         default: return cudaErrorInvalidValue;
     }
 }

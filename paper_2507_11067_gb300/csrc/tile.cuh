@@ -64,10 +64,14 @@ __device__ __forceinline__ void load_center(const float *p, float (&v)[4])
     }
 }
 
+// Queue slots: logical slot kk (output plane j - 2R + kk for input plane j)
+// lives in acc[(kk + ROT) % (2R+1)]; ROT = 0 for a queue that is shifted
+// after every plane, a compile-time rotation for one that is not.
+//
 // Star: plane j adds c_z[R-kk] * centre to the output plane at queue slot kk
 // and its in-plane x/y part to slot R (the plane it centres); the centre
 // values of the thread's points are returned in ctr.
-template <int R, int PY, int BX, int NV>
+template <int R, int PY, int BX, int NV, int ROT = 0>
 __device__ __forceinline__ void star_plane(const float *pl, const StarCoef &cf,
                                            float (&acc)[2 * R + 1][PY][4], float (&ctr)[PY][4],
                                            int tx, int ry0)
@@ -89,17 +93,17 @@ __device__ __forceinline__ void star_plane(const float *pl, const StarCoef &cf,
             for (int d = -R; d <= R; ++d) xy = fmaf(cf.c[0 * W + d + R], win[k + R + d], xy);
 #pragma unroll
             for (int d = -R; d <= R; ++d) xy = fmaf(cf.c[1 * W + d + R], cen[i + R + d][k], xy);
-            acc[R][i][k] += xy;
+            acc[(R + ROT) % W][i][k] += xy;
 #pragma unroll
             for (int kk = 0; kk < W; ++kk)
-                acc[kk][i][k] = fmaf(cf.c[2 * W + 2 * R - kk], c0, acc[kk][i][k]);
+                acc[(kk + ROT) % W][i][k] = fmaf(cf.c[2 * W + 2 * R - kk], c0, acc[(kk + ROT) % W][i][k]);
         }
     }
 }
 
 // Box: window row rr of the plane feeds output row i with dy = rr - R - i;
 // slot kk (output plane z_o) takes the weights of dz = R - kk.
-template <int R, int PY, int BX, int NV>
+template <int R, int PY, int BX, int NV, int ROT = 0>
 __device__ __forceinline__ void box_plane(const float *pl, const BoxCoef &cf,
                                           float (&acc)[2 * R + 1][PY][4], int tx, int ry0)
 {
@@ -117,11 +121,11 @@ __device__ __forceinline__ void box_plane(const float *pl, const BoxCoef &cf,
                 const int dz = R - kk;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    float a = acc[kk][i][k];
+                    float a = acc[(kk + ROT) % W][i][k];
 #pragma unroll
                     for (int dx = -R; dx <= R; ++dx)
                         a = fmaf(cf.c[((dz + R) * W + dy + R) * W + dx + R], row[k + R + dx], a);
-                    acc[kk][i][k] = a;
+                    acc[(kk + ROT) % W][i][k] = a;
                 }
             }
         }
