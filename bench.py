@@ -70,6 +70,23 @@ def sweep_input(shape, r, n, rank):
     return workloads.uniform_grid(n, n, n, r, workload=2, salt=r + 100 * rank)
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's x (x itself without a process group):
+    the job's time is its slowest rank's."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput in G units per second: every rank processes
+    units_per_rank (weak scaling) in `seconds` (the slowest rank's time)."""
+    return world * units_per_rank / seconds / 1e9
+
+
 def flop_per_pt(shape, r):
     return 2 * (6 * r + 1 if shape == "star" else (2 * r + 1) ** 3)
 
@@ -320,13 +337,9 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    elapsed = t_start.elapsed_time(t_end) / 1e3
-    if dist:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(t_start.elapsed_time(t_end) / 1e3, dist, dev)
     pts_step = sum(n ** 3 for _, _, n in plan)
-    value = world * pts_step * steps / elapsed / 1e9
+    value = job_rate(world, pts_step * steps, elapsed)
     kms = [statistics.mean(a.elapsed_time(b) for a, b in ev) for ev in kernel_ev]
 
     # ---- end to end through the public API: host in, host out, every step
@@ -350,14 +363,12 @@ def main():
         e2e_step()
     e_e.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e_s.elapsed_time(e_e) / 1e3
     if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        dist.barrier()
+    e2e_s = max_over_ranks(e_s.elapsed_time(e_e) / 1e3, dist, dev)
     h2d = sum(h.untyped_storage().nbytes() for h in hosts)
     d2h = sum(h.numel() * 4 for h in host_out)
-    e2e_value = world * pts_step * e2e_steps / e2e_s / 1e9
+    e2e_value = job_rate(world, pts_step * e2e_steps, e2e_s)
 
     if rank != 0:
         if dist:
@@ -514,12 +525,10 @@ def run_wave(args):
         out = run()
     t1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    elapsed = t0.elapsed_time(t1) / 1e3
     if dist:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3, dist, dev)
     pts = nshots * n ** 3
     if args.workload == "rtm512":
         units = world * pts * steps
@@ -533,12 +542,14 @@ def run_wave(args):
         rec_host = rec.to("cpu")
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_s = e0.elapsed_time(e1) / 1e3
+        if dist:
+            dist.barrier()
+        e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
         h2d = v_host.numel() * 4 + amps_host.numel() * 4
         d2h = rec_host.numel() * 4
-        value = units / elapsed / 1e9
-        e2e = {"value": units / e2e_s / 1e9, "unit": "GPoint-steps/s", "h2d_bytes_per_step": h2d / steps,
-               "d2h_bytes_per_step": d2h / steps}
+        value = job_rate(world, pts * steps, elapsed)
+        e2e = {"value": job_rate(world, pts * steps, e2e_s), "unit": "GPoint-steps/s",
+               "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps}
         roof = {"bound": "hbm", "achieved": bytes_alg / elapsed / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": bytes_alg / elapsed / 1e9 / hbm_peak,
                 "traffic": captured_traffic("wave_fwd r=4", pts),
@@ -549,9 +560,27 @@ def run_wave(args):
         unit = "GPoint-steps/s"
     else:
         units = world * pts * nsteps * steps
-        value = units / elapsed / 1e9
-        e2e = {"value": value, "unit": "GPoint-steps/s (forward + gradient)", "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": 0}
+        value = job_rate(world, pts * nsteps * steps, elapsed)
+        # end to end: starting velocity, wavelet and observed records in from
+        # pinned host memory, the velocity gradient out, one gradient per step
+        v0_host = v0.cpu().pin_memory()
+        obs_host = obs.cpu().pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vv = v0_host.to(dev, non_blocking=True).requires_grad_(True)
+        aa = amps_host.to(dev, non_blocking=True)
+        oo = obs_host.to(dev, non_blocking=True)
+        rec = WaveFunction.apply(vv, prop, aa, nsteps, every)
+        (0.5 * ((rec - oo) ** 2).sum()).backward()
+        g_host = vv.grad.to("cpu")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+        e2e = {"value": job_rate(world, pts * nsteps, e2e_s), "unit": "GPoint-steps/s (forward + gradient)",
+               "h2d_bytes_per_step": v0_host.numel() * 4 + amps_host.numel() * 4 + obs_host.numel() * 4,
+               "d2h_bytes_per_step": g_host.numel() * g_host.element_size()}
         # forward 16 B + recompute 16 B (+8 B copy) + adjoint 20 B + FP64 gradient RMW 16 B per point-step
         bytes_alg = 76.0 * pts * nsteps * steps
         roof = {"bound": "hbm", "achieved": bytes_alg / elapsed / 1e9, "peak": hbm_peak, "unit": "GB/s",
