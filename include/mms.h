@@ -105,9 +105,11 @@ typedef struct {
  * variant.  The TMA-staged paths need in_pitch_y*4 and in_pitch_z*4 to be
  * multiples of 16 bytes and `in` 16-byte aligned; with MMS_PATH_AUTO an
  * input that breaks this runs on MMS_PATH_NAIVE, with a forced TMA path it
- * returns MMS_E_ALIGN.  Tensor-core paths support the box shape with
- * radius 1..4 and the star shape (as three per-axis banded passes) and
- * return MMS_E_UNSUPPORTED otherwise.
+ * returns MMS_E_ALIGN.  Tensor-core paths support the box and the star of
+ * radius 1..4.  The star runs in two passes: its in-plane x/y part on the
+ * tensor cores into a temporary grid of nx*ny*nz floats, taken from the
+ * device's stream-ordered memory pool (cudaMallocAsync on `stream`, freed on
+ * it after use), then its z part on the CUDA cores.
  * Defined by: paper Sec. 1, Sec. 4.1 (banded products), Sec. 4.3 (box as
  * 2r+1 shifted 1D stencils per plane).
  */
@@ -185,6 +187,10 @@ typedef struct {
     float sponge_a;            /* a */
     int32_t rec_z;             /* receiver plane (interior z), -1 = no records */
     const int32_t *src_xyz;    /* host, 3*nshots interior (x,y,z); x < 0 = no source */
+    int64_t grad_shot_stride;  /* mms_wave_adjoint's gradient: 0 = one nz*ny*nx slice that all
+                                  shots add to; >= nz*ny*nx = shot s adds to its own slice at
+                                  grad_m + s*grad_shot_stride (no atomics; sum the slices with
+                                  mms_sum_f64) */
 } mms_wave_desc;
 
 /*
@@ -198,6 +204,18 @@ typedef struct {
 mms_status mms_wave_step(const mms_wave_desc *desc, const float *coeffs, const float *m,
                          const float *p_cur, float *p_prev, const float *src_amp, float *rec,
                          void *stream);
+
+/*
+ * The step of mms_wave_step with a^{n+1} written to p_next instead of over
+ * a^{n-1}: p_prev is read only.  p_next may equal p_prev (then this is
+ * mms_wave_step); otherwise it must overlap neither p_cur nor p_prev, and
+ * its halo is left as it is (the caller keeps it zero).  Checkpoint
+ * recomputation uses it to lay a segment's states out without copies.
+ * Defined by: the step above (paper Sec. 2.1, Sec. 5.5 for the RTM setting).
+ */
+mms_status mms_wave_step_to(const mms_wave_desc *desc, const float *coeffs, const float *m,
+                            const float *p_cur, const float *p_prev, float *p_next,
+                            const float *src_amp, float *rec, void *stream);
 
 /* Flags of mms_wave_forward. */
 #define MMS_WAVE_GRAPH 1u  /* capture the step sequence once into a CUDA graph and replay it */
@@ -222,8 +240,11 @@ mms_status mms_wave_forward(const mms_wave_desc *desc, const float *coeffs, cons
  * lam_cur: device lam^{n+1} (padded, zero halo); lam_prev: device, in
  * lam^{n+2}, out lam^n; resid: device nshots*ny*nx r^n on the receiver plane
  * (NULL = none); a_n: device forward state a^n (NULL = no gradient term);
- * grad_m: device nz*ny*nx doubles (dense), accumulated.  m must be padded
- * (its halo values are multiplied by the zero halo of lam).
+ * grad_m: device nz*ny*nx doubles (dense), accumulated: with
+ * desc->grad_shot_stride = 0 every shot adds to it (FP64 atomics); with a
+ * stride, shot s adds to grad_m + s*stride only (plain read-modify-write),
+ * nshots slices in all.  m must be padded (its halo values are multiplied by
+ * the zero halo of lam).
  */
 mms_status mms_wave_adjoint(const mms_wave_desc *desc, const float *coeffs, const float *m,
                             const float *lam_cur, float *lam_prev, const float *resid,
@@ -239,6 +260,13 @@ mms_status mms_grad_to_velocity(const double *grad_m, const float *v, double *gr
 
 /* result[0] = sum_i a[i]*b[i] in FP64 over n floats (device in, device out). */
 mms_status mms_dot_f64(const float *a, const float *b, int64_t n, double *result, void *stream);
+
+/* out[i] = sum_{s < nslices} slices[s*stride + i], i < n, in FP64 (device in,
+ * device out): the per-shot gradient slices of mms_wave_adjoint summed.
+ * stride >= n; out may be slices itself (the first slice) but no other
+ * slice.  Plumbing of the gradient path (paper silent on the adjoint). */
+mms_status mms_sum_f64(const double *slices, int32_t nslices, int64_t stride, int64_t n, double *out,
+                       void *stream);
 
 /* ------------------------------------------------------------ status */
 

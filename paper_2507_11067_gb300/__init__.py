@@ -9,12 +9,13 @@ loudly if the library has not been built.
 from ._lib import (BOX, PATHS, STAR, MMSError, apply, apply_dense, auto_path, check_device,
                    default_variant,
                    dot_f64, field_geometry, grad_to_velocity, load, model_from_velocity,
-                   num_variants, padded_empty, pitches, set_variant, to_padded_device, version,
-                   wave_adjoint, wave_desc, wave_forward, wave_step)
+                   num_variants, padded_empty, pitches, set_variant, sum_f64, to_padded_device,
+                   version, wave_adjoint, wave_desc, wave_forward, wave_step, wave_step_to)
 from .build import build
 
 __all__ = ["BOX", "PATHS", "STAR", "MMSError", "apply", "apply_dense", "auto_path", "build",
            "check_device",
            "default_variant", "dot_f64", "field_geometry", "grad_to_velocity", "load",
-           "model_from_velocity", "num_variants", "padded_empty", "pitches", "set_variant",
-           "to_padded_device", "version", "wave_adjoint", "wave_desc", "wave_forward", "wave_step"]
+           "model_from_velocity", "num_variants", "padded_empty", "pitches", "set_variant", "sum_f64",
+           "to_padded_device", "version", "wave_adjoint", "wave_desc", "wave_forward", "wave_step",
+           "wave_step_to"]

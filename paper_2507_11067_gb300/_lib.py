@@ -29,7 +29,8 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_default_variant",
            "mms_set_variant", "mms_wave_step", "mms_wave_forward", "mms_wave_adjoint",
            "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
-           "mms_check_device", "mms_version", "mms_stencil_apply_noalloc"]
+           "mms_check_device", "mms_version", "mms_stencil_apply_noalloc", "mms_wave_step_to",
+           "mms_sum_f64"]
 
 
 class MMSError(RuntimeError):
@@ -53,7 +54,7 @@ class WaveDesc(ctypes.Structure):
                 ("pitch_y", ctypes.c_int64), ("pitch_z", ctypes.c_int64),
                 ("shot_stride", ctypes.c_int64), ("sponge_width", ctypes.c_int32),
                 ("sponge_a", ctypes.c_float), ("rec_z", ctypes.c_int32),
-                ("src_xyz", ctypes.c_void_p)]
+                ("src_xyz", ctypes.c_void_p), ("grad_shot_stride", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -87,6 +88,8 @@ def load():
             "mms_default_variant": [i32, i32, i32, i64, i64, i64],
             "mms_set_variant": [i32, i32, i32, i32],
             "mms_wave_step": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P],
+            "mms_wave_step_to": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
+            "mms_sum_f64": [P, i32, i64, i64, P, P],
             "mms_wave_forward": [ctypes.POINTER(WaveDesc), P, P, P, i32, P, P, P, P, i32,
                                  ctypes.c_uint32, P],
             "mms_wave_adjoint": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
@@ -247,7 +250,7 @@ def version() -> str:
 # ------------------------------------------------------------------ wave
 
 def wave_desc(nx, ny, nz, r, nshots, pitch_y=0, pitch_z=0, shot_stride=0, sponge_width=0,
-              sponge_a=0.0, rec_z=-1, src=None):
+              sponge_a=0.0, rec_z=-1, src=None, grad_shot_stride=0):
     """A WaveDesc plus the host source array it points to (keep both alive)."""
     src_arr = None
     if src is not None:
@@ -255,7 +258,8 @@ def wave_desc(nx, ny, nz, r, nshots, pitch_y=0, pitch_z=0, shot_stride=0, sponge
         if src_arr.size != 3 * nshots:
             raise ValueError("src needs 3 coordinates per shot")
     d = WaveDesc(nx, ny, nz, r, nshots, pitch_y, pitch_z, shot_stride, sponge_width,
-                 float(sponge_a), rec_z, None if src_arr is None else src_arr.ctypes.data)
+                 float(sponge_a), rec_z, None if src_arr is None else src_arr.ctypes.data,
+                 int(grad_shot_stride))
     return d, src_arr
 
 
@@ -271,6 +275,14 @@ def wave_step(desc, coeffs, m, p_cur, p_prev, src_amp, rec=None, stream=None):
     check(load().mms_wave_step(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                _ptr(p_cur), _ptr(p_prev), _ptr(src_amp), _ptr(rec),
                                _stream(stream)))
+
+
+def wave_step_to(desc, coeffs, m, p_cur, p_prev, p_next, src_amp, rec=None, stream=None):
+    """mms_wave_step_to: a^{n+1} into p_next, p_prev read only."""
+    c = _host_coeffs(coeffs)
+    check(load().mms_wave_step_to(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
+                                  _ptr(p_cur), _ptr(p_prev), _ptr(p_next), _ptr(src_amp), _ptr(rec),
+                                  _stream(stream)))
 
 
 def wave_forward(desc, coeffs, m, amps, nsteps, p0, p1, rec_all=None, ckpt=None, ckpt_every=0,
@@ -298,6 +310,15 @@ def model_from_velocity(desc, v, m, dt, h, stream=None):
 def grad_to_velocity(grad_m, v, grad_v, dt, h, stream=None):
     check(load().mms_grad_to_velocity(_ptr(grad_m), _ptr(v), _ptr(grad_v), grad_m.numel(),
                                       float(dt), float(h), _stream(stream)))
+
+
+def sum_f64(slices, out, stream=None):
+    """out = slices.sum(0) in FP64 (mms_sum_f64); slices (k, ...) contiguous,
+    out a tensor of the slice shape (may be slices[0])."""
+    k = slices.shape[0]
+    n = slices[0].numel()
+    check(load().mms_sum_f64(_ptr(slices), int(k), slices.stride(0), n, _ptr(out), _stream(stream)))
+    return out
 
 
 def dot_f64(a, b, result, stream=None):

@@ -309,6 +309,9 @@ static mms_status wave_geo(const mms_wave_desc *d, const float *coeffs, WaveGeo 
     g->sponge_w = d->sponge_width;
     g->sponge_a = d->sponge_a;
     g->rec_z = d->rec_z;
+    g->gss = d->grad_shot_stride;
+    if (g->gss != 0 && g->gss < d->nx * d->ny * d->nz)
+        return fail(MMS_E_ARG, "gradient shot stride %lld below the interior size", (long long)g->gss);
     for (int s = 0; s < d->nshots; ++s) {
         int x = -1, y = -1, z = -1;
         if (d->src_xyz) { x = d->src_xyz[3 * s]; y = d->src_xyz[3 * s + 1]; z = d->src_xyz[3 * s + 2]; }
@@ -354,7 +357,27 @@ mms_status mms_wave_step(const mms_wave_desc *desc, const float *coeffs, const f
     if (!m || !p_cur || !p_prev || !src_amp) return fail(MMS_E_ARG, "null field pointer");
     if (!al16(m) || !al16(p_cur) || !al16(p_prev)) return fail(MMS_E_ALIGN, "wave fields must be 16-byte aligned");
     if (overlaps(p_cur, field_bytes(g), p_prev, field_bytes(g))) return fail(MMS_E_ARG, "p_cur and p_prev overlap");
-    cudaError_t e = launch_wave_fwd(g, coeffs, m, p_cur, p_prev, src_amp, rec, reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_wave_fwd(g, coeffs, m, p_cur, p_prev, p_prev, src_amp, rec,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "wave step launch");
+}
+
+mms_status mms_wave_step_to(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *p_cur,
+                            const float *p_prev, float *p_next, const float *src_amp, float *rec, void *stream)
+{
+    WaveGeo g;
+    mms_status st = wave_geo(desc, coeffs, &g);
+    if (st != MMS_OK) return st;
+    if (!m || !p_cur || !p_prev || !p_next || !src_amp) return fail(MMS_E_ARG, "null field pointer");
+    if (!al16(m) || !al16(p_cur) || !al16(p_prev) || !al16(p_next))
+        return fail(MMS_E_ALIGN, "wave fields must be 16-byte aligned");
+    const size_t fb = field_bytes(g);
+    if (overlaps(p_cur, fb, p_prev, fb)) return fail(MMS_E_ARG, "p_cur and p_prev overlap");
+    if (overlaps(p_cur, fb, p_next, fb)) return fail(MMS_E_ARG, "p_cur and p_next overlap");
+    if (p_next != p_prev && overlaps(p_prev, fb, p_next, fb))
+        return fail(MMS_E_ARG, "p_prev and p_next overlap without being the same field");
+    cudaError_t e = launch_wave_fwd(g, coeffs, m, p_cur, p_prev, p_next, src_amp, rec,
+                                    reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "wave step launch");
 }
 
@@ -388,7 +411,8 @@ mms_status mms_wave_forward(const mms_wave_desc *desc, const float *coeffs, cons
                 if (e == cudaSuccess) e = cudaMemcpyAsync(slot + fb, bufs[1 - c], fb, cudaMemcpyDeviceToDevice, s);
                 if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
             }
-            cudaError_t e = launch_wave_fwd(g, coeffs, m, bufs[c], bufs[1 - c], amps + (int64_t)n * g.nshots,
+            cudaError_t e = launch_wave_fwd(g, coeffs, m, bufs[c], bufs[1 - c], bufs[1 - c],
+                                            amps + (int64_t)n * g.nshots,
                                             rec_all ? rec_all + n * rec_step : nullptr, s);
             if (e != cudaSuccess) return cuda_fail(e, "wave step launch");
             c = 1 - c;
@@ -487,6 +511,23 @@ mms_status mms_grad_to_velocity(const double *grad_m, const float *v, double *gr
     if (!(dt > 0.f) || !(h > 0.f)) return fail(MMS_E_ARG, "dt and h must be positive");
     cudaError_t e = launch_grad_to_velocity(grad_m, v, grad_v, n, dt, h, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "chain-rule kernel launch");
+}
+
+mms_status mms_sum_f64(const double *slices, int32_t nslices, int64_t stride, int64_t n, double *out,
+                       void *stream)
+{
+    if (n < 0) return fail(MMS_E_ARG, "negative length");
+    if (nslices < 1) return fail(MMS_E_ARG, "nslices %d below 1", nslices);
+    if (nslices > 1 && stride < n) return fail(MMS_E_ARG, "slice stride %lld below the length", (long long)stride);
+    if (n == 0) return MMS_OK;
+    if (!slices || !out) return fail(MMS_E_ARG, "null pointer");
+    for (int s = 1; s < nslices; ++s)
+        if (overlaps(out, (size_t)n * 8, slices + (int64_t)s * stride, (size_t)n * 8))
+            return fail(MMS_E_ARG, "out overlaps slice %d", s);
+    if (out != slices && overlaps(out, (size_t)n * 8, slices, (size_t)n * 8))
+        return fail(MMS_E_ARG, "out overlaps the first slice without being it");
+    cudaError_t e = launch_sum_f64(slices, nslices, stride, n, out, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "sum kernel launch");
 }
 
 mms_status mms_dot_f64(const float *a, const float *b, int64_t n, double *result, void *stream)

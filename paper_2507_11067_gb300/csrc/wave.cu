@@ -35,6 +35,23 @@ unsigned *device_error_word()
 
 namespace {
 
+// FP32 -> FP64 by the IEEE-754 layouts (sign kept, exponent rebased by
+// 1023 - 127, fraction shifted up 29 bits), on the integer units: GB300's
+// FP64 pipe issues about two instructions per clock per SM, which a
+// conversion per point and plane would saturate.  Exact for normal numbers,
+// zero, infinities and NaN; FP32 denormals (below 1.2e-38) become zero.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    uint64_t d = (uint64_t)(u & 0x80000000u) << 32;
+    if (e == 0xffu)
+        d |= (uint64_t)0x7ffu << 52 | (uint64_t)(u & 0x7fffffu) << 29;
+    else if (e != 0u)
+        d |= (uint64_t)(e + 896u) << 52 | (uint64_t)(u & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)d);
+}
+
 // Cerjan sponge factor of cell i of n (distance d to the nearest face).
 __device__ __forceinline__ float sponge(int i, int n, int w, float a)
 {
@@ -77,7 +94,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     wave_fwd_kernel(const __grid_constant__ CUtensorMap tcur, const __grid_constant__ CUtensorMap tm,
                     const __grid_constant__ CUtensorMap tprev, const __grid_constant__ CUtensorMap tctr,
                     const __grid_constant__ StarCoef cf,
-                    const __grid_constant__ WaveGeo geo, float *__restrict__ pprev,
+                    const __grid_constant__ WaveGeo geo, float *__restrict__ pnext,
                     const float *__restrict__ amp, float *__restrict__ rec, int tz, int nzc, int vec,
                     unsigned *err)
 {
@@ -174,7 +191,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                 const int y = y0 + ry0 + i;
                 if (y >= geo.ny || gx >= geo.nx) continue;
                 const int64_t mp = (int64_t)(z + R) * geo.pz + (int64_t)(y + R) * geo.py + (gx + R);
-                float *pp = pprev + shot_off + mp;
+                float *pp = pnext + shot_off + mp;
                 float res[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -237,7 +254,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
                     const __grid_constant__ CUtensorMap tl1, const __grid_constant__ StarCoef cf,
                     const __grid_constant__ WaveGeo geo, float *__restrict__ lprev,
                     const float *__restrict__ resid, double *__restrict__ grad, int has_a, int tz,
-                    int nzc, unsigned *err)
+                    int nzc, int gvec, unsigned *err)
 {
     constexpr int PY = 1;
     using G = Geom<R, TX, TY, PY, S>;
@@ -304,28 +321,45 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
     const float gys0 = gyt[ry0 + R];
     const int64_t shot_off = (int64_t)sh * geo.ss;
 
-    for (int j = 0; j < P; ++j) {
+    // Input plane j; the oldest partial sums (output plane j - 2R) are in
+    // queue slot 0.  Returns false when the CTA aborts.  (Rotating the two
+    // queues instead of shifting them, as the sweeps do, spills registers
+    // here and was measured slower.)
+    auto plane = [&](int j) -> bool {
+        constexpr int Q = 0;
         const int s = j % S;
         const float *st = base + (size_t)s * A::STAGE;
         const int zo = j - 2 * R;
         const bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err);
         if (ok) {
-            // q = m * g * lam^{n+1} over the whole staged plane
+            // q = m * g * lam^{n+1} over the whole staged plane, four columns
+            // per item (the staged rows are 16-byte multiples)
             const float gzp = sponge(zb + j - R, geo.nz, geo.sponge_w, geo.sponge_a);
-            for (int e = tid; e < G::PLANE; e += G::NT) {
-                const int c = e % G::BX, rr = e / G::BX;
-                qbuf[e] = st[A::PL + e] * (gxt[c] * gyt[rr] * gzp) * st[e];
+            constexpr int BX4 = G::BX / 4;
+            for (int e4 = tid; e4 < BX4 * G::BY; e4 += G::NT) {
+                const int c4 = e4 % BX4, rr = e4 / BX4;
+                const int e = rr * G::BX + 4 * c4;
+                const float4 lv = *reinterpret_cast<const float4 *>(st + e);
+                const float4 mv = *reinterpret_cast<const float4 *>(st + A::PL + e);
+                const float4 gx = *reinterpret_cast<const float4 *>(gxt + 4 * c4);
+                const float gy = gyt[rr];
+                float4 q;
+                q.x = mv.x * (gx.x * gy * gzp) * lv.x;
+                q.y = mv.y * (gx.y * gy * gzp) * lv.y;
+                q.z = mv.z * (gx.z * gy * gzp) * lv.z;
+                q.w = mv.w * (gx.w * gy * gzp) * lv.w;
+                *reinterpret_cast<float4 *>(qbuf + e) = q;
             }
         } else {
             abort_flag = 1;
         }
         __syncthreads();
-        if (abort_flag) return;
+        if (abort_flag) return false;
         float l2v[4], l1v[4];
         {
             float unused[PY][4];
-            star_plane<R, PY, G::BX, G::NV>(qbuf, cf, accq, unused, tx, ry0);
-            if (has_a) star_plane<R, PY, G::BX, G::NV>(st + 2 * A::PL, cf, acca, unused, tx, ry0);
+            star_plane<R, PY, G::BX, G::NV, Q>(qbuf, cf, accq, unused, tx, ry0);
+            if (has_a) star_plane<R, PY, G::BX, G::NV, Q>(st + 2 * A::PL, cf, acca, unused, tx, ry0);
             if (zo >= 0) {
                 load_center<I::OFF>(st + A::OFF_L2 + ry0 * I::BXI + 4 * tx, l2v);
                 load_center<I::OFF>(st + A::OFF_L1 + ry0 * I::BXI + 4 * tx, l1v);
@@ -342,14 +376,38 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
                 float *lp = lprev + shot_off + mp;
                 const int64_t gi = ((int64_t)z * geo.ny + y) * geo.nx + gx;
                 const bool at_rec = resid && z == geo.rec_z;
+                double gd[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     if (gx + k >= geo.nx) break;
                     const float g = gxs[k] * gys0 * gzv;
-                    float v = 2.f * g * l1v[k] + accq[0][0][k] - g * g * l2v[k];
+                    float v = 2.f * g * l1v[k] + accq[Q][0][k] - g * g * l2v[k];
                     if (at_rec) v += resid[((int64_t)sh * geo.ny + y) * geo.nx + gx + k];
                     lp[k] = v;
-                    if (has_a) atomicAdd(grad + gi + k, (double)g * (double)l1v[k] * (double)acca[0][0][k]);
+                    // the step's term in FP32 (its operands are FP32), accumulated in FP64
+                    if (has_a) gd[k] = widen(g * l1v[k] * acca[Q][0][k]);
+                }
+                if (has_a) {
+                    if (geo.gss == 0) {
+                        // one slice for all shots: other CTAs add to the same points
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (gx + k < geo.nx) atomicAdd(grad + gi + k, gd[k]);
+                    } else {
+                        // this shot's own slice: no other thread touches these points
+                        double *gp = grad + (int64_t)sh * geo.gss + gi;
+                        if (gvec && gx + 3 < geo.nx) {
+                            double2 *g2 = reinterpret_cast<double2 *>(gp);
+                            double2 a = g2[0], b = g2[1];
+                            a.x += gd[0]; a.y += gd[1]; b.x += gd[2]; b.y += gd[3];
+                            g2[0] = a;
+                            g2[1] = b;
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (gx + k < geo.nx) gp[k] += gd[k];
+                        }
+                    }
                 }
             }
         }
@@ -362,7 +420,10 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
             }
 #pragma unroll
         for (int k = 0; k < 4; ++k) accq[W - 1][0][k] = acca[W - 1][0][k] = 0.f;
-    }
+        return true;
+    };
+    for (int j = 0; j < P; ++j)
+        if (!plane(j)) return;
 }
 
 __global__ void model_kernel(WaveGeo geo, const float *__restrict__ v, float *__restrict__ m, float s)
@@ -391,6 +452,16 @@ __global__ void chain_kernel(const double *__restrict__ gm, const float *__restr
         gv[i] = gm[i] * 2.0 * (double)v[i] * s;
 }
 
+__global__ void sum_kernel(const double *__restrict__ slices, int nslices, int64_t stride, int64_t n,
+                           double *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = slices[i];
+        for (int s = 1; s < nslices; ++s) acc += slices[(int64_t)s * stride + i];
+        out[i] = acc;
+    }
+}
+
 __global__ void dot_kernel(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
                            double *__restrict__ res)
 {
@@ -414,7 +485,7 @@ constexpr int kAdjTX = 64, kAdjTY = 16, kAdjS = 2, kAdjTZ = 128;
 
 template <int R>
 cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const float *p_cur,
-                  float *p_prev, const float *amp, float *rec, cudaStream_t st)
+                  const float *p_prev, float *p_next, const float *amp, float *rec, cudaStream_t st)
 {
     using G = Geom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
     using F = FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
@@ -429,11 +500,12 @@ cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
     auto kern = wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
     if (e != cudaSuccess) return e;
-    const int nzc = (g.nz + kFwdTZ - 1) / kFwdTZ;
+    const int tz = kFwdTZ;
+    const int nzc = (g.nz + tz - 1) / tz;
     const dim3 grid((g.nx + kFwdTX - 1) / kFwdTX, (g.ny + kFwdTY - 1) / kFwdTY, nzc * g.nshots);
     const int vec = (R % 4 == 0) && g.py % 4 == 0 && g.pz % 4 == 0 && g.ss % 4 == 0 &&
-                    reinterpret_cast<uintptr_t>(p_prev) % 16 == 0;
-    kern<<<grid, G::NT, F::SMEM, st>>>(mcur, mm, mprev, mctr, cf, g, p_prev, amp, rec, kFwdTZ, nzc, vec,
+                    reinterpret_cast<uintptr_t>(p_next) % 16 == 0;
+    kern<<<grid, G::NT, F::SMEM, st>>>(mcur, mm, mprev, mctr, cf, g, p_next, amp, rec, tz, nzc, vec,
                                        device_error_word());
     return cudaGetLastError();
 }
@@ -461,25 +533,29 @@ cudaError_t adj_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
     auto kern = wave_adj_kernel<R, kAdjTX, kAdjTY, kAdjS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A::SMEM);
     if (e != cudaSuccess) return e;
-    const int nzc = (g.nz + kAdjTZ - 1) / kAdjTZ;
+    const int tz = kAdjTZ;
+    const int nzc = (g.nz + tz - 1) / tz;
     const dim3 grid((g.nx + kAdjTX - 1) / kAdjTX, (g.ny + kAdjTY - 1) / kAdjTY, nzc * g.nshots);
+    // 32-byte aligned rows of four doubles: two double2 per thread
+    const int gvec = g.nx % 4 == 0 && g.gss % 4 == 0 && reinterpret_cast<uintptr_t>(grad) % 32 == 0;
     kern<<<grid, G::NT, A::SMEM, st>>>(ml, mm, ma, m2, m1, cf, g, lam_prev, resid, grad, a_n ? 1 : 0,
-                                       kAdjTZ, nzc, device_error_word());
+                                       tz, nzc, gvec, device_error_word());
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_wave_fwd(const WaveGeo &g, const float *coeffs, const float *m, const float *p_cur,
-                            float *p_prev, const float *src_amp, float *rec, cudaStream_t st)
+                            const float *p_prev, float *p_next, const float *src_amp, float *rec,
+                            cudaStream_t st)
 {
     StarCoef cf{};
     for (int i = 0; i < 3 * (2 * g.r + 1); ++i) cf.c[i] = coeffs[i];
     switch (g.r) {
-        case 1: return fwd_r<1>(g, cf, m, p_cur, p_prev, src_amp, rec, st);
-        case 2: return fwd_r<2>(g, cf, m, p_cur, p_prev, src_amp, rec, st);
-        case 3: return fwd_r<3>(g, cf, m, p_cur, p_prev, src_amp, rec, st);
-        case 4: return fwd_r<4>(g, cf, m, p_cur, p_prev, src_amp, rec, st);
+        case 1: return fwd_r<1>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, st);
+        case 2: return fwd_r<2>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, st);
+        case 3: return fwd_r<3>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, st);
+        case 4: return fwd_r<4>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -512,6 +588,13 @@ cudaError_t launch_grad_to_velocity(const double *gm, const float *v, double *gv
 {
     const double s = ((double)dt * dt) / ((double)h * h);
     chain_kernel<<<152 * 8, 256, 0, st>>>(gm, v, gv, n, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_f64(const double *slices, int nslices, int64_t stride, int64_t n, double *out,
+                           cudaStream_t st)
+{
+    sum_kernel<<<152 * 8, 256, 0, st>>>(slices, nslices, stride, n, out);
     return cudaGetLastError();
 }
 

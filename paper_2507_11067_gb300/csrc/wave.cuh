@@ -14,11 +14,14 @@ struct WaveGeo {
     int sponge_w;
     float sponge_a;
     int rec_z;
+    int64_t gss;  // per-shot gradient slice stride (0 = one shared slice, atomics)
     int src[kMaxShots][3];
 };
 
+// a^{n+1} goes to p_next (== p_prev for the in-place step).
 cudaError_t launch_wave_fwd(const WaveGeo &g, const float *coeffs, const float *m, const float *p_cur,
-                            float *p_prev, const float *src_amp, float *rec, cudaStream_t st);
+                            const float *p_prev, float *p_next, const float *src_amp, float *rec,
+                            cudaStream_t st);
 cudaError_t launch_wave_adj(const WaveGeo &g, const float *coeffs, const float *m, const float *lam_cur,
                             float *lam_prev, const float *resid, const float *a_n, double *grad,
                             cudaStream_t st);
@@ -27,6 +30,8 @@ cudaError_t launch_model_from_velocity(const WaveGeo &g, const float *v, float *
 cudaError_t launch_grad_to_velocity(const double *gm, const float *v, double *gv, int64_t n, float dt,
                                     float h, cudaStream_t st);
 cudaError_t launch_dot_f64(const float *a, const float *b, int64_t n, double *res, cudaStream_t st);
+cudaError_t launch_sum_f64(const double *slices, int nslices, int64_t stride, int64_t n, double *out,
+                           cudaStream_t st);
 
 mms_status fail(mms_status st, const char *fmt, ...);
 mms_status cuda_fail(cudaError_t e, const char *what);

@@ -84,40 +84,57 @@ class WavePropagator:
         return rec, ckpt
 
     def _view(self, flat):
+        """The (nshots, Z, Y, X) field view of a flat field image (e.g. one
+        checkpoint slot), starting where the image starts."""
         py, pz, ss = self.pitch
         X = self.nx + 2 * self.r
         return torch.as_strided(flat, (self.nshots, self.nz + 2 * self.r, self.ny + 2 * self.r, X),
-                                (ss, pz, py, 1), 0)
+                                (ss, pz, py, 1), flat.storage_offset())
 
     # ------------------------------------------------------------ gradient
     def gradient_m(self, amps, resid, ckpt, ckpt_every):
         """dJ/dm (FP64, (nz, ny, nx)) for records whose residual is ``resid``
         (nsteps, nshots, ny, nx), from the forward checkpoints; the velocity
-        (model m) must be the one the checkpoints were made with."""
+        (model m) must be the one the checkpoints were made with.
+
+        Each segment's states are recomputed out of place from the
+        checkpoint images themselves (no copies); with several shots every
+        shot accumulates into its own FP64 slice (no atomics) and the slices
+        are summed once at the end."""
         nsteps = resid.shape[0]
         resid = resid.to(self.device, torch.float32).contiguous()
         amps = amps.to(self.device, torch.float32).contiguous()
-        grad = torch.zeros((self.nz, self.ny, self.nx), device=self.device, dtype=torch.float64)
-        seg = [self.new_fields(zero=False) for _ in range(ckpt_every + 1)]
+        npts = self.nz * self.ny * self.nx
+        per_shot = self.nshots > 1
+        grad = torch.zeros(((self.nshots,) if per_shot else ()) + (self.nz, self.ny, self.nx),
+                           device=self.device, dtype=torch.float64)
+        desc_g = self.desc
+        if per_shot:
+            py, pz, ss = self.pitch
+            desc_g, self._src_keep_g = _lib.wave_desc(self.nx, self.ny, self.nz, self.r, self.nshots, py,
+                                                      pz, ss, self.desc.sponge_width, self.desc.sponge_a,
+                                                      self.rec_z, self.src, grad_shot_stride=npts)
+        # seg[i] = a^{k0+i}; seg[0] and a^{k0-1} are the checkpoint images
+        # themselves, the others are written by the steps (zero halos kept)
+        seg = [None] + [self.new_fields() for _ in range(ckpt_every)]
         lam = [self.new_fields(), self.new_fields()]   # lam^{n+2}, lam^{n+1}
         nseg = self.n_checkpoints(nsteps, ckpt_every)
         for j in range(nseg - 1, -1, -1):
             k0 = j * ckpt_every
             k1 = min(k0 + ckpt_every, nsteps)
-            # seg[i] = a^{k0+i}, i = 0..k1-k0, recomputed from (a^{k0}, a^{k0-1})
-            self.flat(seg[0]).copy_(ckpt[j, 0])
-            self.flat(self.p[0]).copy_(ckpt[j, 1])
-            cur_f, old_f = seg[0], self.p[0]
+            seg[0] = self._view(ckpt[j, 0])
+            old_f, cur_f = self._view(ckpt[j, 1]), seg[0]
             for n in range(k0, k1):
-                # the step overwrites a^{n-1} with a^{n+1} in place: start from a copy
                 nxt = seg[n - k0 + 1]
-                self.flat(nxt).copy_(self.flat(old_f))
-                _lib.wave_step(self.desc, self.coeffs, self.m, cur_f, nxt, amps[n])
+                _lib.wave_step_to(self.desc, self.coeffs, self.m, cur_f, old_f, nxt, amps[n])
                 old_f, cur_f = cur_f, nxt
             for n in range(k1, k0, -1):                   # lam^n, n = k1 .. k0+1
-                _lib.wave_adjoint(self.desc, self.coeffs, self.m, lam[1], lam[0], resid[n - 1],
+                _lib.wave_adjoint(desc_g, self.coeffs, self.m, lam[1], lam[0], resid[n - 1],
                                   seg[n - k0], grad)
                 lam[0], lam[1] = lam[1], lam[0]
+        if per_shot:
+            _lib.sum_f64(grad, grad[0])
+            return grad[0]
         return grad
 
     def gradient_v(self, v, grad_m):

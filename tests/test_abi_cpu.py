@@ -101,3 +101,44 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib._build, "LIB", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="missing"):
         _lib.load()
+
+
+def test_sum_f64_validation(lib):
+    a = np.zeros(64, np.float64)
+    out = np.zeros(16, np.float64)
+    P = ctypes.c_void_p
+    assert lib.mms_sum_f64(a.ctypes.data_as(P), 0, 16, 16, out.ctypes.data_as(P), None) == 1
+    assert lib.mms_sum_f64(a.ctypes.data_as(P), 2, 8, 16, out.ctypes.data_as(P), None) == 1
+    assert lib.mms_sum_f64(a.ctypes.data_as(P), 2, 16, -1, out.ctypes.data_as(P), None) == 1
+    assert lib.mms_sum_f64(a.ctypes.data_as(P), 2, 16, 0, out.ctypes.data_as(P), None) == 0
+    # out may be the first slice, not another one
+    second = ctypes.c_void_p(a.ctypes.data + 16 * 8)
+    assert lib.mms_sum_f64(a.ctypes.data_as(P), 2, 16, 16, second, None) == 1
+    assert b"slice 1" in lib.mms_last_error()
+
+
+def _wave_desc(**kw):
+    src = np.array([3, 3, 3], np.int32)
+    d, keep = _lib.wave_desc(kw.get("n", 16), kw.get("n", 16), kw.get("n", 16), 4, 1,
+                             rec_z=2, src=src, grad_shot_stride=kw.get("gss", 0))
+    return d, (keep, src)
+
+
+def test_wave_gradient_stride_and_step_to_validation(lib):
+    c = np.ones(27, np.float32)
+    P = ctypes.c_void_p
+    buf = [np.zeros(24 ** 3 + 64, np.float32) for _ in range(3)]
+    ptr = [b.ctypes.data_as(P) for b in buf]
+    d, keep = _wave_desc(gss=100)   # below 16^3
+    st = lib.mms_wave_adjoint(ctypes.byref(d), c.ctypes.data_as(P), ptr[0], ptr[1], ptr[2], None, None,
+                              None, None)
+    assert st == 1 and b"gradient shot stride" in lib.mms_last_error()
+    d, keep = _wave_desc()
+    # p_next overlapping p_cur, or overlapping p_prev without being it
+    st = lib.mms_wave_step_to(ctypes.byref(d), c.ctypes.data_as(P), ptr[0], ptr[1], ptr[2], ptr[1],
+                              ptr[0], None, None)
+    assert st == 1 and b"p_cur and p_next overlap" in lib.mms_last_error()
+    shifted = ctypes.c_void_p(buf[2].ctypes.data + 64)
+    st = lib.mms_wave_step_to(ctypes.byref(d), c.ctypes.data_as(P), ptr[0], ptr[1], ptr[2], shifted,
+                              ptr[0], None, None)
+    assert st == 1 and b"p_prev and p_next overlap" in lib.mms_last_error()

@@ -169,6 +169,51 @@ def test_teacher_forced_adjoint_step():
     assert rel(grad.cpu().numpy(), gref) <= TOL
 
 
+def test_out_of_place_step_matches_in_place_step():
+    s = Setup(nshots=2)
+    cur, prev, work, nxt = s.fields
+    s.fill(cur, 21)
+    s.fill(prev, 22)
+    work.copy_(prev)
+    before = prev.clone()
+    mms.wave_step(s.desc, s.cf, s.m, cur, work, s.amps[3])
+    mms.wave_step_to(s.desc, s.cf, s.m, cur, prev, nxt, s.amps[3])
+    torch.cuda.synchronize()
+    mms.check_device()
+    assert torch.equal(nxt, work)            # the same arithmetic, bit for bit
+    assert torch.equal(prev, before)         # a^{n-1} is only read
+    assert not nxt[:, :R].any() and not nxt[:, -R:].any()   # the halo is not written
+
+
+def test_adjoint_per_shot_gradient_slices():
+    s = Setup(nshots=3)
+    lam1, lam2, a_n, lam2b = s.fields
+    for f, sd in ((lam1, 31), (lam2, 32), (a_n, 33)):
+        s.fill(f, sd)
+    lam2b.copy_(lam2)
+    l1, l2, an = s.host(lam1), s.host(lam2), s.host(a_n)
+    g = np.random.default_rng(34)
+    resid = torch.from_numpy(g.normal(size=(s.ns, s.ny, s.nx)).astype(np.float32)).cuda()
+    shared = torch.zeros((s.nz, s.ny, s.nx), device="cuda", dtype=torch.float64)
+    mms.wave_adjoint(s.desc, s.cf, s.m, lam1, lam2, resid, a_n, shared)
+    npts = s.nz * s.ny * s.nx
+    py, pz, ss = mms.field_geometry(lam1)
+    desc_g, _keep = mms.wave_desc(s.nx, s.ny, s.nz, R, s.ns, py, pz, ss, s.w.sponge, s.w.sponge_a,
+                                  s.w.zrec, s.w.src, grad_shot_stride=npts)
+    slices = torch.full((s.ns, s.nz, s.ny, s.nx), 0.25, device="cuda", dtype=torch.float64)
+    mms.wave_adjoint(desc_g, s.cf, s.m, lam1, lam2b, resid, a_n, slices)
+    torch.cuda.synchronize()
+    mms.check_device()
+    assert torch.equal(lam2, lam2b)          # lam^n does not depend on the gradient layout
+    rh = resid.cpu().numpy().astype(np.float64)
+    for sh in range(s.ns):
+        gref = np.full((s.nz, s.ny, s.nx), 0.25)   # accumulated onto what was there
+        s.prob.adjoint_step(l1[sh], l2[sh], rh[sh], an[sh], gref)
+        assert rel(slices[sh].cpu().numpy(), gref) <= TOL
+    total = mms.sum_f64(slices, slices[0]).cpu().numpy() - 0.25 * s.ns
+    assert np.abs(total - shared.cpu().numpy()).max() <= 1e-12 * np.abs(total).max()
+
+
 def _dot(a, b):
     out = torch.zeros(1, device="cuda", dtype=torch.float64)
     mms.dot_f64(a, b, out)
