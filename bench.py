@@ -509,8 +509,9 @@ def run_wave(args):
             loss = 0.5 * ((rec - obs) ** 2).sum()
             loss.backward()
             return vv.grad
-        # forward + per segment recompute + adjoint, plus the copies of the recompute
-        launches = nsteps + 2 * nsteps + 2
+        # forward, recompute and adjoint steps, the two velocity-to-model
+        # kernels (forward, backward) and the chain rule
+        launches = 3 * nsteps + 3
 
     for _ in range(max(1, args.warmup // 3)):
         run()

@@ -285,6 +285,25 @@ def test_gradient_matches_oracle_48cubed():
     assert rel(rec.detach().cpu().numpy(), rec_o) <= 1e-4
 
 
+def test_deterministic_gradient_is_reproducible_and_matches():
+    # per-shot FP64 slices: the same bits on every run, and the atomic
+    # (shared-slice) gradient up to FP64 summation order
+    w_true, w0 = _grad_problem(nsteps=60)
+    n, nsteps = 48, 60
+    prop = WavePropagator(n, n, n, w0.src, w0.zrec, w0.h, w_true.dt, sponge_width=w0.sponge,
+                          sponge_a=w0.sponge_a)
+    amps = torch.from_numpy(w_true.amp[:nsteps]).cuda()
+    rec, ckpt = prop.forward(torch.from_numpy(w0.v).cuda(), amps, nsteps, ckpt_every=20)
+    resid = (rec * 0.5).contiguous()
+    g_a = prop.gradient_m(amps, resid, ckpt, 20).clone()
+    g_d1 = prop.gradient_m(amps, resid, ckpt, 20, deterministic=True).clone()
+    g_d2 = prop.gradient_m(amps, resid, ckpt, 20, deterministic=True).clone()
+    torch.cuda.synchronize()
+    mms.check_device()
+    assert torch.equal(g_d1, g_d2)
+    assert (g_d1 - g_a).abs().max().item() <= 1e-12 * g_a.abs().max().item()
+
+
 def test_gradient_finite_difference_directions():
     # Central differences of J(v) along seeded smooth directions (GPU, FP32
     # propagation: J-cancellation limits the agreement to ~1e-2).
