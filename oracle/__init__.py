@@ -318,6 +318,32 @@ class WaveProblem:
                                         _ptr(np.ascontiguousarray(u)), _ptr(np.ascontiguousarray(w)))
 
 
+def wave_step_points(r: int, coeffs, m_int, sponge, src, s_amp: float, a_cur, a_prev, xyz) -> np.ndarray:
+    """a^{n+1} of one shot at interior points ``xyz`` (npts, 3) = (x, y, z):
+
+        a^{n+1} = G ( 2 a^n + m L a^n - G a^{n-1} + s^n [p = src] ),
+
+    G = g(x) g(y) g(z) the Cerjan profile, L the unscaled star of radius r
+    (the damped leapfrog step of WaveProblem.step, written out point by
+    point).  a_cur, a_prev: padded fields of the shot (zero halo), read in
+    place; m_int: interior m = v^2 dt^2 / h^2; sponge: (width, a) or None;
+    src: (x, y, z) of the shot's source; s_amp: its value s^n.
+    """
+    pts = np.ascontiguousarray(np.asarray(xyz, dtype=np.int64).reshape(-1, 3))
+    lap = stencil_points("star", r, np.asarray(coeffs).reshape(3, -1), a_cur, pts)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    nz, ny, nx = np.asarray(m_int).shape
+    if sponge is None:
+        g = np.ones(len(pts))
+    else:
+        g = sponge_1d(nx, *sponge)[x] * sponge_1d(ny, *sponge)[y] * sponge_1d(nz, *sponge)[z]
+    m = np.asarray(m_int)[z, y, x].astype(np.float64)
+    ac = np.asarray(a_cur)[z + r, y + r, x + r].astype(np.float64)
+    ap = np.asarray(a_prev)[z + r, y + r, x + r].astype(np.float64)
+    s = np.where((x == src[0]) & (y == src[1]) & (z == src[2]), float(s_amp), 0.0)
+    return g * (2.0 * ac + m * lap - g * ap + s)
+
+
 def objective(rec, obs) -> float:
     """J = 1/2 sum |d - d_obs|^2 (FP64)."""
     d = np.asarray(rec, np.float64) - np.asarray(obs, np.float64)

@@ -26,6 +26,17 @@ def _lib():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
 
 
+@pytest.fixture
+def tuned():
+    """The committed tuned table registered, as bench.py does (AUTO then runs
+    the benchmark's paths and variants); cleared again afterwards."""
+    from paper_2507_11067_gb300 import tune
+    chosen = tune.load_table()
+    yield chosen
+    for (shape, r, path) in chosen:
+        mms.set_variant(shape, r, path, -1)
+
+
 def rel(g, o):
     return float(np.abs(np.asarray(g, np.float64) - o).max() / max(np.abs(o).max(), 1e-300))
 
@@ -135,8 +146,10 @@ def test_output_pitch_and_canary():
 
 
 @pytest.mark.parametrize("r", [1, 2])
-def test_box_512_sampled(r):
-    # Full 512^3 box in the benchmark's launch configuration (default variant).
+def test_box_512_sampled(r, tuned):
+    # Full 512^3 box in the benchmark's launch configuration: AUTO with the
+    # tuned table (box r=2 on BF16x3 tensor cores, r=1 on the CUDA cores),
+    # and the CUDA-core path beside it.
     n = 512
     grid = workloads.uniform_grid(n, n, n, r, workload=2, salt=r)
     c = workloads.normal_coeffs("box", r, workload=2, salt=r)
@@ -149,10 +162,12 @@ def test_box_512_sampled(r):
         torch.cuda.synchronize()
         mms.check_device()
         got = out[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()
+        print(f"box r={r} 512^3 {path} ({mms.auto_path('box', r) if path == 'auto' else path}): "
+              f"sampled max-rel {rel(got, ref):.3e}")
         assert rel(got, ref) <= TOL
 
 
-def test_star_1024_sampled_all_radii():
+def test_star_1024_sampled_all_radii(tuned):
     # 1024^3 stars r = 1..4 on 16 sinusoids + 1e-3 noise; the radius-r input
     # is the radius-4 grid with its outer 4-r layers cropped.
     n = 1024
@@ -170,7 +185,8 @@ def test_star_1024_sampled_all_radii():
             # a cropped view starts off the 16-byte grid: re-pitch it on the device
             inp = mms.padded_empty(n, n, n, r, zero=False)
             inp.copy_(inp4[crop])
-        out = mms.apply("star", r, c, inp, path="cuda_core")
+        # AUTO with the tuned table: the benchmark's launch configuration
+        out = mms.apply("star", r, c, inp, path="auto")
         torch.cuda.synchronize()
         mms.check_device()
         got = out[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()

@@ -355,3 +355,49 @@ def test_gpu_adjoint_dot_product_full_map():
     lhs = float((rec.double() * r.double()).sum())
     rhs = float((amps[:, 0].double() * ft_r).sum())
     assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + abs(rhs)), (lhs, rhs)
+
+
+def test_rtm512_graph_step_sampled_full_size():
+    # The acoustic benchmark's configuration: 8 shots x 512^3, radius-4 FD8
+    # star, 20-cell sponge, one step launched through the cached CUDA graph
+    # (mms_wave_forward with MMS_WAVE_GRAPH, as the benchmark runs it),
+    # teacher-forced from seeded random states and checked at sampled points
+    # of every shot (source and receiver plane included) against the oracle.
+    from paper_2507_11067_gb300 import _lib as L
+    from paper_2507_11067_gb300.wave import WavePropagator
+    n, ns = 512, 8
+    w = workloads.WaveInputs(n, n, n, nshots=ns, nsteps=4, workload=4, noise=True)
+    prop = WavePropagator(n, n, n, w.src, w.zrec, w.h, w.dt, sponge_width=w.sponge, sponge_a=w.sponge_a)
+    prop.set_velocity(torch.from_numpy(w.v).cuda())
+    m_int = oracle.model_m(w.v, w.dt, w.h)
+    g = workloads.rng(4, 77)
+    host = []
+    for sh in range(ns):
+        pair = []
+        for field in (prop.p[1], prop.p[0]):      # a^n, a^{n-1}
+            a = np.zeros((n + 2 * R,) * 3, np.float32)
+            a[R:-R, R:-R, R:-R] = 2.0 * g.random((n, n, n), dtype=np.float32) - 1.0
+            field[sh].copy_(torch.from_numpy(a))
+            pair.append(a)
+        host.append(pair)
+    amps = torch.from_numpy(w.amp).cuda().contiguous()
+    rec = torch.empty((1, ns, n, n), device="cuda")
+    L.wave_forward(prop.desc, prop.coeffs, prop.m, amps[2:3], 1, prop.p[0], prop.p[1], rec, graph=True)
+    torch.cuda.synchronize()
+    mms.check_device()
+    out = prop.p[0]                               # a^{n+1} replaced a^{n-1}
+    for sh in range(ns):
+        pts = workloads.sample_points(n, n, n, 600, workload=4, salt=sh)
+        sx, sy, sz = w.src[sh]
+        plane = np.stack([g.integers(0, n, 200), g.integers(0, n, 200), np.full(200, w.zrec)], axis=1)
+        pts = np.concatenate([pts, [[sx, sy, sz]], plane]).astype(np.int64)
+        ref = oracle.wave_step_points(R, workloads.fd8_star_coeffs(), m_int, (w.sponge, w.sponge_a),
+                                      (sx, sy, sz), w.amp[2, sh], host[sh][0], host[sh][1], pts)
+        idx = torch.from_numpy(pts).cuda()
+        got = out[sh][idx[:, 2] + R, idx[:, 1] + R, idx[:, 0] + R].double().cpu().numpy()
+        err = rel(got, ref)
+        print(f"rtm512 graph step, shot {sh}: sampled max-rel {err:.3e}")
+        assert err <= TOL, (sh, err)
+        # the records are the receiver plane of the new state, bit for bit
+        rp = torch.from_numpy(plane).cuda()
+        assert torch.equal(rec[0, sh][rp[:, 1], rp[:, 0]], out[sh][w.zrec + R, rp[:, 1] + R, rp[:, 0] + R])

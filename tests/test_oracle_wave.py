@@ -211,3 +211,27 @@ def test_gradient_matches_finite_differences():
         errs.append(abs(_objective_at(m0 + eps * d, p, obs, nsteps) - j0 - eps * an))
     slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(1.8 < s < 2.2 for s in slopes)
+
+
+def test_step_at_points_equals_the_full_step():
+    # The point-by-point step (used at full size, where a full FP64 step does
+    # not fit the test budget) against the oracle's full-grid step.
+    n = (14, 12, 13)
+    prob, v, dt, h = _problem(n=n, sponge=(4, 0.05), vjit=0.2, src=[(5, 6, 4)], nsteps=4)
+    g = np.random.default_rng(3)
+    a_cur, a_prev = oracle.pad(g.uniform(-1, 1, n), R), oracle.pad(g.uniform(-1, 1, n), R)
+    full = prob.step(a_cur, a_prev, 0, 2)
+    nz, ny, nx = n
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    pts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1)
+    args = (R, oracle.fd2_star_coeffs(R), oracle.model_m(v, dt, h), (4, 0.05), (5, 6, 4))
+    got = oracle.wave_step_points(*args, prob.amp[2, 0], a_cur, a_prev, pts)
+    want = full[R:-R, R:-R, R:-R].ravel()
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    # the source term lands on the source point only, scaled by G there
+    quiet = oracle.wave_step_points(*args, 0.0, a_cur, a_prev, pts)
+    src_idx = (4 * ny + 6) * nx + 5
+    diff = got - quiet
+    g = oracle.sponge_1d(nx, 4, 0.05)[5] * oracle.sponge_1d(ny, 4, 0.05)[6] * oracle.sponge_1d(nz, 4, 0.05)[4]
+    assert prob.amp[2, 0] != 0.0 and diff[src_idx] == pytest.approx(g * prob.amp[2, 0], rel=1e-12)
+    assert np.count_nonzero(diff) == 1
