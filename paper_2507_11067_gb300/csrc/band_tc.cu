@@ -87,7 +87,11 @@ struct Cfg {
     static constexpr int NPROD = PREC == P_TF32 ? 1 : 3;
     static constexpr int BANDCOLS = K * ELT / 4;     // 32-bit TMEM columns per band part
     static constexpr int BAND_TOTAL = WZ * NPARTS * BANDCOLS;
-    static constexpr int YP = 32;                    // staged rows per plane
+    // staged rows per plane: 32, or 36 at radius 2, whose 32 output rows
+    // per tile divide the usual power-of-two extents (N = 4 x 36 = 144 is
+    // a legal MMA N); elsewhere (other radii, and 3xTF32, whose larger bands
+    // leave room for 2 planes per group) N would not be a multiple of 16
+    static constexpr int YP = (R == 2 && PREC != P_3XTF32) ? 36 : 32;
     static constexpr int TY = YP - 2 * R;            // output rows per tile
     static constexpr int NZ = (2 * 4 * YP + BAND_TOTAL <= 512)   ? 4
                               : (2 * 3 * YP + BAND_TOTAL <= 512) ? 3
@@ -150,6 +154,7 @@ struct Cfg {
     // converters' column reads across 8 lines hit 8 different bank groups.
     static constexpr bool SWZ = K * 4 == 128;
     static_assert(SWZ == (K * 4 == 128) && N % 16 == 0 && N <= 256, "MMA N");
+    static_assert(YP == 32 || YP == 36, "the epilogue loads 32 or 36 accumulator columns");
     static_assert(STG_BYTES % 1024 == 0 && CONV_BYTES % 1024 == 0 && PART_BYTES % 16 == 0, "align");
 };
 
@@ -575,8 +580,16 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
             tile_origin(i / G, x0, y0, zt);
             const int z0 = zt + (i % G) * C::NZ;
             for (int zl = eg; zl < C::NZ; zl += C::EG) {
-                uint32_t r[32];
-                tc::tmem_ld_32x32b_x32(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * C::N + zl * C::YP), r);
+                uint32_t r[C::YP];
+                {
+                    const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * C::N + zl * C::YP);
+                    uint32_t (&r32)[32] = *reinterpret_cast<uint32_t (*)[32]>(&r[0]);
+                    tc::tmem_ld_32x32b_x32(ta, r32);
+                    if constexpr (C::YP == 36) {
+                        uint32_t (&r4)[4] = *reinterpret_cast<uint32_t (*)[4]>(&r[32]);
+                        tc::tmem_ld_32x32b_x4(ta + 32, r4);
+                    }
+                }
                 tc::tmem_wait_ld();
                 if (zl + C::EG >= C::NZ) {
                     // this warp's last read of the accumulator: hand it back
@@ -585,7 +598,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
                     if (lane == 0) ptx::mbar_arrive(&empty_d[s]);
                 }
 #pragma unroll
-                for (int c = 0; c < 32; ++c) st_base[c * C::DSM_LD] = __uint_as_float(r[c]);
+                for (int c = 0; c < C::YP; ++c) st_base[c * C::DSM_LD] = __uint_as_float(r[c]);
                 [[maybe_unused]] const unsigned long long tb = MMS_CLOCK();
                 named_sync(1 + eg, 128);
                 wbar += MMS_CLOCK() - tb;
