@@ -192,59 +192,102 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_sample(planes: int, salt: int = 0):
-    """Oracle on the first `planes` output planes of both sweeps; returns
-    (points, seconds, threads)."""
+def oracle_sample(planes: int, salt: int = 0, plan=None):
+    """Oracle on the first `planes` output planes of every sweep of the plan
+    (default: the box workload's two sweeps), on seeded slabs of the same
+    sizes and value distributions; returns (points, seconds, threads)."""
     import oracle
+    plan = plan or WORKLOADS["box512"]
     pts, secs = 0, 0.0
-    for r in RADII:
-        c = workloads.normal_coeffs("box", r, workload=2, salt=r)
-        g = workloads.rng(2, 50 + r + 100 * salt)
-        sub = g.uniform(-1, 1, size=(planes + 2 * r, N + 2 * r, N + 2 * r)).astype(np.float32)
-        sub = sub.astype(np.float64)
+    for shape, r, n in plan:
+        c = sweep_coeffs(shape, r)
+        g = workloads.rng(2 if shape == "box" else 3, 50 + r + 100 * salt)
+        sub = g.uniform(-1, 1, size=(planes + 2 * r, n + 2 * r, n + 2 * r))
         t0 = time.perf_counter()
-        oracle.stencil("box", r, c, sub)
+        oracle.stencil(shape, r, c, sub)
         secs += time.perf_counter() - t0
-        pts += planes * N * N
+        pts += planes * n * n
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return pts, secs, threads
 
 
-def calibrate_planes(budget_s: float) -> int:
-    pts, secs, _ = oracle_sample(2)
+def oracle_wave_sample(planes: int, n: int, gradient: bool, salt: int = 0):
+    """Oracle wave steps on a slab of `planes` z-planes of one n x n shot:
+    one forward step, or for the gradient workload the forward step, its
+    recomputation and the adjoint step with the gradient term (the work of
+    one point-step of the gradient); returns (point-steps, seconds, threads)."""
+    import oracle
+    r = 4
+    g = workloads.rng(4, 80 + 100 * salt)
+    v = g.uniform(1500.0, 4500.0, size=(planes, n, n))
+    dt, h = 0.4 * 10.0 / 4500.0, 10.0
+    prob = oracle.WaveProblem(r, workloads.fd8_star_coeffs(), oracle.model_m(v, dt, h), (20, 0.015),
+                              [(n // 2, n // 2, planes // 2)], np.full((2, 1), 1e-3), 0)
+    a_cur, a_prev = (oracle.pad(g.uniform(-1, 1, (planes, n, n)), r) for _ in range(2))
+    t0 = time.perf_counter()
+    nxt = prob.step(a_cur, a_prev, 0, 1)
+    if gradient:
+        prob.step(a_cur, a_prev, 0, 1)
+        grad = np.zeros((planes, n, n))
+        prob.adjoint_step(nxt, a_cur, None, a_prev, grad)
+    secs = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return planes * n * n, secs, threads
+
+
+def calibrate_planes(budget_s: float, sample=None) -> int:
+    sample = sample or (lambda planes, salt=0: oracle_sample(planes, salt))
+    pts, secs, _ = sample(2)
     per_plane = secs / 2
-    return max(2, min(N, int(budget_s / max(per_plane, 1e-6))))
+    return max(2, min(512, int(budget_s / max(per_plane, 1e-6))))
 
 
 def run_reference(args):
+    """The base contract's reference arm: the FP64 oracle as it stands, on the
+    host cores, timed on bounded samples of the selected workload (each step
+    about MMS_REF_STEP_SECONDS of CPU work)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
     oracle.build()
     budget = float(os.environ.get("MMS_REF_STEP_SECONDS", "6"))
-    planes = calibrate_planes(budget)
+    if args.workload in ("rtm512", "grad256"):
+        n = 512 if args.workload == "rtm512" else 256
+        grad = args.workload == "grad256"
+
+        def sample(planes, salt=0):
+            return oracle_wave_sample(planes, n, grad, salt)
+        unit = "GPoint-steps/s"
+        what = ("forward step" if not grad else "forward step, its recomputation and the adjoint step")
+    else:
+        plan = WORKLOADS[args.workload]
+
+        def sample(planes, salt=0):
+            return oracle_sample(planes, salt, plan)
+        unit = "GPoints/s"
+        what = ", ".join(f"{sh} r={r} {nn}^3" for sh, r, nn in plan)
+    planes = calibrate_planes(budget, sample)
     for _ in range(args.warmup):
-        oracle_sample(max(1, planes // 8))
+        sample(max(2, planes // 8))
     total_pts, total_s = 0, 0.0
     threads = 1
     args.steps = args.steps or 3
     for k in range(args.steps):
-        p, s, threads = oracle_sample(planes, salt=k)
+        p, secs, threads = sample(planes, salt=k)
         total_pts += p
-        total_s += s
+        total_s += secs
     value = total_pts / total_s / 1e9
-    sample = (f"FP64 oracle, box r=1 and r=2 on the first {planes} of 512 output planes of a "
-              f"512^2 x {planes} slab per sweep, per step")
+    sample_txt = f"FP64 oracle ({what}) on a seeded slab of {planes} output planes per sweep, per step"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "GPoints/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": unit,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "GPoints/s", "cores": threads, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": "GPoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "sample": sample_txt},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                         "sample": sample_txt},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -424,13 +467,17 @@ def main():
                                        "tflops": f / sec / 1e12, "alu_frac": f / sec / 1e12 / alu_peak}
 
     cpu = None
-    if not args.no_cpu_baseline and args.workload == "box512":
+    if not args.no_cpu_baseline and world == 1:
         import oracle
         oracle.build()
-        planes = calibrate_planes(5.0)
-        p, s, threads = oracle_sample(planes)
+
+        def sample(p, salt=0):
+            return oracle_sample(p, salt, plan)
+        planes = calibrate_planes(5.0, sample)
+        p, s, threads = sample(planes)
         cpu = {"value": p / s / 1e9, "unit": "GPoints/s", "cores": threads, "kind": "oracle",
-               "sample": f"FP64 oracle, box r=1 and r=2, first {planes} of 512 output planes each"}
+               "sample": f"FP64 oracle, " + ", ".join(f"{sh} r={r}" for sh, r, _ in plan) +
+                         f", a seeded slab of {planes} output planes per sweep"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GPoints/s", "n_gpus": world,
@@ -593,13 +640,26 @@ def run_wave(args):
                 "kernel": "forward + recompute + wave_adj_kernel",
                 "bytes_per_point_step": bpp}
         unit = "GPoint-steps/s"
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        grad = args.workload == "grad256"
+
+        def sample(p, salt=0):
+            return oracle_wave_sample(p, n, grad, salt)
+        planes = calibrate_planes(5.0, sample)
+        p, s, threads = sample(planes)
+        cpu = {"value": p / s / 1e9, "unit": unit, "cores": threads, "kind": "oracle",
+               "sample": f"FP64 oracle {'forward, recompute and adjoint steps' if grad else 'forward step'} "
+                         f"of one shot on a seeded {planes} x {n} x {n} slab"}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / (steps if args.workload == "rtm512" else reps),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": {"workload": WORKLOAD_NAMES[args.workload], "shots": nshots,
                                                 "n": n, "time_steps": nsteps if args.workload != "rtm512" else steps},
-                "roofline": roof, "cpu_baseline": None, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * reps, "clocks": clk,
                 "peaks": {"hbm_gbs": hbm_peak, "source": peak_src}}
         print(json.dumps(line), flush=True)
