@@ -278,6 +278,17 @@ const char *mms_last_error(void);
  * the synchronisation itself failed). */
 mms_status mms_check_device(void *stream);
 
+/*
+ * Failure-detection self-test (no counterpart in the paper): queues on
+ * `stream` a one-block kernel whose bounded wait on an mbarrier phase that
+ * nothing completes runs out after limit_us microseconds (1..2000000).  Like
+ * every bounded wait of the library's kernels, it then sets the timeout bit
+ * of the device error word and returns, so the next mms_check_device returns
+ * MMS_E_TIMEOUT and the context stays usable.  MMS_E_ARG for a limit out of
+ * range.
+ */
+mms_status mms_selftest_timeout(uint32_t limit_us, void *stream);
+
 /* Library version string. */
 const char *mms_version(void);
 

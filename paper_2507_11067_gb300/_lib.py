@@ -30,7 +30,7 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_set_variant", "mms_wave_step", "mms_wave_forward", "mms_wave_adjoint",
            "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
            "mms_check_device", "mms_version", "mms_stencil_apply_noalloc", "mms_wave_step_to",
-           "mms_sum_f64"]
+           "mms_sum_f64", "mms_selftest_timeout"]
 
 
 class MMSError(RuntimeError):
@@ -90,6 +90,7 @@ def load():
             "mms_wave_step": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P],
             "mms_wave_step_to": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
             "mms_sum_f64": [P, i32, i64, i64, P, P],
+            "mms_selftest_timeout": [ctypes.c_uint32, P],
             "mms_wave_forward": [ctypes.POINTER(WaveDesc), P, P, P, i32, P, P, P, P, i32,
                                  ctypes.c_uint32, P],
             "mms_wave_adjoint": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
@@ -319,6 +320,13 @@ def sum_f64(slices, out, stream=None):
     n = slices[0].numel()
     check(load().mms_sum_f64(_ptr(slices), int(k), slices.stride(0), n, _ptr(out), _stream(stream)))
     return out
+
+
+def selftest_timeout(limit_us, stream=None):
+    """Queue the failure-path self-test (mms_selftest_timeout): a kernel
+    whose bounded wait runs out after limit_us; mms_check_device then
+    reports MMS_E_TIMEOUT."""
+    check(load().mms_selftest_timeout(int(limit_us), _stream(stream)))
 
 
 def dot_f64(a, b, result, stream=None):

@@ -530,6 +530,13 @@ mms_status mms_sum_f64(const double *slices, int32_t nslices, int64_t stride, in
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "sum kernel launch");
 }
 
+mms_status mms_selftest_timeout(uint32_t limit_us, void *stream)
+{
+    if (limit_us < 1 || limit_us > 2000000) return fail(MMS_E_ARG, "limit %u us outside 1..2000000", limit_us);
+    cudaError_t e = launch_wait_selftest((unsigned long long)limit_us * 1000ull, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "self-test launch");
+}
+
 mms_status mms_dot_f64(const float *a, const float *b, int64_t n, double *result, void *stream)
 {
     if (n < 0) return fail(MMS_E_ARG, "negative length");

@@ -139,15 +139,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Waits for the phase with the given parity to complete; gives up after
-// kWaitLimitNs, sets the timeout bit of the device error word and returns
-// false.  Never traps.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned *err)
+// limit_ns (kWaitLimitNs by default), sets the timeout bit of the device
+// error word and returns false.  Never traps.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned *err,
+                                                  unsigned long long limit_ns = mms::kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 255u && globaltimer() - t0 > mms::kWaitLimitNs) {
+        if ((it & 255u) == 255u && globaltimer() - t0 > limit_ns) {
             if (err) atomicOr(err, mms::kErrTimeout);
             return false;
         }

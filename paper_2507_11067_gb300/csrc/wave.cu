@@ -35,6 +35,21 @@ unsigned *device_error_word()
 
 namespace {
 
+// Failure-path self-test: one CTA waits, bounded by limit_ns, on an mbarrier
+// phase that nothing completes; the wait runs out, records the timeout in
+// the error word and the kernel returns -- the path that every bounded wait
+// of the library takes, exercised without a fault.
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, unsigned *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    (void)ptx::mbar_wait_bounded(&bar, 0, err, limit_ns);
+}
+
 // FP32 -> FP64 by the IEEE-754 layouts (sign kept, exponent rebased by
 // 1023 - 127, fraction shifted up 29 bits), on the integer units: GB300's
 // FP64 pipe issues about two instructions per clock per SM, which a
@@ -588,6 +603,12 @@ cudaError_t launch_grad_to_velocity(const double *gm, const float *v, double *gv
 {
     const double s = ((double)dt * dt) / ((double)h * h);
     chain_kernel<<<152 * 8, 256, 0, st>>>(gm, v, gv, n, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, cudaStream_t st)
+{
+    wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, device_error_word());
     return cudaGetLastError();
 }
 

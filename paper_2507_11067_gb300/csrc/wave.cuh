@@ -30,6 +30,7 @@ cudaError_t launch_model_from_velocity(const WaveGeo &g, const float *v, float *
 cudaError_t launch_grad_to_velocity(const double *gm, const float *v, double *gv, int64_t n, float dt,
                                     float h, cudaStream_t st);
 cudaError_t launch_dot_f64(const float *a, const float *b, int64_t n, double *res, cudaStream_t st);
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, cudaStream_t st);
 cudaError_t launch_sum_f64(const double *slices, int nslices, int64_t stride, int64_t n, double *out,
                            cudaStream_t st);
 

@@ -142,3 +142,8 @@ def test_wave_gradient_stride_and_step_to_validation(lib):
     st = lib.mms_wave_step_to(ctypes.byref(d), c.ctypes.data_as(P), ptr[0], ptr[1], ptr[2], shifted,
                               ptr[0], None, None)
     assert st == 1 and b"p_prev and p_next overlap" in lib.mms_last_error()
+
+
+def test_selftest_limit_validation(lib):
+    assert lib.mms_selftest_timeout(0, None) == 1
+    assert lib.mms_selftest_timeout(2000001, None) == 1
