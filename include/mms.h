@@ -116,6 +116,26 @@ typedef struct {
 mms_status mms_stencil_apply_ex(const mms_stencil_desc *desc, const float *in, float *out,
                                 void *stream);
 
+/*
+ * The sweep of mms_stencil_apply_ex on grids in HOST memory: host_in and
+ * host_out are host pointers with the layouts and pitches of the
+ * descriptor (input pitches multiples of 4 floats).  The library streams
+ * z-slabs of the input (each with its 2r halo planes; a slab of a padded
+ * grid is one contiguous range) to the device, sweeps them on `stream` and
+ * copies the results back, pipelined over two device slab buffers taken
+ * from the device's stream-ordered memory pool and two copy streams of its
+ * own, so slab k+1 is copied in while slab k is swept and slab k-1 copied
+ * out.  Asynchronous: when the work queued on `stream` has finished,
+ * host_out holds the result (host_in must stay unchanged until then).
+ * Pinned (page-locked) host memory gives asynchronous, overlapped copies;
+ * pageable memory works but its copies are staged and serialised.  Errors
+ * as mms_stencil_apply_ex.
+ * Defined by: the sweep above (paper Sec. 1, Sec. 4.1); the slab pipeline
+ * is the GB300 analogue of the paper's streaming of planes (Sec. 4.4, 4.5).
+ */
+mms_status mms_stencil_apply_host(const mms_stencil_desc *desc, const float *host_in, float *host_out,
+                                  void *stream);
+
 /* The path MMS_PATH_AUTO takes for (shape, radius) on an input that does
  * (tma_aligned = 1) or does not (0) meet the TMA alignment rule above;
  * -1 for an invalid shape or radius.  Host only. */

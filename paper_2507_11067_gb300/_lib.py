@@ -30,7 +30,7 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_set_variant", "mms_wave_step", "mms_wave_forward", "mms_wave_adjoint",
            "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
            "mms_check_device", "mms_version", "mms_stencil_apply_noalloc", "mms_wave_step_to",
-           "mms_sum_f64", "mms_selftest_timeout"]
+           "mms_sum_f64", "mms_selftest_timeout", "mms_stencil_apply_host"]
 
 
 class MMSError(RuntimeError):
@@ -83,6 +83,7 @@ def load():
             "mms_stencil_apply": [i32, i32, P, P, P, i64, i64, i64, P],
             "mms_stencil_apply_ex": [ctypes.POINTER(StencilDesc), P, P, P],
             "mms_stencil_apply_noalloc": [ctypes.POINTER(StencilDesc), P, P, P],
+            "mms_stencil_apply_host": [ctypes.POINTER(StencilDesc), P, P, P],
             "mms_num_variants": [i32, i32, i32],
             "mms_auto_path": [i32, i32, i32],
             "mms_default_variant": [i32, i32, i32, i64, i64, i64],
@@ -212,6 +213,25 @@ def apply_noalloc(r, coeffs, inp, out=None, path="bf16x3", variant=-1, stream=No
                     PATHS[path] if isinstance(path, str) else int(path), int(variant))
     check(load().mms_stencil_apply_noalloc(ctypes.byref(d), _ptr(inp), _ptr(out), _stream(stream)))
     return out
+
+
+def apply_host(shape, r, coeffs, host_in, host_out, path="auto", variant=-1, stream=None):
+    """The sweep on grids in host memory (mms_stencil_apply_host): host_in a
+    CPU float32 (nz+2r, ny+2r, nx+2r) view with unit x stride (pinned for
+    overlapped copies), host_out a CPU (nz, ny, nx) view; the library streams
+    z-slabs through the device.  Asynchronous on `stream`."""
+    import torch
+    if host_in.is_cuda or host_out.is_cuda or host_in.dtype != torch.float32:
+        raise ValueError("host_in and host_out must be CPU float32 tensors")
+    Z, Y, X = host_in.shape
+    nx, ny, nz = X - 2 * r, Y - 2 * r, Z - 2 * r
+    ipy, ipz = pitches(host_in)
+    opy, opz = pitches(host_out)
+    c = _host_coeffs(coeffs)
+    d = StencilDesc(SHAPES[shape], r, c.ctypes.data, nx, ny, nz, ipy, ipz, opy, opz,
+                    PATHS[path] if isinstance(path, str) else int(path), int(variant))
+    check(load().mms_stencil_apply_host(ctypes.byref(d), _ptr(host_in), _ptr(host_out), _stream(stream)))
+    return host_out
 
 
 def apply_dense(shape, r, coeffs, inp, out, stream=None):

@@ -208,11 +208,132 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "tensor-core sweep launch");
 }
 
+// The sweep of apply() on grids in host memory: z-slabs of the input (with
+// their 2r halo planes) are copied in, swept and copied back, pipelined over
+// two device slab buffers and three streams -- copy in and copy out on
+// streams of the call's own, the sweeps on the caller's stream, which at
+// return waits for the last copy back.
+static mms_status apply_host(const mms_stencil_desc *d, const float *in, float *out, void *stream)
+{
+    if (!d) return fail(MMS_E_ARG, "null descriptor");
+    const int r = d->radius;
+    if (d->shape != MMS_STAR && d->shape != MMS_BOX) return fail(MMS_E_ARG, "shape %d is not STAR or BOX", d->shape);
+    if (r < 1 || r > kMaxR) return fail(MMS_E_ARG, "radius %d outside 1..%d", r, kMaxR);
+    if (!d->coeffs) return fail(MMS_E_ARG, "null coefficient array");
+    if (d->nx < 0 || d->ny < 0 || d->nz < 0) return fail(MMS_E_ARG, "negative size");
+    if (d->nx >= (1ll << 30) || d->ny >= (1ll << 30) || d->nz >= (1ll << 30))
+        return fail(MMS_E_ARG, "size above 2^30");
+    if (d->path < MMS_PATH_AUTO || d->path > MMS_PATH_NAIVE) return fail(MMS_E_ARG, "unknown path %d", d->path);
+    if (d->variant < -1) return fail(MMS_E_ARG, "variant %d", d->variant);
+    if (d->nx == 0 || d->ny == 0 || d->nz == 0) return MMS_OK;
+    if (!in || !out) return fail(MMS_E_ARG, "null grid pointer");
+    const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * r;
+    const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
+    const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
+    const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
+    const int64_t opz = d->out_pitch_z ? d->out_pitch_z : d->ny * opy;
+    if (ipy < X || ipz < Y * ipy) return fail(MMS_E_ARG, "input pitches below the padded extents");
+    if (opy < d->nx || opz < d->ny * opy) return fail(MMS_E_ARG, "output pitches below the interior extents");
+    if (ipy % 4 || ipz % 4) return fail(MMS_E_ALIGN, "host input pitches must be multiples of 4 floats");
+    const size_t in_bytes = (size_t)((Z - 1) * ipz + (Y - 1) * ipy + X) * 4;
+    const size_t out_bytes = (size_t)((d->nz - 1) * opz + (d->ny - 1) * opy + d->nx) * 4;
+    if (overlaps(in, in_bytes, out, out_bytes)) return fail(MMS_E_ARG, "input and output overlap");
+
+    // slab depth: about eight slabs, 8..128 planes
+    int64_t tz = ((d->nz + 7) / 8 + 7) / 8 * 8;
+    tz = tz < 8 ? 8 : tz > 128 ? 128 : tz;
+    if (tz > d->nz) tz = d->nz;
+    const int64_t nslab = (d->nz + tz - 1) / tz;
+    const size_t in_slab = (size_t)(tz + 2 * r) * ipz * 4, out_slab = (size_t)tz * opz * 4;
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev[9] = {};
+    char *buf = nullptr;
+    mms_status st = MMS_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking);
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    // staging: [in slab 0 | in slab 1 | out slab 0 | out slab 1], stream-ordered on the caller's stream
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&buf), 2 * (in_slab + out_slab), s);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "host sweep set-up");
+    } else {
+        cudaEvent_t start = ev[0], *in_ready = ev + 1, *in_free = ev + 3, *out_ready = ev + 5, *out_free = ev + 7;
+        float *d_in[2] = {reinterpret_cast<float *>(buf), reinterpret_cast<float *>(buf + in_slab)};
+        float *d_out[2] = {reinterpret_cast<float *>(buf + 2 * in_slab),
+                           reinterpret_cast<float *>(buf + 2 * in_slab + out_slab)};
+        // the copies start after everything queued on the caller's stream so far
+        e = cudaEventRecord(start, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, start, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, start, 0);
+        for (int64_t k = 0; k < nslab && e == cudaSuccess && st == MMS_OK; ++k) {
+            const int b = (int)(k & 1);
+            const int64_t z0 = k * tz, nzt = d->nz - z0 < tz ? d->nz - z0 : tz;
+            const size_t ib = (size_t)((nzt + 2 * r - 1) * ipz + (Y - 1) * ipy + X) * 4;
+            if (k >= 2) e = cudaStreamWaitEvent(s_in, in_free[b], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_in[b], in + z0 * ipz, ib, cudaMemcpyHostToDevice, s_in);
+            if (e == cudaSuccess) e = cudaEventRecord(in_ready[b], s_in);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, in_ready[b], 0);
+            if (e == cudaSuccess && k >= 2) e = cudaStreamWaitEvent(s, out_free[b], 0);
+            if (e != cudaSuccess) break;
+            mms_stencil_desc sd = *d;
+            sd.nz = nzt;
+            sd.in_pitch_y = ipy;
+            sd.in_pitch_z = ipz;
+            sd.out_pitch_y = opy;
+            sd.out_pitch_z = opz;
+            st = apply(&sd, d_in[b], d_out[b], stream);
+            if (st != MMS_OK) break;
+            e = cudaEventRecord(in_free[b], s);
+            if (e == cudaSuccess) e = cudaEventRecord(out_ready[b], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, out_ready[b], 0);
+            // rows of nx values only: the padding of the caller's pitched
+            // output is not part of the result and is left untouched
+            if (e == cudaSuccess) {
+                const size_t w = (size_t)d->nx * 4, pitch = (size_t)opy * 4;
+                if (opz == d->ny * opy) {
+                    e = cudaMemcpy2DAsync(out + z0 * opz, pitch, d_out[b], pitch, w, (size_t)(nzt * d->ny),
+                                          cudaMemcpyDeviceToHost, s_out);
+                } else {
+                    for (int64_t zz = 0; zz < nzt && e == cudaSuccess; ++zz)
+                        e = cudaMemcpy2DAsync(out + (z0 + zz) * opz, pitch, d_out[b] + zz * opz, pitch, w,
+                                              (size_t)d->ny, cudaMemcpyDeviceToHost, s_out);
+                }
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(out_free[b], s_out);
+        }
+        // the caller's stream takes over: it waits for the last copies, then
+        // returns the staging memory to the pool
+        cudaEvent_t done_in = ev[1], done_out = ev[5];
+        cudaError_t j = cudaEventRecord(done_in, s_in);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(s, done_in, 0);
+        if (j == cudaSuccess) j = cudaEventRecord(done_out, s_out);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(s, done_out, 0);
+        cudaError_t f = cudaFreeAsync(buf, s);
+        if (e == cudaSuccess) e = j;
+        if (e == cudaSuccess) e = f;
+        if (st == MMS_OK && e != cudaSuccess) st = cuda_fail(e, "host sweep pipeline");
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (s_in) cudaStreamDestroy(s_in);
+    if (s_out) cudaStreamDestroy(s_out);
+    return st;
+}
+
 }  // namespace mms
 
 using namespace mms;
 
 extern "C" {
+
+mms_status mms_stencil_apply_host(const mms_stencil_desc *desc, const float *host_in, float *host_out,
+                                  void *stream)
+{
+    return apply_host(desc, host_in, host_out, stream);
+}
 
 mms_status mms_stencil_apply(int shape, int radius, const float *coeffs, const float *in, float *out,
                              int64_t nx, int64_t ny, int64_t nz, void *stream)

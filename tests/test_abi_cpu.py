@@ -147,3 +147,16 @@ def test_wave_gradient_stride_and_step_to_validation(lib):
 def test_selftest_limit_validation(lib):
     assert lib.mms_selftest_timeout(0, None) == 1
     assert lib.mms_selftest_timeout(2000001, None) == 1
+
+
+def test_host_sweep_validation(lib):
+    d, c = _desc(radius=2)
+    a = np.zeros(16, np.float32)
+    P = ctypes.c_void_p
+    assert lib.mms_stencil_apply_host(ctypes.byref(d), None, a.ctypes.data_as(P), None) == 1
+    d, c = _desc(ipy=11)      # below the padded extent
+    assert lib.mms_stencil_apply_host(ctypes.byref(d), a.ctypes.data_as(P), a.ctypes.data_as(P), None) == 1
+    d, c = _desc(ipy=13)      # not a multiple of 4 floats
+    assert lib.mms_stencil_apply_host(ctypes.byref(d), a.ctypes.data_as(P), a.ctypes.data_as(P), None) == 3
+    d, c = _desc(nx=0)        # empty interior: nothing to do
+    assert lib.mms_stencil_apply_host(ctypes.byref(d), None, None, None) == 0
