@@ -13,15 +13,17 @@ namespace mms {
 namespace sweep {
 
 // Tile variant: TX x TY outputs per CTA, PY rows per thread, S ring stages,
-// TZ planes per CTA, rotated (true) or shifted (false) queue.
-struct Variant { int tx, ty, py, s, tz; bool rot; };
+// TZ planes per CTA, rotated (true) or shifted (false) queue, and whether one
+// thread waits for each staged plane while the others block at the CTA
+// barrier (true) or every thread polls the stage's mbarrier (false).
+struct Variant { int tx, ty, py, s, tz; bool rot; bool one_wait = false; };
 
 // Box tile variants (shared by the radius-1/2 and radius-3/4 units).
 constexpr Variant kBoxVariants[] = {
     {64, 16, 2, 3, 64, false},  {64, 32, 2, 3, 64, false},  {32, 16, 2, 3, 64, false},
     {64, 16, 4, 3, 64, false},  {64, 8, 2, 3, 128, false},  {128, 16, 2, 3, 32, false},
     {64, 16, 1, 3, 128, false}, {64, 8, 1, 3, 128, false},  {128, 16, 2, 3, 32, true},
-    {64, 16, 2, 3, 64, true},
+    {64, 16, 2, 3, 64, true},   {128, 16, 2, 3, 32, true, true}, {64, 8, 2, 3, 128, false, true},
 };
 constexpr int kNumBox = sizeof(kBoxVariants) / sizeof(Variant);
 
@@ -32,9 +34,12 @@ cudaError_t launch_box_cc_high(const Sweep &s, const CUtensorMap &tmap, const Bo
 // the stage back to TMA, store the output plane it completes and free its
 // slot.  ROT = -1: the queue is shifted after the plane (slot 0 is the
 // oldest); ROT >= 0: the queue is rotated instead, the oldest partial sum in
-// slot ROT (the caller unrolls 2R+1 planes so ROT is a constant).  Returns
-// false when the CTA aborts (a bounded wait ran out).
-template <int R, int TX, int TY, int PY, int S, bool BOX, int ROT, typename Coef>
+// slot ROT (the caller unrolls 2R+1 planes so ROT is a constant).  ONEW: one
+// thread waits for the stage and the CTA barrier releases the others (and
+// tells thread 0 that plane j-1's stage is free); otherwise every thread
+// polls the mbarrier and the barrier follows the plane.  Returns false when
+// the CTA aborts (a bounded wait ran out).
+template <int R, int TX, int TY, int PY, int S, bool BOX, int ROT, bool ONEW, typename Coef>
 __device__ __forceinline__ bool plane_step(int j, int P, const CUtensorMap &tmap, const Coef &cf,
                                            float *planes, uint64_t *full, int &abort_flag,
                                            float (&acc)[2 * R + 1][PY][4], float *out, int nx, int ny,
@@ -45,7 +50,15 @@ __device__ __forceinline__ bool plane_step(int j, int P, const CUtensorMap &tmap
     constexpr int W = G::W;
     constexpr int Q = ROT < 0 ? 0 : ROT;  // physical slot of the oldest partial sum
     const int s = j % S;
-    if (ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err)) {
+    if constexpr (ONEW) {
+        if (threadIdx.x == 0 && !ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err)) abort_flag = 1;
+        __syncthreads();  // stage s is full for all, and every thread is done with plane j-1
+        if (abort_flag) return false;
+        if (threadIdx.x == 0 && j >= 1 && j - 1 + S < P) {
+            const int sp = (j - 1) % S;
+            ptx::mbar_arrive_expect_tx(&full[sp], G::PLANE * sizeof(float));
+            ptx::tma_load_3d(planes + sp * G::STAGE, &tmap, x0, y0, zb + j - 1 + S, &full[sp]);
+        }
         const float *pl = planes + s * G::STAGE;
         if constexpr (BOX)
             box_plane<R, PY, G::BX, G::NV, Q>(pl, cf, acc, tx, ry0);
@@ -54,13 +67,23 @@ __device__ __forceinline__ bool plane_step(int j, int P, const CUtensorMap &tmap
             star_plane<R, PY, G::BX, G::NV, Q>(pl, cf, acc, ctr, tx, ry0);
         }
     } else {
-        abort_flag = 1;
-    }
-    __syncthreads();  // every thread is done with stage s
-    if (abort_flag) return false;
-    if (threadIdx.x == 0 && j + S < P) {
-        ptx::mbar_arrive_expect_tx(&full[s], G::PLANE * sizeof(float));
-        ptx::tma_load_3d(planes + s * G::STAGE, &tmap, x0, y0, zb + j + S, &full[s]);
+        if (ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err)) {
+            const float *pl = planes + s * G::STAGE;
+            if constexpr (BOX)
+                box_plane<R, PY, G::BX, G::NV, Q>(pl, cf, acc, tx, ry0);
+            else {
+                float ctr[PY][4];
+                star_plane<R, PY, G::BX, G::NV, Q>(pl, cf, acc, ctr, tx, ry0);
+            }
+        } else {
+            abort_flag = 1;
+        }
+        __syncthreads();  // every thread is done with stage s
+        if (abort_flag) return false;
+        if (threadIdx.x == 0 && j + S < P) {
+            ptx::mbar_arrive_expect_tx(&full[s], G::PLANE * sizeof(float));
+            ptx::tma_load_3d(planes + s * G::STAGE, &tmap, x0, y0, zb + j + S, &full[s]);
+        }
     }
     const int zo = j - 2 * R;  // output plane completed by plane j
     if (zo >= 0) {
@@ -101,7 +124,7 @@ __device__ __forceinline__ bool plane_step(int j, int P, const CUtensorMap &tmap
 // Runs planes j0 .. j0+2R (those below P) with the queue rotated: input
 // plane j = j0 + u keeps its oldest partial sum (output plane j - 2R) in
 // slot (u + 1) mod (2R+1).
-template <int R, int TX, int TY, int PY, int S, bool BOX, typename Coef, int... U>
+template <int R, int TX, int TY, int PY, int S, bool BOX, bool ONEW, typename Coef, int... U>
 __device__ __forceinline__ bool rotated_block(std::integer_sequence<int, U...>, int j0, int P,
                                               const CUtensorMap &tmap, const Coef &cf, float *planes,
                                               uint64_t *full, int &abort_flag,
@@ -111,14 +134,14 @@ __device__ __forceinline__ bool rotated_block(std::integer_sequence<int, U...>, 
 {
     bool ok = true;
     ((ok = ok && (j0 + U >= P ||
-                  plane_step<R, TX, TY, PY, S, BOX, (U + 1) % (2 * R + 1)>(
+                  plane_step<R, TX, TY, PY, S, BOX, (U + 1) % (2 * R + 1), ONEW>(
                       j0 + U, P, tmap, cf, planes, full, abort_flag, acc, out, nx, ny, opy, opz, x0, y0,
                       zb, tx, ry0, gx, vec_store, err))),
      ...);
     return ok;
 }
 
-template <int R, int TX, int TY, int PY, int S, bool BOX, bool ROTQ, typename Coef>
+template <int R, int TX, int TY, int PY, int S, bool BOX, bool ROTQ, bool ONEW, typename Coef>
 __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     sweep_cc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Coef cf,
                     float *__restrict__ out, int nx, int ny, int nz, int64_t opy, int64_t opz,
@@ -170,25 +193,25 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
         // 2R+1 planes per iteration, so every queue slot index is a constant
         // and no partial sum is moved between registers
         for (int j0 = 0; j0 < P; j0 += W)
-            if (!rotated_block<R, TX, TY, PY, S, BOX, Coef>(std::make_integer_sequence<int, W>{}, j0, P,
+            if (!rotated_block<R, TX, TY, PY, S, BOX, ONEW, Coef>(std::make_integer_sequence<int, W>{}, j0, P,
                                                             tmap, cf, planes, full, abort_flag, acc, out,
                                                             nx, ny, opy, opz, x0, y0, zb, tx, ry0, gx,
                                                             vec_store, err))
                 return;
     } else {
         for (int j = 0; j < P; ++j)
-            if (!plane_step<R, TX, TY, PY, S, BOX, -1>(j, P, tmap, cf, planes, full, abort_flag, acc, out,
+            if (!plane_step<R, TX, TY, PY, S, BOX, -1, ONEW>(j, P, tmap, cf, planes, full, abort_flag, acc, out,
                                                        nx, ny, opy, opz, x0, y0, zb, tx, ry0, gx,
                                                        vec_store, err))
                 return;
     }
 }
 
-template <int R, int TX, int TY, int PY, int S, bool BOX, bool ROTQ, typename Coef>
+template <int R, int TX, int TY, int PY, int S, bool BOX, bool ROTQ, bool ONEW, typename Coef>
 cudaError_t launch_tiled(const Sweep &sw, const CUtensorMap &tmap, const Coef &cf, int tz)
 {
     using G = Geom<R, TX, TY, PY, S>;
-    auto kern = sweep_cc_kernel<R, TX, TY, PY, S, BOX, ROTQ, Coef>;
+    auto kern = sweep_cc_kernel<R, TX, TY, PY, S, BOX, ROTQ, ONEW, Coef>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)G::SMEM);
     if (e != cudaSuccess) return e;
@@ -224,7 +247,8 @@ cudaError_t launch_tiled(const Sweep &sw, const CUtensorMap &tmap, const Coef &c
 #define MMS_SWEEP_CASE(TAB, R, BOX, Coef, sw, tmap, cf, I)                                      \
     case I:                                                                                     \
         if constexpr (I < (int)(sizeof(TAB) / sizeof(Variant)))                                 \
-            return launch_tiled<R, TAB[I].tx, TAB[I].ty, TAB[I].py, TAB[I].s, BOX, TAB[I].rot, Coef>( \
+            return launch_tiled<R, TAB[I].tx, TAB[I].ty, TAB[I].py, TAB[I].s, BOX, TAB[I].rot,        \
+                                TAB[I].one_wait, Coef>(                                           \
                 sw, tmap, cf, TAB[I].tz);                                                       \
         else                                                                                    \
             return cudaErrorInvalidValue;

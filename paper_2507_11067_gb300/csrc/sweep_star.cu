@@ -10,12 +10,12 @@ namespace {
 using sweep::Variant;
 using sweep::launch_tiled;
 
-// Star tile variants (TX, TY, PY, stages, TZ, rotated queue).
+// Star tile variants (TX, TY, PY, stages, TZ, rotated queue, one waiter).
 constexpr Variant kStarVariants[] = {
-    {64, 16, 2, 4, 128, false}, {64, 32, 4, 3, 128, false}, {128, 32, 2, 3, 64, false},
-    {64, 16, 1, 3, 128, false}, {64, 16, 2, 4, 128, true},  {64, 32, 4, 3, 128, true},
-    {128, 32, 2, 3, 64, true},  {64, 16, 2, 6, 128, true},  {64, 16, 2, 8, 128, true},
-    {64, 32, 2, 6, 128, true},  {128, 16, 2, 6, 128, true}, {64, 16, 4, 4, 128, true},
+    {64, 16, 2, 4, 128, false},       {64, 32, 4, 3, 128, false},       {128, 32, 2, 3, 64, false},
+    {64, 16, 2, 3, 128, false, true}, {64, 16, 2, 4, 128, true},        {64, 32, 2, 4, 128, false, true},
+    {128, 32, 2, 3, 64, true},        {64, 16, 2, 4, 128, true, true},  {128, 32, 2, 3, 64, true, true},
+    {64, 32, 4, 3, 128, false, true}, {64, 16, 2, 4, 128, false, true}, {128, 16, 2, 4, 128, false, true},
 };
 constexpr int kNumStar = sizeof(kStarVariants) / sizeof(Variant);
 
