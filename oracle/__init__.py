@@ -83,14 +83,16 @@ SHAPES = {"star": 0, "box": 1}
 
 def n_coeffs(shape: str, r: int) -> int:
     """Number of stored coefficients: 3(2r+1) per-axis weights for a star,
-    (2r+1)^3 for a box (Sec. 1, Fig. 1; Table I point counts)."""
+    (2r+1)^3 for a box (Sec. 1, Fig. 1; Table I point counts); the planar
+    star2d and box2d of Table I's 2D kernels: 2(2r+1) and (2r+1)^2."""
     w = 2 * r + 1
-    return 3 * w if shape == "star" else w ** 3
+    return {"star": 3 * w, "box": w ** 3, "star2d": 2 * w, "box2d": w * w}[shape]
 
 
 def n_points(shape: str, r: int) -> int:
-    """Distinct stencil points: 6r+1 for a 3D star, (2r+1)^3 for a 3D box."""
-    return 6 * r + 1 if shape == "star" else (2 * r + 1) ** 3
+    """Distinct stencil points: 6r+1 for a 3D star, (2r+1)^3 for a 3D box,
+    4r+1 and (2r+1)^2 for their planar counterparts."""
+    return {"star": 6 * r + 1, "box": (2 * r + 1) ** 3, "star2d": 4 * r + 1, "box2d": (2 * r + 1) ** 2}[shape]
 
 
 # ------------------------------------------------------------------ sweeps
@@ -122,6 +124,63 @@ def stencil(shape: str, r: int, coeffs, grid) -> np.ndarray:
     if out.size:
         _load().orc_stencil(SHAPES[shape], r, _ptr(c), _ptr(g), g.shape[2],
                             g.shape[1] * g.shape[2], nx, ny, nz, _ptr(out))
+    return out
+
+
+def stencil2d(shape: str, r: int, coeffs, grid) -> np.ndarray:
+    """The planar stencils of Table I's 2D kernels on nz independent planes.
+
+    ``grid`` is (nz, ny+2r, nx+2r), padded in x and y only; the FP64 result
+    (nz, ny, nx) is, for box2d with weights c[dy][dx],
+        out(x, y, z) = sum_{dy,dx} c[dy][dx] in(x+r+dx, y+r+dy, z),
+    and for star2d with per-axis weights cx, cy the x line plus the y line
+    (the applied centre is cx[0] + cy[0]) -- Sec. 1, Fig. 1 in one plane.
+    """
+    if shape not in ("star2d", "box2d") or r < 1:
+        raise ValueError("planar shape star2d or box2d, radius >= 1")
+    c = np.asarray(coeffs, dtype=np.float64).reshape(-1)
+    if c.size != n_coeffs(shape, r):
+        raise ValueError(f"{shape} r={r} needs {n_coeffs(shape, r)} coefficients, got {c.size}")
+    g = np.asarray(grid, dtype=np.float64)
+    if g.ndim != 3:
+        raise ValueError("grid must be (nz, ny+2r, nx+2r)")
+    nz, ny, nx = g.shape[0], g.shape[1] - 2 * r, g.shape[2] - 2 * r
+    if min(nx, ny) < 0:
+        raise ValueError("grid smaller than its halo")
+    w = 2 * r + 1
+    out = np.zeros((nz, ny, nx))
+    if shape == "box2d":
+        c = c.reshape(w, w)
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                out += c[dy + r, dx + r] * g[:, r + dy:r + dy + ny, r + dx:r + dx + nx]
+    else:
+        cx, cy = c[:w], c[w:]
+        for d in range(-r, r + 1):
+            out += cx[d + r] * g[:, r:r + ny, r + d:r + d + nx]
+            out += cy[d + r] * g[:, r + d:r + d + ny, r:r + nx]
+    return out
+
+
+def stencil2d_points(shape: str, r: int, coeffs, grid, xyz) -> np.ndarray:
+    """stencil2d at the points ``xyz`` (npts, 3) = (x, y, plane) only; the
+    grid is read in place."""
+    pts = np.asarray(xyz, dtype=np.int64).reshape(-1, 3)
+    g = np.asarray(grid)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    c = np.asarray(coeffs, dtype=np.float64).reshape(-1)
+    w = 2 * r + 1
+    out = np.zeros(len(pts))
+    if shape == "box2d":
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                out += c[(dy + r) * w + dx + r] * g[z, y + r + dy, x + r + dx].astype(np.float64)
+    elif shape == "star2d":
+        for d in range(-r, r + 1):
+            out += c[d + r] * g[z, y + r, x + r + d].astype(np.float64)
+            out += c[w + d + r] * g[z, y + r + d, x + r].astype(np.float64)
+    else:
+        raise ValueError("planar shape star2d or box2d")
     return out
 
 

@@ -50,3 +50,13 @@ def test_table1_point_counts(row):
     assert impulse_points(shape, r, dims, seed=r * 10 + dims) == pts
     if dims == 3:
         assert oracle.n_points(shape, r) == pts
+    else:
+        # the oracle's own planar stencil touches the same number of points
+        shape2 = shape + "2d"
+        assert oracle.n_points(shape2, r) == pts
+        g = np.random.default_rng(r)
+        c = g.uniform(0.5, 1.5, oracle.n_coeffs(shape2, r)) * g.choice([-1.0, 1.0], oracle.n_coeffs(shape2, r))
+        n = 4 * r + 3
+        grid = np.zeros((1, n + 2 * r, n + 2 * r))
+        grid[0, r + n // 2, r + n // 2] = 1.0
+        assert np.count_nonzero(oracle.stencil2d(shape2, r, c, grid)) == pts

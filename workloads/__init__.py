@@ -37,11 +37,11 @@ def rng(workload: int, salt: int = 0) -> np.random.Generator:
 
 def n_coeffs(shape: str, r: int) -> int:
     w = 2 * r + 1
-    return 3 * w if shape == "star" else w ** 3
+    return {"star": 3 * w, "box": w ** 3, "star2d": 2 * w, "box2d": w * w}[shape]
 
 
 def n_points(shape: str, r: int) -> int:
-    return 6 * r + 1 if shape == "star" else (2 * r + 1) ** 3
+    return {"star": 6 * r + 1, "box": (2 * r + 1) ** 3, "star2d": 4 * r + 1, "box2d": (2 * r + 1) ** 2}[shape]
 
 
 def padded_shape(nx: int, ny: int, nz: int, r: int):
@@ -63,11 +63,27 @@ def normal_coeffs(shape: str, r: int, workload: int, salt=0) -> np.ndarray:
 
     Box: (2r+1)^3 entries [dz][dy][dx].  Star: (3, 2r+1) per-axis entries
     [axis x,y,z][d+r]; the applied centre is the sum of the three centres.
+    The planar shapes: box2d (2r+1)^2 entries [dy][dx], star2d (2, 2r+1)
+    entries [axis x,y][d+r].
     """
     g = rng(workload, 100 + salt)
     sd = 1.0 / math.sqrt(n_points(shape, r))
     c = g.normal(0.0, sd, size=n_coeffs(shape, r)).astype(np.float32)
-    return c.reshape(3, 2 * r + 1) if shape == "star" else c
+    if shape == "star":
+        return c.reshape(3, 2 * r + 1)
+    if shape == "star2d":
+        return c.reshape(2, 2 * r + 1)
+    return c
+
+
+def uniform_grid2d(nx, ny, nz, r, workload, salt=0, lo=-1.0, hi=1.0) -> np.ndarray:
+    """nz independent planes padded in x and y only: (nz, ny+2r, nx+2r)
+    float32, every value U[lo, hi]."""
+    g = rng(workload, salt)
+    out = np.empty((nz, ny + 2 * r, nx + 2 * r), dtype=np.float32)
+    for z in range(nz):
+        out[z] = g.uniform(lo, hi, size=out.shape[1:])
+    return out
 
 
 def fd8_star_coeffs() -> np.ndarray:
