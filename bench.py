@@ -42,6 +42,7 @@ WORKLOADS = {
     "box512": [("box", 1, 512), ("box", 2, 512)],
     "star1024": [("star", 4, 1024)],
     "star512": [("star", 4, 512)],
+    "plane8192": [("star2d", 2, 8192), ("star2d", 4, 8192), ("box2d", 2, 8192), ("box2d", 3, 8192)],
     "rtm512": None,    # acoustic forward: 8 shots x 512^3, 500 steps (see run_wave)
     "grad256": None,   # adjoint gradient: 2 shots x 256^3, 200 steps, checkpoint 20
 }
@@ -51,6 +52,8 @@ WORKLOAD_NAMES = {
                 "16 sinusoids + 1e-3 noise",
     "star512": "star stencil sweep r=4 (25 pt, FD8 weights), 512^3 FP32 interior + halo, "
                "16 sinusoids + 1e-3 noise (profiling size)",
+    "plane8192": "Table I's 2D kernels (2DStarR2, 2DStarR4, 2DBoxR2, 2DBoxR3) on one 8192^2 FP32 plane "
+                 "each, weights N(0, 1/npts), input U[-1, 1]",
     "rtm512": "batched acoustic forward, 8 shots x 512^3, r=4 FD8 star, 20-cell sponge, h=10 m, "
               "CFL 0.4, 15 Hz Ricker, one CUDA graph per run",
     "grad256": "adjoint gradient of 0.5|d - d_obs|^2 wrt velocity, 2 shots x 256^3, 200 steps, "
@@ -61,10 +64,34 @@ WORKLOAD_NAMES = {
 def sweep_coeffs(shape, r):
     if shape == "star":
         return workloads.star_coeffs(r)
+    if shape in PLANAR:
+        return workloads.normal_coeffs(shape, r, workload=6, salt=r)
     return workloads.normal_coeffs("box", r, workload=2, salt=r)
 
 
+PLANAR = ("star2d", "box2d")
+
+
+def sweep_dims(shape, n):
+    """Interior (nx, ny, nz) of a sweep of size n: n^3, or one n^2 plane."""
+    return (n, n, 1) if shape in PLANAR else (n, n, n)
+
+
+def sweep_points(shape, n):
+    nx, ny, nz = sweep_dims(shape, n)
+    return nx * ny * nz
+
+
+def sweep_bytes(shape, r, n):
+    """Algorithmic bytes: the padded input read once, the output written once."""
+    nx, ny, nz = sweep_dims(shape, n)
+    rz = 0 if shape in PLANAR else r
+    return 4 * ((nx + 2 * r) * (ny + 2 * r) * (nz + 2 * rz) + nx * ny * nz)
+
+
 def sweep_input(shape, r, n, rank):
+    if shape in PLANAR:
+        return workloads.uniform_grid2d(n, n, 1, r, workload=6, salt=r + 100 * rank)
     if shape == "star":
         return workloads.sinusoid_grid(n, n, n, r, workload=3, salt=rank)
     return workloads.uniform_grid(n, n, n, r, workload=2, salt=r + 100 * rank)
@@ -88,7 +115,7 @@ def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
 
 
 def flop_per_pt(shape, r):
-    return 2 * (6 * r + 1 if shape == "star" else (2 * r + 1) ** 3)
+    return 2 * workloads.n_points(shape, r)
 
 
 def peaks():
@@ -134,13 +161,14 @@ TC_TXO = {1: 40, 2: 24, 3: 16, 4: 12}
 TC_PATHS = ("tf32", "3xtf32", "bf16x3")
 
 
-def tc_dense_flop_per_pt(path: str, r: int) -> int:
+def tc_dense_flop_per_pt(path: str, r: int, planar: bool = False) -> int:
     """Dense work the banded MMAs issue per output point (band zeros
-    included): 2 K_pad per (dz, dy) pass, (2r+1)^2 passes, times the split
-    products (3 for 3xTF32 / BF16x3, 1 for TF32)."""
+    included): 2 K_pad per (dz, dy) pass, (2r+1)^2 passes ((2r+1) for a
+    planar stencil), times the split products (3 for 3xTF32 / BF16x3, 1 for
+    TF32)."""
     step = 16 if path == "bf16x3" else 8
     k_pad = -(-(TC_TXO[r] + 2 * r) // step) * step
-    return 2 * k_pad * (2 * r + 1) ** 2 * (1 if path == "tf32" else 3)
+    return 2 * k_pad * (2 * r + 1) ** (1 if planar else 2) * (1 if path == "tf32" else 3)
 
 
 def fp32_alu_peak_tflops(n_sm: int, mhz: float) -> float:
@@ -202,6 +230,14 @@ def oracle_sample(planes: int, salt: int = 0, plan=None):
     for shape, r, n in plan:
         c = sweep_coeffs(shape, r)
         g = workloads.rng(2 if shape == "box" else 3, 50 + r + 100 * salt)
+        if shape in PLANAR:
+            # a slab of `planes` output rows of the n^2 plane
+            sub = g.uniform(-1, 1, size=(1, planes + 2 * r, n + 2 * r))
+            t0 = time.perf_counter()
+            oracle.stencil2d(shape, r, c, sub)
+            secs += time.perf_counter() - t0
+            pts += planes * n
+            continue
         sub = g.uniform(-1, 1, size=(planes + 2 * r, n + 2 * r, n + 2 * r))
         t0 = time.perf_counter()
         oracle.stencil(shape, r, c, sub)
@@ -338,19 +374,21 @@ def main():
     for (shape, r, n) in plan:
         coeffs.append(sweep_coeffs(shape, r))
         grid = sweep_input(shape, r, n, rank)
+        nx_, ny_, nz_ = sweep_dims(shape, n)
+        alloc = mms.padded_empty2d if shape in PLANAR else mms.padded_empty
         # host buffer pinned with the device pitch, so each copy is one memcpy
-        hp = mms.padded_empty(n, n, n, r, device="cpu", zero=False)
+        hp = alloc(nx_, ny_, nz_, r, device="cpu", zero=False)
         hp = torch.as_strided(torch.empty(hp.untyped_storage().nbytes() // 4, pin_memory=True),
                               hp.shape, hp.stride())
         hp.copy_(torch.from_numpy(grid))
         hosts.append(hp)
-        inputs.append(mms.padded_empty(n, n, n, r, device=dev, zero=False))
+        inputs.append(alloc(nx_, ny_, nz_, r, device=dev, zero=False))
         inputs[-1].copy_(hosts[-1])
-        outputs.append(torch.empty((n, n, n), device=dev))
-        host_out.append(torch.empty((n, n, n), pin_memory=True))
+        outputs.append(torch.empty((nz_, ny_, nx_), device=dev))
+        host_out.append(torch.empty((nz_, ny_, nx_), pin_memory=True))
         del grid
     stream = torch.cuda.current_stream(dev)
-    steps = args.steps or max(20, int(2000 / max(1, sum(n ** 3 for _, _, n in plan) / 2.7e8)))
+    steps = args.steps or max(20, int(2000 / max(1, sum(sweep_points(sh, n) for sh, _, n in plan) / 2.7e8)))
 
     def sweep(i):
         shape, r, _ = plan[i]
@@ -381,7 +419,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     elapsed = max_over_ranks(t_start.elapsed_time(t_end) / 1e3, dist, dev)
-    pts_step = sum(n ** 3 for _, _, n in plan)
+    pts_step = sum(sweep_points(sh, n) for sh, _, n in plan)
     value = job_rate(world, pts_step * steps, elapsed)
     kms = [statistics.mean(a.elapsed_time(b) for a, b in ev) for ev in kernel_ev]
 
@@ -391,7 +429,7 @@ def main():
     # copy in, sweep, copy out, pipelined).  Consecutive steps alternate
     # between two streams, so one step's slab pipeline overlaps the next's.
     streams = [stream, torch.cuda.Stream(dev)]
-    hout_sets = [host_out, [torch.empty((n, n, n), pin_memory=True) for (_, _, n) in plan]]
+    hout_sets = [host_out, [torch.empty(o.shape, pin_memory=True) for o in host_out]]
 
     def e2e_step(k):
         st = streams[k % 2]
@@ -431,20 +469,21 @@ def main():
     di = max(range(len(plan)), key=lambda i: kms[i])
     shape, r, n = plan[di]
     sec = kms[di] / 1e3
-    bytes_alg = 4 * ((n + 2 * r) ** 3 + n ** 3)
-    flops = flop_per_pt(shape, r) * n ** 3
+    npts = sweep_points(shape, n)
+    bytes_alg = sweep_bytes(shape, r, n)
+    flops = flop_per_pt(shape, r) * npts
     resolved = mms.auto_path(shape, r) if path_used == "auto" else path_used
-    if resolved in TC_PATHS and shape == "box":
+    if resolved in TC_PATHS and shape != "star":
         # tensor pipe: the banded products' dense work against the BF16 peak
         # (TF32 at the nominal TF32/BF16 ratio 1.1/2.25)
         tpk, tsrc = bf16_sustained_peak()
         if resolved != "bf16x3":
             tpk, tsrc = tpk * 1.1 / 2.25, tsrc + " x 1.1/2.25 (TF32)"
-        dense = tc_dense_flop_per_pt(resolved, r) * n ** 3
+        dense = tc_dense_flop_per_pt(resolved, r, shape in PLANAR) * npts
         roofline = {"bound": "tensor", "achieved": dense / sec / 1e12, "peak": tpk, "unit": "TFLOP/s",
                     "frac": dense / sec / 1e12 / tpk, "traffic": None,
                     "peak_note": f"MEASURED_PEAKS.json bf16 ({tsrc}); achieved counts the banded MMAs' "
-                                 f"dense work, {tc_dense_flop_per_pt(resolved, r)} flop/pt (band zeros "
+                                 f"dense work, {tc_dense_flop_per_pt(resolved, r, shape in PLANAR)} flop/pt (band zeros "
                                  f"included); the stencil's own {flop_per_pt(shape, r)} flop/pt run at "
                                  f"{flops / sec / 1e12:.1f} TFLOP/s"}
     elif flops / bytes_alg > alu_peak * 1e12 / (hbm_peak * 1e9):
@@ -456,10 +495,10 @@ def main():
         roofline = {"bound": "hbm", "achieved": bytes_alg / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "frac": bytes_alg / sec / 1e9 / hbm_peak, "traffic": None,
                     "peak_note": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
-    var = mms.default_variant(shape, r, resolved, n, n, n)
-    roofline["kernel"] = f"{shape} r={r} {n}^3 sweep ({resolved}, variant {var})"
+    var = mms.default_variant(shape, r, resolved, *sweep_dims(shape, n))
+    roofline["kernel"] = f"{shape} r={r} {n}^{2 if shape in PLANAR else 3} sweep ({resolved}, variant {var})"
     roofline["ms"] = kms[di]
-    tr = captured_traffic(f"{resolved} {shape} r={r} v{var}", n ** 3)
+    tr = captured_traffic(f"{resolved} {shape} r={r} v{var}", npts)
     roofline["traffic"] = tr
     if tr:
         roofline["traffic_over_algorithmic"] = tr / bytes_alg
@@ -467,9 +506,9 @@ def main():
     sweeps = {}
     for i, (shape, r, n) in enumerate(plan):
         sec = kms[i] / 1e3
-        b = 4 * ((n + 2 * r) ** 3 + n ** 3)
-        f = flop_per_pt(shape, r) * n ** 3
-        sweeps[f"{shape}_r{r}_{n}"] = {"ms": kms[i], "gpts": n ** 3 / sec / 1e9,
+        b = sweep_bytes(shape, r, n)
+        f = flop_per_pt(shape, r) * sweep_points(shape, n)
+        sweeps[f"{shape}_r{r}_{n}"] = {"ms": kms[i], "gpts": sweep_points(shape, n) / sec / 1e9,
                                        "hbm_gbs": b / sec / 1e9, "hbm_frac": b / sec / 1e9 / hbm_peak,
                                        "tflops": f / sec / 1e12, "alu_frac": f / sec / 1e12 / alu_peak}
 
@@ -492,7 +531,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAMES[args.workload], "path": path_used,
-                   "sweeps": [f"{sh} r={r} {n}^3" for sh, r, n in plan],
+                   "sweeps": [f"{sh} r={r} {n}^{2 if sh in PLANAR else 3}" for sh, r, n in plan],
                    "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline, "cpu_baseline": cpu,

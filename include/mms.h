@@ -49,10 +49,12 @@ typedef enum {
     MMS_E_NOMEM = 7         /* host-side allocation of a cache entry failed */
 } mms_status;
 
-/* Stencil shapes (paper Sec. 1, Fig. 1). */
+/* Stencil shapes (paper Sec. 1, Fig. 1; Table I lists 3D and 2D kernels). */
 typedef enum {
-    MMS_STAR = 0,  /* axis neighbours only: 6r+1 points */
-    MMS_BOX = 1    /* full (2r+1)^3 cube */
+    MMS_STAR = 0,    /* axis neighbours only: 6r+1 points */
+    MMS_BOX = 1,     /* full (2r+1)^3 cube */
+    MMS_STAR2D = 2,  /* planar star, x and y neighbours: 4r+1 points per plane */
+    MMS_BOX2D = 3    /* planar box, (2r+1)^2 points per plane */
 } mms_shape;
 
 /* Computation paths of a sweep. */
@@ -70,8 +72,18 @@ typedef enum {
  *   star: 3*(2r+1) values, c[axis*(2r+1) + d+r] for axis 0=x, 1=y, 2=z and
  *         d = -r..r; the applied centre weight is cx[0]+cy[0]+cz[0];
  *   box:  (2r+1)^3 values, c[((dz+r)*(2r+1) + dy+r)*(2r+1) + dx+r].
+ *   star2d: 2*(2r+1) values, c[axis*(2r+1) + d+r] for axis 0=x, 1=y; the
+ *         applied centre is cx[0]+cy[0];
+ *   box2d:  (2r+1)^2 values, c[(dy+r)*(2r+1) + dx+r].
  * The paper's Sec. 4.1 turns each axis's 1D weights into a banded coefficient
  * matrix; the library builds those bands from these arrays.
+ *
+ * The planar shapes (Table I's 2D kernels) apply to nz independent planes
+ * padded by r in x and y only: input element (X,Y,z), 0 <= X < nx+2r,
+ * 0 <= Y < ny+2r, 0 <= z < nz, lives at in[z*in_pitch_z + Y*in_pitch_y + X]
+ * (dense in_pitch_z = (ny+2r)*in_pitch_y) and
+ *     out(x,y,z) = sum_d c_d * in(x+r+dx, y+r+dy, z);
+ * nz = 1 is a single 2D grid.
  */
 
 /*

@@ -6,16 +6,16 @@ autograd wrapper of the wave propagator and the tile autotuner.  Importing
 the package does not load the library; the first call does, and fails
 loudly if the library has not been built.
 """
-from ._lib import (BOX, PATHS, STAR, MMSError, apply, apply_dense, apply_host, auto_path, check_device,
+from ._lib import (BOX, BOX2D, PATHS, STAR, STAR2D, MMSError, apply, apply_dense, apply_host, auto_path, check_device,
                    default_variant,
                    dot_f64, field_geometry, grad_to_velocity, load, model_from_velocity,
-                   num_variants, padded_empty, pitches, set_variant, sum_f64, to_padded_device,
+                   num_variants, padded_empty, padded_empty2d, pitches, set_variant, sum_f64, to_padded_device, to_padded_device2d,
                    version, wave_adjoint, wave_desc, wave_forward, wave_step, wave_step_to)
 from .build import build
 
-__all__ = ["BOX", "PATHS", "STAR", "MMSError", "apply", "apply_dense", "apply_host", "auto_path", "build",
+__all__ = ["BOX", "BOX2D", "PATHS", "STAR", "STAR2D", "MMSError", "apply", "apply_dense", "apply_host", "auto_path", "build",
            "check_device",
            "default_variant", "dot_f64", "field_geometry", "grad_to_velocity", "load",
-           "model_from_velocity", "num_variants", "padded_empty", "pitches", "set_variant", "sum_f64",
-           "to_padded_device", "version", "wave_adjoint", "wave_desc", "wave_forward", "wave_step",
+           "model_from_velocity", "num_variants", "padded_empty", "padded_empty2d", "pitches", "set_variant", "sum_f64",
+           "to_padded_device", "to_padded_device2d", "version", "wave_adjoint", "wave_desc", "wave_forward", "wave_step",
            "wave_step_to"]

@@ -15,8 +15,17 @@ import numpy as np
 
 from . import build as _build
 
-STAR, BOX = 0, 1
-SHAPES = {"star": STAR, "box": BOX, STAR: STAR, BOX: BOX}
+STAR, BOX, STAR2D, BOX2D = 0, 1, 2, 3
+SHAPES = {"star": STAR, "box": BOX, "star2d": STAR2D, "box2d": BOX2D,
+          STAR: STAR, BOX: BOX, STAR2D: STAR2D, BOX2D: BOX2D}
+PLANAR = (STAR2D, BOX2D)
+
+
+def interior(shape, r, padded_shape):
+    """(nx, ny, nz) of a padded (Z, Y, X) grid: the planar shapes have no z
+    halo (nz independent planes)."""
+    Z, Y, X = padded_shape
+    return X - 2 * r, Y - 2 * r, Z - (0 if SHAPES[shape] in PLANAR else 2 * r)
 PATHS = {"auto": 0, "cuda_core": 1, "tf32": 2, "3xtf32": 3, "bf16x3": 4, "naive": 5}
 PATH_NAMES = {v: k for k, v in PATHS.items()}
 STATUS = {0: "MMS_OK", 1: "MMS_E_ARG", 2: "MMS_E_UNSUPPORTED", 3: "MMS_E_ALIGN", 4: "MMS_E_CUDA",
@@ -162,6 +171,25 @@ def pitches(t):
     return t.stride(1), t.stride(0)
 
 
+def padded_empty2d(nx, ny, nz, r, device="cuda", align=32, zero=True):
+    """nz planes padded by r in x and y only: a (nz, ny+2r, nx+2r) view over
+    storage whose row pitch is rounded up to `align` elements."""
+    import torch
+    X, Y = nx + 2 * r, ny + 2 * r
+    py = -(-X // align) * align
+    base = (torch.zeros if zero else torch.empty)((nz, Y, py), device=device, dtype=torch.float32)
+    return base[..., :X]
+
+
+def to_padded_device2d(grid: np.ndarray, r: int, device="cuda", align=32):
+    """Copy host planes (nz, ny+2r, nx+2r) into a pitched device view."""
+    import torch
+    Z, Y, X = grid.shape
+    t = padded_empty2d(X - 2 * r, Y - 2 * r, Z, r, device=device, align=align, zero=False)
+    t.copy_(torch.from_numpy(np.ascontiguousarray(grid, dtype=np.float32)))
+    return t
+
+
 def to_padded_device(grid: np.ndarray, r: int, device="cuda", align=32):
     """Copy a host padded grid (nz+2r, ny+2r, nx+2r) into a pitched device view."""
     import torch
@@ -182,8 +210,7 @@ def apply(shape, r, coeffs, inp, out=None, path="auto", variant=-1, stream=None)
     import torch
     if not inp.is_cuda or inp.dtype != torch.float32:
         raise ValueError("input must be a CUDA float32 tensor")
-    Z, Y, X = inp.shape
-    nx, ny, nz = X - 2 * r, Y - 2 * r, Z - 2 * r
+    nx, ny, nz = interior(shape, r, inp.shape)
     if out is None:
         out = torch.empty((nz, ny, nx), device=inp.device, dtype=torch.float32)
     ipy, ipz = pitches(inp)
@@ -202,8 +229,7 @@ def apply_noalloc(r, coeffs, inp, out=None, path="bf16x3", variant=-1, stream=No
     import torch
     if not inp.is_cuda or inp.dtype != torch.float32:
         raise ValueError("input must be a CUDA float32 tensor")
-    Z, Y, X = inp.shape
-    nx, ny, nz = X - 2 * r, Y - 2 * r, Z - 2 * r
+    nx, ny, nz = interior(shape, r, inp.shape)
     if out is None:
         out = torch.empty((nz, ny, nx), device=inp.device, dtype=torch.float32)
     ipy, ipz = pitches(inp)
@@ -223,8 +249,7 @@ def apply_host(shape, r, coeffs, host_in, host_out, path="auto", variant=-1, str
     import torch
     if host_in.is_cuda or host_out.is_cuda or host_in.dtype != torch.float32:
         raise ValueError("host_in and host_out must be CPU float32 tensors")
-    Z, Y, X = host_in.shape
-    nx, ny, nz = X - 2 * r, Y - 2 * r, Z - 2 * r
+    nx, ny, nz = interior(shape, r, host_in.shape)
     ipy, ipz = pitches(host_in)
     opy, opz = pitches(host_out)
     c = _host_coeffs(coeffs)
@@ -237,9 +262,9 @@ def apply_host(shape, r, coeffs, host_in, host_out, path="auto", variant=-1, str
 def apply_dense(shape, r, coeffs, inp, out, stream=None):
     """mms_stencil_apply on dense contiguous tensors (AUTO path)."""
     c = _host_coeffs(coeffs)
-    Z, Y, X = inp.shape
+    nx, ny, nz = interior(shape, r, inp.shape)
     check(load().mms_stencil_apply(SHAPES[shape], r, c.ctypes.data_as(ctypes.c_void_p), _ptr(inp),
-                                   _ptr(out), X - 2 * r, Y - 2 * r, Z - 2 * r, _stream(stream)))
+                                   _ptr(out), nx, ny, nz, _stream(stream)))
     return out
 
 

@@ -19,8 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmms.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["abi.cu", "sweep_cc.cu", "sweep_star.cu", "sweep_box_high.cu", "wave.cu", "band_tc.cu",
-           "noalloc.cu"]
+SOURCES = ["abi.cu", "sweep_cc.cu", "sweep_star.cu", "sweep_box_high.cu", "sweep_2d.cu", "wave.cu",
+           "band_tc.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

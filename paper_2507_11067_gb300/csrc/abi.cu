@@ -80,7 +80,7 @@ bool encode_tmap_4d(CUtensorMap *map, const float *base, int64_t X, int64_t Y, i
 
 // ------------------------------------------------------- variant table
 static std::mutex g_var_mu;
-static int g_tuned[2][kMaxR + 1][8];
+static int g_tuned[4][kMaxR + 1][8];
 static bool g_tuned_init = false;
 
 static int tuned_variant(int shape, int r, int path)
@@ -97,9 +97,10 @@ static int tuned_variant(int shape, int r, int path)
 
 static int num_variants(int shape, int r, int path)
 {
-    if (shape < 0 || shape > 1 || r < 1 || r > kMaxR) return 0;
+    if (shape < 0 || shape > 3 || r < 1 || r > kMaxR) return 0;
     switch (path) {
-        case MMS_PATH_CUDA_CORE: return shape == MMS_STAR ? star_cc_variants() : box_cc_variants();
+        case MMS_PATH_CUDA_CORE:
+            return shape == MMS_STAR ? star_cc_variants() : shape == MMS_BOX ? box_cc_variants() : plane_cc_variants();
         case MMS_PATH_NAIVE: return 1;
         case MMS_PATH_TF32:
         case MMS_PATH_3XTF32:
@@ -143,7 +144,7 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
 {
     if (!d) return fail(MMS_E_ARG, "null descriptor");
     const int shape = d->shape, r = d->radius;
-    if (shape != MMS_STAR && shape != MMS_BOX) return fail(MMS_E_ARG, "shape %d is not STAR or BOX", shape);
+    if (shape < MMS_STAR || shape > MMS_BOX2D) return fail(MMS_E_ARG, "shape %d is not STAR, BOX, STAR2D or BOX2D", shape);
     if (r < 1 || r > kMaxR) return fail(MMS_E_ARG, "radius %d outside 1..%d", r, kMaxR);
     if (!d->coeffs) return fail(MMS_E_ARG, "null coefficient array");
     if (d->nx < 0 || d->ny < 0 || d->nz < 0) return fail(MMS_E_ARG, "negative size");
@@ -152,7 +153,8 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
     if (d->path < MMS_PATH_AUTO || d->path > MMS_PATH_NAIVE) return fail(MMS_E_ARG, "unknown path %d", d->path);
     if (d->nx == 0 || d->ny == 0 || d->nz == 0) return MMS_OK;
     if (!in || !out) return fail(MMS_E_ARG, "null grid pointer");
-    const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * r;
+    // planar shapes: nz independent planes, padded in x and y only
+    const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + (is_planar(shape) ? 0 : 2 * r);
     const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
     const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
     const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
@@ -182,10 +184,14 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
     CUtensorMap map;
     if (path == MMS_PATH_CUDA_CORE) {
         int bx, by;
-        if (shape == MMS_STAR) star_cc_box(r, v, &bx, &by); else box_cc_box(r, v, &bx, &by);
+        if (shape == MMS_STAR) star_cc_box(r, v, &bx, &by);
+        else if (shape == MMS_BOX) box_cc_box(r, v, &bx, &by);
+        else plane_cc_box(r, v, &bx, &by);
         if (!encode_tmap_3d(&map, in, X, Y, Z, ipy, ipz, bx, by, 1))
             return fail(MMS_E_CUDA, "cuTensorMapEncodeTiled refused the input grid");
-        cudaError_t e = shape == MMS_STAR ? launch_star_cc(s, map, v) : launch_box_cc(s, map, v);
+        cudaError_t e = shape == MMS_STAR ? launch_star_cc(s, map, v)
+                        : shape == MMS_BOX ? launch_box_cc(s, map, v)
+                                           : launch_plane_cc(s, map, v);
         return e == cudaSuccess ? MMS_OK : cuda_fail(e, "CUDA-core sweep launch");
     }
     int bx, by, bz, swz;
@@ -217,7 +223,9 @@ static mms_status apply_host(const mms_stencil_desc *d, const float *in, float *
 {
     if (!d) return fail(MMS_E_ARG, "null descriptor");
     const int r = d->radius;
-    if (d->shape != MMS_STAR && d->shape != MMS_BOX) return fail(MMS_E_ARG, "shape %d is not STAR or BOX", d->shape);
+    if (d->shape < MMS_STAR || d->shape > MMS_BOX2D)
+        return fail(MMS_E_ARG, "shape %d is not STAR, BOX, STAR2D or BOX2D", d->shape);
+    const int rz = is_planar(d->shape) ? 0 : r;  // z halo of the input
     if (r < 1 || r > kMaxR) return fail(MMS_E_ARG, "radius %d outside 1..%d", r, kMaxR);
     if (!d->coeffs) return fail(MMS_E_ARG, "null coefficient array");
     if (d->nx < 0 || d->ny < 0 || d->nz < 0) return fail(MMS_E_ARG, "negative size");
@@ -227,7 +235,7 @@ static mms_status apply_host(const mms_stencil_desc *d, const float *in, float *
     if (d->variant < -1) return fail(MMS_E_ARG, "variant %d", d->variant);
     if (d->nx == 0 || d->ny == 0 || d->nz == 0) return MMS_OK;
     if (!in || !out) return fail(MMS_E_ARG, "null grid pointer");
-    const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * r;
+    const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * rz;
     const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
     const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
     const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
@@ -244,7 +252,7 @@ static mms_status apply_host(const mms_stencil_desc *d, const float *in, float *
     tz = tz < 8 ? 8 : tz > 128 ? 128 : tz;
     if (tz > d->nz) tz = d->nz;
     const int64_t nslab = (d->nz + tz - 1) / tz;
-    const size_t in_slab = (size_t)(tz + 2 * r) * ipz * 4, out_slab = (size_t)tz * opz * 4;
+    const size_t in_slab = (size_t)(tz + 2 * rz) * ipz * 4, out_slab = (size_t)tz * opz * 4;
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaStream_t s_in = nullptr, s_out = nullptr;
@@ -270,7 +278,7 @@ static mms_status apply_host(const mms_stencil_desc *d, const float *in, float *
         for (int64_t k = 0; k < nslab && e == cudaSuccess && st == MMS_OK; ++k) {
             const int b = (int)(k & 1);
             const int64_t z0 = k * tz, nzt = d->nz - z0 < tz ? d->nz - z0 : tz;
-            const size_t ib = (size_t)((nzt + 2 * r - 1) * ipz + (Y - 1) * ipy + X) * 4;
+            const size_t ib = (size_t)((nzt + 2 * rz - 1) * ipz + (Y - 1) * ipy + X) * 4;
             if (k >= 2) e = cudaStreamWaitEvent(s_in, in_free[b], 0);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(d_in[b], in + z0 * ipz, ib, cudaMemcpyHostToDevice, s_in);
@@ -359,7 +367,7 @@ int32_t mms_num_variants(int shape, int radius, int path) { return num_variants(
 
 int32_t mms_auto_path(int shape, int radius, int tma_aligned)
 {
-    if ((shape != MMS_STAR && shape != MMS_BOX) || radius < 1 || radius > kMaxR) return -1;
+    if (shape < MMS_STAR || shape > MMS_BOX2D || radius < 1 || radius > kMaxR) return -1;
     return auto_path(shape, radius, tma_aligned != 0);
 }
 
@@ -371,7 +379,7 @@ int32_t mms_default_variant(int shape, int radius, int path, int64_t nx, int64_t
 
 mms_status mms_set_variant(int shape, int radius, int path, int32_t variant)
 {
-    if (shape < 0 || shape > 1 || radius < 1 || radius > kMaxR || path < 0 || path > MMS_PATH_NAIVE)
+    if (shape < 0 || shape > 3 || radius < 1 || radius > kMaxR || path < 0 || path > MMS_PATH_NAIVE)
         return fail(MMS_E_ARG, "bad (shape, radius, path)");
     if (variant < -1 || variant >= num_variants(shape, radius, path))
         return fail(MMS_E_ARG, "variant %d out of range", variant);

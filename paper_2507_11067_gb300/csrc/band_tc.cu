@@ -199,6 +199,7 @@ struct TcArgs {
     int vec;                      // 16-byte output rows: float4 stores
     int tiles_x, tiles_y, tiles;  // tiles = tiles_x * tiles_y * zchunks
     int groups;                   // groups (of NZ planes) per tile
+    int zoff;                     // input plane of output plane 0 (R for a z-padded grid, 0 for planar shapes)
 };
 
 // Warp roles: 0 = TMA producer, 1 = MMA issuer of the even groups (and TMEM
@@ -234,7 +235,6 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
 {
     using C = Cfg<R, PREC, LDG, PLANAR>;
     constexpr int W = C::W;
-    constexpr int ZOFF = R - C::RZ;  // padded-plane offset of an output's centre plane
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 1024-byte alignment: the TMA swizzle pattern repeats every 1024 bytes
     unsigned char *smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
                 tile_origin(k / CPT, x0, y0, zt);
                 ptx::mbar_arrive_expect_tx(&full_stg[st], C::STG_BYTES);
                 ptx::tma_load_3d(stg + (size_t)st * (C::STG_BYTES / 4), &tmap, x0, y0,
-                                 zt + (k % CPT) * C::NZ + ZOFF, &full_stg[st]);
+                                 zt + (k % CPT) * C::NZ + a.zoff, &full_stg[st]);
             }
             __syncwarp();
         }
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
             if constexpr (LDG) {
                 int x0, y0, zt;
                 tile_origin(k / CPT, x0, y0, zt);
-                const int zc = zt + (k % CPT) * C::NZ + ZOFF;
+                const int zc = zt + (k % CPT) * C::NZ + a.zoff;
 #pragma unroll
                 for (int t = 0; t < IPT; ++t) {
                     const int it = ct + t * CT;
@@ -680,7 +680,10 @@ cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int groups)
         a.ipz = s.ipz;
         a.X = (int)s.nx + 2 * R;
         a.Y = (int)s.ny + 2 * R;
-        a.Z = (int)s.nz + 2 * R;
+        // planar shapes (a batch of 2D grids) have no z halo; otherwise an
+        // output's centre plane is R - RZ planes into the padded grid
+        a.Z = (int)s.nz + (is_planar(s.shape) ? 0 : 2 * R);
+        a.zoff = is_planar(s.shape) ? 0 : R - C::RZ;
         a.out = s.out;
         a.opy = s.opy;
         a.opz = s.opz;
@@ -871,6 +874,7 @@ cudaError_t launch_zpass(const Sweep &s, const float *T, int64_t tpy, int64_t tp
 
 int band_tc_supported(int shape, int r, int path)
 {
+    // the box runs the 3D kernel; the star's x/y pass and the planar shapes the planar one
     return shape == MMS_BOX ? supported<false>(r, path) : supported<true>(r, path);
 }
 
@@ -879,7 +883,7 @@ int band_tc_variants(int shape, int r, int path) { return band_tc_supported(shap
 void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz, int *swz)
 {
     (void)v;
-    const bool planar = shape == MMS_STAR;
+    const bool planar = shape != MMS_BOX;
     switch (prec_of(path)) {
         case P_TF32: planar ? box_dims<P_TF32, true>(r, bx, by, bz, swz) : box_dims<P_TF32, false>(r, bx, by, bz, swz); return;
         case P_3XTF32: planar ? box_dims<P_3XTF32, true>(r, bx, by, bz, swz) : box_dims<P_3XTF32, false>(r, bx, by, bz, swz); return;
@@ -894,10 +898,26 @@ cudaError_t launch_band_tc(const Sweep &s, int path, const CUtensorMap &map, int
 {
     if (v < 0 || v >= kNumVariants) return cudaErrorInvalidValue;
     if (s.shape == MMS_BOX) return launch_tc<false>(s, path, map, v);
+    const int w = 2 * s.r + 1;
+    if (is_planar(s.shape)) {
+        // Table I's 2D kernels: the planar banded pass straight into the output
+        float c2[(2 * kMaxR + 1) * (2 * kMaxR + 1)] = {};
+        if (s.shape == MMS_BOX2D) {
+            for (int i = 0; i < w * w; ++i) c2[i] = s.coeffs[i];
+        } else {
+            for (int d = -s.r; d <= s.r; ++d) {
+                c2[s.r * w + d + s.r] += s.coeffs[d + s.r];          // x line
+                c2[(d + s.r) * w + s.r] += s.coeffs[w + d + s.r];    // y line
+            }
+        }
+        Sweep p = s;
+        p.coeffs = c2;
+        return launch_tc<true>(p, path, map, v);
+    }
     // Star: the in-plane x/y part (with the three centre weights) as a planar
     // banded pass on tensor cores into `scratch` (the paper's temporary buffer
     // for x/y partial results, Sec. 4.3), then the z part on CUDA cores.
-    const int r = s.r, w = 2 * r + 1;
+    const int r = s.r;
     float c2[(2 * kMaxR + 1) * (2 * kMaxR + 1)] = {};
     for (int d = -r; d <= r; ++d) {
         c2[r * w + d + r] += s.coeffs[0 * w + d + r];  // x line (dy = 0)

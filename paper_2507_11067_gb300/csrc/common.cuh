@@ -51,6 +51,14 @@ int box_cc_variants();
 void star_cc_box(int r, int v, int *bx, int *by);
 void box_cc_box(int r, int v, int *bx, int *by);
 
+// Planar (2D) CUDA-core sweeps (sweep_2d.cu).
+cudaError_t launch_plane_cc(const Sweep &s, const CUtensorMap &tmap, int variant);
+int plane_cc_variants();
+void plane_cc_box(int r, int v, int *bx, int *by);
+
+// Planar shapes have no z halo.
+__host__ __device__ constexpr bool is_planar(int shape) { return shape == MMS_STAR2D || shape == MMS_BOX2D; }
+
 // Tensor-core banded sweeps (band_tc.cu).
 int band_tc_supported(int shape, int r, int path);
 // The star runs as a planar tensor-core pass into `scratch` (nx*ny*nz floats,

@@ -41,9 +41,19 @@ __global__ void naive_kernel(int shape, int r, const __grid_constant__ BoxCoef c
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
-        const float *c0 = in + (z + r) * ipz + (y + r) * ipy + (x + r);
+        // the planar shapes have no z halo
+        const float *c0 = in + (z + (is_planar(shape) ? 0 : r)) * ipz + (y + r) * ipy + (x + r);
         float acc = 0.f;
-        if (shape == MMS_STAR) {
+        if (shape == MMS_STAR2D) {
+            for (int d = -r; d <= r; ++d) {
+                acc = fmaf(cf.c[d + r], c0[d], acc);
+                acc = fmaf(cf.c[w + d + r], c0[d * ipy], acc);
+            }
+        } else if (shape == MMS_BOX2D) {
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx)
+                    acc = fmaf(cf.c[(dy + r) * w + dx + r], c0[dy * ipy + dx], acc);
+        } else if (shape == MMS_STAR) {
             for (int d = -r; d <= r; ++d) {
                 acc = fmaf(cf.c[0 * w + d + r], c0[d], acc);
                 acc = fmaf(cf.c[1 * w + d + r], c0[d * ipy], acc);
@@ -83,7 +93,7 @@ cudaError_t launch_naive(const Sweep &s)
 {
     BoxCoef cf{};
     const int w = 2 * s.r + 1;
-    const int n = s.shape == MMS_STAR ? 3 * w : w * w * w;
+    const int n = s.shape == MMS_STAR ? 3 * w : s.shape == MMS_BOX ? w * w * w : s.shape == MMS_STAR2D ? 2 * w : w * w;
     for (int i = 0; i < n; ++i) cf.c[i] = s.coeffs[i];
     const int64_t total = s.nx * s.ny * s.nz;
     int blocks = (int)((total + 255) / 256);

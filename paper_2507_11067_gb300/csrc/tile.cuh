@@ -132,4 +132,57 @@ __device__ __forceinline__ void box_plane(const float *pl, const BoxCoef &cf,
     }
 }
 
+// Planar star (Table I's 2D kernels): the thread's 4 x PY outputs of a staged
+// tile, x line (weights c[0..2R]) plus y line (weights c[2R+1..4R+1]).
+template <int R, int PY, int BX, int NV>
+__device__ __forceinline__ void star2d_tile(const float *pl, const StarCoef &cf, float (&o)[PY][4], int tx,
+                                            int ry0)
+{
+    constexpr int W = 2 * R + 1;
+    float cen[PY + 2 * R][4];
+#pragma unroll
+    for (int rr = 0; rr < PY + 2 * R; ++rr) load_center<R>(pl + (ry0 + rr) * BX + 4 * tx, cen[rr]);
+#pragma unroll
+    for (int i = 0; i < PY; ++i) {
+        float win[4 * NV];
+        load_row<NV>(pl + (ry0 + R + i) * BX + 4 * tx, win);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int d = -R; d <= R; ++d) acc = fmaf(cf.c[d + R], win[k + R + d], acc);
+#pragma unroll
+            for (int d = -R; d <= R; ++d) acc = fmaf(cf.c[W + d + R], cen[i + R + d][k], acc);
+            o[i][k] = acc;
+        }
+    }
+}
+
+// Planar box: window row rr of the tile feeds output row i with dy = rr - R - i.
+template <int R, int PY, int BX, int NV>
+__device__ __forceinline__ void box2d_tile(const float *pl, const BoxCoef &cf, float (&o)[PY][4], int tx,
+                                           int ry0)
+{
+    constexpr int W = 2 * R + 1;
+#pragma unroll
+    for (int i = 0; i < PY; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[i][k] = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < PY + 2 * R; ++rr) {
+        float row[4 * NV];
+        load_row<NV>(pl + (ry0 + rr) * BX + 4 * tx, row);
+#pragma unroll
+        for (int i = 0; i < PY; ++i) {
+            const int dy = rr - R - i;
+            if (dy < -R || dy > R) continue;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int dx = -R; dx <= R; ++dx)
+                    o[i][k] = fmaf(cf.c[(dy + R) * W + dx + R], row[k + R + dx], o[i][k]);
+        }
+    }
+}
+
 }  // namespace mms

@@ -44,12 +44,13 @@ def tune(shape, r, path, nx, ny, nz, coeffs=None, reps=10, table=TABLE, write=Tr
     import torch
     import numpy as np
     dev = torch.cuda.current_device()
-    inp = _lib.padded_empty(nx, ny, nz, r, device=dev, zero=False)
+    alloc = _lib.padded_empty2d if _lib.SHAPES[shape] in _lib.PLANAR else _lib.padded_empty
+    inp = alloc(nx, ny, nz, r, device=dev, zero=False)
     inp.uniform_(-1, 1, generator=torch.Generator(device=dev).manual_seed(seed))
     out = torch.empty((nz, ny, nx), device=dev)
     if coeffs is None:
         w = 2 * r + 1
-        n = 3 * w if shape == "star" else w ** 3
+        n = {"star": 3 * w, "box": w ** 3, "star2d": 2 * w, "box2d": w * w}[shape]
         coeffs = np.random.default_rng(seed).normal(0, n ** -0.5, n).astype(np.float32)
     ms = time_variants(shape, r, path, inp, out, coeffs, reps=reps)
     best = int(min(range(len(ms)), key=lambda i: ms[i]))

@@ -160,3 +160,12 @@ def test_host_sweep_validation(lib):
     assert lib.mms_stencil_apply_host(ctypes.byref(d), a.ctypes.data_as(P), a.ctypes.data_as(P), None) == 3
     d, c = _desc(nx=0)        # empty interior: nothing to do
     assert lib.mms_stencil_apply_host(ctypes.byref(d), None, None, None) == 0
+
+
+def test_planar_shapes_are_known(lib):
+    assert mms.num_variants("star2d", 2, "cuda_core") > 0
+    assert mms.num_variants("box2d", 3, "bf16x3") > 0
+    assert lib.mms_auto_path(4, 2, 1) == -1
+    d, c = _desc(shape=4)
+    buf = ctypes.create_string_buffer(64)
+    assert lib.mms_stencil_apply_ex(ctypes.byref(d), buf, buf, None) == 1
