@@ -229,7 +229,7 @@ def apply_noalloc(r, coeffs, inp, out=None, path="bf16x3", variant=-1, stream=No
     import torch
     if not inp.is_cuda or inp.dtype != torch.float32:
         raise ValueError("input must be a CUDA float32 tensor")
-    nx, ny, nz = interior(shape, r, inp.shape)
+    nx, ny, nz = interior("star", r, inp.shape)
     if out is None:
         out = torch.empty((nz, ny, nx), device=inp.device, dtype=torch.float32)
     ipy, ipz = pitches(inp)
