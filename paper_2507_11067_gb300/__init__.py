@@ -2,7 +2,8 @@
 
 The compute path is the CUDA library ``libmms.so`` (``csrc/``, C ABI in
 ``include/mms.h``); this package is its thin Python binding plus the
-autograd wrapper of the wave propagator and the tile autotuner.  Importing
+autograd wrapper of the wave propagator, the tile autotuner and the z-slab
+decomposition across ranks (``distributed``).  Importing
 the package does not load the library; the first call does, and fails
 loudly if the library has not been built.
 """
