@@ -45,6 +45,7 @@ WORKLOADS = {
     "plane8192": [("star2d", 2, 8192), ("star2d", 4, 8192), ("box2d", 2, 8192), ("box2d", 3, 8192)],
     "rtm512": None,    # acoustic forward: 8 shots x 512^3, 500 steps (see run_wave)
     "grad256": None,   # adjoint gradient: 2 shots x 256^3, 200 steps, checkpoint 20
+    "vti512": None,    # VTI forward: 4 shots x 512^3 (see run_aniso)
 }
 WORKLOAD_NAMES = {
     "box512": WORKLOAD,
@@ -58,7 +59,11 @@ WORKLOAD_NAMES = {
               "CFL 0.4, 15 Hz Ricker, one CUDA graph per run",
     "grad256": "adjoint gradient of 0.5|d - d_obs|^2 wrt velocity, 2 shots x 256^3, 200 steps, "
                "checkpoint every 20 with recompute, FP64 accumulation",
+    "vti512": "VTI forward (sigma_H, sigma_V of Sec. 2.1), 4 shots x 512^3, r=4 FD8 star, layered vp with "
+              "per-layer eps, delta, 20-cell sponge, h=10 m, CFL 0.4, 15 Hz Ricker",
 }
+ANISO = {"vti512": dict(kind="vti", n=512, shots=4, bytes_per_point_step=32,
+                        kernel="vti_fwd_kernel (two coupled r=4 stars + leapfrog + sponge + source + receivers)")}
 
 
 def sweep_coeffs(shape, r):
@@ -271,6 +276,27 @@ def oracle_wave_sample(planes: int, n: int, gradient: bool, salt: int = 0):
     return planes * n * n, secs, threads
 
 
+def oracle_aniso_sample(planes: int, n: int, kind: str, salt: int = 0):
+    """One FP64 oracle step of the anisotropic workload on a slab of `planes`
+    z-planes of one n x n shot; returns (point-steps, seconds, threads)."""
+    from oracle import aniso
+    r = 4
+    a = workloads.AnisoInputs(n, n, planes, 1, 2, workload=6, noise=False, salt=80 + salt)
+    g = workloads.rng(6, 90 + salt)
+    fields = [oracle_pad(g.uniform(-1, 1, (planes, n, n)), r) for _ in range(4)]
+    mh, mv = aniso.vti_medium(a.vp, a.eps, a.delta, a.dt, a.h)
+    t0 = time.perf_counter()
+    aniso.vti_step(r, workloads.fd8_star_coeffs(), mh, mv, (20, 0.015), a.src[0], 1e-3, *fields)
+    secs = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return planes * n * n, secs, threads
+
+
+def oracle_pad(f, r):
+    import oracle
+    return oracle.pad(f, r)
+
+
 def calibrate_planes(budget_s: float, sample=None) -> int:
     sample = sample or (lambda planes, salt=0: oracle_sample(planes, salt))
     pts, secs, _ = sample(2)
@@ -296,6 +322,13 @@ def run_reference(args):
             return oracle_wave_sample(planes, n, grad, salt)
         unit = "GPoint-steps/s"
         what = ("forward step" if not grad else "forward step, its recomputation and the adjoint step")
+    elif args.workload in ANISO:
+        spec = ANISO[args.workload]
+
+        def sample(planes, salt=0):
+            return oracle_aniso_sample(planes, spec["n"], spec["kind"], salt)
+        unit = "GPoint-steps/s"
+        what = f"{spec['kind'].upper()} step"
     else:
         plan = WORKLOADS[args.workload]
 
@@ -348,6 +381,8 @@ def main():
         return run_reference(args)
     if args.workload in ("rtm512", "grad256"):
         return run_wave(args)
+    if args.workload in ANISO:
+        return run_aniso(args)
 
     import torch
     import paper_2507_11067_gb300 as mms
@@ -710,6 +745,124 @@ def run_wave(args):
                                                 "n": n, "time_steps": nsteps if args.workload != "rtm512" else steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * reps, "clocks": clk,
+                "peaks": {"hbm_gbs": hbm_peak, "source": peak_src}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_aniso(args):
+    """The anisotropic forward workloads on one GPU: `steps` time steps of all
+    shots, one fused launch per step (shots are independent: under torchrun
+    each rank runs its own, weak scaling)."""
+    import torch
+    import paper_2507_11067_gb300 as mms
+    spec = ANISO[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mms.build()
+    mms.load()
+    hbm_peak, _, _, peak_src = peaks()
+    n, r = spec["n"], 4
+    nshots = args.shots or spec["shots"]
+    steps = args.steps or 200
+    a = workloads.AnisoInputs(n, n, n, nshots, steps, workload=6, salt=rank)
+    cf = workloads.fd8_star_coeffs()
+    f = [mms.padded_empty(n, n, n, r, device=dev, nshots=nshots) for _ in range(4)]
+    py, pz, ss = mms.field_geometry(f[0])
+    desc, _src = mms.wave_desc(n, n, n, r, nshots, py, pz, ss, a.wave.sponge, a.wave.sponge_a, a.zrec, a.src)
+    med = [mms.padded_empty(n, n, n, r, device=dev) for _ in range(2)]
+    host_in = [torch.from_numpy(x).pin_memory() for x in (a.vp, a.eps, a.delta)]
+    amps_host = torch.from_numpy(a.amp).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    rec = torch.zeros((steps, nshots, n, n), device=dev)
+
+    def run(k, inputs, amps, record=True):
+        if inputs is not None:
+            mms.vti_model(desc, *inputs, med[0], med[1], a.dt, a.h)
+            for x in f:
+                x.zero_()
+        cur = list(f)
+        for i in range(k):
+            mms.vti_step(desc, cf, med[0], med[1], cur[0], cur[1], cur[2], cur[3], cur[2], cur[3], amps[i],
+                         rec[i] if record else None)
+            cur = [cur[2], cur[3], cur[0], cur[1]]
+        return cur
+
+    dev_in = [x.to(dev) for x in host_in]
+    amps = amps_host.to(dev)
+    run(0, dev_in, amps)
+    for _ in range(args.warmup):
+        run(1, None, amps)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    run(steps, None, amps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3, dist, dev)
+    pts = nshots * n ** 3
+    bpp = spec["bytes_per_point_step"]
+    bytes_alg = float(bpp) * pts * steps
+    # end to end: the medium and the wavelet in from pinned host memory, the
+    # model kernel, the steps with receivers, the records out
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ins = [x.to(dev, non_blocking=True) for x in host_in]
+    aa = amps_host.to(dev, non_blocking=True)
+    run(steps, ins, aa)
+    rec_host = rec.to("cpu")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+    h2d = sum(x.numel() * 4 for x in host_in) + amps_host.numel() * 4
+    d2h = rec_host.numel() * 4
+    value = job_rate(world, pts * steps, elapsed)
+    e2e = {"value": job_rate(world, pts * steps, e2e_s), "unit": "GPoint-steps/s",
+           "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps}
+    key = f"{spec['kind']}_fwd r=4"
+    roof = {"bound": "hbm", "achieved": bytes_alg / elapsed / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": bytes_alg / elapsed / 1e9 / hbm_peak, "traffic": captured_traffic(key, nshots * n ** 3),
+            "kernel": spec["kernel"], "bytes_per_point_step": bpp}
+    if roof["traffic"]:
+        roof["traffic_over_algorithmic"] = roof["traffic"] / (float(bpp) * pts)
+    unit = "GPoint-steps/s"
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+
+        def sample(p, salt=0):
+            return oracle_aniso_sample(p, n, spec["kind"], salt)
+        planes = calibrate_planes(5.0, sample)
+        p, secs, threads = sample(planes)
+        cpu = {"value": p / secs / 1e9, "unit": unit, "cores": threads, "kind": "oracle",
+               "sample": f"FP64 oracle {spec['kind'].upper()} step of one shot on a seeded {planes} x {n} x {n} slab"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD_NAMES[args.workload], "shots": nshots, "n": n,
+                           "time_steps": steps, "l2": "inputs larger than L2"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": steps, "clocks": clk,
                 "peaks": {"hbm_gbs": hbm_peak, "source": peak_src}}
         print(json.dumps(line), flush=True)
     if dist:

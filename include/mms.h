@@ -300,6 +300,43 @@ mms_status mms_dot_f64(const float *a, const float *b, int64_t n, double *result
 mms_status mms_sum_f64(const double *slices, int32_t nslices, int64_t stride, int64_t n, double *out,
                        void *stream);
 
+/* ------------------------------------------------- anisotropic media */
+
+/*
+ * VTI medium (paper Sec. 2.1): from dense interior arrays vp, eps, delta
+ * (nz*ny*nx floats each, device) writes two padded fields in the geometry of
+ * `desc` (halo 0): mv = vp^2 dt^2/h^2 sqrt(1 + 2 delta) and
+ * rho = (1 + 2 eps) / sqrt(1 + 2 delta).  Requires 1 + 2 delta > 0.
+ * MMS_E_ARG for null pointers or dt, h not positive.
+ */
+mms_status mms_vti_model(const mms_wave_desc *desc, const float *vp, const float *eps, const float *delta,
+                         float *mv, float *rho, float dt, float h, void *stream);
+
+/*
+ * One step of the VTI system of the paper's Sec. 2.1, as printed there
+ * (sigma_H, sigma_V the horizontal and vertical stresses), for all shots:
+ *     sH^{n+1} = G*( 2 sH^n - G*sH^{n-1} + mv*(rho*Lh sH^n + Lz sV^n) + s^n )
+ *     sV^{n+1} = G*( 2 sV^n - G*sV^{n-1} + mv*(Lh sV^n + rho*Lz sH^n) + s^n )
+ * i.e. mh = mv*rho = m(1 + 2 eps) and mv = m sqrt(1 + 2 delta) multiply the
+ * printed terms; Lh = the x and y rows of the star weights `coeffs` (host,
+ * 3*(2r+1), unscaled), Lz = the z row; G, the source (added to both
+ * stresses), the zero halo, shots and pitches as for mms_wave_step.
+ * mv, rho: padded medium fields of mms_vti_model (one for all shots).
+ * sh_cur, sv_cur, sh_prev, sv_prev: device, read; sh_next, sv_next: device,
+ * written (interior only), each either the matching *_prev field (in place)
+ * or a field overlapping none of the others.  rec: device nshots*ny*nx
+ * receiving sH^{n+1} on the plane rec_z (NULL = none).  All fields 16-byte
+ * aligned (MMS_E_ALIGN otherwise); MMS_E_ARG for overlaps or null pointers.
+ */
+mms_status mms_vti_step(const mms_wave_desc *desc, const float *coeffs, const float *mv, const float *rho,
+                        const float *sh_cur, const float *sv_cur, const float *sh_prev, const float *sv_prev,
+                        float *sh_next, float *sv_next, const float *src_amp, float *rec, void *stream);
+
+/* Tile variants of the anisotropic steps (kind 0 = VTI): their count, and
+ * the one used by later calls of this process (MMS_E_ARG out of range). */
+int32_t mms_aniso_num_variants(int32_t kind);
+mms_status mms_aniso_set_variant(int32_t kind, int32_t variant);
+
 /* ------------------------------------------------------------ status */
 
 /* Thread-local message of the last non-OK status of this thread. */

@@ -39,7 +39,8 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_set_variant", "mms_wave_step", "mms_wave_forward", "mms_wave_adjoint",
            "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
            "mms_check_device", "mms_version", "mms_stencil_apply_noalloc", "mms_wave_step_to",
-           "mms_sum_f64", "mms_selftest_timeout", "mms_stencil_apply_host"]
+           "mms_sum_f64", "mms_selftest_timeout", "mms_stencil_apply_host", "mms_vti_model", "mms_vti_step",
+           "mms_aniso_num_variants", "mms_aniso_set_variant"]
 
 
 class MMSError(RuntimeError):
@@ -108,6 +109,10 @@ def load():
                                         ctypes.c_float, P],
             "mms_grad_to_velocity": [P, P, P, i64, ctypes.c_float, ctypes.c_float, P],
             "mms_dot_f64": [P, P, i64, P, P],
+            "mms_vti_model": [ctypes.POINTER(WaveDesc), P, P, P, P, P, ctypes.c_float, ctypes.c_float, P],
+            "mms_vti_step": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P, P, P, P, P],
+            "mms_aniso_num_variants": [i32],
+            "mms_aniso_set_variant": [i32, i32],
             "mms_last_error": [],
             "mms_check_device": [P],
             "mms_version": [],
@@ -356,6 +361,33 @@ def model_from_velocity(desc, v, m, dt, h, stream=None):
 def grad_to_velocity(grad_m, v, grad_v, dt, h, stream=None):
     check(load().mms_grad_to_velocity(_ptr(grad_m), _ptr(v), _ptr(grad_v), grad_m.numel(),
                                       float(dt), float(h), _stream(stream)))
+
+
+def vti_model(desc, vp, eps, delta, mv, rho, dt, h, stream=None):
+    """mms_vti_model: the padded VTI medium (mv, rho) from dense vp, eps, delta."""
+    check(load().mms_vti_model(ctypes.byref(desc), _ptr(vp), _ptr(eps), _ptr(delta), _ptr(mv), _ptr(rho),
+                               float(dt), float(h), _stream(stream)))
+
+
+def vti_step(desc, coeffs, mv, rho, sh_cur, sv_cur, sh_prev, sv_prev, sh_next, sv_next, src_amp, rec=None,
+             stream=None):
+    """mms_vti_step: (sigma_H, sigma_V)^{n+1} into sh_next, sv_next (which may
+    be sh_prev, sv_prev)."""
+    c = _host_coeffs(coeffs)
+    check(load().mms_vti_step(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(mv), _ptr(rho),
+                              _ptr(sh_cur), _ptr(sv_cur), _ptr(sh_prev), _ptr(sv_prev), _ptr(sh_next),
+                              _ptr(sv_next), _ptr(src_amp), _ptr(rec), _stream(stream)))
+
+
+ANISO_KINDS = {"vti": 0}
+
+
+def aniso_num_variants(kind="vti"):
+    return int(load().mms_aniso_num_variants(ANISO_KINDS[kind]))
+
+
+def aniso_set_variant(kind, variant):
+    check(load().mms_aniso_set_variant(ANISO_KINDS[kind], int(variant)))
 
 
 def sum_f64(slices, out, stream=None):

@@ -618,6 +618,61 @@ mms_status mms_wave_adjoint(const mms_wave_desc *desc, const float *coeffs, cons
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "adjoint step launch");
 }
 
+mms_status mms_vti_model(const mms_wave_desc *desc, const float *vp, const float *eps, const float *delta,
+                         float *mv, float *rho, float dt, float h, void *stream)
+{
+    WaveGeo g;
+    static const float dummy[27] = {0};
+    mms_status st = wave_geo(desc, dummy, &g);
+    if (st != MMS_OK) return st;
+    if (!vp || !eps || !delta || !mv || !rho) return fail(MMS_E_ARG, "null pointer");
+    if (!(dt > 0.f) || !(h > 0.f)) return fail(MMS_E_ARG, "dt and h must be positive");
+    const size_t mb = (size_t)g.pz * (g.nz + 2 * g.r) * 4;
+    if (overlaps(mv, mb, rho, mb)) return fail(MMS_E_ARG, "mv and rho overlap");
+    cudaError_t e = launch_vti_model(g, vp, eps, delta, mv, rho, dt, h, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "VTI model kernel launch");
+}
+
+mms_status mms_vti_step(const mms_wave_desc *desc, const float *coeffs, const float *mv, const float *rho,
+                        const float *sh_cur, const float *sv_cur, const float *sh_prev, const float *sv_prev,
+                        float *sh_next, float *sv_next, const float *src_amp, float *rec, void *stream)
+{
+    WaveGeo g;
+    mms_status st = wave_geo(desc, coeffs, &g);
+    if (st != MMS_OK) return st;
+    if (!mv || !rho || !sh_cur || !sv_cur || !sh_prev || !sv_prev || !sh_next || !sv_next || !src_amp)
+        return fail(MMS_E_ARG, "null field pointer");
+    const void *all[8] = {mv, rho, sh_cur, sv_cur, sh_prev, sv_prev, sh_next, sv_next};
+    for (const void *q : all)
+        if (!al16(q)) return fail(MMS_E_ALIGN, "VTI fields must be 16-byte aligned");
+    const size_t fb = field_bytes(g);
+    const float *rd[4] = {sh_cur, sv_cur, sh_prev, sv_prev};
+    for (int a = 0; a < 4; ++a)
+        for (int b = a + 1; b < 4; ++b)
+            if (overlaps(rd[a], fb, rd[b], fb)) return fail(MMS_E_ARG, "VTI input fields %d and %d overlap", a, b);
+    if (overlaps(sh_next, fb, sv_next, fb)) return fail(MMS_E_ARG, "sh_next and sv_next overlap");
+    const float *nx2[2] = {sh_next, sv_next};
+    for (int o = 0; o < 2; ++o)
+        for (int a = 0; a < 4; ++a) {
+            if (a == 2 + o && nx2[o] == rd[a]) continue;  // in place over the matching previous state
+            if (overlaps(nx2[o], fb, rd[a], fb))
+                return fail(MMS_E_ARG, "%s overlaps an input field other than its own previous state",
+                            o ? "sv_next" : "sh_next");
+        }
+    cudaError_t e = launch_vti_step(g, coeffs, mv, rho, sh_cur, sv_cur, sh_prev, sv_prev, sh_next, sv_next, src_amp,
+                                    rec, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "VTI step launch");
+}
+
+int32_t mms_aniso_num_variants(int32_t kind) { return kind == 0 ? vti_num_variants() : 0; }
+
+mms_status mms_aniso_set_variant(int32_t kind, int32_t variant)
+{
+    if (kind != 0) return fail(MMS_E_ARG, "unknown anisotropic kind %d", kind);
+    if (!vti_set_variant(variant)) return fail(MMS_E_ARG, "variant %d outside 0..%d", variant, vti_num_variants() - 1);
+    return MMS_OK;
+}
+
 mms_status mms_model_from_velocity(const mms_wave_desc *desc, const float *v, float *m, float dt, float h,
                                    void *stream)
 {

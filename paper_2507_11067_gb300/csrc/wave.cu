@@ -67,25 +67,6 @@ __device__ __forceinline__ double widen(float f)
     return __longlong_as_double((long long)d);
 }
 
-// Cerjan sponge factor of cell i of n (distance d to the nearest face).
-__device__ __forceinline__ float sponge(int i, int n, int w, float a)
-{
-    const int d = min(i, n - 1 - i);
-    if (d < w) {
-        const float t = a * (float)(w - d);
-        return expf(-t * t);
-    }
-    return 1.f;
-}
-
-// Interior tile (TX x TY) of m or a^{n-1} that completes with output plane
-// zo: TMA box x start rounded down to a 16-byte boundary, OFF columns in.
-template <int R, int TX>
-struct Interior {
-    static constexpr int OFF = R % 4;                   // column of output x0 inside the box
-    static constexpr int BXI = OFF == 0 ? TX : TX + 4;  // box width (16-byte multiple)
-};
-
 // Ring stage s: [a^n plane + halo | m tile | a^{n-1} tile | a^n tile].  The
 // interior tiles of output plane zo = j - 2R (m, a^{n-1} and the centre
 // values of a^n) ride in the stage of input plane j, the plane that completes

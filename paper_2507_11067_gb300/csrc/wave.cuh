@@ -34,6 +34,35 @@ cudaError_t launch_wait_selftest(unsigned long long limit_ns, cudaStream_t st);
 cudaError_t launch_sum_f64(const double *slices, int nslices, int64_t stride, int64_t n, double *out,
                            cudaStream_t st);
 
+// VTI step (aniso.cu): sigma_H, sigma_V at n+1 into hnext/vnext (which may
+// be hprev/vprev); medium mv, rho padded like the fields (one, all shots).
+cudaError_t launch_vti_step(const WaveGeo &g, const float *coeffs, const float *mv, const float *rho,
+                            const float *hcur, const float *vcur, const float *hprev, const float *vprev,
+                            float *hnext, float *vnext, const float *src_amp, float *rec, cudaStream_t st);
+cudaError_t launch_vti_model(const WaveGeo &g, const float *vp, const float *eps, const float *delta, float *mv,
+                             float *rho, float dt, float h, cudaStream_t st);
+int vti_num_variants();
+bool vti_set_variant(int v);
+
+// Cerjan sponge factor of cell i of n (distance d to the nearest face).
+__device__ __forceinline__ float sponge(int i, int n, int w, float a)
+{
+    const int d = min(i, n - 1 - i);
+    if (d < w) {
+        const float t = a * (float)(w - d);
+        return expf(-t * t);
+    }
+    return 1.f;
+}
+
+// Interior tile (TX x TY) of m or a^{n-1} that completes with output plane
+// zo: TMA box x start rounded down to a 16-byte boundary, OFF columns in.
+template <int R, int TX>
+struct Interior {
+    static constexpr int OFF = R % 4;                   // column of output x0 inside the box
+    static constexpr int BXI = OFF == 0 ? TX : TX + 4;  // box width (16-byte multiple)
+};
+
 mms_status fail(mms_status st, const char *fmt, ...);
 mms_status cuda_fail(cudaError_t e, const char *what);
 

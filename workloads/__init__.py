@@ -23,6 +23,8 @@ WORKLOADS = {
     3: "star r=1..4, 1024^3 interior, FD8 at r=4 else N(0, 1/npts), 16 sinusoids + 1e-3 noise",
     4: "acoustic forward, 8 shots x 512^3, 500 steps, r=4 FD8, h=10, sponge 20",
     5: "acoustic gradient, 2 shots x 256^3, 200 steps, checkpoint every 20",
+    6: "VTI forward, 4 shots x 512^3, r=4 FD8, layered vp with per-layer eps, delta",
+    7: "TTI forward, 2 shots x 512^3, r=4 FD8 and FD1 weights, layered medium with smooth tilt",
 }
 
 # Standard 8th-order (radius-4) central second-derivative weights c_0..c_4
@@ -206,3 +208,49 @@ def _smooth_noise(shape, g, sigma):
     from scipy.ndimage import gaussian_filter
     e = gaussian_filter(g.standard_normal(shape), sigma=sigma, mode="reflect")
     return 0.05 * e / np.abs(e).max()
+
+
+# ------------------------------------------------------- anisotropic inputs
+
+class AnisoInputs:
+    """Inputs of the VTI and TTI workloads (float32 interior fields).
+
+    vp: the layered velocity of WaveInputs (6 layers, 1500..4500 m/s, 5 %
+    smooth noise); eps in [0, 0.3] and delta in [-0.1, 0.2] seeded per layer
+    (Thomsen parameters of sedimentary layers); vs = vp / 2; alpha = 1;
+    theta (tilt) = a seeded dip in [0, 45] degrees per layer plus a smooth
+    field of +-10 degrees; phi (azimuth) = a seeded azimuth plus a smooth field
+    of +-30 degrees.  dt follows CFL 0.4 on the fastest speed
+    vp sqrt(1 + 2 eps); the sources, receivers and wavelet are those of
+    WaveInputs with that dt.
+    """
+
+    def __init__(self, nx, ny, nz, nshots, nsteps, workload=6, h=10.0, sponge=20, tti=False, salt=0,
+                 noise=True):
+        g = rng(workload, salt)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.vp = layered_velocity(nx, ny, nz, g, noise)
+        depths = np.sort(g.choice(np.arange(1, max(nz, 7)), size=5, replace=False))
+        layer = np.minimum(np.searchsorted(depths, np.arange(nz), side="right"), 5)
+        eps_l = g.uniform(0.0, 0.3, 6)
+        delta_l = g.uniform(-0.1, 0.2, 6)
+        shape = (nz, ny, nx)
+        self.eps = np.ascontiguousarray(np.broadcast_to(eps_l[layer][:, None, None], shape), np.float32)
+        self.delta = np.ascontiguousarray(np.broadcast_to(delta_l[layer][:, None, None], shape), np.float32)
+        vfast = float((self.vp.astype(np.float64) * np.sqrt(1.0 + 2.0 * self.eps)).max())
+        self.wave = WaveInputs(nx, ny, nz, nshots, nsteps, workload=workload, h=h, sponge=sponge, salt=salt,
+                               v=self.vp, cfl=0.4 * float(self.vp.max()) / vfast)
+        self.h, self.dt = self.wave.h, self.wave.dt
+        self.src, self.zrec, self.amp = self.wave.src, self.wave.zrec, self.wave.amp
+        if tti:
+            self.vs = (0.5 * self.vp).astype(np.float32)
+            self.alpha = np.ones(shape, np.float32)
+            dip = g.uniform(0.0, math.pi / 4, 6)[layer][:, None, None]
+            azi = float(g.uniform(-math.pi, math.pi))
+            if noise:
+                tn = _smooth_noise(shape, g, sigma=8.0) / 0.05 * math.radians(10.0)
+                pn = _smooth_noise(shape, g, sigma=8.0) / 0.05 * math.radians(30.0)
+            else:
+                tn = pn = 0.0
+            self.theta = np.ascontiguousarray(dip + tn, np.float32)
+            self.phi = np.ascontiguousarray(azi + pn + np.zeros(shape), np.float32)
