@@ -46,6 +46,7 @@ WORKLOADS = {
     "rtm512": None,    # acoustic forward: 8 shots x 512^3, 500 steps (see run_wave)
     "grad256": None,   # adjoint gradient: 2 shots x 256^3, 200 steps, checkpoint 20
     "vti512": None,    # VTI forward: 4 shots x 512^3 (see run_aniso)
+    "tti512": None,    # TTI forward: 2 shots x 512^3 (see run_aniso)
 }
 WORKLOAD_NAMES = {
     "box512": WORKLOAD,
@@ -61,9 +62,16 @@ WORKLOAD_NAMES = {
                "checkpoint every 20 with recompute, FP64 accumulation",
     "vti512": "VTI forward (sigma_H, sigma_V of Sec. 2.1), 4 shots x 512^3, r=4 FD8 star, layered vp with "
               "per-layer eps, delta, 20-cell sponge, h=10 m, CFL 0.4, 15 Hz Ricker",
+    "tti512": "TTI forward (p, q with H1, H2 of Sec. 2.1), 2 shots x 512^3, r=4 FD8 second- and first-derivative "
+              "weights, layered vp with per-layer eps, delta, vs = vp/2, alpha = 1, smooth tilt, 20-cell sponge",
 }
 ANISO = {"vti512": dict(kind="vti", n=512, shots=4, bytes_per_point_step=32,
-                        kernel="vti_fwd_kernel (two coupled r=4 stars + leapfrog + sponge + source + receivers)")}
+                        kernel="vti_fwd_kernel (two coupled r=4 stars + leapfrog + sponge + source + receivers)"),
+         # per point-step: two derivative passes (read the field and the tilt,
+         # 16 B; write Lap f and H1 f, 8 B) and the combine (read 4 work
+         # fields, 5 medium fields, p and q at n and n-1: 52 B; write 8 B)
+         "tti512": dict(kind="tti", n=512, shots=2, bytes_per_point_step=108,
+                        kernel="whole step: tti_deriv_kernel for p and q + tti_combine_kernel")}
 
 
 def sweep_coeffs(shape, r):
@@ -281,12 +289,19 @@ def oracle_aniso_sample(planes: int, n: int, kind: str, salt: int = 0):
     z-planes of one n x n shot; returns (point-steps, seconds, threads)."""
     from oracle import aniso
     r = 4
-    a = workloads.AnisoInputs(n, n, planes, 1, 2, workload=6, noise=False, salt=80 + salt)
+    tti = kind == "tti"
+    a = workloads.AnisoInputs(n, n, planes, 1, 2, workload=7 if tti else 6, noise=False, salt=80 + salt, tti=tti)
     g = workloads.rng(6, 90 + salt)
     fields = [oracle_pad(g.uniform(-1, 1, (planes, n, n)), r) for _ in range(4)]
-    mh, mv = aniso.vti_medium(a.vp, a.eps, a.delta, a.dt, a.h)
-    t0 = time.perf_counter()
-    aniso.vti_step(r, workloads.fd8_star_coeffs(), mh, mv, (20, 0.015), a.src[0], 1e-3, *fields)
+    if tti:
+        med = aniso.tti_medium(a.vp, a.vs, a.eps, a.delta, a.alpha, a.dt, a.h)
+        tilt = aniso.tilt_axis(a.theta, a.phi)
+        t0 = time.perf_counter()
+        aniso.tti_step(r, med, tilt, (20, 0.015), a.src[0], 1e-3, *fields)
+    else:
+        mh, mv = aniso.vti_medium(a.vp, a.eps, a.delta, a.dt, a.h)
+        t0 = time.perf_counter()
+        aniso.vti_step(r, workloads.fd8_star_coeffs(), mh, mv, (20, 0.015), a.src[0], 1e-3, *fields)
     secs = time.perf_counter() - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return planes * n * n, secs, threads
@@ -774,26 +789,40 @@ def run_aniso(args):
     n, r = spec["n"], 4
     nshots = args.shots or spec["shots"]
     steps = args.steps or 200
-    a = workloads.AnisoInputs(n, n, n, nshots, steps, workload=6, salt=rank)
-    cf = workloads.fd8_star_coeffs()
+    tti = spec["kind"] == "tti"
+    a = workloads.AnisoInputs(n, n, n, nshots, steps, workload=7 if tti else 6, salt=rank, tti=tti)
     f = [mms.padded_empty(n, n, n, r, device=dev, nshots=nshots) for _ in range(4)]
     py, pz, ss = mms.field_geometry(f[0])
     desc, _src = mms.wave_desc(n, n, n, r, nshots, py, pz, ss, a.wave.sponge, a.wave.sponge_a, a.zrec, a.src)
-    med = [mms.padded_empty(n, n, n, r, device=dev) for _ in range(2)]
-    host_in = [torch.from_numpy(x).pin_memory() for x in (a.vp, a.eps, a.delta)]
+    if tti:
+        host_in = [torch.from_numpy(x).pin_memory() for x in (a.vp, a.vs, a.eps, a.delta, a.alpha, a.theta, a.phi)]
+        med = [torch.empty((8, n, n, n), device=dev)]
+        work = torch.empty((4, nshots, n, n, n), device=dev)
+        w2, w1 = workloads.fd8_rows()
+    else:
+        host_in = [torch.from_numpy(x).pin_memory() for x in (a.vp, a.eps, a.delta)]
+        med = [mms.padded_empty(n, n, n, r, device=dev) for _ in range(2)]
+        cf = workloads.fd8_star_coeffs()
     amps_host = torch.from_numpy(a.amp).pin_memory()
     stream = torch.cuda.current_stream(dev)
     rec = torch.zeros((steps, nshots, n, n), device=dev)
 
     def run(k, inputs, amps, record=True):
         if inputs is not None:
-            mms.vti_model(desc, *inputs, med[0], med[1], a.dt, a.h)
+            if tti:
+                mms.tti_model(desc, *inputs, med[0], a.dt, a.h)
+            else:
+                mms.vti_model(desc, *inputs, med[0], med[1], a.dt, a.h)
             for x in f:
                 x.zero_()
         cur = list(f)
         for i in range(k):
-            mms.vti_step(desc, cf, med[0], med[1], cur[0], cur[1], cur[2], cur[3], cur[2], cur[3], amps[i],
-                         rec[i] if record else None)
+            if tti:
+                mms.tti_step(desc, w2, w1, med[0], cur[0], cur[1], cur[2], cur[3], cur[2], cur[3], work, amps[i],
+                             rec[i] if record else None)
+            else:
+                mms.vti_step(desc, cf, med[0], med[1], cur[0], cur[1], cur[2], cur[3], cur[2], cur[3], amps[i],
+                             rec[i] if record else None)
             cur = [cur[2], cur[3], cur[0], cur[1]]
         return cur
 
@@ -862,7 +891,7 @@ def run_aniso(args):
                 "config": {"workload": WORKLOAD_NAMES[args.workload], "shots": nshots, "n": n,
                            "time_steps": steps, "l2": "inputs larger than L2"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": steps, "clocks": clk,
+                "gpu_launches": steps * (3 if tti else 1), "clocks": clk,
                 "peaks": {"hbm_gbs": hbm_peak, "source": peak_src}}
         print(json.dumps(line), flush=True)
     if dist:

@@ -332,6 +332,43 @@ mms_status mms_vti_step(const mms_wave_desc *desc, const float *coeffs, const fl
                         const float *sh_cur, const float *sv_cur, const float *sh_prev, const float *sv_prev,
                         float *sh_next, float *sv_next, const float *src_amp, float *rec, void *stream);
 
+/*
+ * TTI medium (paper Sec. 2.1): from dense interior arrays (nz*ny*nx floats
+ * each, device) vp, vs, eps, delta, alpha, theta (tilt), phi (azimuth),
+ * writes `med`, 8 dense interior fields one after another:
+ *     [a, b, c, d, alpha, nx, ny, nz]
+ * a = vpx^2 s = vp^2 (1 + 2 eps) s, b = vpz^2 s = vp^2 s,
+ * c = vpn^2 s = vp^2 (1 + 2 delta) s, d = vsz^2 s = vs^2 s (s = dt^2/h^2),
+ * and the tilt axis n = (sin th cos ph, sin th sin ph, cos th).  The paper
+ * names vpx, vpz, vpn, vsz and alpha without defining them; these are the
+ * usual Thomsen-parameter readings.  MMS_E_ARG for null pointers or dt, h
+ * not positive.
+ */
+mms_status mms_tti_model(const mms_wave_desc *desc, const float *vp, const float *vs, const float *eps,
+                         const float *delta, const float *alpha, const float *theta, const float *phi,
+                         float *med, float dt, float h, void *stream);
+
+/*
+ * One step of the TTI system of the paper's Sec. 2.1 for all shots:
+ *     p^{n+1} = G*( 2 p^n - G*p^{n-1} + a H2p + alpha b H1q + d (H1p - alpha H1q) + s^n )
+ *     q^{n+1} = G*( 2 q^n - G*q^{n-1} + c/alpha H2p + b H1q - d (H2p/alpha - H2q) + s^n )
+ * with H1 f = nx^2 f_xx + ny^2 f_yy + nz^2 f_zz + 2 nx ny f_xy + 2 ny nz f_yz
+ * + 2 nx nz f_xz and H2 f = f_xx + f_yy + f_zz - H1 f.  Axis derivatives use
+ * the second-derivative weights w2 (host, 2r+1 floats, offsets -r..r); a
+ * mixed derivative composes two first-derivative rows w1 (host, 2r+1 floats,
+ * offsets -r..r) on the zero-padded field (paper Sec. 4.7).  med: the 8
+ * dense fields of mms_tti_model.  Fields, shots, G, source (added to p and
+ * q), receivers (p^{n+1} on rec_z) and overlap rules as for mms_vti_step.
+ * work: device scratch of 4*nshots*nx*ny*nz floats, 16-byte aligned,
+ * overlapping no field, owned by the caller (the call allocates nothing).
+ * Three launches on `stream`: the derivative pass for p, for q, and the
+ * pointwise combine.
+ */
+mms_status mms_tti_step(const mms_wave_desc *desc, const float *w2, const float *w1, const float *med,
+                        const float *p_cur, const float *q_cur, const float *p_prev, const float *q_prev,
+                        float *p_next, float *q_next, float *work, const float *src_amp, float *rec,
+                        void *stream);
+
 /* Tile variants of the anisotropic steps (kind 0 = VTI): their count, and
  * the one used by later calls of this process (MMS_E_ARG out of range). */
 int32_t mms_aniso_num_variants(int32_t kind);

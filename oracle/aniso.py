@@ -246,3 +246,49 @@ def tti_step(r, medium, n, sponge, src, s_amp, p_cur, q_cur, p_prev, q_prev, row
     g = _damping(vpx2.shape, sponge)
     s = _source(vpx2.shape, src, s_amp)
     return (_leapfrog(r, g, p_cur, p_prev, rhs_p, s), _leapfrog(r, g, q_cur, q_prev, rhs_q, s))
+
+
+def tti_step_points(r, medium, n, sponge, src, s_amp, p_cur, q_cur, p_prev, q_prev, xyz, row2=None, row1=None):
+    """The TTI step at interior points ``xyz`` (npts, 3) only: returns
+    (p^{n+1}, q^{n+1}) there.  medium, n: full interior fields as in
+    ``tti_step`` (indexed at the points); fields read in place (FP32 or
+    FP64, zero halo).  Each derivative is the same sum as in
+    ``second_derivatives``, gathered point by point."""
+    r = int(r)
+    row2 = fd2_row(r) if row2 is None else np.asarray(row2, np.float64).reshape(-1)
+    row1 = fd1_row(r) if row1 is None else np.asarray(row1, np.float64).reshape(-1)
+    pts = np.ascontiguousarray(np.asarray(xyz, dtype=np.int64).reshape(-1, 3))
+    x, y, z = pts[:, 0] + r, pts[:, 1] + r, pts[:, 2] + r       # padded indices
+    offs = range(-r, r + 1)
+
+    def derivs(f):
+        f = np.asarray(f)
+        at = lambda dx, dy, dz: f[z + dz, y + dy, x + dx].astype(np.float64)
+        d = {"xx": sum(row2[i + r] * at(i, 0, 0) for i in offs),
+             "yy": sum(row2[i + r] * at(0, i, 0) for i in offs),
+             "zz": sum(row2[i + r] * at(0, 0, i) for i in offs),
+             "xy": sum(row1[i + r] * row1[j + r] * at(i, j, 0) for i in offs for j in offs),
+             "xz": sum(row1[i + r] * row1[j + r] * at(i, 0, j) for i in offs for j in offs),
+             "yz": sum(row1[i + r] * row1[j + r] * at(0, i, j) for i in offs for j in offs)}
+        return d
+
+    px, py_, pz = pts[:, 0], pts[:, 1], pts[:, 2]
+    take = lambda a: np.asarray(a)[pz, py_, px].astype(np.float64)
+    vpx2, vpz2, vpn2, vsz2, alpha = (take(a) for a in medium)
+    nn = tuple(take(c) for c in n)
+    dp, dq = derivs(p_cur), derivs(q_cur)
+    h1p, h1q = h1(nn, dp), h1(nn, dq)
+    h2p = dp["xx"] + dp["yy"] + dp["zz"] - h1p
+    h2q = dq["xx"] + dq["yy"] + dq["zz"] - h1q
+    rhs_p = vpx2 * h2p + alpha * vpz2 * h1q + vsz2 * (h1p - alpha * h1q)
+    rhs_q = vpn2 / alpha * h2p + vpz2 * h1q - vsz2 * (h2p / alpha - h2q)
+    nz_, ny_, nx_ = np.asarray(p_cur).shape
+    nz_, ny_, nx_ = nz_ - 2 * r, ny_ - 2 * r, nx_ - 2 * r
+    if sponge is None:
+        g = np.ones(len(pts))
+    else:
+        g = sponge_1d(nx_, *sponge)[px] * sponge_1d(ny_, *sponge)[py_] * sponge_1d(nz_, *sponge)[pz]
+    s = np.where((px == src[0]) & (py_ == src[1]) & (pz == src[2]), float(s_amp), 0.0)
+    at0 = lambda f: np.asarray(f)[z, y, x].astype(np.float64)
+    return (g * (2.0 * at0(p_cur) - g * at0(p_prev) + rhs_p + s),
+            g * (2.0 * at0(q_cur) - g * at0(q_prev) + rhs_q + s))

@@ -40,7 +40,7 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
            "mms_check_device", "mms_version", "mms_stencil_apply_noalloc", "mms_wave_step_to",
            "mms_sum_f64", "mms_selftest_timeout", "mms_stencil_apply_host", "mms_vti_model", "mms_vti_step",
-           "mms_aniso_num_variants", "mms_aniso_set_variant"]
+           "mms_aniso_num_variants", "mms_aniso_set_variant", "mms_tti_model", "mms_tti_step"]
 
 
 class MMSError(RuntimeError):
@@ -111,6 +111,9 @@ def load():
             "mms_dot_f64": [P, P, i64, P, P],
             "mms_vti_model": [ctypes.POINTER(WaveDesc), P, P, P, P, P, ctypes.c_float, ctypes.c_float, P],
             "mms_vti_step": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P, P, P, P, P],
+            "mms_tti_model": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P, ctypes.c_float, ctypes.c_float,
+                              P],
+            "mms_tti_step": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P, P, P, P, P, P],
             "mms_aniso_num_variants": [i32],
             "mms_aniso_set_variant": [i32, i32],
             "mms_last_error": [],
@@ -377,6 +380,25 @@ def vti_step(desc, coeffs, mv, rho, sh_cur, sv_cur, sh_prev, sv_prev, sh_next, s
     check(load().mms_vti_step(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(mv), _ptr(rho),
                               _ptr(sh_cur), _ptr(sv_cur), _ptr(sh_prev), _ptr(sv_prev), _ptr(sh_next),
                               _ptr(sv_next), _ptr(src_amp), _ptr(rec), _stream(stream)))
+
+
+def tti_model(desc, vp, vs, eps, delta, alpha, theta, phi, med, dt, h, stream=None):
+    """mms_tti_model: med (8, nz, ny, nx) = [a, b, c, d, alpha, nx, ny, nz]."""
+    check(load().mms_tti_model(ctypes.byref(desc), _ptr(vp), _ptr(vs), _ptr(eps), _ptr(delta), _ptr(alpha),
+                               _ptr(theta), _ptr(phi), _ptr(med), float(dt), float(h), _stream(stream)))
+
+
+def tti_step(desc, w2, w1, med, p_cur, q_cur, p_prev, q_prev, p_next, q_next, work, src_amp, rec=None,
+             stream=None):
+    """mms_tti_step: (p, q)^{n+1} into p_next, q_next (which may be p_prev,
+    q_prev); work: 4*nshots*nx*ny*nz floats of scratch."""
+    a2, a1 = _host_coeffs(w2), _host_coeffs(w1)
+    if a2.size != 2 * desc.radius + 1 or a1.size != 2 * desc.radius + 1:
+        raise ValueError("w2 and w1 need 2r+1 weights each")
+    check(load().mms_tti_step(ctypes.byref(desc), a2.ctypes.data_as(ctypes.c_void_p),
+                              a1.ctypes.data_as(ctypes.c_void_p), _ptr(med), _ptr(p_cur), _ptr(q_cur),
+                              _ptr(p_prev), _ptr(q_prev), _ptr(p_next), _ptr(q_next), _ptr(work), _ptr(src_amp),
+                              _ptr(rec), _stream(stream)))
 
 
 ANISO_KINDS = {"vti": 0}

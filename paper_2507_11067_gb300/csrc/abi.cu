@@ -664,6 +664,66 @@ mms_status mms_vti_step(const mms_wave_desc *desc, const float *coeffs, const fl
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "VTI step launch");
 }
 
+mms_status mms_tti_model(const mms_wave_desc *desc, const float *vp, const float *vs, const float *eps,
+                         const float *delta, const float *alpha, const float *theta, const float *phi,
+                         float *med, float dt, float h, void *stream)
+{
+    WaveGeo g;
+    static const float dummy[27] = {0};
+    mms_status st = wave_geo(desc, dummy, &g);
+    if (st != MMS_OK) return st;
+    if (!vp || !vs || !eps || !delta || !alpha || !theta || !phi || !med) return fail(MMS_E_ARG, "null pointer");
+    if (!(dt > 0.f) || !(h > 0.f)) return fail(MMS_E_ARG, "dt and h must be positive");
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    const float *ins[7] = {vp, vs, eps, delta, alpha, theta, phi};
+    for (const float *q : ins)
+        if (overlaps(q, (size_t)n * 4, med, (size_t)n * 32)) return fail(MMS_E_ARG, "med overlaps an input");
+    cudaError_t e = launch_tti_model(n, vp, vs, eps, delta, alpha, theta, phi, med, dt, h,
+                                     reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "TTI model kernel launch");
+}
+
+mms_status mms_tti_step(const mms_wave_desc *desc, const float *w2, const float *w1, const float *med,
+                        const float *p_cur, const float *q_cur, const float *p_prev, const float *q_prev,
+                        float *p_next, float *q_next, float *work, const float *src_amp, float *rec, void *stream)
+{
+    WaveGeo g;
+    static const float dummy[27] = {0};
+    mms_status st = wave_geo(desc, dummy, &g);
+    if (st != MMS_OK) return st;
+    if (!w2 || !w1) return fail(MMS_E_ARG, "null weight array");
+    if (!med || !p_cur || !q_cur || !p_prev || !q_prev || !p_next || !q_next || !work || !src_amp)
+        return fail(MMS_E_ARG, "null field pointer");
+    const void *al[9] = {med, p_cur, q_cur, p_prev, q_prev, p_next, q_next, work, nullptr};
+    for (int i = 0; i < 8; ++i)
+        if (!al16(al[i])) return fail(MMS_E_ALIGN, "TTI fields and work must be 16-byte aligned");
+    const size_t fb = field_bytes(g);
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    const size_t wb = (size_t)4 * g.nshots * n * 4;
+    const float *rd[4] = {p_cur, q_cur, p_prev, q_prev};
+    for (int a = 0; a < 4; ++a)
+        for (int b = a + 1; b < 4; ++b)
+            if (overlaps(rd[a], fb, rd[b], fb)) return fail(MMS_E_ARG, "TTI input fields %d and %d overlap", a, b);
+    if (overlaps(p_next, fb, q_next, fb)) return fail(MMS_E_ARG, "p_next and q_next overlap");
+    const float *nx2[2] = {p_next, q_next};
+    for (int o = 0; o < 2; ++o) {
+        for (int a = 0; a < 4; ++a) {
+            if (a == 2 + o && nx2[o] == rd[a]) continue;
+            if (overlaps(nx2[o], fb, rd[a], fb))
+                return fail(MMS_E_ARG, "%s overlaps an input field other than its own previous state",
+                            o ? "q_next" : "p_next");
+        }
+        if (overlaps(nx2[o], fb, work, wb)) return fail(MMS_E_ARG, "work overlaps an output field");
+        if (overlaps(nx2[o], fb, med, (size_t)n * 32)) return fail(MMS_E_ARG, "an output field overlaps med");
+    }
+    for (int a = 0; a < 4; ++a)
+        if (overlaps(rd[a], fb, work, wb)) return fail(MMS_E_ARG, "work overlaps an input field");
+    if (overlaps(med, (size_t)n * 32, work, wb)) return fail(MMS_E_ARG, "work overlaps med");
+    cudaError_t e = launch_tti_step(g, w2, w1, med, p_cur, q_cur, p_prev, q_prev, p_next, q_next, work, src_amp, rec,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "TTI step launch");
+}
+
 int32_t mms_aniso_num_variants(int32_t kind) { return kind == 0 ? vti_num_variants() : 0; }
 
 mms_status mms_aniso_set_variant(int32_t kind, int32_t variant)

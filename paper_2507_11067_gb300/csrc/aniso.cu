@@ -1,5 +1,7 @@
-// aniso.cu -- fused wave steps of the coupled anisotropic systems of the
-// paper's Sec. 2.1: VTI (two stresses sigma_H, sigma_V).
+// aniso.cu -- wave steps of the coupled anisotropic systems of the paper's
+// Sec. 2.1: VTI (two stresses sigma_H, sigma_V; one fused kernel) and TTI
+// (fields p, q with the tilted operators H1, H2; a derivative pass per field
+// and a pointwise combine).
 //
 // VTI.  With mh = m (1+2 eps), mv = m sqrt(1+2 delta) (m = vp^2 dt^2/h^2)
 // the printed system is
@@ -278,11 +280,322 @@ __global__ void vti_model_kernel(WaveGeo geo, const float *__restrict__ vp, cons
     }
 }
 
+// ------------------------------------------------------------------ TTI
+//
+// Per field f (p, then q) the derivative pass writes Lap f and H1 f:
+//     H1 f = nx^2 f_xx + ny^2 f_yy + nz^2 f_zz + 2 nx ny f_xy + 2 ny nz f_yz + 2 nx nz f_xz
+// with n = (sin th cos ph, sin th sin ph, cos th) the tilt axis.  The axis
+// terms use the second-derivative row w2; a mixed term composes two
+// first-derivative rows w1 (Sec. 4.7), and since composed first derivatives
+// commute, f_xz = D_z (D_x f) and f_yz = D_z (D_y f): every arriving plane
+// adds its D_x f, D_y f and centre value, weighted along z, to three register
+// queues (f_xz, f_yz, f_zz).  The in-plane terms f_xx, f_yy and
+// f_xy = sum_b w1[b] D_x f(y + b) come from the output's centre plane, which
+// a ring of R + 3 planes still holds when the output completes, so no
+// per-point value has to wait in registers for the tilt.  The tilt (nx, ny,
+// nz) of the output point is read directly from memory.
+//
+// The combine pass applies the printed coupling with a = vpx^2, b = vpz^2,
+// c = vpn^2, d = vsz^2 (all times dt^2/h^2) and alpha:
+//     p'' = a H2p + alpha b H1q + d (H1p - alpha H1q)
+//     q'' = c/alpha H2p + b H1q - d (H2p/alpha - H2q),     H2 = Lap - H1
+// and the damped leapfrog update, source and receivers of the acoustic step.
+
+struct TtiCoef {
+    float w2[2 * kMaxR + 1];
+    float w1[2 * kMaxR + 1];
+};
+
+template <int R, int TX, int TY>
+struct TtiGeom {
+    using G = Geom<R, TX, TY, 1, R + 3>;
+    static constexpr int S = R + 3;  // planes j - R .. j + 2 resident at step j
+    static constexpr int PL = (G::PLANE + 31) & ~31;
+    static constexpr size_t SMEM = 128 + (size_t)S * PL * 4 + S * sizeof(uint64_t) + 16;
+};
+
+// Dense interior arrays (nshots stacked where per shot): x fastest.
+struct TtiDense {
+    int64_t sy, sz, ss;  // strides of y, z, shot (elements)
+};
+
+template <int R, int TX, int TY>
+__global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
+    tti_deriv_kernel(const __grid_constant__ CUtensorMap tf, const __grid_constant__ TtiCoef cf,
+                     const __grid_constant__ WaveGeo geo, const float *__restrict__ tilt, TtiDense dn,
+                     float *__restrict__ lap, float *__restrict__ h1, int tz, int nzc, int vec, unsigned *err)
+{
+    using T = TtiGeom<R, TX, TY>;
+    using G = typename T::G;
+    constexpr int W = G::W;
+    constexpr int S = T::S;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_align128(smem_raw);
+    float *planes = reinterpret_cast<float *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * T::PL * sizeof(float));
+    int &abort_flag = *reinterpret_cast<int *>(full + S);
+
+    const int tid = threadIdx.x;
+    const int tx = tid % G::NTX, ty = tid / G::NTX;
+    const int sh = blockIdx.z / nzc, zc = blockIdx.z % nzc;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, zb = zc * tz;
+    const int nzt = min(tz, geo.nz - zb);
+    const int P = nzt + 2 * R;
+    const int gx = x0 + 4 * tx, y = y0 + ty;
+    const int64_t npts = (int64_t)geo.nz * dn.sz;  // one tilt component
+
+    auto issue = [&](int j) {
+        const int s = j % S;
+        ptx::mbar_arrive_expect_tx(&full[s], G::PLANE * 4);
+        ptx::tma_load_4d(planes + (size_t)s * T::PL, &tf, x0, y0, zb + j, sh, &full[s]);
+    };
+    if (tid == 0) {
+        ptx::prefetch_tmap(&tf);
+#pragma unroll
+        for (int s = 0; s < S; ++s) ptx::mbar_init(&full[s], 1);
+        ptx::fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int j = 0; j < S && j < P; ++j) issue(j);
+
+    float qzz[W][4], qxz[W][4], qyz[W][4];
+#pragma unroll
+    for (int kk = 0; kk < W; ++kk)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qzz[kk][k] = qxz[kk][k] = qyz[kk][k] = 0.f;
+
+    const bool inside = y < geo.ny && gx < geo.nx;
+    for (int j = 0; j < P; ++j) {
+        const int zo = j - 2 * R;
+        // the output's tilt, read early so that its latency overlaps the plane work
+        float n3[3][4] = {};
+        if (zo >= 0 && inside) {
+            const int64_t o = (int64_t)(zb + zo) * dn.sz + (int64_t)y * dn.sy + gx;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float *src = tilt + c * npts + o;
+                if (vec) {
+                    const float4 t = __ldg(reinterpret_cast<const float4 *>(src));
+                    n3[c][0] = t.x; n3[c][1] = t.y; n3[c][2] = t.z; n3[c][3] = t.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) n3[c][k] = gx + k < geo.nx ? __ldg(src + k) : 0.f;
+                }
+            }
+        }
+        const int s = j % S;
+        const float *pl = planes + (size_t)s * T::PL;
+        float fxx[4], fyy[4], fxy[4];
+        bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err);
+        if (ok) {
+            // arriving plane: centre value, D_x f, D_y f of the thread's points
+            float win[4 * G::NV];
+            load_row<G::NV>(pl + (ty + R) * G::BX + 4 * tx, win);
+            float dx[4], dy[4], c0[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                c0[k] = win[k + R];
+                dx[k] = 0.f;
+#pragma unroll
+                for (int d = 1; d <= R; ++d)
+                    dx[k] = fmaf(cf.w1[R + d], win[k + R + d], fmaf(cf.w1[R - d], win[k + R - d], dx[k]));
+                dy[k] = 0.f;
+            }
+#pragma unroll
+            for (int d = -R; d <= R; ++d) {
+                if (d == 0) continue;
+                float a[4];
+                load_center<R>(pl + (ty + R + d) * G::BX + 4 * tx, a);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dy[k] = fmaf(cf.w1[R + d], a[k], dy[k]);
+            }
+#pragma unroll
+            for (int kk = 0; kk < W; ++kk)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int d = R - kk;  // offset of this plane from slot kk's output plane
+                    qzz[kk][k] = fmaf(cf.w2[R + d], c0[k], qzz[kk][k]);
+                    if (d != 0) {
+                        qxz[kk][k] = fmaf(cf.w1[R + d], dx[k], qxz[kk][k]);
+                        qyz[kk][k] = fmaf(cf.w1[R + d], dy[k], qyz[kk][k]);
+                    }
+                }
+            if (zo >= 0) {
+                // centre plane of the completed output: f_xx, f_yy, f_xy
+                const float *pc = planes + (size_t)((j - R) % S) * T::PL;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) fxx[k] = fyy[k] = fxy[k] = 0.f;
+#pragma unroll
+                for (int b = -R; b <= R; ++b) {
+                    float w[4 * G::NV];
+                    load_row<G::NV>(pc + (ty + R + b) * G::BX + 4 * tx, w);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        fyy[k] = fmaf(cf.w2[R + b], w[k + R], fyy[k]);
+                        if (b == 0) {
+#pragma unroll
+                            for (int a = -R; a <= R; ++a) fxx[k] = fmaf(cf.w2[R + a], w[k + R + a], fxx[k]);
+                        } else {
+                            float ddx = 0.f;
+#pragma unroll
+                            for (int a = 1; a <= R; ++a)
+                                ddx = fmaf(cf.w1[R + a], w[k + R + a], fmaf(cf.w1[R - a], w[k + R - a], ddx));
+                            fxy[k] = fmaf(cf.w1[R + b], ddx, fxy[k]);
+                        }
+                    }
+                }
+            }
+        } else {
+            abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) return;
+        // plane j - R is no longer needed: its stage takes plane j - R + S
+        if (tid == 0 && j >= R && j - R + S < P) issue(j - R + S);
+        if (zo >= 0 && inside) {
+            float l[4], h[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float nx = n3[0][k], ny = n3[1][k], nz = n3[2][k];
+                l[k] = fxx[k] + fyy[k] + qzz[0][k];
+                float t = nx * nx * fxx[k];
+                t = fmaf(ny * ny, fyy[k], t);
+                t = fmaf(nz * nz, qzz[0][k], t);
+                t = fmaf(2.f * nx * ny, fxy[k], t);
+                t = fmaf(2.f * ny * nz, qyz[0][k], t);
+                t = fmaf(2.f * nx * nz, qxz[0][k], t);
+                h[k] = t;
+            }
+            const int64_t o = (int64_t)sh * dn.ss + (int64_t)(zb + zo) * dn.sz + (int64_t)y * dn.sy + gx;
+            if (vec) {
+                *reinterpret_cast<float4 *>(lap + o) = make_float4(l[0], l[1], l[2], l[3]);
+                *reinterpret_cast<float4 *>(h1 + o) = make_float4(h[0], h[1], h[2], h[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (gx + k < geo.nx) {
+                        lap[o + k] = l[k];
+                        h1[o + k] = h[k];
+                    }
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < W - 1; ++kk)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                qzz[kk][k] = qzz[kk + 1][k];
+                qxz[kk][k] = qxz[kk + 1][k];
+                qyz[kk][k] = qyz[kk + 1][k];
+            }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qzz[W - 1][k] = qxz[W - 1][k] = qyz[W - 1][k] = 0.f;
+    }
+}
+
+// Pointwise combine: one thread per (shot, z, y, 4 x).  med: 5 dense
+// interior fields (a, b, c, d, alpha); work: Lap p, H1 p, Lap q, H1 q.
+__global__ void tti_combine_kernel(WaveGeo geo, TtiDense dn, const float *__restrict__ med,
+                                   const float *__restrict__ lp, const float *__restrict__ hp,
+                                   const float *__restrict__ lq, const float *__restrict__ hq,
+                                   const float *__restrict__ pc, const float *__restrict__ qc,
+                                   const float *__restrict__ pp, const float *__restrict__ qp,
+                                   float *__restrict__ pn, float *__restrict__ qn,
+                                   const float *__restrict__ amp, float *__restrict__ rec)
+{
+    const int r = geo.r;
+    const int nxq = (geo.nx + 3) / 4;
+    const int64_t per_shot = (int64_t)geo.nz * geo.ny * nxq;
+    const int64_t total = per_shot * geo.nshots;
+    const int64_t npts = (int64_t)geo.nz * dn.sz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int sh = (int)(i / per_shot);
+        const int64_t rem = i % per_shot;
+        const int xq = (int)(rem % nxq);
+        const int y = (int)((rem / nxq) % geo.ny);
+        const int z = (int)(rem / ((int64_t)nxq * geo.ny));
+        const float gy = sponge(y, geo.ny, geo.sponge_w, geo.sponge_a) * sponge(z, geo.nz, geo.sponge_w, geo.sponge_a);
+        const float s_amp = amp[sh];
+        const int64_t od = (int64_t)z * dn.sz + (int64_t)y * dn.sy;
+        const int64_t ow = (int64_t)sh * dn.ss + od;
+        const int64_t of = (int64_t)sh * geo.ss + (int64_t)(z + r) * geo.pz + (int64_t)(y + r) * geo.py + r;
+        for (int k = 0; k < 4; ++k) {
+            const int x = 4 * xq + k;
+            if (x >= geo.nx) break;
+            const float a = med[od + x], b = med[npts + od + x], c = med[2 * npts + od + x];
+            const float d = med[3 * npts + od + x], al = med[4 * npts + od + x];
+            const float H1p = hp[ow + x], H1q = hq[ow + x];
+            const float H2p = lp[ow + x] - H1p, H2q = lq[ow + x] - H1q;
+            const float inv = 1.f / al;
+            const float rp = a * H2p + al * b * H1q + d * (H1p - al * H1q);
+            const float rq = c * inv * H2p + b * H1q - d * (H2p * inv - H2q);
+            const float g = sponge(x, geo.nx, geo.sponge_w, geo.sponge_a) * gy;
+            const bool at_src = x == geo.src[sh][0] && y == geo.src[sh][1] && z == geo.src[sh][2];
+            const float s = at_src ? s_amp : 0.f;
+            const float vp = g * (2.f * pc[of + x] - g * pp[of + x] + rp + s);
+            const float vq = g * (2.f * qc[of + x] - g * qp[of + x] + rq + s);
+            pn[of + x] = vp;
+            qn[of + x] = vq;
+            if (rec && z == geo.rec_z) rec[((int64_t)sh * geo.ny + y) * geo.nx + x] = vp;
+        }
+    }
+}
+
+// The medium of the TTI step from the Thomsen parameters: 8 dense interior
+// fields [a, b, c, d, alpha, nx, ny, nz] with a = vp^2 (1+2 eps) s,
+// b = vp^2 s, c = vp^2 (1+2 delta) s, d = vs^2 s (s = dt^2/h^2).
+__global__ void tti_model_kernel(int64_t n, const float *__restrict__ vp, const float *__restrict__ vs,
+                                 const float *__restrict__ eps, const float *__restrict__ delta,
+                                 const float *__restrict__ alpha, const float *__restrict__ theta,
+                                 const float *__restrict__ phi, float *__restrict__ med, float s)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v2 = vp[i] * vp[i] * s;
+        float st, ct, sp, cp;
+        sincosf(theta[i], &st, &ct);
+        sincosf(phi[i], &sp, &cp);
+        med[i] = v2 * (1.f + 2.f * eps[i]);
+        med[n + i] = v2;
+        med[2 * n + i] = v2 * (1.f + 2.f * delta[i]);
+        med[3 * n + i] = vs[i] * vs[i] * s;
+        med[4 * n + i] = alpha[i];
+        med[5 * n + i] = st * cp;
+        med[6 * n + i] = st * sp;
+        med[7 * n + i] = ct;
+    }
+}
+
+constexpr int kTtiTX = 64, kTtiTY = 8, kTtiTZ = 128;
+
+template <int R>
+cudaError_t tti_deriv_r(const WaveGeo &g, const TtiCoef &cf, const float *f, const float *tilt, TtiDense dn,
+                        float *lap, float *h1, cudaStream_t st)
+{
+    using T = TtiGeom<R, kTtiTX, kTtiTY>;
+    using G = typename T::G;
+    const int X = g.nx + 2 * R, Y = g.ny + 2 * R, Z = g.nz + 2 * R;
+    CUtensorMap tf;
+    if (!encode_tmap_4d(&tf, f, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1))
+        return cudaErrorInvalidValue;
+    auto kern = tti_deriv_kernel<R, kTtiTX, kTtiTY>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+    if (e != cudaSuccess) return e;
+    const int tz = kTtiTZ;
+    const int nzc = (g.nz + tz - 1) / tz;
+    const dim3 grid((g.nx + kTtiTX - 1) / kTtiTX, (g.ny + kTtiTY - 1) / kTtiTY, nzc * g.nshots);
+    const int vec = g.nx % 4 == 0 && reinterpret_cast<uintptr_t>(tilt) % 16 == 0 &&
+                    reinterpret_cast<uintptr_t>(lap) % 16 == 0 && reinterpret_cast<uintptr_t>(h1) % 16 == 0;
+    kern<<<grid, G::NT, T::SMEM, st>>>(tf, cf, g, tilt, dn, lap, h1, tz, nzc, vec, device_error_word());
+    return cudaGetLastError();
+}
+
 // Tile variants of the VTI step: (TX, TY, stages, z chunk).
 struct VtiVariant { int tx, ty, s, tz; };
 // Variant 0 is the default (fastest on GB300 for 4 shots x 512^3, r = 4).
-constexpr VtiVariant kVtiVariants[] = {{64, 8, 3, 128}, {64, 16, 2, 128}, {32, 16, 3, 128}, {64, 16, 3, 128},
-                                       {64, 8, 4, 128}, {64, 8, 3, 256}, {128, 8, 2, 128}, {32, 8, 3, 128},
+constexpr VtiVariant kVtiVariants[] = {{64, 8, 3, 256}, {64, 16, 2, 128}, {32, 16, 3, 128}, {64, 16, 3, 128},
+                                       {64, 8, 4, 128}, {64, 8, 3, 128}, {128, 8, 2, 128}, {32, 8, 3, 128},
                                        {64, 8, 2, 128}};
 constexpr int kNumVtiVariants = sizeof(kVtiVariants) / sizeof(kVtiVariants[0]);
 int g_vti_variant = 0;
@@ -364,6 +677,45 @@ cudaError_t launch_vti_step(const WaveGeo &g, const float *coeffs, const float *
         case 4: return vti_r<4>(v, g, cf, mv, rho, hcur, vcur, hprev, vprev, hnext, vnext, src_amp, rec, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_tti_step(const WaveGeo &g, const float *w2, const float *w1, const float *med,
+                            const float *pc, const float *qc, const float *pp, const float *qp, float *pn, float *qn,
+                            float *work, const float *src_amp, float *rec, cudaStream_t st)
+{
+    TtiCoef cf{};
+    for (int i = 0; i < 2 * g.r + 1; ++i) {
+        cf.w2[i] = w2[i];
+        cf.w1[i] = w1[i];
+    }
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    TtiDense dn{g.nx, (int64_t)g.nx * g.ny, n};
+    float *lp = work, *hp = work + g.nshots * n, *lq = work + 2 * g.nshots * n, *hq = work + 3 * g.nshots * n;
+    const float *tilt = med + 5 * n;
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
+        const float *fld = f ? qc : pc;
+        float *l = f ? lq : lp, *h = f ? hq : hp;
+        switch (g.r) {
+            case 1: e = tti_deriv_r<1>(g, cf, fld, tilt, dn, l, h, st); break;
+            case 2: e = tti_deriv_r<2>(g, cf, fld, tilt, dn, l, h, st); break;
+            case 3: e = tti_deriv_r<3>(g, cf, fld, tilt, dn, l, h, st); break;
+            case 4: e = tti_deriv_r<4>(g, cf, fld, tilt, dn, l, h, st); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    tti_combine_kernel<<<152 * 8, 256, 0, st>>>(g, dn, med, lp, hp, lq, hq, pc, qc, pp, qp, pn, qn, src_amp, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tti_model(int64_t n, const float *vp, const float *vs, const float *eps, const float *delta,
+                             const float *alpha, const float *theta, const float *phi, float *med, float dt, float h,
+                             cudaStream_t st)
+{
+    const float s = (dt * dt) / (h * h);
+    tti_model_kernel<<<152 * 8, 256, 0, st>>>(n, vp, vs, eps, delta, alpha, theta, phi, med, s);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_vti_model(const WaveGeo &g, const float *vp, const float *eps, const float *delta, float *mv,

@@ -41,6 +41,15 @@ cudaError_t launch_vti_step(const WaveGeo &g, const float *coeffs, const float *
                             float *hnext, float *vnext, const float *src_amp, float *rec, cudaStream_t st);
 cudaError_t launch_vti_model(const WaveGeo &g, const float *vp, const float *eps, const float *delta, float *mv,
                              float *rho, float dt, float h, cudaStream_t st);
+// TTI step (aniso.cu): derivative passes for p and q into `work` (4 *
+// nshots * nx*ny*nz floats: Lap p, H1 p, Lap q, H1 q), then the combine into
+// pn/qn (which may be pp/qp).  med: 8 dense interior fields.
+cudaError_t launch_tti_step(const WaveGeo &g, const float *w2, const float *w1, const float *med,
+                            const float *pc, const float *qc, const float *pp, const float *qp, float *pn, float *qn,
+                            float *work, const float *src_amp, float *rec, cudaStream_t st);
+cudaError_t launch_tti_model(int64_t n, const float *vp, const float *vs, const float *eps, const float *delta,
+                             const float *alpha, const float *theta, const float *phi, float *med, float dt, float h,
+                             cudaStream_t st);
 int vti_num_variants();
 bool vti_set_variant(int v);
 

@@ -1,4 +1,4 @@
-"""GPU parity of the fused VTI step against the FP64 oracle (oracle/aniso.py).
+"""GPU parity of the VTI and TTI steps against the FP64 oracle (oracle/aniso.py).
 
 Teacher-forced: the oracle takes the GPU's FP32 states and medium inputs
 and does one FP64 step; the bar is max|gpu - oracle| / max|oracle| <= 1e-5
@@ -209,3 +209,163 @@ def test_vti_512_sampled_full_size():
     eh, ev = rel(gh, oh), rel(gv, ov)
     print(f"VTI 512^3 sampled ({len(pts)} points): {eh:.2e} {ev:.2e}")
     assert eh <= TOL and ev <= TOL
+
+
+# ------------------------------------------------------------------ TTI
+
+class Tti:
+    def __init__(self, nx=45, ny=38, nz=41, r=4, nshots=2, sponge=6, seed=0, nsteps=30, rec=True):
+        self.nx, self.ny, self.nz, self.r, self.ns = nx, ny, nz, r, nshots
+        self.a = workloads.AnisoInputs(nx, ny, nz, nshots, nsteps, workload=7, sponge=sponge, salt=seed, tti=True)
+        g = np.random.default_rng(200 + seed)
+        n3 = (nz, ny, nx)
+        # per-point medium and tilt: every coefficient of H1 and of the
+        # coupling varies from point to point
+        self.inputs = [self.a.vp, (0.4 * self.a.vp * g.uniform(0.9, 1.1, n3)).astype(np.float32),
+                       g.uniform(0.0, 0.3, n3).astype(np.float32), g.uniform(-0.1, 0.2, n3).astype(np.float32),
+                       g.uniform(0.7, 1.3, n3).astype(np.float32), g.uniform(0.0, np.pi / 2, n3).astype(np.float32),
+                       g.uniform(-np.pi, np.pi, n3).astype(np.float32)]
+        self.w2 = aniso.fd2_row(r).astype(np.float32)
+        self.w1 = aniso.fd1_row(r).astype(np.float32)
+        self.med = torch.empty((8, nz, ny, nx), device="cuda")
+        self.work = torch.empty((4, nshots, nz, ny, nx), device="cuda")
+        self.f = [mms.padded_empty(nx, ny, nz, r, nshots=nshots) for _ in range(6)]
+        py, pz, ss = mms.field_geometry(self.f[0])
+        self.desc, self._src = mms.wave_desc(nx, ny, nz, r, nshots, py, pz, ss, sponge, self.a.wave.sponge_a,
+                                             self.a.zrec if rec else -1, self.a.src)
+        dev = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in self.inputs]
+        mms.tti_model(self.desc, *dev, self.med, self.a.dt, self.a.h)
+        self.amps = torch.from_numpy(self.a.amp).cuda().contiguous()
+        vp, vs, eps, delta, alpha, th, ph = self.inputs
+        self.med_o = aniso.tti_medium(vp, vs, eps, delta, alpha, self.a.dt, self.a.h)
+        self.tilt_o = aniso.tilt_axis(th, ph)
+        self.sponge = (sponge, self.a.wave.sponge_a) if sponge else None
+
+    fill = Vti.fill
+
+    def step(self, pc, qc, pp, qp, pn, qn, amp, rec=None):
+        mms.tti_step(self.desc, self.w2, self.w1, self.med, pc, qc, pp, qp, pn, qn, self.work, amp, rec)
+
+    def oracle_step(self, pc, qc, pp, qp, n, sh):
+        return aniso.tti_step(self.r, self.med_o, self.tilt_o, self.sponge, self.a.src[sh], float(self.a.amp[n, sh]),
+                              pc[sh], qc[sh], pp[sh], qp[sh], self.w2, self.w1)
+
+
+def test_tti_model_matches_the_oracle_medium():
+    s = Tti()
+    med = s.med.cpu().numpy().astype(np.float64)
+    for k in range(5):
+        assert rel(med[k], s.med_o[k]) <= 1e-6, k
+    for k in range(3):
+        assert np.abs(med[5 + k] - s.tilt_o[k]).max() <= 1e-6, k
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_tti_teacher_forced_step(r):
+    s = Tti(nx=45 + r, ny=38, nz=41 - r, r=r, seed=r)
+    pc, qc, pp, qp, pn, qn = s.f
+    for k, f in enumerate((pc, qc, pp, qp)):
+        s.fill(f, 30 * r + k)
+    s.amps[4] = 3.0
+    s.a.amp[4] = 3.0
+    rec = torch.zeros((s.ns, s.ny, s.nx), device="cuda")
+    ins = [_host(f) for f in (pc, qc, pp, qp)]
+    s.step(pc, qc, pp, qp, pn, qn, s.amps[4], rec)
+    torch.cuda.synchronize()
+    mms.check_device()
+    gp, gq = _host(pn), _host(qn)
+    for sh in range(s.ns):
+        op, oq = s.oracle_step(*ins, 4, sh)
+        ep, eq = rel(gp[sh], op), rel(gq[sh], oq)
+        print(f"TTI r={r} shot {sh}: p {ep:.2e}, q {eq:.2e}")
+        assert ep <= TOL and eq <= TOL
+        assert np.all(gp[sh][:r] == 0) and np.all(gq[sh][:, :, -r:] == 0)
+        np.testing.assert_array_equal(rec[sh].cpu().numpy(), pn[sh, r + s.a.zrec, r:-r, r:-r].cpu().numpy())
+
+
+def test_tti_in_place_equals_out_of_place():
+    s = Tti(nx=70, ny=37, nz=45, nshots=1, rec=False)
+    pc, qc, pp, qp, pn, qn = s.f
+    for k, f in enumerate((pc, qc, pp, qp)):
+        s.fill(f, 60 + k)
+    s.step(pc, qc, pp, qp, pn, qn, s.amps[3])
+    pp2 = mms.padded_empty(s.nx, s.ny, s.nz, s.r, nshots=1)
+    qp2 = mms.padded_empty(s.nx, s.ny, s.nz, s.r, nshots=1)
+    pp2.copy_(pp)
+    qp2.copy_(qp)
+    s.step(pc, qc, pp2, qp2, pp2, qp2, s.amps[3])
+    torch.cuda.synchronize()
+    mms.check_device()
+    assert torch.equal(pp2, pn) and torch.equal(qp2, qn)
+
+
+def test_tti_trajectory_from_rest():
+    s = Tti(nx=48, ny=44, nz=40, nshots=2, sponge=8, nsteps=30)
+    pc, qc, pp, qp, pn, qn = s.f
+    r = s.r
+    o = [[np.zeros(pc.shape[1:]) for _ in range(4)] for _ in range(s.ns)]
+    cur = [pc, qc, pp, qp]
+    for n in range(30):
+        s.step(cur[0], cur[1], cur[2], cur[3], cur[2], cur[3], s.amps[n])
+        cur = [cur[2], cur[3], cur[0], cur[1]]
+        for sh in range(s.ns):
+            p1, q1 = aniso.tti_step(r, s.med_o, s.tilt_o, s.sponge, s.a.src[sh], float(s.a.amp[n, sh]), *o[sh],
+                                    s.w2, s.w1)
+            o[sh] = [p1, q1, o[sh][0], o[sh][1]]
+    torch.cuda.synchronize()
+    mms.check_device()
+    gp, gq = _host(cur[0]), _host(cur[1])
+    for sh in range(s.ns):
+        ep, eq = rel(gp[sh], o[sh][0]), rel(gq[sh], o[sh][1])
+        print(f"TTI 30-step trajectory shot {sh}: {ep:.2e} {eq:.2e}")
+        assert np.abs(o[sh][0]).max() > 0
+        assert ep <= 1e-4 and eq <= 1e-4
+
+
+def test_tti_refuses_bad_work_and_weights():
+    s = Tti(nx=20, ny=20, nz=20, nshots=1)
+    pc, qc, pp, qp, pn, qn = s.f
+    with pytest.raises(mms.MMSError):       # work over an output field
+        mms.tti_step(s.desc, s.w2, s.w1, s.med, pc, qc, pp, qp, pn, qn, pn, s.amps[0])
+    with pytest.raises(mms.MMSError):       # outputs overlap
+        mms.tti_step(s.desc, s.w2, s.w1, s.med, pc, qc, pp, qp, pn, pn, s.work, s.amps[0])
+    with pytest.raises(ValueError):
+        mms.tti_step(s.desc, s.w2[:-1], s.w1, s.med, pc, qc, pp, qp, pn, qn, s.work, s.amps[0])
+
+
+def test_tti_512_sampled_full_size():
+    n, r = 512, 4
+    a = workloads.AnisoInputs(n, n, n, 1, 4, workload=7, tti=True)
+    w2 = aniso.fd2_row(r).astype(np.float32)
+    w1 = aniso.fd1_row(r).astype(np.float32)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    med = torch.empty((8, n, n, n), device="cuda")
+    f = [mms.padded_empty(n, n, n, r, nshots=1) for _ in range(4)]
+    py, pz, ss = mms.field_geometry(f[0])
+    desc, _src = mms.wave_desc(n, n, n, r, 1, py, pz, ss, 20, a.wave.sponge_a, a.zrec, a.src)
+    mms.tti_model(desc, dev(a.vp), dev(a.vs), dev(a.eps), dev(a.delta), dev(a.alpha), dev(a.theta), dev(a.phi),
+                  med, a.dt, a.h)
+    g = np.random.default_rng(19)
+    host = []
+    for k in range(4):
+        x = np.zeros(f[k].shape[1:], np.float32)
+        x[r:-r, r:-r, r:-r] = g.uniform(-1, 1, (n, n, n)).astype(np.float32)
+        f[k][0].copy_(torch.from_numpy(x))
+        host.append(x)
+    work = torch.empty((4, 1, n, n, n), device="cuda")
+    pn = mms.padded_empty(n, n, n, r, nshots=1, zero=False)
+    qn = mms.padded_empty(n, n, n, r, nshots=1, zero=False)
+    amp = torch.full((1,), 2.5, device="cuda")
+    mms.tti_step(desc, w2, w1, med, f[0], f[1], f[2], f[3], pn, qn, work, amp)
+    torch.cuda.synchronize()
+    mms.check_device()
+    pts = np.vstack([workloads.sample_points(n, n, n, 2000, workload=7), [a.src[0]]])
+    med_o = aniso.tti_medium(a.vp, a.vs, a.eps, a.delta, a.alpha, a.dt, a.h)
+    tilt_o = aniso.tilt_axis(a.theta, a.phi)
+    op, oq = aniso.tti_step_points(r, med_o, tilt_o, (20, a.wave.sponge_a), a.src[0], 2.5, *host, pts, w2, w1)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    gp = pn[0].cpu().numpy()[z + r, y + r, x + r]
+    gq = qn[0].cpu().numpy()[z + r, y + r, x + r]
+    ep, eq = rel(gp, op), rel(gq, oq)
+    print(f"TTI 512^3 sampled ({len(pts)} points): {ep:.2e} {eq:.2e}")
+    assert ep <= TOL and eq <= TOL

@@ -26,6 +26,12 @@ def test_fd1_weights_closed_forms():
     assert aniso.fd1_weights(4) == [Fraction(4, 5), Fraction(-1, 5), Fraction(4, 105), Fraction(-1, 280)]
 
 
+def test_workload_fd8_rows_are_the_exact_weights():
+    w2, w1 = workloads.fd8_rows()
+    np.testing.assert_allclose(w2, aniso.fd2_row(4).astype(np.float32), rtol=0, atol=0)
+    np.testing.assert_allclose(w1, aniso.fd1_row(4).astype(np.float32), rtol=0, atol=0)
+
+
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
 def test_fd1_row_is_exact_to_order_2r(r):
     row = aniso.fd1_row(r)
@@ -271,3 +277,19 @@ def test_tti_isotropic_is_the_acoustic_step():
         scale = np.abs(a_cur).max()
         np.testing.assert_allclose(p, a_cur, rtol=0, atol=1e-11 * scale)
         np.testing.assert_allclose(q, a_cur, rtol=0, atol=1e-11 * scale)
+
+
+def test_tti_points_equal_the_full_step():
+    r = 3
+    n = (9, 11, 10)
+    g = np.random.default_rng(12)
+    med, tilt = _tti_medium(n, seed=3)
+    f = [_padded(g.uniform(-1, 1, size=n), r) for _ in range(4)]
+    src = (4, 5, 3)
+    full = aniso.tti_step(r, med, tilt, (2, 0.2), src, 0.9, *f)
+    pts = np.array([[x, y, z] for z in range(n[0]) for y in range(n[1]) for x in range(n[2])][::5])
+    pts = np.vstack([pts, [src]])
+    pp, pq = aniso.tti_step_points(r, med, tilt, (2, 0.2), src, 0.9, *f, pts)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    np.testing.assert_allclose(pp, full[0][z + r, y + r, x + r], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(pq, full[1][z + r, y + r, x + r], rtol=1e-12, atol=1e-12)

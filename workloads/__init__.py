@@ -33,6 +33,12 @@ WORKLOADS = {
 FD8 = (-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0)
 
 
+# Standard 8th-order (radius-4) central first-derivative weights b_1..b_4
+# (Fornberg 1988), the inputs of the TTI mixed derivatives; checked against
+# the oracle's exact rational solve in the tests.
+FD1_8 = (4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0)
+
+
 def rng(workload: int, salt: int = 0) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(SEED_BASE + workload + 1000 * salt))
 
@@ -92,6 +98,15 @@ def fd8_star_coeffs() -> np.ndarray:
     """(3, 9) float32: the FD8 weights on each axis (centre applied 3x)."""
     row = [FD8[abs(d)] for d in range(-4, 5)]
     return np.array([row, row, row], dtype=np.float32)
+
+
+def fd8_rows():
+    """The radius-4 second- and first-derivative rows over offsets -4..4
+    (float32), the TTI workload's weights."""
+    w2 = np.array([FD8[abs(d)] for d in range(-4, 5)], np.float32)
+    w1 = np.array([-FD1_8[-d - 1] if d < 0 else (0.0 if d == 0 else FD1_8[d - 1]) for d in range(-4, 5)],
+                  np.float32)
+    return w2, w1
 
 
 def star_coeffs(r: int, workload: int = 3, salt=0) -> np.ndarray:
