@@ -387,6 +387,8 @@ def main():
     ap.add_argument("--path", default="auto")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0,
+                    help="grid edge of the anisotropic workloads (0 = the workload's own 512; smaller for profiling)")
     ap.add_argument("--shots", type=int, default=0,
                     help="shots of the wave workloads (0 = the workload's own: 8 for rtm512, 2 for grad256)")
     args = ap.parse_args()
@@ -786,7 +788,7 @@ def run_aniso(args):
     mms.build()
     mms.load()
     hbm_peak, _, _, peak_src = peaks()
-    n, r = spec["n"], 4
+    n, r = args.n or spec["n"], 4
     nshots = args.shots or spec["shots"]
     steps = args.steps or 200
     tti = spec["kind"] == "tti"
