@@ -47,6 +47,7 @@ WORKLOADS = {
     "grad256": None,   # adjoint gradient: 2 shots x 256^3, 200 steps, checkpoint 20
     "vti512": None,    # VTI forward: 4 shots x 512^3 (see run_aniso)
     "tti512": None,    # TTI forward: 2 shots x 512^3 (see run_aniso)
+    "fp64_512": [("star", 4, 512), ("box", 1, 512)],   # FP64 sweeps (see run_f64)
 }
 WORKLOAD_NAMES = {
     "box512": WORKLOAD,
@@ -65,6 +66,8 @@ WORKLOAD_NAMES = {
     "tti512": "TTI forward (p, q with H1, H2 of Sec. 2.1), 2 shots x 512^3, r=4 FD8 second- and first-derivative "
               "weights, layered vp with per-layer eps, delta, vs = vp/2, alpha = 1, smooth tilt, 20-cell sponge",
 }
+WORKLOAD_NAMES["fp64_512"] = ("FP64 sweeps: star r=4 (FD8 weights) and box r=1 (weights N(0, 1/27)), 512^3 "
+                              "FP64 interior + halo, input U[-1, 1]")
 ANISO = {"vti512": dict(kind="vti", n=512, shots=4, bytes_per_point_step=32,
                         kernel="vti_fwd_kernel (two coupled r=4 stars + leapfrog + sponge + source + receivers)"),
          # per point-step: two derivative passes (read the field and the tilt,
@@ -400,6 +403,8 @@ def main():
         return run_wave(args)
     if args.workload in ANISO:
         return run_aniso(args)
+    if args.workload == "fp64_512":
+        return run_f64(args)
 
     import torch
     import paper_2507_11067_gb300 as mms
@@ -894,6 +899,128 @@ def run_aniso(args):
                            "time_steps": steps, "l2": "inputs larger than L2"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": steps * (3 if tti else 1), "clocks": clk,
+                "peaks": {"hbm_gbs": hbm_peak, "source": peak_src}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_f64(args):
+    """FP64 sweeps on one GPU (independent grids per rank, weak scaling):
+    bound by the FP64 pipe, reported against its peak."""
+    import torch
+    import paper_2507_11067_gb300 as mms
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mms.build()
+    mms.load()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    hbm_peak, _, sm_max_mhz, peak_src = peaks()
+    plan = WORKLOADS[args.workload]
+    coeffs, ins, outs, hosts, houts = [], [], [], [], []
+    for shape, r, n in plan:
+        coeffs.append(np.asarray(sweep_coeffs(shape, r), np.float64))
+        grid = sweep_input(shape, r, n, rank)
+        d = mms.padded_empty(n, n, n, r, device=dev, dtype=torch.float64, zero=False)
+        h = torch.empty(d.shape, dtype=torch.float64, pin_memory=True)
+        h.copy_(torch.from_numpy(grid))
+        d.copy_(h)
+        del grid
+        ins.append(d)
+        hosts.append(h)
+        outs.append(torch.empty((n, n, n), device=dev, dtype=torch.float64))
+        houts.append(torch.empty((n, n, n), dtype=torch.float64, pin_memory=True))
+    stream = torch.cuda.current_stream(dev)
+    steps = args.steps or 5
+
+    def sweep(i):
+        shape, r, _ = plan[i]
+        mms.apply_f64(shape, r, coeffs[i], ins[i], outs[i])
+
+    for _ in range(args.warmup):
+        for i in range(len(plan)):
+            sweep(i)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    ev = [[] for _ in plan]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        for i in range(len(plan)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sweep(i)
+            b.record(stream)
+            ev[i].append((a, b))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3, dist, dev)
+    pts_step = sum(n ** 3 for _, _, n in plan)
+    value = job_rate(world, pts_step * steps, elapsed)
+    kms = [statistics.mean(a.elapsed_time(b) for a, b in e) for e in ev]
+    # end to end: pinned host grids in, the FP64 sweeps, results out
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = 2
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for i in range(len(plan)):
+            ins[i].copy_(hosts[i], non_blocking=True)
+            sweep(i)
+            houts[i].copy_(outs[i], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+    # FP64 pipe: 2 FMAs per clock per SM (GB300's nominal 1.25 TFLOP/s FP64)
+    fp64_peak = n_sm * 2 * 2 * sm_max_mhz * 1e6 / 1e12
+    fmas = {"star": lambda r: 6 * r + 1, "box": lambda r: (2 * r + 1) ** 3}
+    di = max(range(len(plan)), key=lambda i: kms[i])
+    shape, r, n = plan[di]
+    flops = 2 * fmas[shape](r) * n ** 3
+    roof = {"bound": "alu", "achieved": flops / (kms[di] / 1e3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": flops / (kms[di] / 1e3) / 1e12 / fp64_peak, "traffic": None,
+            "kernel": f"f64_kernel {shape} r={r} {n}^3", "ms": kms[di],
+            "peak_note": f"{n_sm} SMs x 2 FP64 FMA/clock x 2 flop x {sm_max_mhz:.0f} MHz (GB300's nominal FP64 rate)",
+            "flop_per_point": 2 * fmas[shape](r)}
+    sweeps = {f"{sh} r={rr}": {"ms": kms[i], "gpts": n_ ** 3 / (kms[i] / 1e3) / 1e9,
+                                "fp64_tflops": 2 * fmas[sh](rr) * n_ ** 3 / (kms[i] / 1e3) / 1e12}
+              for i, (sh, rr, n_) in enumerate(plan)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+
+        def sample(p, salt=0):
+            return oracle_sample(p, salt, plan)
+        planes = calibrate_planes(5.0, sample)
+        p, secs, threads = sample(planes)
+        cpu = {"value": p / secs / 1e9, "unit": "GPoints/s", "cores": threads, "kind": "oracle",
+               "sample": "FP64 oracle, " + ", ".join(f"{sh} r={rr}" for sh, rr, _ in plan) +
+                         f", on a seeded slab of {planes} output planes of each grid"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GPoints/s", "n_gpus": world, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD_NAMES[args.workload], "l2": "inputs larger than L2"},
+                "roofline": roof, "sweeps": sweeps, "cpu_baseline": cpu,
+                "e2e": {"value": job_rate(world, pts_step * e2e_steps, e2e_s), "unit": "GPoints/s",
+                        "h2d_bytes_per_step": sum(h.numel() * 8 for h in hosts),
+                        "d2h_bytes_per_step": sum(h.numel() * 8 for h in houts)},
+                "gpu_launches": steps * len(plan), "clocks": clk,
                 "peaks": {"hbm_gbs": hbm_peak, "source": peak_src}}
         print(json.dumps(line), flush=True)
     if dist:

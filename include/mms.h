@@ -195,6 +195,21 @@ mms_status mms_set_variant(int shape, int radius, int path, int32_t variant);
 mms_status mms_stencil_apply_noalloc(const mms_stencil_desc *desc, const float *in, float *out,
                                      void *stream);
 
+/*
+ * FP64 sweep (the paper's motivation compares GPU stencil libraries in FP64,
+ * Sec. 3.2): the definition of mms_stencil_apply_ex in double precision on
+ * the CUDA cores.  desc gives shape, radius, sizes and pitches (in doubles;
+ * 0 = dense); desc->coeffs is not read -- the weights come in `coeffs`
+ * (host doubles, layout as for mms_stencil_apply); desc->path must be
+ * MMS_PATH_AUTO or MMS_PATH_CUDA_CORE and desc->variant is ignored.
+ * in/out: device doubles, 8-byte aligned, not overlapping.  Bound by
+ * GB300's FP64 pipe (about 2 FMAs per clock per SM): a star of radius r
+ * costs 6r + 1 FMAs per point (its three centre weights folded into one),
+ * a box (2r+1)^3.  Errors as for mms_stencil_apply_ex.
+ */
+mms_status mms_stencil_apply_f64(const mms_stencil_desc *desc, const double *coeffs, const double *in,
+                                 double *out, void *stream);
+
 /* ------------------------------------------------------- acoustic wave */
 
 /*

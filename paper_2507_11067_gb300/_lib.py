@@ -21,6 +21,12 @@ SHAPES = {"star": STAR, "box": BOX, "star2d": STAR2D, "box2d": BOX2D,
 PLANAR = (STAR2D, BOX2D)
 
 
+def n_coeffs(shape, r):
+    """Stored weights of a shape: 3(2r+1) star, (2r+1)^3 box, 2(2r+1) star2d, (2r+1)^2 box2d."""
+    w = 2 * r + 1
+    return {"star": 3 * w, "box": w ** 3, "star2d": 2 * w, "box2d": w * w}[shape]
+
+
 def interior(shape, r, padded_shape):
     """(nx, ny, nz) of a padded (Z, Y, X) grid: the planar shapes have no z
     halo (nz independent planes)."""
@@ -40,7 +46,7 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
            "mms_check_device", "mms_version", "mms_stencil_apply_noalloc", "mms_wave_step_to",
            "mms_sum_f64", "mms_selftest_timeout", "mms_stencil_apply_host", "mms_vti_model", "mms_vti_step",
-           "mms_aniso_num_variants", "mms_aniso_set_variant", "mms_tti_model", "mms_tti_step"]
+           "mms_aniso_num_variants", "mms_aniso_set_variant", "mms_tti_model", "mms_tti_step", "mms_stencil_apply_f64"]
 
 
 class MMSError(RuntimeError):
@@ -94,6 +100,7 @@ def load():
             "mms_stencil_apply_ex": [ctypes.POINTER(StencilDesc), P, P, P],
             "mms_stencil_apply_noalloc": [ctypes.POINTER(StencilDesc), P, P, P],
             "mms_stencil_apply_host": [ctypes.POINTER(StencilDesc), P, P, P],
+            "mms_stencil_apply_f64": [ctypes.POINTER(StencilDesc), P, P, P, P],
             "mms_num_variants": [i32, i32, i32],
             "mms_auto_path": [i32, i32, i32],
             "mms_default_variant": [i32, i32, i32, i64, i64, i64],
@@ -227,6 +234,29 @@ def apply(shape, r, coeffs, inp, out=None, path="auto", variant=-1, stream=None)
     d = StencilDesc(SHAPES[shape], r, c.ctypes.data, nx, ny, nz, ipy, ipz, opy, opz,
                     PATHS[path] if isinstance(path, str) else int(path), int(variant))
     check(load().mms_stencil_apply_ex(ctypes.byref(d), _ptr(inp), _ptr(out), _stream(stream)))
+    return out
+
+
+def apply_f64(shape, r, coeffs, inp, out=None, stream=None):
+    """The FP64 sweep (mms_stencil_apply_f64): inp a CUDA float64 padded view
+    with unit x stride (any pitches), out an interior view or None."""
+    import torch
+    if not inp.is_cuda or inp.dtype != torch.float64:
+        raise ValueError("input must be a CUDA float64 tensor")
+    nx, ny, nz = interior(shape, r, inp.shape)
+    if out is None:
+        out = torch.empty((nz, ny, nx), device=inp.device, dtype=torch.float64)
+    if out.dtype != torch.float64:
+        raise ValueError("output must be float64")
+    ipy, ipz = pitches(inp)
+    opy, opz = pitches(out)
+    c = np.ascontiguousarray(np.asarray(coeffs.detach().cpu().numpy() if hasattr(coeffs, "detach") else coeffs,
+                                        dtype=np.float64).reshape(-1))
+    if c.size != n_coeffs(shape, r):
+        raise ValueError(f"{shape} r={r} needs {n_coeffs(shape, r)} coefficients")
+    d = StencilDesc(SHAPES[shape], r, None, nx, ny, nz, ipy, ipz, opy, opz, PATHS["auto"], -1)
+    check(load().mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(ctypes.c_void_p), _ptr(inp), _ptr(out),
+                                       _stream(stream)))
     return out
 
 

@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libmms.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["abi.cu", "sweep_cc.cu", "sweep_star.cu", "sweep_box_high.cu", "sweep_2d.cu", "wave.cu",
-           "band_tc.cu", "noalloc.cu", "aniso.cu"]
+           "band_tc.cu", "noalloc.cu", "aniso.cu", "sweep_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -214,6 +214,52 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "tensor-core sweep launch");
 }
 
+cudaError_t launch_f64(int shape, int r, const double *coeffs, int ncoef, const double *in, int64_t ipy, int64_t ipz,
+                       double *out, int64_t opy, int64_t opz, int64_t nx, int64_t ny, int64_t nz, cudaStream_t st);
+
+static int n_coeffs(int shape, int r)
+{
+    const int w = 2 * r + 1;
+    switch (shape) {
+        case MMS_STAR: return 3 * w;
+        case MMS_BOX: return w * w * w;
+        case MMS_STAR2D: return 2 * w;
+        default: return w * w;
+    }
+}
+
+static mms_status apply_f64(const mms_stencil_desc *d, const double *coeffs, const double *in, double *out,
+                            void *stream)
+{
+    if (!d) return fail(MMS_E_ARG, "null descriptor");
+    const int shape = d->shape, r = d->radius;
+    if (shape < MMS_STAR || shape > MMS_BOX2D) return fail(MMS_E_ARG, "shape %d is not STAR, BOX, STAR2D or BOX2D", shape);
+    if (r < 1 || r > kMaxR) return fail(MMS_E_ARG, "radius %d outside 1..%d", r, kMaxR);
+    if (!coeffs) return fail(MMS_E_ARG, "null coefficient array");
+    if (d->nx < 0 || d->ny < 0 || d->nz < 0) return fail(MMS_E_ARG, "negative size");
+    if (d->nx >= (1ll << 30) || d->ny >= (1ll << 30) || d->nz >= (1ll << 30))
+        return fail(MMS_E_ARG, "size above 2^30");
+    if (d->path != MMS_PATH_AUTO && d->path != MMS_PATH_CUDA_CORE)
+        return fail(MMS_E_UNSUPPORTED, "FP64 sweeps run on the CUDA cores only (path %d)", d->path);
+    if (d->nx == 0 || d->ny == 0 || d->nz == 0) return MMS_OK;
+    if (!in || !out) return fail(MMS_E_ARG, "null grid pointer");
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 8)
+        return fail(MMS_E_ALIGN, "FP64 grids must be 8-byte aligned");
+    const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + (is_planar(shape) ? 0 : 2 * r);
+    const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
+    const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
+    const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
+    const int64_t opz = d->out_pitch_z ? d->out_pitch_z : d->ny * opy;
+    if (ipy < X || ipz < Y * ipy) return fail(MMS_E_ARG, "input pitches (%lld, %lld) below the padded extents", (long long)ipy, (long long)ipz);
+    if (opy < d->nx || opz < d->ny * opy) return fail(MMS_E_ARG, "output pitches (%lld, %lld) below the interior extents", (long long)opy, (long long)opz);
+    const size_t in_bytes = (size_t)((Z - 1) * ipz + (Y - 1) * ipy + X) * 8;
+    const size_t out_bytes = (size_t)((d->nz - 1) * opz + (d->ny - 1) * opy + d->nx) * 8;
+    if (overlaps(in, in_bytes, out, out_bytes)) return fail(MMS_E_ARG, "input and output overlap");
+    cudaError_t e = launch_f64(shape, r, coeffs, n_coeffs(shape, r), in, ipy, ipz, out, opy, opz, d->nx, d->ny, d->nz,
+                               reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "FP64 sweep launch");
+}
+
 // The sweep of apply() on grids in host memory: z-slabs of the input (with
 // their 2r halo planes) are copied in, swept and copied back, pipelined over
 // two device slab buffers and three streams -- copy in and copy out on
@@ -356,6 +402,12 @@ mms_status mms_stencil_apply(int shape, int radius, const float *coeffs, const f
     d.path = MMS_PATH_AUTO;
     d.variant = -1;
     return apply(&d, in, out, stream);
+}
+
+mms_status mms_stencil_apply_f64(const mms_stencil_desc *desc, const double *coeffs, const double *in, double *out,
+                                 void *stream)
+{
+    return apply_f64(desc, coeffs, in, out, stream);
 }
 
 mms_status mms_stencil_apply_ex(const mms_stencil_desc *desc, const float *in, float *out, void *stream)

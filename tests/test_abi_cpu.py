@@ -169,3 +169,23 @@ def test_planar_shapes_are_known(lib):
     d, c = _desc(shape=4)
     buf = ctypes.create_string_buffer(64)
     assert lib.mms_stencil_apply_ex(ctypes.byref(d), buf, buf, None) == 1
+
+
+def test_f64_sweep_validation(lib):
+    P = ctypes.c_void_p
+    c = np.ones(729, np.float64)
+    a = np.zeros(64, np.float64)
+    buf = ctypes.create_string_buffer(1024)
+    d, _ = _desc(radius=2)
+    assert lib.mms_stencil_apply_f64(ctypes.byref(d), None, a.ctypes.data_as(P), a.ctypes.data_as(P), None) == 1
+    assert lib.mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(P), None, None, None) == 1
+    d, _ = _desc(radius=5)
+    assert lib.mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(P), buf, buf, None) == 1
+    d, _ = _desc(path=3)      # a tensor-core path: FP64 runs on the CUDA cores only
+    assert lib.mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(P), buf, buf, None) == 2
+    d, _ = _desc()
+    assert lib.mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(P), buf, buf, None) == 1   # overlap
+    odd = ctypes.c_void_p(ctypes.addressof(buf) + 4)
+    assert lib.mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(P), odd, buf, None) == 3
+    d, _ = _desc(nz=0)
+    assert lib.mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(P), None, None, None) == 0
