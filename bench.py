@@ -70,11 +70,12 @@ WORKLOAD_NAMES["fp64_512"] = ("FP64 sweeps: star r=4 (FD8 weights) and box r=1 (
                               "FP64 interior + halo, input U[-1, 1]")
 ANISO = {"vti512": dict(kind="vti", n=512, shots=4, bytes_per_point_step=32,
                         kernel="vti_fwd_kernel (two coupled r=4 stars + leapfrog + sponge + source + receivers)"),
-         # per point-step: two derivative passes (read the field and the tilt,
-         # 16 B; write Lap f and H1 f, 8 B) and the combine (read 4 work
-         # fields, 5 medium fields, p and q at n and n-1: 52 B; write 8 B)
-         "tti512": dict(kind="tti", n=512, shots=2, bytes_per_point_step=108,
-                        kernel="whole step: tti_deriv_kernel for p and q + tti_combine_kernel")}
+         # per point-step: the p pass (read p and the tilt, 16 B; write Lap p
+         # and H1 p, 8 B) and the q pass with the combine fused in (read q,
+         # Lap p, H1 p, the 8 medium fields, p^n, p^{n-1}, q^{n-1}: 56 B;
+         # write p^{n+1}, q^{n+1}: 8 B)
+         "tti512": dict(kind="tti", n=512, shots=2, bytes_per_point_step=88,
+                        kernel="whole step: tti_deriv_kernel<p> + tti_deriv_kernel<q, combine fused>")}
 
 
 def sweep_coeffs(shape, r):
@@ -898,7 +899,7 @@ def run_aniso(args):
                 "config": {"workload": WORKLOAD_NAMES[args.workload], "shots": nshots, "n": n,
                            "time_steps": steps, "l2": "inputs larger than L2"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": steps * (3 if tti else 1), "clocks": clk,
+                "gpu_launches": steps * (2 if tti else 1), "clocks": clk,
                 "peaks": {"hbm_gbs": hbm_peak, "source": peak_src}}
         print(json.dumps(line), flush=True)
     if dist:

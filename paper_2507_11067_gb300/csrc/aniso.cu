@@ -306,12 +306,22 @@ struct TtiCoef {
     float w1[2 * kMaxR + 1];
 };
 
-template <int R, int TX, int TY>
+template <int R, int TX, int TY, bool FUSED>
 struct TtiGeom {
     using G = Geom<R, TX, TY, 1, R + 3>;
+    using I = Interior<R, TX>;
     static constexpr int S = R + 3;  // planes j - R .. j + 2 resident at step j
     static constexpr int PL = (G::PLANE + 31) & ~31;
-    static constexpr size_t SMEM = 128 + (size_t)S * PL * 4 + S * sizeof(uint64_t) + 16;
+    // fused q pass: a 2-deep ring of the completing output's tiles --
+    // 10 dense (Lap p, H1 p, a, b, c, d, alpha, nx, ny, nz) and 3 padded
+    // interior tiles (p^n, p^{n-1}, q^{n-1})
+    static constexpr int DT = (TX * TY + 31) & ~31;
+    static constexpr int PT = (I::BXI * TY + 31) & ~31;
+    static constexpr int CT = FUSED ? 10 * DT + 3 * PT : 0;
+    static constexpr int CRING = FUSED ? 2 : 0;
+    static constexpr size_t SMEM =
+        128 + ((size_t)S * PL + (size_t)CRING * CT) * 4 + (S + CRING) * sizeof(uint64_t) + 16;
+    static_assert(SMEM <= 227 * 1024, "TTI rings exceed shared memory");
 };
 
 // Dense interior arrays (nshots stacked where per shot): x fastest.
@@ -319,21 +329,121 @@ struct TtiDense {
     int64_t sy, sz, ss;  // strides of y, z, shot (elements)
 };
 
-template <int R, int TX, int TY>
+// What the fused q pass reads and writes besides the q planes.
+struct TtiFused {
+    CUtensorMap med;           // 8 dense fields (x, y, z, field)
+    CUtensorMap work;          // Lap p, H1 p, ... slices (x, y, z, field * nshots + shot)
+    CUtensorMap pc, pp, qp;    // padded interior tiles of p^n, p^{n-1}, q^{n-1}
+    float *pn, *qn;
+    const float *amp;
+    float *rec;
+};
+
+// The arriving plane's contributions to the z queues: centre value (f_zz),
+// D_x f (f_xz) and D_y f (f_yz), each weighted for the slot's offset.
+template <int R, int NV, int BX>
+__device__ __forceinline__ void tti_arrive(const float *pl, const TtiCoef &cf, int tx, int ty,
+                                           float (&qzz)[2 * R + 1][4], float (&qxz)[2 * R + 1][4],
+                                           float (&qyz)[2 * R + 1][4])
+{
+    constexpr int W = 2 * R + 1;
+    float win[4 * NV];
+    load_row<NV>(pl + (ty + R) * BX + 4 * tx, win);
+    float dx[4], dy[4], c0[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        c0[k] = win[k + R];
+        dx[k] = 0.f;
+#pragma unroll
+        for (int d = 1; d <= R; ++d)
+            dx[k] = fmaf(cf.w1[R + d], win[k + R + d], fmaf(cf.w1[R - d], win[k + R - d], dx[k]));
+        dy[k] = 0.f;
+    }
+#pragma unroll
+    for (int d = -R; d <= R; ++d) {
+        if (d == 0) continue;
+        float a[4];
+        load_center<R>(pl + (ty + R + d) * BX + 4 * tx, a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dy[k] = fmaf(cf.w1[R + d], a[k], dy[k]);
+    }
+#pragma unroll
+    for (int kk = 0; kk < W; ++kk)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int d = R - kk;  // offset of this plane from slot kk's output plane
+            qzz[kk][k] = fmaf(cf.w2[R + d], c0[k], qzz[kk][k]);
+            if (d != 0) {
+                qxz[kk][k] = fmaf(cf.w1[R + d], dx[k], qxz[kk][k]);
+                qyz[kk][k] = fmaf(cf.w1[R + d], dy[k], qyz[kk][k]);
+            }
+        }
+}
+
+// The in-plane terms of the output's centre plane: f_xx, f_yy and
+// f_xy = sum_b w1[b] D_x f(y + b); also returns the centre values.
+template <int R, int NV, int BX>
+__device__ __forceinline__ void tti_centre(const float *pc, const TtiCoef &cf, int tx, int ty, float (&fxx)[4],
+                                           float (&fyy)[4], float (&fxy)[4], float (&ctr)[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fxx[k] = fyy[k] = fxy[k] = 0.f;
+#pragma unroll
+    for (int b = -R; b <= R; ++b) {
+        float w[4 * NV];
+        load_row<NV>(pc + (ty + R + b) * BX + 4 * tx, w);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            fyy[k] = fmaf(cf.w2[R + b], w[k + R], fyy[k]);
+            if (b == 0) {
+                ctr[k] = w[k + R];
+#pragma unroll
+                for (int a = -R; a <= R; ++a) fxx[k] = fmaf(cf.w2[R + a], w[k + R + a], fxx[k]);
+            } else {
+                float ddx = 0.f;
+#pragma unroll
+                for (int a = 1; a <= R; ++a)
+                    ddx = fmaf(cf.w1[R + a], w[k + R + a], fmaf(cf.w1[R - a], w[k + R - a], ddx));
+                fxy[k] = fmaf(cf.w1[R + b], ddx, fxy[k]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float tti_h1(float nx, float ny, float nz, float fxx, float fyy, float fzz, float fxy,
+                                        float fxz, float fyz)
+{
+    float t = nx * nx * fxx;
+    t = fmaf(ny * ny, fyy, t);
+    t = fmaf(nz * nz, fzz, t);
+    t = fmaf(2.f * nx * ny, fxy, t);
+    t = fmaf(2.f * ny * nz, fyz, t);
+    return fmaf(2.f * nx * nz, fxz, t);
+}
+
+// The derivative pass of one field (FUSED = false: writes Lap f and H1 f),
+// or the q pass with the combine fused in (FUSED = true: reads Lap p, H1 p
+// and the medium with the completing output's tiles, writes p^{n+1} and
+// q^{n+1}).
+template <int R, int TX, int TY, bool FUSED>
 __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
     tti_deriv_kernel(const __grid_constant__ CUtensorMap tf, const __grid_constant__ TtiCoef cf,
                      const __grid_constant__ WaveGeo geo, const float *__restrict__ tilt, TtiDense dn,
-                     float *__restrict__ lap, float *__restrict__ h1, int tz, int nzc, int vec, unsigned *err)
+                     float *__restrict__ lap, float *__restrict__ h1, const __grid_constant__ TtiFused fu,
+                     int tz, int nzc, int vec, unsigned *err)
 {
-    using T = TtiGeom<R, TX, TY>;
+    using T = TtiGeom<R, TX, TY, FUSED>;
     using G = typename T::G;
+    using I = Interior<R, TX>;
     constexpr int W = G::W;
     constexpr int S = T::S;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_align128(smem_raw);
     float *planes = reinterpret_cast<float *>(smem);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * T::PL * sizeof(float));
-    int &abort_flag = *reinterpret_cast<int *>(full + S);
+    float *ctiles = planes + (size_t)S * T::PL;
+    uint64_t *full = reinterpret_cast<uint64_t *>(ctiles + (size_t)T::CRING * T::CT);
+    uint64_t *cfull = full + S;
+    int &abort_flag = *reinterpret_cast<int *>(cfull + T::CRING);
 
     const int tid = threadIdx.x;
     const int tx = tid % G::NTX, ty = tid / G::NTX;
@@ -342,23 +452,52 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
     const int nzt = min(tz, geo.nz - zb);
     const int P = nzt + 2 * R;
     const int gx = x0 + 4 * tx, y = y0 + ty;
-    const int64_t npts = (int64_t)geo.nz * dn.sz;  // one tilt component
+    const int64_t npts = (int64_t)geo.nz * dn.sz;  // one dense field
 
     auto issue = [&](int j) {
         const int s = j % S;
         ptx::mbar_arrive_expect_tx(&full[s], G::PLANE * 4);
         ptx::tma_load_4d(planes + (size_t)s * T::PL, &tf, x0, y0, zb + j, sh, &full[s]);
     };
+    // fused: the tiles of output plane zo into completion slot zo % 2
+    auto issue_c = [&](int zo) {
+        if constexpr (FUSED) {
+            const int c = zo % 2;
+            float *ct = ctiles + (size_t)c * T::CT;
+            ptx::mbar_arrive_expect_tx(&cfull[c], (10 * TX * TY + 3 * I::BXI * TY) * 4);
+            const int z = zb + zo;
+            ptx::tma_load_4d(ct + 0 * T::DT, &fu.work, x0, y0, z, sh, &cfull[c]);                // Lap p
+            ptx::tma_load_4d(ct + 1 * T::DT, &fu.work, x0, y0, z, geo.nshots + sh, &cfull[c]);   // H1 p
+#pragma unroll
+            for (int f = 0; f < 8; ++f) ptx::tma_load_4d(ct + (2 + f) * T::DT, &fu.med, x0, y0, z, f, &cfull[c]);
+            const int xs = x0 + (R & ~3), zp = z + R;
+            ptx::tma_load_4d(ct + 10 * T::DT, &fu.pc, xs, y0 + R, zp, sh, &cfull[c]);
+            ptx::tma_load_4d(ct + 10 * T::DT + T::PT, &fu.pp, xs, y0 + R, zp, sh, &cfull[c]);
+            ptx::tma_load_4d(ct + 10 * T::DT + 2 * T::PT, &fu.qp, xs, y0 + R, zp, sh, &cfull[c]);
+        }
+    };
     if (tid == 0) {
         ptx::prefetch_tmap(&tf);
 #pragma unroll
         for (int s = 0; s < S; ++s) ptx::mbar_init(&full[s], 1);
+#pragma unroll
+        for (int c = 0; c < T::CRING; ++c) ptx::mbar_init(&cfull[c], 1);
         ptx::fence_mbar_init();
         abort_flag = 0;
     }
     __syncthreads();
-    if (tid == 0)
+    if (tid == 0) {
         for (int j = 0; j < S && j < P; ++j) issue(j);
+        if constexpr (FUSED)
+            for (int zo = 0; zo < 2 && zo < nzt; ++zo) issue_c(zo);
+    }
+
+    float gxs[4] = {1.f, 1.f, 1.f, 1.f}, gys = 1.f;
+    if constexpr (FUSED) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gxs[k] = sponge(gx + k, geo.nx, geo.sponge_w, geo.sponge_a);
+        gys = sponge(y, geo.ny, geo.sponge_w, geo.sponge_a);
+    }
 
     float qzz[W][4], qxz[W][4], qyz[W][4];
 #pragma unroll
@@ -369,9 +508,9 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
     const bool inside = y < geo.ny && gx < geo.nx;
     for (int j = 0; j < P; ++j) {
         const int zo = j - 2 * R;
-        // the output's tilt, read early so that its latency overlaps the plane work
+        // unfused: the output's tilt, read early so that its latency overlaps the plane work
         float n3[3][4] = {};
-        if (zo >= 0 && inside) {
+        if (!FUSED && zo >= 0 && inside) {
             const int64_t o = (int64_t)(zb + zo) * dn.sz + (int64_t)y * dn.sy + gx;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -386,99 +525,103 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
             }
         }
         const int s = j % S;
-        const float *pl = planes + (size_t)s * T::PL;
-        float fxx[4], fyy[4], fxy[4];
+        float fxx[4], fyy[4], fxy[4], ctr[4];
+        // fused completion values: Lap p, H1 p, a, b, c, d, alpha, nx, ny, nz, p^n, p^{n-1}, q^{n-1}
+        float cv[13][4];
         bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err);
         if (ok) {
-            // arriving plane: centre value, D_x f, D_y f of the thread's points
-            float win[4 * G::NV];
-            load_row<G::NV>(pl + (ty + R) * G::BX + 4 * tx, win);
-            float dx[4], dy[4], c0[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                c0[k] = win[k + R];
-                dx[k] = 0.f;
-#pragma unroll
-                for (int d = 1; d <= R; ++d)
-                    dx[k] = fmaf(cf.w1[R + d], win[k + R + d], fmaf(cf.w1[R - d], win[k + R - d], dx[k]));
-                dy[k] = 0.f;
-            }
-#pragma unroll
-            for (int d = -R; d <= R; ++d) {
-                if (d == 0) continue;
-                float a[4];
-                load_center<R>(pl + (ty + R + d) * G::BX + 4 * tx, a);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) dy[k] = fmaf(cf.w1[R + d], a[k], dy[k]);
-            }
-#pragma unroll
-            for (int kk = 0; kk < W; ++kk)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int d = R - kk;  // offset of this plane from slot kk's output plane
-                    qzz[kk][k] = fmaf(cf.w2[R + d], c0[k], qzz[kk][k]);
-                    if (d != 0) {
-                        qxz[kk][k] = fmaf(cf.w1[R + d], dx[k], qxz[kk][k]);
-                        qyz[kk][k] = fmaf(cf.w1[R + d], dy[k], qyz[kk][k]);
-                    }
-                }
+            tti_arrive<R, G::NV, G::BX>(planes + (size_t)s * T::PL, cf, tx, ty, qzz, qxz, qyz);
             if (zo >= 0) {
-                // centre plane of the completed output: f_xx, f_yy, f_xy
-                const float *pc = planes + (size_t)((j - R) % S) * T::PL;
+                tti_centre<R, G::NV, G::BX>(planes + (size_t)((j - R) % S) * T::PL, cf, tx, ty, fxx, fyy, fxy, ctr);
+                if constexpr (FUSED) {
+                    const int c = zo % 2;
+                    ok = ptx::mbar_wait_bounded(&cfull[c], (uint32_t)(zo / 2) & 1u, err);
+                    if (ok) {
+                        const float *ct = ctiles + (size_t)c * T::CT;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) fxx[k] = fyy[k] = fxy[k] = 0.f;
-#pragma unroll
-                for (int b = -R; b <= R; ++b) {
-                    float w[4 * G::NV];
-                    load_row<G::NV>(pc + (ty + R + b) * G::BX + 4 * tx, w);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        fyy[k] = fmaf(cf.w2[R + b], w[k + R], fyy[k]);
-                        if (b == 0) {
-#pragma unroll
-                            for (int a = -R; a <= R; ++a) fxx[k] = fmaf(cf.w2[R + a], w[k + R + a], fxx[k]);
-                        } else {
-                            float ddx = 0.f;
-#pragma unroll
-                            for (int a = 1; a <= R; ++a)
-                                ddx = fmaf(cf.w1[R + a], w[k + R + a], fmaf(cf.w1[R - a], w[k + R - a], ddx));
-                            fxy[k] = fmaf(cf.w1[R + b], ddx, fxy[k]);
+                        for (int f = 0; f < 10; ++f) {
+                            const float4 t = *reinterpret_cast<const float4 *>(ct + f * T::DT + ty * TX + 4 * tx);
+                            cv[f][0] = t.x; cv[f][1] = t.y; cv[f][2] = t.z; cv[f][3] = t.w;
                         }
+#pragma unroll
+                        for (int f = 0; f < 3; ++f)
+                            load_center<I::OFF>(ct + 10 * T::DT + f * T::PT + ty * I::BXI + 4 * tx, cv[10 + f]);
                     }
                 }
             }
-        } else {
-            abort_flag = 1;
         }
+        if (!ok) abort_flag = 1;
         __syncthreads();
         if (abort_flag) return;
-        // plane j - R is no longer needed: its stage takes plane j - R + S
-        if (tid == 0 && j >= R && j - R + S < P) issue(j - R + S);
+        // plane j - R is no longer needed: its stage takes plane j - R + S;
+        // the completion slot of zo takes output zo + 2
+        if (tid == 0) {
+            if (j >= R && j - R + S < P) issue(j - R + S);
+            if constexpr (FUSED)
+                if (zo >= 0 && zo + 2 < nzt) issue_c(zo + 2);
+        }
         if (zo >= 0 && inside) {
-            float l[4], h[4];
+            if constexpr (!FUSED) {
+                float l[4], h[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float nx = n3[0][k], ny = n3[1][k], nz = n3[2][k];
-                l[k] = fxx[k] + fyy[k] + qzz[0][k];
-                float t = nx * nx * fxx[k];
-                t = fmaf(ny * ny, fyy[k], t);
-                t = fmaf(nz * nz, qzz[0][k], t);
-                t = fmaf(2.f * nx * ny, fxy[k], t);
-                t = fmaf(2.f * ny * nz, qyz[0][k], t);
-                t = fmaf(2.f * nx * nz, qxz[0][k], t);
-                h[k] = t;
-            }
-            const int64_t o = (int64_t)sh * dn.ss + (int64_t)(zb + zo) * dn.sz + (int64_t)y * dn.sy + gx;
-            if (vec) {
-                *reinterpret_cast<float4 *>(lap + o) = make_float4(l[0], l[1], l[2], l[3]);
-                *reinterpret_cast<float4 *>(h1 + o) = make_float4(h[0], h[1], h[2], h[3]);
+                for (int k = 0; k < 4; ++k) {
+                    l[k] = fxx[k] + fyy[k] + qzz[0][k];
+                    h[k] = tti_h1(n3[0][k], n3[1][k], n3[2][k], fxx[k], fyy[k], qzz[0][k], fxy[k], qxz[0][k],
+                                  qyz[0][k]);
+                }
+                const int64_t o = (int64_t)sh * dn.ss + (int64_t)(zb + zo) * dn.sz + (int64_t)y * dn.sy + gx;
+                if (vec) {
+                    *reinterpret_cast<float4 *>(lap + o) = make_float4(l[0], l[1], l[2], l[3]);
+                    *reinterpret_cast<float4 *>(h1 + o) = make_float4(h[0], h[1], h[2], h[3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (gx + k < geo.nx) {
+                            lap[o + k] = l[k];
+                            h1[o + k] = h[k];
+                        }
+                }
             } else {
+                const int z = zb + zo;
+                const float gzy = gys * sponge(z, geo.nz, geo.sponge_w, geo.sponge_a);
+                const float samp = fu.amp[sh];
+                const int sx = geo.src[sh][0], sy = geo.src[sh][1], sz = geo.src[sh][2];
+                float rp4[4], rq4[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (gx + k < geo.nx) {
-                        lap[o + k] = l[k];
-                        h1[o + k] = h[k];
-                    }
+                for (int k = 0; k < 4; ++k) {
+                    const float H1q = tti_h1(cv[7][k], cv[8][k], cv[9][k], fxx[k], fyy[k], qzz[0][k], fxy[k],
+                                             qxz[0][k], qyz[0][k]);
+                    const float H2q = fxx[k] + fyy[k] + qzz[0][k] - H1q;
+                    const float H1p = cv[1][k], H2p = cv[0][k] - H1p;
+                    const float a = cv[2][k], b = cv[3][k], c = cv[4][k], d = cv[5][k], al = cv[6][k];
+                    const float inv = al != 0.f ? 1.f / al : 0.f;  // alpha > 0 inside the grid
+                    const float rp = a * H2p + al * b * H1q + d * (H1p - al * H1q);
+                    const float rq = c * inv * H2p + b * H1q - d * (H2p * inv - H2q);
+                    const float g = gxs[k] * gzy;
+                    const float sv = (gx + k == sx && y == sy && z == sz) ? samp : 0.f;
+                    rp4[k] = g * (2.f * cv[10][k] - g * cv[11][k] + rp + sv);
+                    rq4[k] = g * (2.f * ctr[k] - g * cv[12][k] + rq + sv);
+                }
+                const int64_t mp = (int64_t)sh * geo.ss + (int64_t)(z + R) * geo.pz + (int64_t)(y + R) * geo.py +
+                                   (gx + R);
+                float *op = fu.pn + mp, *oq = fu.qn + mp;
+                if (vec && R % 4 == 0 && gx + 3 < geo.nx) {
+                    *reinterpret_cast<float4 *>(op) = make_float4(rp4[0], rp4[1], rp4[2], rp4[3]);
+                    *reinterpret_cast<float4 *>(oq) = make_float4(rq4[0], rq4[1], rq4[2], rq4[3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (gx + k < geo.nx) {
+                            op[k] = rp4[k];
+                            oq[k] = rq4[k];
+                        }
+                }
+                if (fu.rec && z == geo.rec_z) {
+                    float *rp = fu.rec + ((int64_t)sh * geo.ny + y) * geo.nx + gx;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (gx + k < geo.nx) rp[k] = rp4[k];
+                }
             }
         }
 #pragma unroll
@@ -569,26 +712,57 @@ __global__ void tti_model_kernel(int64_t n, const float *__restrict__ vp, const 
 
 constexpr int kTtiTX = 64, kTtiTY = 8, kTtiTZ = 128;
 
-template <int R>
+template <int R, bool FUSED>
 cudaError_t tti_deriv_r(const WaveGeo &g, const TtiCoef &cf, const float *f, const float *tilt, TtiDense dn,
-                        float *lap, float *h1, cudaStream_t st)
+                        float *lap, float *h1, const TtiFused &fu, cudaStream_t st)
 {
-    using T = TtiGeom<R, kTtiTX, kTtiTY>;
+    using T = TtiGeom<R, kTtiTX, kTtiTY, FUSED>;
     using G = typename T::G;
     const int X = g.nx + 2 * R, Y = g.ny + 2 * R, Z = g.nz + 2 * R;
     CUtensorMap tf;
     if (!encode_tmap_4d(&tf, f, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1))
         return cudaErrorInvalidValue;
-    auto kern = tti_deriv_kernel<R, kTtiTX, kTtiTY>;
+    auto kern = tti_deriv_kernel<R, kTtiTX, kTtiTY, FUSED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
     const int tz = kTtiTZ;
     const int nzc = (g.nz + tz - 1) / tz;
     const dim3 grid((g.nx + kTtiTX - 1) / kTtiTX, (g.ny + kTtiTY - 1) / kTtiTY, nzc * g.nshots);
-    const int vec = g.nx % 4 == 0 && reinterpret_cast<uintptr_t>(tilt) % 16 == 0 &&
-                    reinterpret_cast<uintptr_t>(lap) % 16 == 0 && reinterpret_cast<uintptr_t>(h1) % 16 == 0;
-    kern<<<grid, G::NT, T::SMEM, st>>>(tf, cf, g, tilt, dn, lap, h1, tz, nzc, vec, device_error_word());
+    int vec = g.nx % 4 == 0 && reinterpret_cast<uintptr_t>(tilt) % 16 == 0 &&
+              reinterpret_cast<uintptr_t>(lap) % 16 == 0 && reinterpret_cast<uintptr_t>(h1) % 16 == 0;
+    if (FUSED)
+        vec = g.py % 4 == 0 && g.pz % 4 == 0 && g.ss % 4 == 0 && reinterpret_cast<uintptr_t>(fu.pn) % 16 == 0 &&
+              reinterpret_cast<uintptr_t>(fu.qn) % 16 == 0;
+    kern<<<grid, G::NT, T::SMEM, st>>>(tf, cf, g, tilt, dn, lap, h1, fu, tz, nzc, vec, device_error_word());
     return cudaGetLastError();
+}
+
+template <bool FUSED>
+cudaError_t tti_deriv(const WaveGeo &g, const TtiCoef &cf, const float *f, const float *tilt, TtiDense dn,
+                      float *lap, float *h1, const TtiFused &fu, cudaStream_t st)
+{
+    switch (g.r) {
+        case 1: return tti_deriv_r<1, FUSED>(g, cf, f, tilt, dn, lap, h1, fu, st);
+        case 2: return tti_deriv_r<2, FUSED>(g, cf, f, tilt, dn, lap, h1, fu, st);
+        case 3: return tti_deriv_r<3, FUSED>(g, cf, f, tilt, dn, lap, h1, fu, st);
+        case 4: return tti_deriv_r<4, FUSED>(g, cf, f, tilt, dn, lap, h1, fu, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Tensor maps of the fused q pass (dense maps need nx % 4 == 0: 16-byte rows).
+template <int R>
+bool tti_fused_maps(const WaveGeo &g, const float *med, const float *work, const float *pc, const float *pp,
+                    const float *qp, TtiFused *fu)
+{
+    using I = Interior<R, kTtiTX>;
+    const int X = g.nx + 2 * R, Y = g.ny + 2 * R, Z = g.nz + 2 * R;
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny, n = sz * g.nz;
+    return encode_tmap_4d(&fu->med, med, g.nx, g.ny, g.nz, 8, sy, sz, n, kTtiTX, kTtiTY, 1) &&
+           encode_tmap_4d(&fu->work, work, g.nx, g.ny, g.nz, 2 * g.nshots, sy, sz, n, kTtiTX, kTtiTY, 1) &&
+           encode_tmap_4d(&fu->pc, pc, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kTtiTY, 1) &&
+           encode_tmap_4d(&fu->pp, pp, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kTtiTY, 1) &&
+           encode_tmap_4d(&fu->qp, qp, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kTtiTY, 1);
 }
 
 // Tile variants of the VTI step: (TX, TY, stages, z chunk).
@@ -692,18 +866,28 @@ cudaError_t launch_tti_step(const WaveGeo &g, const float *w2, const float *w1, 
     TtiDense dn{g.nx, (int64_t)g.nx * g.ny, n};
     float *lp = work, *hp = work + g.nshots * n, *lq = work + 2 * g.nshots * n, *hq = work + 3 * g.nshots * n;
     const float *tilt = med + 5 * n;
-    cudaError_t e = cudaSuccess;
-    for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
-        const float *fld = f ? qc : pc;
-        float *l = f ? lq : lp, *h = f ? hq : hp;
+    TtiFused fu{};
+    // p pass, then the q pass with the combine fused in (two launches); rows
+    // that TMA cannot stage (nx % 4 != 0) take a q pass and a separate combine
+    cudaError_t e = tti_deriv<false>(g, cf, pc, tilt, dn, lp, hp, fu, st);
+    if (e != cudaSuccess) return e;
+    if (g.nx % 4 == 0) {
+        bool ok = false;
         switch (g.r) {
-            case 1: e = tti_deriv_r<1>(g, cf, fld, tilt, dn, l, h, st); break;
-            case 2: e = tti_deriv_r<2>(g, cf, fld, tilt, dn, l, h, st); break;
-            case 3: e = tti_deriv_r<3>(g, cf, fld, tilt, dn, l, h, st); break;
-            case 4: e = tti_deriv_r<4>(g, cf, fld, tilt, dn, l, h, st); break;
+            case 1: ok = tti_fused_maps<1>(g, med, work, pc, pp, qp, &fu); break;
+            case 2: ok = tti_fused_maps<2>(g, med, work, pc, pp, qp, &fu); break;
+            case 3: ok = tti_fused_maps<3>(g, med, work, pc, pp, qp, &fu); break;
+            case 4: ok = tti_fused_maps<4>(g, med, work, pc, pp, qp, &fu); break;
             default: return cudaErrorInvalidValue;
         }
+        if (!ok) return cudaErrorInvalidValue;
+        fu.pn = pn;
+        fu.qn = qn;
+        fu.amp = src_amp;
+        fu.rec = rec;
+        return tti_deriv<true>(g, cf, qc, tilt, dn, nullptr, nullptr, fu, st);
     }
+    e = tti_deriv<false>(g, cf, qc, tilt, dn, lq, hq, fu, st);
     if (e != cudaSuccess) return e;
     tti_combine_kernel<<<152 * 8, 256, 0, st>>>(g, dn, med, lp, hp, lq, hq, pc, qc, pp, qp, pn, qn, src_amp, rec);
     return cudaGetLastError();

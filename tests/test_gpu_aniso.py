@@ -283,8 +283,9 @@ def test_tti_teacher_forced_step(r):
         np.testing.assert_array_equal(rec[sh].cpu().numpy(), pn[sh, r + s.a.zrec, r:-r, r:-r].cpu().numpy())
 
 
-def test_tti_in_place_equals_out_of_place():
-    s = Tti(nx=70, ny=37, nz=45, nshots=1, rec=False)
+@pytest.mark.parametrize("nx", [70, 72])   # separate combine (nx % 4 != 0) and the fused q pass
+def test_tti_in_place_equals_out_of_place(nx):
+    s = Tti(nx=nx, ny=37, nz=45, nshots=1, rec=False)
     pc, qc, pp, qp, pn, qn = s.f
     for k, f in enumerate((pc, qc, pp, qp)):
         s.fill(f, 60 + k)
@@ -297,6 +298,11 @@ def test_tti_in_place_equals_out_of_place():
     torch.cuda.synchronize()
     mms.check_device()
     assert torch.equal(pp2, pn) and torch.equal(qp2, qn)
+    ins = [_host(f) for f in (pc, qc, pp, qp)]
+    op, oq = s.oracle_step(*ins, 3, 0)
+    ep, eq = rel(_host(pn)[0], op), rel(_host(qn)[0], oq)
+    print(f"TTI nx={nx}: {ep:.2e} {eq:.2e}")
+    assert ep <= TOL and eq <= TOL
 
 
 def test_tti_trajectory_from_rest():
