@@ -306,8 +306,12 @@ struct TtiCoef {
     float w1[2 * kMaxR + 1];
 };
 
-template <int R, int TX, int TY, bool FUSED>
+// MODE 0: p or q pass, tilt by plain loads (rows TMA cannot stage);
+// MODE 1: the same with the tilt tiles by TMA; MODE 2: the q pass with the
+// combine fused in.
+template <int R, int TX, int TY, int MODE>
 struct TtiGeom {
+    static constexpr bool FUSED = MODE == 2;
     using G = Geom<R, TX, TY, 1, R + 3>;
     using I = Interior<R, TX>;
     static constexpr int S = R + 3;  // planes j - R .. j + 2 resident at step j
@@ -317,10 +321,14 @@ struct TtiGeom {
     // interior tiles (p^n, p^{n-1}, q^{n-1})
     static constexpr int DT = (TX * TY + 31) & ~31;
     static constexpr int PT = (I::BXI * TY + 31) & ~31;
-    static constexpr int CT = FUSED ? 10 * DT + 3 * PT : 0;
-    static constexpr int CRING = FUSED ? 2 : 0;
-    static constexpr size_t SMEM =
-        128 + ((size_t)S * PL + (size_t)CRING * CT) * 4 + (S + CRING) * sizeof(uint64_t) + 16;
+    static constexpr int CT = FUSED ? 10 * DT + 3 * PT : MODE == 1 ? 3 * DT : 0;
+    static constexpr int CRING = MODE >= 1 ? 2 : 0;
+    // D_y f of the last R + 1 planes, BX columns wide (the plane's column
+    // indexing, x halo included) and TY rows: f_xy = D_x (D_y f) at completion
+    static constexpr int DR = R + 1;
+    static constexpr int DYT = (G::BX * TY + 31) & ~31;
+    static constexpr size_t SMEM = 128 + ((size_t)S * PL + (size_t)CRING * CT + (size_t)DR * DYT) * 4 +
+                                   (S + CRING) * sizeof(uint64_t) + 16;
     static_assert(SMEM <= 227 * 1024, "TTI rings exceed shared memory");
 };
 
@@ -341,10 +349,10 @@ struct TtiFused {
 
 // The arriving plane's contributions to the z queues: centre value (f_zz),
 // D_x f (f_xz) and D_y f (f_yz), each weighted for the slot's offset.
-template <int R, int NV, int BX>
+template <int R, int NV, int BX, int NTX>
 __device__ __forceinline__ void tti_arrive(const float *pl, const TtiCoef &cf, int tx, int ty,
                                            float (&qzz)[2 * R + 1][4], float (&qxz)[2 * R + 1][4],
-                                           float (&qyz)[2 * R + 1][4])
+                                           float (&qyz)[2 * R + 1][4], float *dyrow)
 {
     constexpr int W = 2 * R + 1;
     float win[4 * NV];
@@ -367,6 +375,21 @@ __device__ __forceinline__ void tti_arrive(const float *pl, const TtiCoef &cf, i
 #pragma unroll
         for (int k = 0; k < 4; ++k) dy[k] = fmaf(cf.w1[R + d], a[k], dy[k]);
     }
+    // D_y f into the ring row at the plane's column indices; the edge threads
+    // add the x-halo columns (R on each side) that f_xy's window reaches
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dyrow[4 * tx + R + k] = dy[k];
+    if (tx == 0 || tx == NTX - 1) {
+        const int c0 = tx == 0 ? 0 : 4 * NTX + R;
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            float v = 0.f;
+#pragma unroll
+            for (int d = -R; d <= R; ++d)
+                if (d != 0) v = fmaf(cf.w1[R + d], pl[(ty + R + d) * BX + c0 + c], v);
+            dyrow[c0 + c] = v;
+        }
+    }
 #pragma unroll
     for (int kk = 0; kk < W; ++kk)
 #pragma unroll
@@ -383,30 +406,31 @@ __device__ __forceinline__ void tti_arrive(const float *pl, const TtiCoef &cf, i
 // The in-plane terms of the output's centre plane: f_xx, f_yy and
 // f_xy = sum_b w1[b] D_x f(y + b); also returns the centre values.
 template <int R, int NV, int BX>
-__device__ __forceinline__ void tti_centre(const float *pc, const TtiCoef &cf, int tx, int ty, float (&fxx)[4],
-                                           float (&fyy)[4], float (&fxy)[4], float (&ctr)[4])
+__device__ __forceinline__ void tti_centre(const float *pc, const float *dyrow, const TtiCoef &cf, int tx, int ty,
+                                           float (&fxx)[4], float (&fyy)[4], float (&fxy)[4], float (&ctr)[4])
 {
+    float w[4 * NV], v[4 * NV];
+    load_row<NV>(pc + (ty + R) * BX + 4 * tx, w);
+    load_row<NV>(dyrow + 4 * tx, v);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) fxx[k] = fyy[k] = fxy[k] = 0.f;
+    for (int k = 0; k < 4; ++k) {
+        ctr[k] = w[k + R];
+        fxx[k] = 0.f;
+        fxy[k] = 0.f;
+#pragma unroll
+        for (int a = -R; a <= R; ++a) fxx[k] = fmaf(cf.w2[R + a], w[k + R + a], fxx[k]);
+#pragma unroll
+        for (int a = 1; a <= R; ++a)
+            fxy[k] = fmaf(cf.w1[R + a], v[k + R + a], fmaf(cf.w1[R - a], v[k + R - a], fxy[k]));
+        fyy[k] = cf.w2[R] * w[k + R];
+    }
 #pragma unroll
     for (int b = -R; b <= R; ++b) {
-        float w[4 * NV];
-        load_row<NV>(pc + (ty + R + b) * BX + 4 * tx, w);
+        if (b == 0) continue;
+        float a[4];
+        load_center<R>(pc + (ty + R + b) * BX + 4 * tx, a);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            fyy[k] = fmaf(cf.w2[R + b], w[k + R], fyy[k]);
-            if (b == 0) {
-                ctr[k] = w[k + R];
-#pragma unroll
-                for (int a = -R; a <= R; ++a) fxx[k] = fmaf(cf.w2[R + a], w[k + R + a], fxx[k]);
-            } else {
-                float ddx = 0.f;
-#pragma unroll
-                for (int a = 1; a <= R; ++a)
-                    ddx = fmaf(cf.w1[R + a], w[k + R + a], fmaf(cf.w1[R - a], w[k + R - a], ddx));
-                fxy[k] = fmaf(cf.w1[R + b], ddx, fxy[k]);
-            }
-        }
+        for (int k = 0; k < 4; ++k) fyy[k] = fmaf(cf.w2[R + b], a[k], fyy[k]);
     }
 }
 
@@ -421,27 +445,28 @@ __device__ __forceinline__ float tti_h1(float nx, float ny, float nz, float fxx,
     return fmaf(2.f * nx * nz, fxz, t);
 }
 
-// The derivative pass of one field (FUSED = false: writes Lap f and H1 f),
-// or the q pass with the combine fused in (FUSED = true: reads Lap p, H1 p
-// and the medium with the completing output's tiles, writes p^{n+1} and
-// q^{n+1}).
-template <int R, int TX, int TY, bool FUSED>
+// The derivative pass of one field (MODE 0 and 1: writes Lap f and H1 f),
+// or the q pass with the combine fused in (MODE 2: reads Lap p, H1 p and the
+// medium with the completing output's tiles, writes p^{n+1} and q^{n+1}).
+template <int R, int TX, int TY, int MODE>
 __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
     tti_deriv_kernel(const __grid_constant__ CUtensorMap tf, const __grid_constant__ TtiCoef cf,
                      const __grid_constant__ WaveGeo geo, const float *__restrict__ tilt, TtiDense dn,
                      float *__restrict__ lap, float *__restrict__ h1, const __grid_constant__ TtiFused fu,
                      int tz, int nzc, int vec, unsigned *err)
 {
-    using T = TtiGeom<R, TX, TY, FUSED>;
+    using T = TtiGeom<R, TX, TY, MODE>;
     using G = typename T::G;
     using I = Interior<R, TX>;
     constexpr int W = G::W;
     constexpr int S = T::S;
+    constexpr bool FUSED = T::FUSED;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_align128(smem_raw);
     float *planes = reinterpret_cast<float *>(smem);
     float *ctiles = planes + (size_t)S * T::PL;
-    uint64_t *full = reinterpret_cast<uint64_t *>(ctiles + (size_t)T::CRING * T::CT);
+    float *dyring = ctiles + (size_t)T::CRING * T::CT;
+    uint64_t *full = reinterpret_cast<uint64_t *>(dyring + (size_t)T::DR * T::DYT);
     uint64_t *cfull = full + S;
     int &abort_flag = *reinterpret_cast<int *>(cfull + T::CRING);
 
@@ -461,6 +486,13 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
     };
     // fused: the tiles of output plane zo into completion slot zo % 2
     auto issue_c = [&](int zo) {
+        if constexpr (MODE == 1) {
+            const int c = zo % 2;
+            float *ct = ctiles + (size_t)c * T::CT;
+            ptx::mbar_arrive_expect_tx(&cfull[c], 3 * TX * TY * 4);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) ptx::tma_load_4d(ct + f * T::DT, &fu.med, x0, y0, zb + zo, 5 + f, &cfull[c]);
+        }
         if constexpr (FUSED) {
             const int c = zo % 2;
             float *ct = ctiles + (size_t)c * T::CT;
@@ -488,7 +520,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
     __syncthreads();
     if (tid == 0) {
         for (int j = 0; j < S && j < P; ++j) issue(j);
-        if constexpr (FUSED)
+        if constexpr (MODE >= 1)
             for (int zo = 0; zo < 2 && zo < nzt; ++zo) issue_c(zo);
     }
 
@@ -510,7 +542,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
         const int zo = j - 2 * R;
         // unfused: the output's tilt, read early so that its latency overlaps the plane work
         float n3[3][4] = {};
-        if (!FUSED && zo >= 0 && inside) {
+        if (MODE == 0 && zo >= 0 && inside) {
             const int64_t o = (int64_t)(zb + zo) * dn.sz + (int64_t)y * dn.sy + gx;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -530,9 +562,25 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
         float cv[13][4];
         bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err);
         if (ok) {
-            tti_arrive<R, G::NV, G::BX>(planes + (size_t)s * T::PL, cf, tx, ty, qzz, qxz, qyz);
+            tti_arrive<R, G::NV, G::BX, G::NTX>(planes + (size_t)s * T::PL, cf, tx, ty, qzz, qxz, qyz,
+                                                dyring + (size_t)(j % T::DR) * T::DYT + ty * G::BX);
             if (zo >= 0) {
-                tti_centre<R, G::NV, G::BX>(planes + (size_t)((j - R) % S) * T::PL, cf, tx, ty, fxx, fyy, fxy, ctr);
+                // the centre plane j - R and its D_y f, stored R steps ago
+                tti_centre<R, G::NV, G::BX>(planes + (size_t)((j - R) % S) * T::PL,
+                                            dyring + (size_t)((j - R) % T::DR) * T::DYT + ty * G::BX, cf, tx, ty,
+                                            fxx, fyy, fxy, ctr);
+                if constexpr (MODE == 1) {
+                    const int c = zo % 2;
+                    ok = ptx::mbar_wait_bounded(&cfull[c], (uint32_t)(zo / 2) & 1u, err);
+                    if (ok) {
+                        const float *ct = ctiles + (size_t)c * T::CT;
+#pragma unroll
+                        for (int f = 0; f < 3; ++f) {
+                            const float4 t = *reinterpret_cast<const float4 *>(ct + f * T::DT + ty * TX + 4 * tx);
+                            n3[f][0] = t.x; n3[f][1] = t.y; n3[f][2] = t.z; n3[f][3] = t.w;
+                        }
+                    }
+                }
                 if constexpr (FUSED) {
                     const int c = zo % 2;
                     ok = ptx::mbar_wait_bounded(&cfull[c], (uint32_t)(zo / 2) & 1u, err);
@@ -557,7 +605,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, R + 3>::NT)
         // the completion slot of zo takes output zo + 2
         if (tid == 0) {
             if (j >= R && j - R + S < P) issue(j - R + S);
-            if constexpr (FUSED)
+            if constexpr (MODE >= 1)
                 if (zo >= 0 && zo + 2 < nzt) issue_c(zo + 2);
         }
         if (zo >= 0 && inside) {
@@ -712,17 +760,17 @@ __global__ void tti_model_kernel(int64_t n, const float *__restrict__ vp, const 
 
 constexpr int kTtiTX = 64, kTtiTY = 8, kTtiTZ = 128;
 
-template <int R, bool FUSED>
+template <int R, int MODE>
 cudaError_t tti_deriv_r(const WaveGeo &g, const TtiCoef &cf, const float *f, const float *tilt, TtiDense dn,
                         float *lap, float *h1, const TtiFused &fu, cudaStream_t st)
 {
-    using T = TtiGeom<R, kTtiTX, kTtiTY, FUSED>;
+    using T = TtiGeom<R, kTtiTX, kTtiTY, MODE>;
     using G = typename T::G;
     const int X = g.nx + 2 * R, Y = g.ny + 2 * R, Z = g.nz + 2 * R;
     CUtensorMap tf;
     if (!encode_tmap_4d(&tf, f, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1))
         return cudaErrorInvalidValue;
-    auto kern = tti_deriv_kernel<R, kTtiTX, kTtiTY, FUSED>;
+    auto kern = tti_deriv_kernel<R, kTtiTX, kTtiTY, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
     const int tz = kTtiTZ;
@@ -730,22 +778,22 @@ cudaError_t tti_deriv_r(const WaveGeo &g, const TtiCoef &cf, const float *f, con
     const dim3 grid((g.nx + kTtiTX - 1) / kTtiTX, (g.ny + kTtiTY - 1) / kTtiTY, nzc * g.nshots);
     int vec = g.nx % 4 == 0 && reinterpret_cast<uintptr_t>(tilt) % 16 == 0 &&
               reinterpret_cast<uintptr_t>(lap) % 16 == 0 && reinterpret_cast<uintptr_t>(h1) % 16 == 0;
-    if (FUSED)
+    if (MODE == 2)
         vec = g.py % 4 == 0 && g.pz % 4 == 0 && g.ss % 4 == 0 && reinterpret_cast<uintptr_t>(fu.pn) % 16 == 0 &&
               reinterpret_cast<uintptr_t>(fu.qn) % 16 == 0;
     kern<<<grid, G::NT, T::SMEM, st>>>(tf, cf, g, tilt, dn, lap, h1, fu, tz, nzc, vec, device_error_word());
     return cudaGetLastError();
 }
 
-template <bool FUSED>
+template <int MODE>
 cudaError_t tti_deriv(const WaveGeo &g, const TtiCoef &cf, const float *f, const float *tilt, TtiDense dn,
                       float *lap, float *h1, const TtiFused &fu, cudaStream_t st)
 {
     switch (g.r) {
-        case 1: return tti_deriv_r<1, FUSED>(g, cf, f, tilt, dn, lap, h1, fu, st);
-        case 2: return tti_deriv_r<2, FUSED>(g, cf, f, tilt, dn, lap, h1, fu, st);
-        case 3: return tti_deriv_r<3, FUSED>(g, cf, f, tilt, dn, lap, h1, fu, st);
-        case 4: return tti_deriv_r<4, FUSED>(g, cf, f, tilt, dn, lap, h1, fu, st);
+        case 1: return tti_deriv_r<1, MODE>(g, cf, f, tilt, dn, lap, h1, fu, st);
+        case 2: return tti_deriv_r<2, MODE>(g, cf, f, tilt, dn, lap, h1, fu, st);
+        case 3: return tti_deriv_r<3, MODE>(g, cf, f, tilt, dn, lap, h1, fu, st);
+        case 4: return tti_deriv_r<4, MODE>(g, cf, f, tilt, dn, lap, h1, fu, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -867,10 +915,9 @@ cudaError_t launch_tti_step(const WaveGeo &g, const float *w2, const float *w1, 
     float *lp = work, *hp = work + g.nshots * n, *lq = work + 2 * g.nshots * n, *hq = work + 3 * g.nshots * n;
     const float *tilt = med + 5 * n;
     TtiFused fu{};
-    // p pass, then the q pass with the combine fused in (two launches); rows
-    // that TMA cannot stage (nx % 4 != 0) take a q pass and a separate combine
-    cudaError_t e = tti_deriv<false>(g, cf, pc, tilt, dn, lp, hp, fu, st);
-    if (e != cudaSuccess) return e;
+    // Rows of 16 bytes (nx % 4 == 0): the p pass with its tilt by TMA, then
+    // the q pass with the combine fused in (two launches).  Otherwise a p
+    // pass and a q pass with plain tilt loads and a separate combine.
     if (g.nx % 4 == 0) {
         bool ok = false;
         switch (g.r) {
@@ -881,13 +928,17 @@ cudaError_t launch_tti_step(const WaveGeo &g, const float *w2, const float *w1, 
             default: return cudaErrorInvalidValue;
         }
         if (!ok) return cudaErrorInvalidValue;
+        cudaError_t e = tti_deriv<1>(g, cf, pc, tilt, dn, lp, hp, fu, st);
+        if (e != cudaSuccess) return e;
         fu.pn = pn;
         fu.qn = qn;
         fu.amp = src_amp;
         fu.rec = rec;
-        return tti_deriv<true>(g, cf, qc, tilt, dn, nullptr, nullptr, fu, st);
+        return tti_deriv<2>(g, cf, qc, tilt, dn, nullptr, nullptr, fu, st);
     }
-    e = tti_deriv<false>(g, cf, qc, tilt, dn, lq, hq, fu, st);
+    cudaError_t e = tti_deriv<0>(g, cf, pc, tilt, dn, lp, hp, fu, st);
+    if (e != cudaSuccess) return e;
+    e = tti_deriv<0>(g, cf, qc, tilt, dn, lq, hq, fu, st);
     if (e != cudaSuccess) return e;
     tti_combine_kernel<<<152 * 8, 256, 0, st>>>(g, dn, med, lp, hp, lq, hq, pc, qc, pp, qp, pn, qn, src_amp, rec);
     return cudaGetLastError();
