@@ -158,7 +158,6 @@ def captured_traffic(key: str, points: int):
     """DRAM bytes of one launch from the committed ncu capture of this kernel
     (profiles/traffic.json), scaled by points; None when the kernel's sources
     changed since the capture."""
-    import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -167,9 +166,21 @@ def captured_traffic(key: str, points: int):
         return None
     for f, h in rec["sources"].items():
         path = os.path.join(ROOT, "paper_2507_11067_gb300", "csrc", f)
-        if not os.path.exists(path) or hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] != h:
+        if not os.path.exists(path) or code_hash(path) != h:
             return None
     return rec["dram_bytes_per_point"] * points
+
+
+def code_hash(path: str) -> str:
+    """Hash of a CUDA source without its comments and blank lines: the
+    kernel the counters were taken on, whatever its comments say."""
+    import hashlib
+    import re
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    code = "\n".join(l.rstrip() for l in text.splitlines() if l.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 # x outputs per tile of the tensor-core box kernel by radius; its MMA K is
@@ -993,7 +1004,7 @@ def run_f64(args):
     shape, r, n = plan[di]
     flops = 2 * fmas[shape](r) * n ** 3
     roof = {"bound": "alu", "achieved": flops / (kms[di] / 1e3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": flops / (kms[di] / 1e3) / 1e12 / fp64_peak, "traffic": None,
+            "frac": flops / (kms[di] / 1e3) / 1e12 / fp64_peak, "traffic": captured_traffic(f"f64 {shape} r={r}", n ** 3),
             "kernel": f"f64_kernel {shape} r={r} {n}^3", "ms": kms[di],
             "peak_note": f"{n_sm} SMs x 2 FP64 FMA/clock x 2 flop x {sm_max_mhz:.0f} MHz (GB300's nominal FP64 rate)",
             "flop_per_point": 2 * fmas[shape](r)}

@@ -376,8 +376,9 @@ mms_status mms_tti_model(const mms_wave_desc *desc, const float *vp, const float
  * q), receivers (p^{n+1} on rec_z) and overlap rules as for mms_vti_step.
  * work: device scratch of 4*nshots*nx*ny*nz floats, 16-byte aligned,
  * overlapping no field, owned by the caller (the call allocates nothing).
- * Three launches on `stream`: the derivative pass for p, for q, and the
- * pointwise combine.
+ * Launches on `stream`: with nx a multiple of 4, two (the derivative pass of
+ * p, then the pass of q with the coupling and the update fused in); other
+ * sizes three (the two passes and a pointwise combine).
  */
 mms_status mms_tti_step(const mms_wave_desc *desc, const float *w2, const float *w1, const float *med,
                         const float *p_cur, const float *q_cur, const float *p_prev, const float *q_prev,

@@ -1,7 +1,7 @@
 // aniso.cu -- wave steps of the coupled anisotropic systems of the paper's
 // Sec. 2.1: VTI (two stresses sigma_H, sigma_V; one fused kernel) and TTI
-// (fields p, q with the tilted operators H1, H2; a derivative pass per field
-// and a pointwise combine).
+// (fields p, q with the tilted operators H1, H2; a derivative pass for p,
+// then one for q with the coupling and the update fused in).
 //
 // VTI.  With mh = m (1+2 eps), mv = m sqrt(1+2 delta) (m = vp^2 dt^2/h^2)
 // the printed system is
@@ -289,14 +289,16 @@ __global__ void vti_model_kernel(WaveGeo geo, const float *__restrict__ vp, cons
 // first-derivative rows w1 (Sec. 4.7), and since composed first derivatives
 // commute, f_xz = D_z (D_x f) and f_yz = D_z (D_y f): every arriving plane
 // adds its D_x f, D_y f and centre value, weighted along z, to three register
-// queues (f_xz, f_yz, f_zz).  The in-plane terms f_xx, f_yy and
-// f_xy = sum_b w1[b] D_x f(y + b) come from the output's centre plane, which
-// a ring of R + 3 planes still holds when the output completes, so no
-// per-point value has to wait in registers for the tilt.  The tilt (nx, ny,
-// nz) of the output point is read directly from memory.
+// queues (f_xz, f_yz, f_zz).  The in-plane terms f_xx and f_yy come from the
+// output's centre plane, which a ring of R + 3 planes still holds when the
+// output completes, and f_xy = D_x (D_y f) from a ring of the last R + 1
+// planes' D_y f, so no per-point value has to wait in registers for the
+// tilt.  The tilt (nx, ny, nz) of the output point arrives by TMA (or by
+// plain loads where rows are not 16-byte multiples).
 //
-// The combine pass applies the printed coupling with a = vpx^2, b = vpz^2,
-// c = vpn^2, d = vsz^2 (all times dt^2/h^2) and alpha:
+// The q pass (or, for rows TMA cannot stage, a separate pointwise combine)
+// applies the printed coupling with a = vpx^2, b = vpz^2, c = vpn^2,
+// d = vsz^2 (all times dt^2/h^2) and alpha:
 //     p'' = a H2p + alpha b H1q + d (H1p - alpha H1q)
 //     q'' = c/alpha H2p + b H1q - d (H2p/alpha - H2q),     H2 = Lap - H1
 // and the damped leapfrog update, source and receivers of the acoustic step.
@@ -403,8 +405,8 @@ __device__ __forceinline__ void tti_arrive(const float *pl, const TtiCoef &cf, i
         }
 }
 
-// The in-plane terms of the output's centre plane: f_xx, f_yy and
-// f_xy = sum_b w1[b] D_x f(y + b); also returns the centre values.
+// The in-plane terms of the output's centre plane: f_xx, f_yy, and f_xy as
+// D_x of the plane's D_y f row (dyrow); also returns the centre values.
 template <int R, int NV, int BX>
 __device__ __forceinline__ void tti_centre(const float *pc, const float *dyrow, const TtiCoef &cf, int tx, int ty,
                                            float (&fxx)[4], float (&fyy)[4], float (&fxy)[4], float (&ctr)[4])
