@@ -242,6 +242,8 @@ cudaError_t launch_tiled(const Sweep &sw, const CUtensorMap &tmap, const Coef &c
         MMS_SWEEP_CASE(TAB, R, BOX, Coef, sw, tmap, cf, 9)                                      \
         MMS_SWEEP_CASE(TAB, R, BOX, Coef, sw, tmap, cf, 10)                                     \
         MMS_SWEEP_CASE(TAB, R, BOX, Coef, sw, tmap, cf, 11)                                     \
+        MMS_SWEEP_CASE(TAB, R, BOX, Coef, sw, tmap, cf, 12)                                     \
+        MMS_SWEEP_CASE(TAB, R, BOX, Coef, sw, tmap, cf, 13)                                     \
         default: return cudaErrorInvalidValue;                                                  \
     }
 #define MMS_SWEEP_CASE(TAB, R, BOX, Coef, sw, tmap, cf, I)                                      \

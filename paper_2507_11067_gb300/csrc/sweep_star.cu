@@ -16,6 +16,8 @@ constexpr Variant kStarVariants[] = {
     {64, 16, 2, 3, 128, false, true}, {64, 16, 2, 4, 128, true},        {64, 32, 2, 4, 128, false, true},
     {128, 32, 2, 3, 64, true},        {64, 16, 2, 4, 128, true, true},  {128, 32, 2, 3, 64, true, true},
     {64, 32, 4, 3, 128, false, true}, {64, 16, 2, 4, 128, false, true}, {128, 16, 2, 4, 128, false, true},
+    // 256-plane z chunks: half the z-halo re-reads of the 128-plane ones
+    {64, 16, 2, 4, 256, false, true}, {64, 16, 2, 3, 256, false, true},
 };
 constexpr int kNumStar = sizeof(kStarVariants) / sizeof(Variant);
 
