@@ -169,6 +169,34 @@ def test_teacher_forced_adjoint_step():
     assert rel(grad.cpu().numpy(), gref) <= TOL
 
 
+def test_grad256_adjoint_step_full_size():
+    # the gradient workload's size and launch (2 shots x 256^3, 20-cell
+    # sponge, receivers on the first non-sponge plane): one teacher-forced
+    # adjoint step with its FP64 gradient term, every point against the oracle
+    s = Setup(nx=256, ny=256, nz=256, nshots=2, nsteps=4, sponge=20, seed=3)
+    lam1, lam2, a_n = s.fields[0], s.fields[1], s.fields[2]
+    for f, sd in ((lam1, 31), (lam2, 32), (a_n, 33)):
+        s.fill(f, sd)
+    l1, l2, an = s.host(lam1), s.host(lam2), s.host(a_n)
+    g = np.random.default_rng(34)
+    resid = torch.from_numpy(g.normal(size=(s.ns, s.ny, s.nx)).astype(np.float32)).cuda()
+    grad = torch.zeros((s.nz, s.ny, s.nx), device="cuda", dtype=torch.float64)
+    mms.wave_adjoint(s.desc, s.cf, s.m, lam1, lam2, resid, a_n, grad)
+    torch.cuda.synchronize()
+    mms.check_device()
+    got = lam2.cpu().numpy()
+    gref = np.zeros((s.nz, s.ny, s.nx))
+    rh = resid.cpu().numpy().astype(np.float64)
+    for sh in range(s.ns):
+        ref = s.prob.adjoint_step(l1[sh], l2[sh], rh[sh], an[sh], gref)
+        e = rel(got[sh], ref)
+        print(f"adjoint step 256^3 shot {sh}: {e:.2e}")
+        assert e <= TOL
+    e = rel(grad.cpu().numpy(), gref)
+    print(f"gradient term 256^3: {e:.2e}")
+    assert e <= TOL
+
+
 def test_out_of_place_step_matches_in_place_step():
     s = Setup(nshots=2)
     cur, prev, work, nxt = s.fields
