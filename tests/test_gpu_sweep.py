@@ -191,4 +191,12 @@ def test_star_1024_sampled_all_radii(tuned):
         mms.check_device()
         got = out[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()
         assert rel(got, ref) <= TOL, r
+        # the per-axis banded tensor-core passes with the 3xTF32 split, same grid
+        out = mms.apply("star", r, c, inp, out, path="3xtf32")
+        torch.cuda.synchronize()
+        mms.check_device()
+        got = out[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()
+        e = rel(got, ref)
+        print(f"star r={r} 1024^3 3xTF32 two-pass: {e:.2e}")
+        assert e <= TOL, ("3xtf32", r)
         del out, inp
