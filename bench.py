@@ -365,7 +365,7 @@ def run_reference(args):
         def sample(planes, salt=0):
             return oracle_sample(planes, salt, plan)
         unit = "GPoints/s"
-        what = ", ".join(f"{sh} r={r} {nn}^3" for sh, r, nn in plan)
+        what = ", ".join(f"{sh} r={r} {nn}^{2 if sh in PLANAR else 3}" for sh, r, nn in plan)
     planes = calibrate_planes(budget, sample)
     for _ in range(args.warmup):
         sample(max(2, planes // 8))
