@@ -747,11 +747,12 @@ def run_wave(args):
         e2e = {"value": job_rate(world, pts * nsteps, e2e_s), "unit": "GPoint-steps/s (forward + gradient)",
                "h2d_bytes_per_step": v0_host.numel() * 4 + amps_host.numel() * 4 + obs_host.numel() * 4,
                "d2h_bytes_per_step": g_host.numel() * g_host.element_size()}
-        # per shot-point and step: forward 16 B, recompute 16 B (out of place,
-        # no copies), adjoint 20 B (lam^{n+1}, lam^{n+2}, m, a^n read, lam^n
-        # written), and the FP64 gradient's read-modify-write, 16 B per point
-        # shared by the shots (their atomic adds meet in L2)
-        bpp = 52.0 + 16.0 / nshots
+        # per shot-point and step: forward 16 B, recompute 20 B (out of place,
+        # no copies; it also writes L a^n), adjoint 20 B (lam^{n+1}, lam^{n+2},
+        # m, L a^n read, lam^n written), and the FP64 gradient's
+        # read-modify-write, 16 B per point shared by the shots (their atomic
+        # adds meet in L2)
+        bpp = 56.0 + 16.0 / nshots
         bytes_alg = bpp * pts * nsteps * steps
         roof = {"bound": "hbm", "achieved": bytes_alg / elapsed / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": bytes_alg / elapsed / 1e9 / hbm_peak, "traffic": None,

@@ -297,6 +297,29 @@ mms_status mms_wave_adjoint(const mms_wave_desc *desc, const float *coeffs, cons
                             const float *lam_cur, float *lam_prev, const float *resid,
                             const float *a_n, double *grad_m, void *stream);
 
+/*
+ * mms_wave_step_to that also writes L a^n -- the star of `coeffs` applied
+ * to p_cur, the term the step itself computes -- into lap_out at every
+ * interior point (same geometry as the fields; its halo is left as it is).
+ * The gradient's recompute passes it to mms_wave_adjoint_lap, which then
+ * needs neither a^n's planes nor a second stencil.  lap_out: device, 16-byte
+ * aligned, overlapping none of the fields (MMS_E_ARG otherwise).
+ * Plumbing of the gradient path (the paper is silent on the adjoint).
+ */
+mms_status mms_wave_step_lap(const mms_wave_desc *desc, const float *coeffs, const float *m,
+                             const float *p_cur, const float *p_prev, float *p_next, float *lap_out,
+                             const float *src_amp, float *rec, void *stream);
+
+/*
+ * mms_wave_adjoint with the gradient term read from lap_a = L a^n (as
+ * written by mms_wave_step_lap; interior points read) instead of being
+ * computed from a^n: same lam^n, same gradient up to the summation order of
+ * L a^n.  lap_a NULL = no gradient term.
+ */
+mms_status mms_wave_adjoint_lap(const mms_wave_desc *desc, const float *coeffs, const float *m,
+                                const float *lam_cur, float *lam_prev, const float *resid,
+                                const float *lap_a, double *grad_m, void *stream);
+
 /* m = v^2 dt^2 / h^2 into a padded field (halo set to 0); v dense nz*ny*nx. */
 mms_status mms_model_from_velocity(const mms_wave_desc *desc, const float *v, float *m,
                                    float dt, float h, void *stream);

@@ -46,7 +46,8 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_model_from_velocity", "mms_grad_to_velocity", "mms_dot_f64", "mms_last_error",
            "mms_check_device", "mms_version", "mms_stencil_apply_noalloc", "mms_wave_step_to",
            "mms_sum_f64", "mms_selftest_timeout", "mms_stencil_apply_host", "mms_vti_model", "mms_vti_step",
-           "mms_aniso_num_variants", "mms_aniso_set_variant", "mms_tti_model", "mms_tti_step", "mms_stencil_apply_f64"]
+           "mms_aniso_num_variants", "mms_aniso_set_variant", "mms_tti_model", "mms_tti_step", "mms_stencil_apply_f64", "mms_wave_step_lap",
+           "mms_wave_adjoint_lap"]
 
 
 class MMSError(RuntimeError):
@@ -112,6 +113,8 @@ def load():
             "mms_wave_forward": [ctypes.POINTER(WaveDesc), P, P, P, i32, P, P, P, P, i32,
                                  ctypes.c_uint32, P],
             "mms_wave_adjoint": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
+            "mms_wave_adjoint_lap": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
+            "mms_wave_step_lap": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P, P],
             "mms_model_from_velocity": [ctypes.POINTER(WaveDesc), P, P, ctypes.c_float,
                                         ctypes.c_float, P],
             "mms_grad_to_velocity": [P, P, P, i64, ctypes.c_float, ctypes.c_float, P],
@@ -384,6 +387,22 @@ def wave_adjoint(desc, coeffs, m, lam_cur, lam_prev, resid=None, a_n=None, grad_
     check(load().mms_wave_adjoint(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                   _ptr(lam_cur), _ptr(lam_prev), _ptr(resid), _ptr(a_n),
                                   _ptr(grad_m), _stream(stream)))
+
+
+def wave_step_lap(desc, coeffs, m, p_cur, p_prev, p_next, lap_out, src_amp, rec=None, stream=None):
+    """mms_wave_step_lap: a^{n+1} into p_next and L a^n into lap_out."""
+    c = _host_coeffs(coeffs)
+    check(load().mms_wave_step_lap(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m), _ptr(p_cur),
+                                   _ptr(p_prev), _ptr(p_next), _ptr(lap_out), _ptr(src_amp), _ptr(rec),
+                                   _stream(stream)))
+
+
+def wave_adjoint_lap(desc, coeffs, m, lam_cur, lam_prev, resid=None, lap_a=None, grad_m=None, stream=None):
+    """mms_wave_adjoint_lap: the adjoint step with the gradient term from L a^n."""
+    c = _host_coeffs(coeffs)
+    check(load().mms_wave_adjoint_lap(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
+                                      _ptr(lam_cur), _ptr(lam_prev), _ptr(resid), _ptr(lap_a), _ptr(grad_m),
+                                      _stream(stream)))
 
 
 def model_from_velocity(desc, v, m, dt, h, stream=None):

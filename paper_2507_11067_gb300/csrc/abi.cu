@@ -652,8 +652,9 @@ mms_status mms_wave_forward(const mms_wave_desc *desc, const float *coeffs, cons
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "graph launch");
 }
 
-mms_status mms_wave_adjoint(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *lam_cur,
-                            float *lam_prev, const float *resid, const float *a_n, double *grad_m, void *stream)
+static mms_status wave_adjoint(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *lam_cur,
+                               float *lam_prev, const float *resid, const float *a_n, double *grad_m, void *stream,
+                               bool lapin)
 {
     WaveGeo g;
     mms_status st = wave_geo(desc, coeffs, &g);
@@ -666,8 +667,43 @@ mms_status mms_wave_adjoint(const mms_wave_desc *desc, const float *coeffs, cons
     if (overlaps(lam_cur, field_bytes(g), lam_prev, field_bytes(g))) return fail(MMS_E_ARG, "lam_cur and lam_prev overlap");
     if (a_n && overlaps(a_n, field_bytes(g), lam_prev, field_bytes(g))) return fail(MMS_E_ARG, "a_n and lam_prev overlap");
     cudaError_t e = launch_wave_adj(g, coeffs, m, lam_cur, lam_prev, resid, a_n, grad_m,
-                                    reinterpret_cast<cudaStream_t>(stream));
+                                    reinterpret_cast<cudaStream_t>(stream), lapin);
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "adjoint step launch");
+}
+
+mms_status mms_wave_adjoint(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *lam_cur,
+                            float *lam_prev, const float *resid, const float *a_n, double *grad_m, void *stream)
+{
+    return wave_adjoint(desc, coeffs, m, lam_cur, lam_prev, resid, a_n, grad_m, stream, false);
+}
+
+mms_status mms_wave_adjoint_lap(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *lam_cur,
+                                float *lam_prev, const float *resid, const float *lap_a, double *grad_m, void *stream)
+{
+    return wave_adjoint(desc, coeffs, m, lam_cur, lam_prev, resid, lap_a, grad_m, stream, true);
+}
+
+mms_status mms_wave_step_lap(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *p_cur,
+                             const float *p_prev, float *p_next, float *lap_out, const float *src_amp, float *rec,
+                             void *stream)
+{
+    WaveGeo g;
+    mms_status st = wave_geo(desc, coeffs, &g);
+    if (st != MMS_OK) return st;
+    if (!m || !p_cur || !p_prev || !p_next || !lap_out || !src_amp) return fail(MMS_E_ARG, "null field pointer");
+    if (!al16(m) || !al16(p_cur) || !al16(p_prev) || !al16(p_next) || !al16(lap_out))
+        return fail(MMS_E_ALIGN, "wave fields must be 16-byte aligned");
+    const size_t fb = field_bytes(g);
+    if (overlaps(p_cur, fb, p_prev, fb)) return fail(MMS_E_ARG, "p_cur and p_prev overlap");
+    if (overlaps(p_cur, fb, p_next, fb)) return fail(MMS_E_ARG, "p_cur and p_next overlap");
+    if (p_next != p_prev && overlaps(p_prev, fb, p_next, fb))
+        return fail(MMS_E_ARG, "p_prev and p_next overlap without being the same field");
+    const void *others[3] = {p_cur, p_prev, p_next};
+    for (const void *q : others)
+        if (overlaps(lap_out, fb, q, fb)) return fail(MMS_E_ARG, "lap_out overlaps a field");
+    cudaError_t e = launch_wave_fwd(g, coeffs, m, p_cur, p_prev, p_next, src_amp, rec,
+                                    reinterpret_cast<cudaStream_t>(stream), lap_out);
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "wave step launch");
 }
 
 mms_status mms_vti_model(const mms_wave_desc *desc, const float *vp, const float *eps, const float *delta,

@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                     const __grid_constant__ CUtensorMap tprev, const __grid_constant__ CUtensorMap tctr,
                     const __grid_constant__ StarCoef cf,
                     const __grid_constant__ WaveGeo geo, float *__restrict__ pnext,
-                    const float *__restrict__ amp, float *__restrict__ rec, int tz, int nzc, int vec,
-                    unsigned *err)
+                    const float *__restrict__ amp, float *__restrict__ rec, float *__restrict__ lapout,
+                    int tz, int nzc, int vec, unsigned *err)
 {
     using G = Geom<R, TX, TY, PY, S>;
     using F = FwdGeom<R, TX, TY, PY, S>;
@@ -203,6 +203,16 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                     for (int k = 0; k < 4; ++k)
                         if (gx + k < geo.nx) pp[k] = res[k];
                 }
+                if (lapout) {  // L a^n itself, for the gradient's adjoint steps
+                    float *lo = lapout + shot_off + mp;
+                    if (vec && gx + 3 < geo.nx) {
+                        *reinterpret_cast<float4 *>(lo) = make_float4(acc[0][i][0], acc[0][i][1], acc[0][i][2], acc[0][i][3]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (gx + k < geo.nx) lo[k] = acc[0][i][k];
+                    }
+                }
                 if (rec && z == geo.rec_z) {
                     float *rp = rec + ((int64_t)sh * geo.ny + y) * geo.nx + gx;
 #pragma unroll
@@ -243,7 +253,10 @@ struct AdjGeom {
     static constexpr size_t SMEM = 128 + OFF_BAR * 4 + S * 8 + 16;
 };
 
-template <int R, int TX, int TY, int S>
+// LAPIN: the gradient term reads L a^n as a completed tile (written by the
+// forward step that produced a^{n+1}) instead of staging a^n and applying
+// the stencil here; the a^n plane's ring slot then holds that tile.
+template <int R, int TX, int TY, int S, bool LAPIN>
 __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
     wave_adj_kernel(const __grid_constant__ CUtensorMap tlam, const __grid_constant__ CUtensorMap tm,
                     const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tl2,
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
     const int P = nzt + 2 * R;
     const int ry0 = ty * PY;
     const int gx = x0 + 4 * tx;
-    const uint32_t plane_bytes = (has_a ? 3u : 2u) * G::PLANE * sizeof(float);
+    const uint32_t plane_bytes = (has_a && !LAPIN ? 3u : 2u) * G::PLANE * sizeof(float);
 
     for (int c = tid; c < G::BX; c += G::NT) gxt[c] = sponge(x0 + c - R, geo.nx, geo.sponge_w, geo.sponge_a);
     for (int rr = tid; rr < G::BY; rr += G::NT) gyt[rr] = sponge(y0 + rr - R, geo.ny, geo.sponge_w, geo.sponge_a);
@@ -282,7 +295,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
         ptx::prefetch_tmap(&tm);
         ptx::prefetch_tmap(&tl2);
         ptx::prefetch_tmap(&tl1);
-        if (has_a) ptx::prefetch_tmap(&ta);
+        if (has_a) ptx::prefetch_tmap(&ta);  // a^n planes, or L a^n tiles
 #pragma unroll
         for (int s = 0; s < S; ++s) ptx::mbar_init(&full[s], 1);
         ptx::fence_mbar_init();
@@ -292,15 +305,17 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
     auto issue = [&](int j, int s) {
         float *st = base + (size_t)s * A::STAGE;
         const bool inner = j >= 2 * R;
-        ptx::mbar_arrive_expect_tx(&full[s], plane_bytes + (inner ? 2u * I::BXI * TY * 4u : 0u));
+        const uint32_t tiles = inner ? (LAPIN && has_a ? 3u : 2u) : 0u;
+        ptx::mbar_arrive_expect_tx(&full[s], plane_bytes + tiles * I::BXI * TY * 4u);
         ptx::tma_load_4d(st, &tlam, x0, y0, zb + j, sh, &full[s]);
         ptx::tma_load_3d(st + A::PL, &tm, x0, y0, zb + j, &full[s]);
-        if (has_a) ptx::tma_load_4d(st + 2 * A::PL, &ta, x0, y0, zb + j, sh, &full[s]);
+        if (has_a && !LAPIN) ptx::tma_load_4d(st + 2 * A::PL, &ta, x0, y0, zb + j, sh, &full[s]);
         if (inner) {
             const int zp = zb + j - R;
             const int xs = x0 + (R & ~3);
             ptx::tma_load_4d(st + A::OFF_L2, &tl2, xs, y0 + R, zp, sh, &full[s]);
             ptx::tma_load_4d(st + A::OFF_L1, &tl1, xs, y0 + R, zp, sh, &full[s]);
+            if (LAPIN && has_a) ptx::tma_load_4d(st + 2 * A::PL, &ta, xs, y0 + R, zp, sh, &full[s]);
         }
     };
     if (tid == 0)
@@ -351,14 +366,15 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
         }
         __syncthreads();
         if (abort_flag) return false;
-        float l2v[4], l1v[4];
+        float l2v[4], l1v[4], lav[4];
         {
             float unused[PY][4];
             star_plane<R, PY, G::BX, G::NV, Q>(qbuf, cf, accq, unused, tx, ry0);
-            if (has_a) star_plane<R, PY, G::BX, G::NV, Q>(st + 2 * A::PL, cf, acca, unused, tx, ry0);
+            if (!LAPIN && has_a) star_plane<R, PY, G::BX, G::NV, Q>(st + 2 * A::PL, cf, acca, unused, tx, ry0);
             if (zo >= 0) {
                 load_center<I::OFF>(st + A::OFF_L2 + ry0 * I::BXI + 4 * tx, l2v);
                 load_center<I::OFF>(st + A::OFF_L1 + ry0 * I::BXI + 4 * tx, l1v);
+                if (LAPIN && has_a) load_center<I::OFF>(st + 2 * A::PL + ry0 * I::BXI + 4 * tx, lav);
             }
         }
         __syncthreads();
@@ -381,7 +397,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, 1, S>::NT, 2)
                     if (at_rec) v += resid[((int64_t)sh * geo.ny + y) * geo.nx + gx + k];
                     lp[k] = v;
                     // the step's term in FP32 (its operands are FP32), accumulated in FP64
-                    if (has_a) gd[k] = widen(g * l1v[k] * acca[Q][0][k]);
+                    if (has_a) gd[k] = widen(g * l1v[k] * (LAPIN ? lav[k] : acca[Q][0][k]));
                 }
                 if (has_a) {
                     if (geo.gss == 0) {
@@ -481,7 +497,8 @@ constexpr int kAdjTX = 64, kAdjTY = 16, kAdjS = 2, kAdjTZ = 128;
 
 template <int R>
 cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const float *p_cur,
-                  const float *p_prev, float *p_next, const float *amp, float *rec, cudaStream_t st)
+                  const float *p_prev, float *p_next, const float *amp, float *rec, float *lapout,
+                  cudaStream_t st)
 {
     using G = Geom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
     using F = FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
@@ -500,13 +517,13 @@ cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
     const int nzc = (g.nz + tz - 1) / tz;
     const dim3 grid((g.nx + kFwdTX - 1) / kFwdTX, (g.ny + kFwdTY - 1) / kFwdTY, nzc * g.nshots);
     const int vec = (R % 4 == 0) && g.py % 4 == 0 && g.pz % 4 == 0 && g.ss % 4 == 0 &&
-                    reinterpret_cast<uintptr_t>(p_next) % 16 == 0;
-    kern<<<grid, G::NT, F::SMEM, st>>>(mcur, mm, mprev, mctr, cf, g, p_next, amp, rec, tz, nzc, vec,
+                    reinterpret_cast<uintptr_t>(p_next) % 16 == 0 && reinterpret_cast<uintptr_t>(lapout) % 16 == 0;
+    kern<<<grid, G::NT, F::SMEM, st>>>(mcur, mm, mprev, mctr, cf, g, p_next, amp, rec, lapout, tz, nzc, vec,
                                        device_error_word());
     return cudaGetLastError();
 }
 
-template <int R>
+template <int R, bool LAPIN>
 cudaError_t adj_r(const WaveGeo &g, const StarCoef &cf, const float *m, const float *lam_cur,
                   float *lam_prev, const float *resid, const float *a_n, double *grad, cudaStream_t st)
 {
@@ -521,12 +538,14 @@ cudaError_t adj_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
         !encode_tmap_4d(&m1, lam_cur, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kAdjTY, 1))
         return cudaErrorInvalidValue;
     if (a_n) {
-        if (!encode_tmap_4d(&ma, a_n, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1))
+        // a^n planes with halo, or (LAPIN) interior tiles of L a^n
+        if (!encode_tmap_4d(&ma, a_n, X, Y, Z, g.nshots, g.py, g.pz, g.ss, LAPIN ? I::BXI : G::BX,
+                            LAPIN ? kAdjTY : G::BY, 1))
             return cudaErrorInvalidValue;
     } else {
         ma = ml;
     }
-    auto kern = wave_adj_kernel<R, kAdjTX, kAdjTY, kAdjS>;
+    auto kern = wave_adj_kernel<R, kAdjTX, kAdjTY, kAdjS, LAPIN>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A::SMEM);
     if (e != cudaSuccess) return e;
     const int tz = kAdjTZ;
@@ -543,32 +562,36 @@ cudaError_t adj_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
 
 cudaError_t launch_wave_fwd(const WaveGeo &g, const float *coeffs, const float *m, const float *p_cur,
                             const float *p_prev, float *p_next, const float *src_amp, float *rec,
-                            cudaStream_t st)
+                            cudaStream_t st, float *lapout)
 {
     StarCoef cf{};
     for (int i = 0; i < 3 * (2 * g.r + 1); ++i) cf.c[i] = coeffs[i];
     switch (g.r) {
-        case 1: return fwd_r<1>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, st);
-        case 2: return fwd_r<2>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, st);
-        case 3: return fwd_r<3>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, st);
-        case 4: return fwd_r<4>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, st);
+        case 1: return fwd_r<1>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, lapout, st);
+        case 2: return fwd_r<2>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, lapout, st);
+        case 3: return fwd_r<3>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, lapout, st);
+        case 4: return fwd_r<4>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, lapout, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_wave_adj(const WaveGeo &g, const float *coeffs, const float *m, const float *lam_cur,
                             float *lam_prev, const float *resid, const float *a_n, double *grad,
-                            cudaStream_t st)
+                            cudaStream_t st, bool lapin)
 {
     StarCoef cf{};
     for (int i = 0; i < 3 * (2 * g.r + 1); ++i) cf.c[i] = coeffs[i];
+#define MMS_ADJ(R_)                                                                              \
+    return lapin ? adj_r<R_, true>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st)            \
+                 : adj_r<R_, false>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st);
     switch (g.r) {
-        case 1: return adj_r<1>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st);
-        case 2: return adj_r<2>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st);
-        case 3: return adj_r<3>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st);
-        case 4: return adj_r<4>(g, cf, m, lam_cur, lam_prev, resid, a_n, grad, st);
+        case 1: MMS_ADJ(1)
+        case 2: MMS_ADJ(2)
+        case 3: MMS_ADJ(3)
+        case 4: MMS_ADJ(4)
         default: return cudaErrorInvalidValue;
     }
+#undef MMS_ADJ
 }
 
 cudaError_t launch_model_from_velocity(const WaveGeo &g, const float *v, float *m, float dt, float h,

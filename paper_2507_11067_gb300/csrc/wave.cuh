@@ -18,13 +18,15 @@ struct WaveGeo {
     int src[kMaxShots][3];
 };
 
-// a^{n+1} goes to p_next (== p_prev for the in-place step).
+// a^{n+1} goes to p_next (== p_prev for the in-place step); with lapout,
+// L a^n of every interior point goes there too (same geometry).
 cudaError_t launch_wave_fwd(const WaveGeo &g, const float *coeffs, const float *m, const float *p_cur,
                             const float *p_prev, float *p_next, const float *src_amp, float *rec,
-                            cudaStream_t st);
+                            cudaStream_t st, float *lapout = nullptr);
+// lapin: a_n holds L a^n (interior read) instead of a^n.
 cudaError_t launch_wave_adj(const WaveGeo &g, const float *coeffs, const float *m, const float *lam_cur,
                             float *lam_prev, const float *resid, const float *a_n, double *grad,
-                            cudaStream_t st);
+                            cudaStream_t st, bool lapin = false);
 cudaError_t launch_model_from_velocity(const WaveGeo &g, const float *v, float *m, float dt, float h,
                                        cudaStream_t st);
 cudaError_t launch_grad_to_velocity(const double *gm, const float *v, double *gv, int64_t n, float dt,

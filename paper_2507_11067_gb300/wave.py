@@ -97,8 +97,9 @@ class WavePropagator:
         (nsteps, nshots, ny, nx), from the forward checkpoints; the velocity
         (model m) must be the one the checkpoints were made with.
 
-        Each segment's states are recomputed out of place from the
-        checkpoint images themselves (no copies).  The shots add their terms
+        Each segment is recomputed out of place from the checkpoint images
+        themselves (no copies), keeping L a^n of every step for the adjoint
+        steps (mms_wave_step_lap / mms_wave_adjoint_lap).  The shots add their terms
         to one FP64 gradient with atomics, whose order varies from run to
         run; ``deterministic`` gives every shot its own FP64 slice (plain
         read-modify-write, summed once at the end) for bit-reproducible
@@ -116,24 +117,32 @@ class WavePropagator:
             desc_g, self._src_keep_g = _lib.wave_desc(self.nx, self.ny, self.nz, self.r, self.nshots, py,
                                                       pz, ss, self.desc.sponge_width, self.desc.sponge_a,
                                                       self.rec_z, self.src, grad_shot_stride=npts)
-        # seg[i] = a^{k0+i}; seg[0] and a^{k0-1} are the checkpoint images
-        # themselves, the others are written by the steps (zero halos kept)
-        seg = [None] + [self.new_fields() for _ in range(ckpt_every)]
+        # The recompute of a segment steps a^{k0} .. a^{k1-1} forward from the
+        # checkpoint images (never overwritten) through two scratch fields and
+        # keeps what the adjoint needs: lap[i] = L a^{k0+i}, which each step
+        # computes anyway.  The adjoint step that forms lam^n adds
+        # g lam^{n+1} (L a^n); for n = k1 that is the next segment's lap[0],
+        # carried over (for the last segment lam^{Nt+1} = 0: no term).
+        scratch = [self.new_fields(zero=True), self.new_fields(zero=True)]
+        lap = [self.new_fields() for _ in range(ckpt_every)]
+        carry, have_carry = self.new_fields(), False
         lam = [self.new_fields(), self.new_fields()]   # lam^{n+2}, lam^{n+1}
         nseg = self.n_checkpoints(nsteps, ckpt_every)
         for j in range(nseg - 1, -1, -1):
             k0 = j * ckpt_every
             k1 = min(k0 + ckpt_every, nsteps)
-            seg[0] = self._view(ckpt[j, 0])
-            old_f, cur_f = self._view(ckpt[j, 1]), seg[0]
+            old_f, cur_f = self._view(ckpt[j, 1]), self._view(ckpt[j, 0])
             for n in range(k0, k1):
-                nxt = seg[n - k0 + 1]
-                _lib.wave_step_to(self.desc, self.coeffs, self.m, cur_f, old_f, nxt, amps[n])
+                # out of place; from the third step on, over a^{n-1}
+                nxt = scratch[(n - k0) % 2]
+                _lib.wave_step_lap(self.desc, self.coeffs, self.m, cur_f, old_f, nxt, lap[n - k0], amps[n])
                 old_f, cur_f = cur_f, nxt
             for n in range(k1, k0, -1):                   # lam^n, n = k1 .. k0+1
-                _lib.wave_adjoint(desc_g, self.coeffs, self.m, lam[1], lam[0], resid[n - 1],
-                                  seg[n - k0], grad)
+                la = lap[n - k0] if n < k1 else (carry if have_carry else None)
+                _lib.wave_adjoint_lap(desc_g, self.coeffs, self.m, lam[1], lam[0], resid[n - 1], la, grad)
                 lam[0], lam[1] = lam[1], lam[0]
+            lap[0], carry = carry, lap[0]
+            have_carry = True
         if per_shot:
             _lib.sum_f64(grad, grad[0])
             return grad[0]

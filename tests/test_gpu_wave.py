@@ -197,6 +197,50 @@ def test_grad256_adjoint_step_full_size():
     assert e <= TOL
 
 
+def test_step_lap_and_adjoint_lap():
+    # mms_wave_step_lap: the same a^{n+1} as mms_wave_step_to, plus L a^n;
+    # mms_wave_adjoint_lap fed that L a^n: the same lam^n as mms_wave_adjoint
+    # fed a^n, and the same gradient up to the summation order of L a^n
+    s = Setup(nshots=2)
+    cur, prev, nxt, lap = s.fields
+    s.fill(cur, 41)
+    s.fill(prev, 42)
+    ref_next = mms.padded_empty(s.nx, s.ny, s.nz, R, nshots=2)
+    mms.wave_step_to(s.desc, s.cf, s.m, cur, prev, ref_next, s.amps[2])
+    mms.wave_step_lap(s.desc, s.cf, s.m, cur, prev, nxt, lap, s.amps[2])
+    torch.cuda.synchronize()
+    mms.check_device()
+    assert torch.equal(nxt, ref_next)
+    c = s.host(cur)
+    for sh in range(2):
+        ref = oracle.stencil("star", R, s.cf, c[sh])
+        assert rel(lap[sh, R:-R, R:-R, R:-R].cpu().numpy(), ref) <= TOL
+    lam1 = mms.padded_empty(s.nx, s.ny, s.nz, R, nshots=2)
+    s.fill(lam1, 43)
+    g = np.random.default_rng(44)
+    resid = torch.from_numpy(g.normal(size=(2, s.ny, s.nx)).astype(np.float32)).cuda()
+    out = []
+    for fn, a in ((mms.wave_adjoint, cur), (mms.wave_adjoint_lap, lap)):
+        lam2 = mms.padded_empty(s.nx, s.ny, s.nz, R, nshots=2)
+        s.fill(lam2, 45)
+        grad = torch.zeros((s.nz, s.ny, s.nx), device="cuda", dtype=torch.float64)
+        fn(s.desc, s.cf, s.m, lam1, lam2, resid, a, grad)
+        torch.cuda.synchronize()
+        mms.check_device()
+        out.append((lam2.clone(), grad.cpu().numpy()))
+    assert torch.equal(out[0][0], out[1][0])
+    assert rel(out[1][1], out[0][1]) <= 1e-6
+    # no gradient term without L a^n
+    lam2 = mms.padded_empty(s.nx, s.ny, s.nz, R, nshots=2)
+    s.fill(lam2, 45)
+    grad = torch.zeros((s.nz, s.ny, s.nx), device="cuda", dtype=torch.float64)
+    mms.wave_adjoint_lap(s.desc, s.cf, s.m, lam1, lam2, resid, None, grad)
+    torch.cuda.synchronize()
+    assert torch.equal(lam2, out[0][0]) and float(grad.abs().max()) == 0.0
+    with pytest.raises(mms.MMSError):
+        mms.wave_step_lap(s.desc, s.cf, s.m, cur, prev, nxt, cur, s.amps[2])   # L a^n over a^n
+
+
 def test_out_of_place_step_matches_in_place_step():
     s = Setup(nshots=2)
     cur, prev, work, nxt = s.fields
