@@ -85,7 +85,7 @@ struct FwdGeom {
     static constexpr size_t SMEM = 128 + (size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16;
 };
 
-template <int R, int TX, int TY, int PY, int S>
+template <int R, int TX, int TY, int PY, int S, bool LAPOUT>
 __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     wave_fwd_kernel(const __grid_constant__ CUtensorMap tcur, const __grid_constant__ CUtensorMap tm,
                     const __grid_constant__ CUtensorMap tprev, const __grid_constant__ CUtensorMap tctr,
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                     for (int k = 0; k < 4; ++k)
                         if (gx + k < geo.nx) pp[k] = res[k];
                 }
-                if (lapout) {  // L a^n itself, for the gradient's adjoint steps
+                if constexpr (LAPOUT) {  // L a^n itself, for the gradient's adjoint steps
                     float *lo = lapout + shot_off + mp;
                     if (vec && gx + 3 < geo.nx) {
                         *reinterpret_cast<float4 *>(lo) = make_float4(acc[0][i][0], acc[0][i][1], acc[0][i][2], acc[0][i][3]);
@@ -510,7 +510,8 @@ cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
         !encode_tmap_4d(&mprev, p_prev, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kFwdTY, 1) ||
         !encode_tmap_4d(&mctr, p_cur, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kFwdTY, 1))
         return cudaErrorInvalidValue;
-    auto kern = wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
+    auto kern = lapout ? wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, true>
+                       : wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
     if (e != cudaSuccess) return e;
     const int tz = kFwdTZ;
