@@ -54,3 +54,27 @@ def test_sample_points_cover_corners():
     assert p.dtype == np.int64 and p.shape[1] == 3
     assert (p[:, 0] < 10).all() and (p[:, 1] < 20).all() and (p[:, 2] < 30).all()
     assert any((q == [9, 19, 29]).all() for q in p)
+
+
+def test_aniso_inputs_are_seeded_and_in_range():
+    import math
+    a = workloads.AnisoInputs(40, 30, 50, 2, 12, tti=True)
+    b = workloads.AnisoInputs(40, 30, 50, 2, 12, tti=True)
+    for name in ("vp", "eps", "delta", "vs", "alpha", "theta", "phi", "amp"):
+        assert np.array_equal(getattr(a, name), getattr(b, name)), name
+    c = workloads.AnisoInputs(40, 30, 50, 2, 12, tti=True, salt=1)
+    assert not np.array_equal(a.vp, c.vp)
+    assert a.vp.shape == a.eps.shape == a.theta.shape == (50, 30, 40)
+    assert 0.0 <= a.eps.min() and a.eps.max() <= 0.3
+    assert -0.1 <= a.delta.min() and a.delta.max() <= 0.2
+    assert np.allclose(a.vs, 0.5 * a.vp) and np.all(a.alpha == 1.0)
+    assert a.theta.min() > -math.radians(15) and a.theta.max() < math.radians(60)
+    # eps and delta are constant within each depth layer
+    assert np.all(np.ptp(a.eps, axis=(1, 2)) == 0) and np.all(np.ptp(a.delta, axis=(1, 2)) == 0)
+    # CFL 0.4 on the fastest (horizontal) speed
+    vfast = float((a.vp.astype(np.float64) * np.sqrt(1 + 2 * a.eps)).max())
+    assert abs(vfast * a.dt / a.h - 0.4) < 1e-6
+    # first-derivative weights row: antisymmetric, the FD1_8 values
+    w2, w1 = workloads.fd8_rows()
+    assert np.allclose(w1, -w1[::-1]) and w1[4] == 0 and np.isclose(w1[5], 0.8)
+    assert np.isclose(w2.sum(), 0.0, atol=1e-6)
