@@ -701,6 +701,9 @@ mms_status mms_wave_step_lap(const mms_wave_desc *desc, const float *coeffs, con
     const void *others[3] = {p_cur, p_prev, p_next};
     for (const void *q : others)
         if (overlaps(lap_out, fb, q, fb)) return fail(MMS_E_ARG, "lap_out overlaps a field");
+    if (overlaps(lap_out, fb, m, (size_t)g.pz * (g.nz + 2 * g.r) * 4) ||
+        overlaps(p_next, fb, m, (size_t)g.pz * (g.nz + 2 * g.r) * 4))
+        return fail(MMS_E_ARG, "an output field overlaps m");
     cudaError_t e = launch_wave_fwd(g, coeffs, m, p_cur, p_prev, p_next, src_amp, rec,
                                     reinterpret_cast<cudaStream_t>(stream), lap_out);
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "wave step launch");
@@ -716,7 +719,11 @@ mms_status mms_vti_model(const mms_wave_desc *desc, const float *vp, const float
     if (!vp || !eps || !delta || !mv || !rho) return fail(MMS_E_ARG, "null pointer");
     if (!(dt > 0.f) || !(h > 0.f)) return fail(MMS_E_ARG, "dt and h must be positive");
     const size_t mb = (size_t)g.pz * (g.nz + 2 * g.r) * 4;
+    const size_t nb = (size_t)g.nx * g.ny * g.nz * 4;
     if (overlaps(mv, mb, rho, mb)) return fail(MMS_E_ARG, "mv and rho overlap");
+    const float *ins[3] = {vp, eps, delta};
+    for (const float *q : ins)
+        if (overlaps(q, nb, mv, mb) || overlaps(q, nb, rho, mb)) return fail(MMS_E_ARG, "mv or rho overlaps an input");
     cudaError_t e = launch_vti_model(g, vp, eps, delta, mv, rho, dt, h, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "VTI model kernel launch");
 }
@@ -739,6 +746,10 @@ mms_status mms_vti_step(const mms_wave_desc *desc, const float *coeffs, const fl
         for (int b = a + 1; b < 4; ++b)
             if (overlaps(rd[a], fb, rd[b], fb)) return fail(MMS_E_ARG, "VTI input fields %d and %d overlap", a, b);
     if (overlaps(sh_next, fb, sv_next, fb)) return fail(MMS_E_ARG, "sh_next and sv_next overlap");
+    const size_t mb = (size_t)g.pz * (g.nz + 2 * g.r) * 4;
+    if (overlaps(sh_next, fb, mv, mb) || overlaps(sh_next, fb, rho, mb) || overlaps(sv_next, fb, mv, mb) ||
+        overlaps(sv_next, fb, rho, mb))
+        return fail(MMS_E_ARG, "an output field overlaps the medium");
     const float *nx2[2] = {sh_next, sv_next};
     for (int o = 0; o < 2; ++o)
         for (int a = 0; a < 4; ++a) {

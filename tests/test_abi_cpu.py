@@ -189,3 +189,24 @@ def test_f64_sweep_validation(lib):
     assert lib.mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(P), odd, buf, None) == 3
     d, _ = _desc(nz=0)
     assert lib.mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(P), None, None, None) == 0
+
+
+def test_anisotropic_and_lap_outputs_may_not_alias_their_inputs(lib):
+    # validation happens before anything is enqueued: host buffers suffice
+    P = ctypes.c_void_p
+    nx, ny, nz, r = 10, 8, 8, 1          # padded rows of 12 floats: 16-byte pitches
+    d, _src = _lib.wave_desc(nx, ny, nz, r, 1)
+    fb = (nz + 2 * r) * (ny + 2 * r) * (nx + 2 * r)
+    bufs = [np.zeros(fb + 16, np.float32) for _ in range(8)]
+    a = [ctypes.c_void_p((b.ctypes.data + 15) & ~15) for b in bufs]
+    c = np.ones(9, np.float32).ctypes.data_as(P)
+    amp = np.zeros(1, np.float32).ctypes.data_as(P)
+    # sh_next over mv
+    assert lib.mms_vti_step(ctypes.byref(d), c, a[0], a[1], a[2], a[3], a[4], a[5], a[0], a[6], amp, None, None) == 1
+    assert b"medium" in lib.mms_last_error()
+    # vti model: mv over vp
+    assert lib.mms_vti_model(ctypes.byref(d), a[0], a[1], a[2], a[0], a[3], ctypes.c_float(1e-3),
+                             ctypes.c_float(10.0), None) == 1
+    # step_lap: lap_out over m
+    assert lib.mms_wave_step_lap(ctypes.byref(d), c, a[0], a[1], a[2], a[3], a[0], amp, None, None) == 1
+    assert b"overlaps m" in lib.mms_last_error()
