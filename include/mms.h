@@ -214,7 +214,7 @@ mms_status mms_stencil_apply_f64(const mms_stencil_desc *desc, const double *coe
 
 /*
  * Geometry of the damped acoustic wave step used for reverse time migration
- * (paper Sec. 2.1 names RTM with radius-4 stencils; Sec. 5.5 runs it).  The
+ * (paper Sec. 2.1 names RTM with radius-4 stencils; Sec. 5.6 runs it).  The
  * paper prints no discretisation; the step is
  *     a^{n+1} = G*( (2 + m*L) a^n - G*a^{n-1} + s^n )
  * with L the star stencil of `radius` (unscaled weights), m = v^2 dt^2/h^2,
@@ -258,7 +258,7 @@ mms_status mms_wave_step(const mms_wave_desc *desc, const float *coeffs, const f
  * mms_wave_step); otherwise it must overlap neither p_cur nor p_prev, and
  * its halo is left as it is (the caller keeps it zero).  Checkpoint
  * recomputation uses it to lay a segment's states out without copies.
- * Defined by: the step above (paper Sec. 2.1, Sec. 5.5 for the RTM setting).
+ * Defined by: the step above (paper Sec. 2.1, Sec. 5.6 for the RTM setting).
  */
 mms_status mms_wave_step_to(const mms_wave_desc *desc, const float *coeffs, const float *m,
                             const float *p_cur, const float *p_prev, float *p_next,

@@ -15,7 +15,7 @@ What it computes, and where the paper defines it:
   high-order finite differences (Sec. 2.1: radius 4 gives 8th-order accuracy),
   obtained by solving the moment (Taylor) conditions in exact rationals.
 * ``wave_forward`` / ``wave_gradient``: the acoustic wave step used in place
-  of the paper's RTM kernels (Sec. 2.1, Sec. 5.5) and its discrete adjoint;
+  of the paper's RTM kernels (Sec. 2.1, Sec. 5.6) and its discrete adjoint;
   the paper prints no discretisation, so the step is the leapfrog form
   written in ``oracle.c``.
 

@@ -30,7 +30,7 @@
  *
  * The wave step and its adjoint follow the discretisation stated in the
  * functions below; the paper names reverse time migration (Sec. 2.1,
- * Sec. 5.5) but prints no discretisation, so the readings are those listed in
+ * Sec. 5.6) but prints no discretisation, so the readings are those listed in
  * the design notes (leapfrog, Cerjan sponge, zero halo).
  */
 #include <math.h>

@@ -3,7 +3,7 @@
 The forward model is the damped leapfrog step of mms_wave_step (star
 stencil of radius r, Cerjan sponge, one point source per shot, receivers on
 one z plane); the paper names reverse time migration with radius-4 stencils
-as its application (Sec. 2.1, Sec. 5.5).  ``WaveFunction`` exposes the
+as its application (Sec. 2.1, Sec. 5.6).  ``WaveFunction`` exposes the
 records d(v) to torch.autograd: its backward runs the discrete adjoint
 (mms_wave_adjoint) over checkpointed segments, recomputing each segment's
 states from the checkpoint stored every ``ckpt_every`` steps, and returns
