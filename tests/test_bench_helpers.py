@@ -1,0 +1,61 @@
+"""bench.py's bookkeeping on CPU: the traffic of a committed ncu capture is
+used only while the kernel's code is the one captured (a comment-insensitive
+hash), and the roofline helpers count what they say."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def test_code_hash_ignores_comments_but_not_code(tmp_path):
+    a = tmp_path / "a.cu"
+    a.write_text("// header\n__global__ void k(float *x)\n{\n    x[0] = 1.f;  // one\n}\n")
+    h = bench.code_hash(str(a))
+    a.write_text("/* another\n   header */\n__global__ void k(float *x)\n{\n\n    x[0] = 1.f;\n}\n")
+    assert bench.code_hash(str(a)) == h
+    a.write_text("__global__ void k(float *x)\n{\n    x[0] = 2.f;\n}\n")
+    assert bench.code_hash(str(a)) != h
+
+
+def test_committed_traffic_matches_the_committed_sources():
+    # every recorded capture names sources that exist, and the keys the bench
+    # looks up for its default and wave workloads resolve
+    t = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    for key, rec in t.items():
+        assert os.path.exists(os.path.join(bench.ROOT, rec["capture"])), key
+        for f in rec["sources"]:
+            assert os.path.exists(os.path.join(bench.ROOT, "paper_2507_11067_gb300", "csrc", f)), (key, f)
+    assert bench.captured_traffic("bf16x3 box r=2 v0", 512 ** 3) == pytest.approx(
+        t["bf16x3 box r=2 v0"]["dram_bytes_per_point"] * 512 ** 3)
+    assert bench.captured_traffic("no such kernel", 10) is None
+
+
+def test_traffic_goes_null_when_a_source_changes(tmp_path, monkeypatch):
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    (root / "paper_2507_11067_gb300" / "csrc").mkdir(parents=True)
+    src = root / "paper_2507_11067_gb300" / "csrc" / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    rec = {"k r=1": {"dram_bytes_per_point": 8.0, "capture": "profiles/k.md", "size": "1",
+                     "sources": {"k.cu": bench.code_hash(str(src))}}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.captured_traffic("k r=1", 100) == 800.0
+    src.write_text("// same kernel, new comment\n__global__ void k() {}\n")
+    assert bench.captured_traffic("k r=1", 100) == 800.0
+    src.write_text("__global__ void k() { int a = 0; }\n")
+    assert bench.captured_traffic("k r=1", 100) is None
+
+
+def test_tensor_core_dense_work_per_point():
+    # 2 * K_pad * (2r+1)^2 passes * 3 products (BF16x3), K_pad = TXO + 2r rounded to 16
+    assert bench.tc_dense_flop_per_pt("bf16x3", 2) == 4800
+    assert bench.tc_dense_flop_per_pt("bf16x3", 4) == 15552
+    assert bench.tc_dense_flop_per_pt("bf16x3", 1) == 2592
+
+
+def test_job_rate_and_fp32_peak():
+    assert bench.job_rate(4, 1e9, 2.0) == pytest.approx(2.0)
+    assert bench.fp32_alu_peak_tflops(152, 2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
