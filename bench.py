@@ -205,11 +205,14 @@ def fp32_alu_peak_tflops(n_sm: int, mhz: float) -> float:
 
 
 class Clocks:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """nvidia-smi sampled every 200 ms while the timed region runs; the raw
+    samples go to $MMS_CLOCKS_DIR (default: the system temp directory)."""
 
     def __init__(self, gpu_index: int):
+        import tempfile
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        folder = os.environ.get("MMS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, f"clocks_bench_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
