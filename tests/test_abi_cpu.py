@@ -52,7 +52,7 @@ def _desc(**kw):
 
 
 @pytest.mark.parametrize("kw,status", [
-    (dict(radius=0), 1), (dict(radius=5), 1), (dict(shape=2), 1), (dict(nx=-1), 1),
+    (dict(radius=0), 1), (dict(radius=5), 1), (dict(shape=9), 1), (dict(shape=-1), 1), (dict(nx=-1), 1),
     (dict(path=9), 1), (dict(ipy=3), 1), (dict(opy=2), 1), (dict(variant=-2), 1),
 ])
 def test_argument_validation(lib, kw, status):
