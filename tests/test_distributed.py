@@ -60,6 +60,8 @@ def _sweep_worker(rank, world, port, cases, q):
                 slab[-r:] = 1e30
             res = ss.iterate(slab, steps, overlap=overlap)
             q.put((k, rank, ss.z0, ss.z1, res.numpy().copy()))
+    except Exception as e:          # reported to the parent instead of leaving it waiting
+        q.put(("error", rank, repr(e), None, None))
     finally:
         dist.destroy_process_group()
 
@@ -79,16 +81,20 @@ CASES = [
     ("star", 2, (13, 10, 11), 3, False),
     ("box", 1, (9, 8, 14), 4, True),
     ("star", 4, (12, 9, 20), 2, True),
-    ("star", 2, (8, 7, 7), 2, True),     # 3 ranks get 3, 2, 2 planes: thinner than 2r, no split
+    ("star", 2, (8, 7, 8), 2, True),     # 3 or 4 ranks get slabs of 2-3 planes: thinner than 2r, no split
 ]
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_slabs_equal_the_single_domain_sweeps(world):
     cases = CASES
     ctx, q, procs = _run(world, _sweep_worker, (cases,))
+    got = []
     try:
-        got = [q.get(timeout=300) for _ in range(world * len(cases))]
+        while len(got) < world * len(cases):
+            item = q.get(timeout=300)
+            assert item[0] != "error", item
+            got.append(item)
     finally:
         for p in procs:
             p.join(timeout=60)
