@@ -157,8 +157,11 @@ int32_t mms_auto_path(int shape, int radius, int tma_aligned);
  * 0..n-1.  Returns 0 for an unsupported combination.  Host only. */
 int32_t mms_num_variants(int shape, int radius, int path);
 
-/* Library choice of variant for (shape, radius, path, nx, ny, nz), after any
- * mms_set_variant override.  Host only. */
+/* Library choice of variant for (shape, radius, path, nx, ny, nz): the one
+ * registered by mms_set_variant, else variant 0; -1 for an unsupported
+ * combination.  The choice does not depend on the sizes at present (they are
+ * in the signature so that a size-dependent table needs no ABI change).
+ * Host only. */
 int32_t mms_default_variant(int shape, int radius, int path, int64_t nx, int64_t ny, int64_t nz);
 
 /* Record a tuned variant for (shape, radius, path); used by MMS_PATH_AUTO

@@ -109,13 +109,11 @@ static int num_variants(int shape, int r, int path)
     }
 }
 
-static int default_variant(int shape, int r, int path, int64_t nx, int64_t ny, int64_t nz)
+// The registered (tuned) variant, else variant 0.
+static int default_variant(int shape, int r, int path)
 {
     const int t = tuned_variant(shape, r, path);
-    if (t >= 0 && t < num_variants(shape, r, path)) return t;
-    (void)nx; (void)ny; (void)nz;
-    if (path == MMS_PATH_CUDA_CORE) return 0;
-    return 0;
+    return t >= 0 && t < num_variants(shape, r, path) ? t : 0;
 }
 
 static bool tma_ok(const float *in, int64_t ipy, int64_t ipz)
@@ -179,7 +177,7 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
         return fail(MMS_E_ALIGN, "TMA path needs a 16-byte aligned input and pitches that are multiples of 4 floats");
     const int nvar = num_variants(shape, r, path);
     if (nvar == 0) return fail(MMS_E_UNSUPPORTED, "path %d does not support shape %d radius %d", path, shape, r);
-    int v = d->variant >= 0 ? d->variant : default_variant(shape, r, path, d->nx, d->ny, d->nz);
+    int v = d->variant >= 0 ? d->variant : default_variant(shape, r, path);
     if (v >= nvar) return fail(MMS_E_ARG, "variant %d of %d", v, nvar);
     CUtensorMap map;
     if (path == MMS_PATH_CUDA_CORE) {
@@ -425,8 +423,9 @@ int32_t mms_auto_path(int shape, int radius, int tma_aligned)
 
 int32_t mms_default_variant(int shape, int radius, int path, int64_t nx, int64_t ny, int64_t nz)
 {
+    (void)nx; (void)ny; (void)nz;
     if (num_variants(shape, radius, path) == 0) return -1;
-    return default_variant(shape, radius, path, nx, ny, nz);
+    return default_variant(shape, radius, path);
 }
 
 mms_status mms_set_variant(int shape, int radius, int path, int32_t variant)
@@ -508,6 +507,29 @@ static bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) % 16) =
 
 static size_t field_bytes(const WaveGeo &g) { return (size_t)g.nshots * g.ss * 4; }
 
+// Extent of m (one padded field, shared by the shots).
+static size_t model_bytes(const WaveGeo &g) { return (size_t)g.pz * (g.nz + 2 * g.r) * 4; }
+
+// Extent of one step's receiver records (nshots x ny x nx floats).
+static size_t rec_bytes(const WaveGeo &g) { return (size_t)g.nshots * g.ny * g.nx * 4; }
+
+// Extent of the FP64 gradient: one interior, or one slice per shot.
+static size_t grad_bytes(const WaveGeo &g)
+{
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    return (size_t)(g.gss ? (g.nshots - 1) * g.gss + n : n) * 8;
+}
+
+// The records written by a step must not overlap anything it reads or writes.
+static mms_status check_rec(const WaveGeo &g, const float *rec, const void *const *fields, int nf, const float *m)
+{
+    if (!rec || g.rec_z < 0) return MMS_OK;
+    for (int i = 0; i < nf; ++i)
+        if (overlaps(rec, rec_bytes(g), fields[i], field_bytes(g))) return fail(MMS_E_ARG, "rec overlaps a field");
+    if (overlaps(rec, rec_bytes(g), m, model_bytes(g))) return fail(MMS_E_ARG, "rec overlaps m");
+    return MMS_OK;
+}
+
 struct GraphEntry {
     uint64_t key;
     cudaGraphExec_t exec;
@@ -538,6 +560,9 @@ mms_status mms_wave_step(const mms_wave_desc *desc, const float *coeffs, const f
     if (!m || !p_cur || !p_prev || !src_amp) return fail(MMS_E_ARG, "null field pointer");
     if (!al16(m) || !al16(p_cur) || !al16(p_prev)) return fail(MMS_E_ALIGN, "wave fields must be 16-byte aligned");
     if (overlaps(p_cur, field_bytes(g), p_prev, field_bytes(g))) return fail(MMS_E_ARG, "p_cur and p_prev overlap");
+    if (overlaps(p_prev, field_bytes(g), m, model_bytes(g))) return fail(MMS_E_ARG, "an output field overlaps m");
+    const void *fs[2] = {p_cur, p_prev};
+    if ((st = check_rec(g, rec, fs, 2, m)) != MMS_OK) return st;
     cudaError_t e = launch_wave_fwd(g, coeffs, m, p_cur, p_prev, p_prev, src_amp, rec,
                                     reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "wave step launch");
@@ -557,6 +582,9 @@ mms_status mms_wave_step_to(const mms_wave_desc *desc, const float *coeffs, cons
     if (overlaps(p_cur, fb, p_next, fb)) return fail(MMS_E_ARG, "p_cur and p_next overlap");
     if (p_next != p_prev && overlaps(p_prev, fb, p_next, fb))
         return fail(MMS_E_ARG, "p_prev and p_next overlap without being the same field");
+    if (overlaps(p_next, fb, m, model_bytes(g))) return fail(MMS_E_ARG, "an output field overlaps m");
+    const void *fs[3] = {p_cur, p_prev, p_next};
+    if ((st = check_rec(g, rec, fs, 3, m)) != MMS_OK) return st;
     cudaError_t e = launch_wave_fwd(g, coeffs, m, p_cur, p_prev, p_next, src_amp, rec,
                                     reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "wave step launch");
@@ -578,8 +606,17 @@ mms_status mms_wave_forward(const mms_wave_desc *desc, const float *coeffs, cons
     if (flags & ~MMS_WAVE_GRAPH) return fail(MMS_E_ARG, "unknown flags 0x%x", flags);
     if (nsteps == 0) return MMS_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const size_t fb = field_bytes(g);
+    const size_t fb = field_bytes(g), mb = model_bytes(g);
     const int64_t rec_step = (int64_t)g.nshots * g.ny * g.nx;
+    if (overlaps(p0, fb, m, mb) || overlaps(p1, fb, m, mb)) return fail(MMS_E_ARG, "a wavefield overlaps m");
+    // checkpoint slots: one pair of fields for every ckpt_every steps
+    const size_t cb = ckpt ? (size_t)((nsteps + ckpt_every - 1) / ckpt_every) * 2 * fb : 0;
+    const size_t rb = rec_all ? (size_t)nsteps * rec_step * 4 : 0;
+    if (ckpt && (overlaps(ckpt, cb, p0, fb) || overlaps(ckpt, cb, p1, fb) || overlaps(ckpt, cb, m, mb)))
+        return fail(MMS_E_ARG, "ckpt overlaps a wavefield or m");
+    if (rec_all && (overlaps(rec_all, rb, p0, fb) || overlaps(rec_all, rb, p1, fb) || overlaps(rec_all, rb, m, mb) ||
+                    (ckpt && overlaps(rec_all, rb, ckpt, cb))))
+        return fail(MMS_E_ARG, "rec_all overlaps a wavefield, m or ckpt");
 
     auto enqueue = [&]() -> mms_status {
         float *bufs[2] = {p0, p1};
@@ -666,6 +703,15 @@ static mms_status wave_adjoint(const mms_wave_desc *desc, const float *coeffs, c
         return fail(MMS_E_ALIGN, "wave fields must be 16-byte aligned");
     if (overlaps(lam_cur, field_bytes(g), lam_prev, field_bytes(g))) return fail(MMS_E_ARG, "lam_cur and lam_prev overlap");
     if (a_n && overlaps(a_n, field_bytes(g), lam_prev, field_bytes(g))) return fail(MMS_E_ARG, "a_n and lam_prev overlap");
+    if (overlaps(lam_prev, field_bytes(g), m, model_bytes(g))) return fail(MMS_E_ARG, "lam_prev overlaps m");
+    if (resid && overlaps(resid, rec_bytes(g), lam_prev, field_bytes(g))) return fail(MMS_E_ARG, "resid overlaps lam_prev");
+    if (grad_m) {
+        const size_t gb = grad_bytes(g), fb = field_bytes(g);
+        if (overlaps(grad_m, gb, m, model_bytes(g)) || overlaps(grad_m, gb, lam_cur, fb) ||
+            overlaps(grad_m, gb, lam_prev, fb) || (a_n && overlaps(grad_m, gb, a_n, fb)) ||
+            (resid && overlaps(grad_m, gb, resid, rec_bytes(g))))
+            return fail(MMS_E_ARG, "grad_m overlaps a field");
+    }
     cudaError_t e = launch_wave_adj(g, coeffs, m, lam_cur, lam_prev, resid, a_n, grad_m,
                                     reinterpret_cast<cudaStream_t>(stream), lapin);
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "adjoint step launch");
@@ -841,6 +887,7 @@ mms_status mms_model_from_velocity(const mms_wave_desc *desc, const float *v, fl
     if (st != MMS_OK) return st;
     if (!v || !m) return fail(MMS_E_ARG, "null pointer");
     if (!(dt > 0.f) || !(h > 0.f)) return fail(MMS_E_ARG, "dt and h must be positive");
+    if (overlaps(v, (size_t)g.nx * g.ny * g.nz * 4, m, model_bytes(g))) return fail(MMS_E_ARG, "m overlaps v");
     cudaError_t e = launch_model_from_velocity(g, v, m, dt, h, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "model kernel launch");
 }
@@ -852,6 +899,10 @@ mms_status mms_grad_to_velocity(const double *grad_m, const float *v, double *gr
     if (n == 0) return MMS_OK;
     if (!grad_m || !v || !grad_v) return fail(MMS_E_ARG, "null pointer");
     if (!(dt > 0.f) || !(h > 0.f)) return fail(MMS_E_ARG, "dt and h must be positive");
+    // element-wise: grad_v may be grad_m itself, but not a shifted copy of it
+    if (grad_v != grad_m && overlaps(grad_v, (size_t)n * 8, grad_m, (size_t)n * 8))
+        return fail(MMS_E_ARG, "grad_v overlaps grad_m without being it");
+    if (overlaps(grad_v, (size_t)n * 8, v, (size_t)n * 4)) return fail(MMS_E_ARG, "grad_v overlaps v");
     cudaError_t e = launch_grad_to_velocity(grad_m, v, grad_v, n, dt, h, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "chain-rule kernel launch");
 }
@@ -885,6 +936,8 @@ mms_status mms_dot_f64(const float *a, const float *b, int64_t n, double *result
     if (n < 0) return fail(MMS_E_ARG, "negative length");
     if (!result) return fail(MMS_E_ARG, "null result pointer");
     if (n > 0 && (!a || !b)) return fail(MMS_E_ARG, "null input pointer");
+    if (n > 0 && (overlaps(result, 8, a, (size_t)n * 4) || overlaps(result, 8, b, (size_t)n * 4)))
+        return fail(MMS_E_ARG, "result overlaps an input");
     cudaError_t e = launch_dot_f64(a, b, n, result, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "dot kernel launch");
 }

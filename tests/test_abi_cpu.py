@@ -210,3 +210,40 @@ def test_anisotropic_and_lap_outputs_may_not_alias_their_inputs(lib):
     # step_lap: lap_out over m
     assert lib.mms_wave_step_lap(ctypes.byref(d), c, a[0], a[1], a[2], a[3], a[0], amp, None, None) == 1
     assert b"overlaps m" in lib.mms_last_error()
+
+
+def test_wave_outputs_may_not_alias_their_inputs(lib):
+    # validation happens before anything is enqueued: host buffers suffice
+    P = ctypes.c_void_p
+    nx, ny, nz, r = 10, 8, 8, 1
+    d, _src = _lib.wave_desc(nx, ny, nz, r, 1, rec_z=0)
+    fb = (nz + 2 * r) * (ny + 2 * r) * (nx + 2 * r)
+    bufs = [np.zeros(fb + 16, np.float32) for _ in range(6)]
+    a = [ctypes.c_void_p((b.ctypes.data + 15) & ~15) for b in bufs]
+    c = np.ones(9, np.float32).ctypes.data_as(P)
+    amp = np.zeros(4, np.float32).ctypes.data_as(P)
+
+    def refused(status, words):
+        assert status == 1
+        assert words in lib.mms_last_error(), lib.mms_last_error()
+
+    m, p, q, x, y, z = a
+    refused(lib.mms_wave_step(ctypes.byref(d), c, m, p, m, amp, None, None), b"overlaps m")
+    refused(lib.mms_wave_step(ctypes.byref(d), c, m, p, q, amp, p, None), b"rec overlaps")
+    refused(lib.mms_wave_step_to(ctypes.byref(d), c, m, p, q, m, amp, None, None), b"overlaps m")
+    refused(lib.mms_wave_forward(ctypes.byref(d), c, m, amp, 2, m, q, None, None, 1, 0, None), b"overlaps m")
+    refused(lib.mms_wave_forward(ctypes.byref(d), c, m, amp, 2, p, q, None, p, 1, 0, None), b"ckpt overlaps")
+    refused(lib.mms_wave_forward(ctypes.byref(d), c, m, amp, 2, p, q, m, None, 1, 0, None), b"rec_all overlaps")
+    refused(lib.mms_wave_adjoint(ctypes.byref(d), c, m, p, m, None, None, None, None), b"lam_prev overlaps m")
+    refused(lib.mms_wave_adjoint(ctypes.byref(d), c, m, p, q, None, x, p, None), b"grad_m overlaps")
+    refused(lib.mms_wave_adjoint(ctypes.byref(d), c, m, p, q, q, None, None, None), b"resid overlaps")
+    refused(lib.mms_model_from_velocity(ctypes.byref(d), m, m, ctypes.c_float(1e-3), ctypes.c_float(10.0), None),
+            b"overlaps v")
+    n = nx * ny * nz
+    g = np.zeros(n + 8, np.float64)
+    gp = g.ctypes.data
+    refused(lib.mms_grad_to_velocity(P(gp), x, P(gp + 8), n, ctypes.c_float(1e-3), ctypes.c_float(10.0), None),
+            b"grad_v overlaps grad_m")
+    refused(lib.mms_grad_to_velocity(P(gp), x, x, n, ctypes.c_float(1e-3), ctypes.c_float(10.0), None),
+            b"grad_v overlaps v")
+    refused(lib.mms_dot_f64(x, y, n, x, None), b"result overlaps")
