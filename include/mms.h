@@ -244,6 +244,17 @@ typedef struct {
 } mms_wave_desc;
 
 /*
+ * Aliasing rules of the wave entry points, checked before anything is
+ * queued (MMS_E_ARG, nothing written, otherwise): a buffer a call writes --
+ * the new state, lam^n, rec / rec_all, ckpt, grad_m, lap_out -- overlaps
+ * neither m nor any other buffer of the call, except where an entry point
+ * allows an in-place update by name (p_next = p_prev).  Extents: a field is
+ * nshots*shot_stride floats, m one padded field, a record nshots*ny*nx
+ * floats per step, a checkpoint 2 fields, grad_m nz*ny*nx doubles (or
+ * (nshots-1)*grad_shot_stride + nz*ny*nx with per-shot slices).
+ */
+
+/*
  * One forward step for all shots.
  * coeffs: host 3*(2r+1) star weights; m: device padded field (one, shared by
  * all shots; its halo is never read); p_cur: device a^n (nshots stacked);
@@ -323,15 +334,19 @@ mms_status mms_wave_adjoint_lap(const mms_wave_desc *desc, const float *coeffs, 
                                 const float *lam_cur, float *lam_prev, const float *resid,
                                 const float *lap_a, double *grad_m, void *stream);
 
-/* m = v^2 dt^2 / h^2 into a padded field (halo set to 0); v dense nz*ny*nx. */
+/* m = v^2 dt^2 / h^2 into a padded field (halo set to 0); v dense nz*ny*nx.
+ * MMS_E_ARG for null pointers, dt or h not positive, or m overlapping v. */
 mms_status mms_model_from_velocity(const mms_wave_desc *desc, const float *v, float *m,
                                    float dt, float h, void *stream);
 
-/* grad_v = grad_m * 2 v dt^2 / h^2 (chain rule of m = v^2 dt^2/h^2), n values. */
+/* grad_v = grad_m * 2 v dt^2 / h^2 (chain rule of m = v^2 dt^2/h^2), n values.
+ * grad_v may be grad_m itself (element-wise); MMS_E_ARG when it overlaps v,
+ * or grad_m without being it. */
 mms_status mms_grad_to_velocity(const double *grad_m, const float *v, double *grad_v, int64_t n,
                                 float dt, float h, void *stream);
 
-/* result[0] = sum_i a[i]*b[i] in FP64 over n floats (device in, device out). */
+/* result[0] = sum_i a[i]*b[i] in FP64 over n floats (device in, device out).
+ * MMS_E_ARG when result overlaps a or b. */
 mms_status mms_dot_f64(const float *a, const float *b, int64_t n, double *result, void *stream);
 
 /* out[i] = sum_{s < nslices} slices[s*stride + i], i < n, in FP64 (device in,
