@@ -24,7 +24,7 @@ PLANAR = (STAR2D, BOX2D)
 def n_coeffs(shape, r):
     """Stored weights of a shape: 3(2r+1) star, (2r+1)^3 box, 2(2r+1) star2d, (2r+1)^2 box2d."""
     w = 2 * r + 1
-    return {"star": 3 * w, "box": w ** 3, "star2d": 2 * w, "box2d": w * w}[shape]
+    return {STAR: 3 * w, BOX: w ** 3, STAR2D: 2 * w, BOX2D: w * w}[SHAPES[shape]]
 
 
 def interior(shape, r, padded_shape):
@@ -50,10 +50,71 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_wave_adjoint_lap"]
 
 
+MAX_SHOTS = 64  # largest mms_wave_desc.nshots the library takes
+
+
 class MMSError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class ArgumentError(MMSError, ValueError):
+    """An argument the binding refuses before calling the library (status
+    MMS_E_ARG): a buffer of the wrong type, place or size."""
+
+    def __init__(self, msg: str):
+        super().__init__(1, msg)
+
+
+def _extent(t) -> int:
+    """Bytes from the view's first element to the end of its storage."""
+    st = t.untyped_storage()
+    return st.data_ptr() + st.nbytes() - t.data_ptr()
+
+
+def _device_problem(t):
+    """Why t cannot be handed to a kernel on the current CUDA device, or None."""
+    import torch
+    if not t.is_cuda:
+        return "must be a CUDA tensor"
+    cur = torch.cuda.current_device()
+    if t.device.index != cur:
+        return f"is on {t.device}, the kernels run on cuda:{cur}"
+    return None
+
+
+def _need(t, name, dtype=None, nbytes=0, required=True, dense=False, host=False):
+    """Refuse a buffer the library cannot use: of another dtype, not dense
+    where the call reads it as a dense array, too short for the nbytes the
+    call touches from its first element, or on the wrong side (a CUDA tensor
+    of the current device; with host=True, a CPU tensor)."""
+    import torch
+    if t is None:
+        if required:
+            raise ArgumentError(f"{name} is required")
+        return
+    if not isinstance(t, torch.Tensor):
+        raise ArgumentError(f"{name} must be a torch tensor, not {type(t).__name__}")
+    dtype = dtype or torch.float32
+    if t.dtype != dtype:
+        raise ArgumentError(f"{name} must be {dtype}, not {t.dtype}")
+    if dense and not t.is_contiguous():
+        raise ArgumentError(f"{name} must be contiguous")
+    if nbytes > 0 and _extent(t) < nbytes:
+        raise ArgumentError(f"{name} holds {_extent(t)} bytes from its first element; the call touches {nbytes}")
+    if host:
+        if t.is_cuda:
+            raise ArgumentError(f"{name} must be a CPU tensor")
+    else:
+        why = _device_problem(t)
+        if why:
+            raise ArgumentError(f"{name} {why}")
+
+
+def _need_shape(t, name, shape):
+    if tuple(t.shape) != tuple(shape):
+        raise ArgumentError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
 
 class StencilDesc(ctypes.Structure):
@@ -160,11 +221,21 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _host_coeffs(coeffs) -> np.ndarray:
+def _f64():
+    import torch
+    return torch.float64
+
+
+def _host_coeffs(coeffs, count=None, dtype=np.float32) -> np.ndarray:
+    """The weights as a contiguous host array; with count, refused unless it
+    holds exactly that many (the library reads count values)."""
     c = coeffs
     if hasattr(c, "detach"):
         c = c.detach().cpu().numpy()
-    return np.ascontiguousarray(np.asarray(c, dtype=np.float32).reshape(-1))
+    c = np.ascontiguousarray(np.asarray(c, dtype=dtype).reshape(-1))
+    if count is not None and c.size != count:
+        raise ArgumentError(f"{count} weights expected, got {c.size}")
+    return c
 
 
 # ------------------------------------------------------------ allocation
@@ -226,14 +297,15 @@ def apply(shape, r, coeffs, inp, out=None, path="auto", variant=-1, stream=None)
     pitches); out: (nz, ny, nx) view or None (allocated).  Returns out.
     """
     import torch
-    if not inp.is_cuda or inp.dtype != torch.float32:
-        raise ValueError("input must be a CUDA float32 tensor")
+    _need(inp, "input")
     nx, ny, nz = interior(shape, r, inp.shape)
     if out is None:
         out = torch.empty((nz, ny, nx), device=inp.device, dtype=torch.float32)
+    _need(out, "output")
+    _need_shape(out, "output", (nz, ny, nx))
     ipy, ipz = pitches(inp)
     opy, opz = pitches(out)
-    c = _host_coeffs(coeffs)
+    c = _host_coeffs(coeffs, n_coeffs(shape, r))
     d = StencilDesc(SHAPES[shape], r, c.ctypes.data, nx, ny, nz, ipy, ipz, opy, opz,
                     PATHS[path] if isinstance(path, str) else int(path), int(variant))
     check(load().mms_stencil_apply_ex(ctypes.byref(d), _ptr(inp), _ptr(out), _stream(stream)))
@@ -244,19 +316,15 @@ def apply_f64(shape, r, coeffs, inp, out=None, stream=None):
     """The FP64 sweep (mms_stencil_apply_f64): inp a CUDA float64 padded view
     with unit x stride (any pitches), out an interior view or None."""
     import torch
-    if not inp.is_cuda or inp.dtype != torch.float64:
-        raise ValueError("input must be a CUDA float64 tensor")
+    _need(inp, "input", torch.float64)
     nx, ny, nz = interior(shape, r, inp.shape)
     if out is None:
         out = torch.empty((nz, ny, nx), device=inp.device, dtype=torch.float64)
-    if out.dtype != torch.float64:
-        raise ValueError("output must be float64")
+    _need(out, "output", torch.float64)
+    _need_shape(out, "output", (nz, ny, nx))
     ipy, ipz = pitches(inp)
     opy, opz = pitches(out)
-    c = np.ascontiguousarray(np.asarray(coeffs.detach().cpu().numpy() if hasattr(coeffs, "detach") else coeffs,
-                                        dtype=np.float64).reshape(-1))
-    if c.size != n_coeffs(shape, r):
-        raise ValueError(f"{shape} r={r} needs {n_coeffs(shape, r)} coefficients")
+    c = _host_coeffs(coeffs, n_coeffs(shape, r), np.float64)
     d = StencilDesc(SHAPES[shape], r, None, nx, ny, nz, ipy, ipz, opy, opz, PATHS["auto"], -1)
     check(load().mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(ctypes.c_void_p), _ptr(inp), _ptr(out),
                                        _stream(stream)))
@@ -268,14 +336,15 @@ def apply_noalloc(r, coeffs, inp, out=None, path="bf16x3", variant=-1, stream=No
     call (mms_stencil_apply_noalloc); same arguments as ``apply`` with
     shape "star".  Interiors above NOALLOC_MAX_POINTS points are refused."""
     import torch
-    if not inp.is_cuda or inp.dtype != torch.float32:
-        raise ValueError("input must be a CUDA float32 tensor")
+    _need(inp, "input")
     nx, ny, nz = interior("star", r, inp.shape)
     if out is None:
         out = torch.empty((nz, ny, nx), device=inp.device, dtype=torch.float32)
+    _need(out, "output")
+    _need_shape(out, "output", (nz, ny, nx))
     ipy, ipz = pitches(inp)
     opy, opz = pitches(out)
-    c = _host_coeffs(coeffs)
+    c = _host_coeffs(coeffs, n_coeffs("star", r))
     d = StencilDesc(SHAPES["star"], r, c.ctypes.data, nx, ny, nz, ipy, ipz, opy, opz,
                     PATHS[path] if isinstance(path, str) else int(path), int(variant))
     check(load().mms_stencil_apply_noalloc(ctypes.byref(d), _ptr(inp), _ptr(out), _stream(stream)))
@@ -287,13 +356,13 @@ def apply_host(shape, r, coeffs, host_in, host_out, path="auto", variant=-1, str
     CPU float32 (nz+2r, ny+2r, nx+2r) view with unit x stride (pinned for
     overlapped copies), host_out a CPU (nz, ny, nx) view; the library streams
     z-slabs through the device.  Asynchronous on `stream`."""
-    import torch
-    if host_in.is_cuda or host_out.is_cuda or host_in.dtype != torch.float32:
-        raise ValueError("host_in and host_out must be CPU float32 tensors")
+    _need(host_in, "host_in", host=True)
+    _need(host_out, "host_out", host=True)
     nx, ny, nz = interior(shape, r, host_in.shape)
+    _need_shape(host_out, "host_out", (nz, ny, nx))
     ipy, ipz = pitches(host_in)
     opy, opz = pitches(host_out)
-    c = _host_coeffs(coeffs)
+    c = _host_coeffs(coeffs, n_coeffs(shape, r))
     d = StencilDesc(SHAPES[shape], r, c.ctypes.data, nx, ny, nz, ipy, ipz, opy, opz,
                     PATHS[path] if isinstance(path, str) else int(path), int(variant))
     check(load().mms_stencil_apply_host(ctypes.byref(d), _ptr(host_in), _ptr(host_out), _stream(stream)))
@@ -302,8 +371,11 @@ def apply_host(shape, r, coeffs, host_in, host_out, path="auto", variant=-1, str
 
 def apply_dense(shape, r, coeffs, inp, out, stream=None):
     """mms_stencil_apply on dense contiguous tensors (AUTO path)."""
-    c = _host_coeffs(coeffs)
+    _need(inp, "input", dense=True)
     nx, ny, nz = interior(shape, r, inp.shape)
+    _need(out, "output", dense=True)
+    _need_shape(out, "output", (nz, ny, nx))
+    c = _host_coeffs(coeffs, n_coeffs(shape, r))
     check(load().mms_stencil_apply(SHAPES[shape], r, c.ctypes.data_as(ctypes.c_void_p), _ptr(inp),
                                    _ptr(out), nx, ny, nz, _stream(stream)))
     return out
@@ -350,6 +422,37 @@ def wave_desc(nx, ny, nz, r, nshots, pitch_y=0, pitch_z=0, shot_stride=0, sponge
     return d, src_arr
 
 
+class _WaveExtent:
+    """Bytes each buffer of a wave call touches, from the geometry of its
+    descriptor.  A descriptor the library refuses anyway (sizes, radius or
+    shot count out of range) gets no size requirements here: the library
+    reports it before it touches any buffer."""
+
+    def __init__(self, desc):
+        r, ns = desc.radius, desc.nshots
+        self.ok = 1 <= r <= 4 and min(desc.nx, desc.ny, desc.nz) >= 1 and 1 <= ns <= MAX_SHOTS
+        X, Y, Z = desc.nx + 2 * r, desc.ny + 2 * r, desc.nz + 2 * r
+        py = desc.pitch_y or X
+        pz = desc.pitch_z or Y * py
+        ss = desc.shot_stride or Z * pz
+        one = (Z - 1) * pz + (Y - 1) * py + X          # elements of one padded field the kernels reach
+        self.n = desc.nx * desc.ny * desc.nz
+        self.shot_stride = ss
+        gss = desc.grad_shot_stride
+        k = 1 if self.ok else 0
+        self.model = k * 4 * one
+        self.field = k * 4 * ((ns - 1) * ss + one)
+        self.whole_field = k * 4 * ns * ss           # what a checkpoint copy moves
+        self.rec = k * 4 * ns * desc.ny * desc.nx
+        self.amp = k * 4 * ns
+        self.grad = k * 8 * ((ns - 1) * gss + self.n if gss else self.n)
+        self.dense = k * 4 * self.n
+
+
+def _wave_coeffs(desc, coeffs):
+    return _host_coeffs(coeffs, 3 * (2 * desc.radius + 1))
+
+
 def field_geometry(fields):
     """(pitch_y, pitch_z, shot_stride) of a (nshots, Z, Y, X) stacked view."""
     if fields.dim() != 4 or fields.stride(3) != 1:
@@ -358,7 +461,13 @@ def field_geometry(fields):
 
 
 def wave_step(desc, coeffs, m, p_cur, p_prev, src_amp, rec=None, stream=None):
-    c = _host_coeffs(coeffs)
+    x = _WaveExtent(desc)
+    _need(m, "m", nbytes=x.model)
+    for t, name in ((p_cur, "p_cur"), (p_prev, "p_prev")):
+        _need(t, name, nbytes=x.field)
+    _need(src_amp, "src_amp", nbytes=x.amp)
+    _need(rec, "rec", nbytes=x.rec, required=False)
+    c = _wave_coeffs(desc, coeffs)
     check(load().mms_wave_step(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                _ptr(p_cur), _ptr(p_prev), _ptr(src_amp), _ptr(rec),
                                _stream(stream)))
@@ -366,7 +475,13 @@ def wave_step(desc, coeffs, m, p_cur, p_prev, src_amp, rec=None, stream=None):
 
 def wave_step_to(desc, coeffs, m, p_cur, p_prev, p_next, src_amp, rec=None, stream=None):
     """mms_wave_step_to: a^{n+1} into p_next, p_prev read only."""
-    c = _host_coeffs(coeffs)
+    x = _WaveExtent(desc)
+    _need(m, "m", nbytes=x.model)
+    for t, name in ((p_cur, "p_cur"), (p_prev, "p_prev"), (p_next, "p_next")):
+        _need(t, name, nbytes=x.field)
+    _need(src_amp, "src_amp", nbytes=x.amp)
+    _need(rec, "rec", nbytes=x.rec, required=False)
+    c = _wave_coeffs(desc, coeffs)
     check(load().mms_wave_step_to(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                   _ptr(p_cur), _ptr(p_prev), _ptr(p_next), _ptr(src_amp), _ptr(rec),
                                   _stream(stream)))
@@ -374,7 +489,19 @@ def wave_step_to(desc, coeffs, m, p_cur, p_prev, p_next, src_amp, rec=None, stre
 
 def wave_forward(desc, coeffs, m, amps, nsteps, p0, p1, rec_all=None, ckpt=None, ckpt_every=0,
                  graph=False, stream=None):
-    c = _host_coeffs(coeffs)
+    x = _WaveExtent(desc)
+    nsteps, every = int(nsteps), int(ckpt_every)
+    steps = max(nsteps, 0)
+    _need(m, "m", nbytes=x.model)
+    for t, name in ((p0, "p0"), (p1, "p1")):
+        _need(t, name, nbytes=x.whole_field if ckpt is not None else x.field)
+    _need(amps, "amps", nbytes=steps * x.amp)
+    _need(rec_all, "rec_all", nbytes=steps * x.rec, required=False)
+    if ckpt is not None and every >= 1:
+        _need(ckpt, "ckpt", nbytes=-(-steps // every) * 2 * x.whole_field)
+    else:
+        _need(ckpt, "ckpt", required=False)
+    c = _wave_coeffs(desc, coeffs)
     check(load().mms_wave_forward(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                   _ptr(amps), int(nsteps), _ptr(p0), _ptr(p1), _ptr(rec_all),
                                   _ptr(ckpt), int(ckpt_every), WAVE_GRAPH if graph else 0,
@@ -383,7 +510,14 @@ def wave_forward(desc, coeffs, m, amps, nsteps, p0, p1, rec_all=None, ckpt=None,
 
 def wave_adjoint(desc, coeffs, m, lam_cur, lam_prev, resid=None, a_n=None, grad_m=None,
                  stream=None):
-    c = _host_coeffs(coeffs)
+    x = _WaveExtent(desc)
+    _need(m, "m", nbytes=x.model)
+    for t, name in ((lam_cur, "lam_cur"), (lam_prev, "lam_prev")):
+        _need(t, name, nbytes=x.field)
+    _need(resid, "resid", nbytes=x.rec, required=False)
+    _need(a_n, "a_n", nbytes=x.field, required=False)
+    _need(grad_m, "grad_m", _f64(), nbytes=x.grad, required=False)
+    c = _wave_coeffs(desc, coeffs)
     check(load().mms_wave_adjoint(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                   _ptr(lam_cur), _ptr(lam_prev), _ptr(resid), _ptr(a_n),
                                   _ptr(grad_m), _stream(stream)))
@@ -391,7 +525,13 @@ def wave_adjoint(desc, coeffs, m, lam_cur, lam_prev, resid=None, a_n=None, grad_
 
 def wave_step_lap(desc, coeffs, m, p_cur, p_prev, p_next, lap_out, src_amp, rec=None, stream=None):
     """mms_wave_step_lap: a^{n+1} into p_next and L a^n into lap_out."""
-    c = _host_coeffs(coeffs)
+    x = _WaveExtent(desc)
+    _need(m, "m", nbytes=x.model)
+    for t, name in ((p_cur, "p_cur"), (p_prev, "p_prev"), (p_next, "p_next"), (lap_out, "lap_out")):
+        _need(t, name, nbytes=x.field)
+    _need(src_amp, "src_amp", nbytes=x.amp)
+    _need(rec, "rec", nbytes=x.rec, required=False)
+    c = _wave_coeffs(desc, coeffs)
     check(load().mms_wave_step_lap(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m), _ptr(p_cur),
                                    _ptr(p_prev), _ptr(p_next), _ptr(lap_out), _ptr(src_amp), _ptr(rec),
                                    _stream(stream)))
@@ -399,24 +539,43 @@ def wave_step_lap(desc, coeffs, m, p_cur, p_prev, p_next, lap_out, src_amp, rec=
 
 def wave_adjoint_lap(desc, coeffs, m, lam_cur, lam_prev, resid=None, lap_a=None, grad_m=None, stream=None):
     """mms_wave_adjoint_lap: the adjoint step with the gradient term from L a^n."""
-    c = _host_coeffs(coeffs)
+    x = _WaveExtent(desc)
+    _need(m, "m", nbytes=x.model)
+    for t, name in ((lam_cur, "lam_cur"), (lam_prev, "lam_prev")):
+        _need(t, name, nbytes=x.field)
+    _need(resid, "resid", nbytes=x.rec, required=False)
+    _need(lap_a, "lap_a", nbytes=x.field, required=False)
+    _need(grad_m, "grad_m", _f64(), nbytes=x.grad, required=False)
+    c = _wave_coeffs(desc, coeffs)
     check(load().mms_wave_adjoint_lap(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                       _ptr(lam_cur), _ptr(lam_prev), _ptr(resid), _ptr(lap_a), _ptr(grad_m),
                                       _stream(stream)))
 
 
 def model_from_velocity(desc, v, m, dt, h, stream=None):
+    x = _WaveExtent(desc)
+    _need(v, "v", nbytes=x.dense, dense=True)
+    _need(m, "m", nbytes=x.model)
     check(load().mms_model_from_velocity(ctypes.byref(desc), _ptr(v), _ptr(m), float(dt),
                                          float(h), _stream(stream)))
 
 
 def grad_to_velocity(grad_m, v, grad_v, dt, h, stream=None):
+    _need(grad_m, "grad_m", _f64(), dense=True)
+    n = grad_m.numel()
+    _need(v, "v", nbytes=4 * n, dense=True)
+    _need(grad_v, "grad_v", _f64(), nbytes=8 * n, dense=True)
     check(load().mms_grad_to_velocity(_ptr(grad_m), _ptr(v), _ptr(grad_v), grad_m.numel(),
                                       float(dt), float(h), _stream(stream)))
 
 
 def vti_model(desc, vp, eps, delta, mv, rho, dt, h, stream=None):
     """mms_vti_model: the padded VTI medium (mv, rho) from dense vp, eps, delta."""
+    x = _WaveExtent(desc)
+    for t, name in ((vp, "vp"), (eps, "eps"), (delta, "delta")):
+        _need(t, name, nbytes=x.dense, dense=True)
+    for t, name in ((mv, "mv"), (rho, "rho")):
+        _need(t, name, nbytes=x.model)
     check(load().mms_vti_model(ctypes.byref(desc), _ptr(vp), _ptr(eps), _ptr(delta), _ptr(mv), _ptr(rho),
                                float(dt), float(h), _stream(stream)))
 
@@ -425,7 +584,15 @@ def vti_step(desc, coeffs, mv, rho, sh_cur, sv_cur, sh_prev, sv_prev, sh_next, s
              stream=None):
     """mms_vti_step: (sigma_H, sigma_V)^{n+1} into sh_next, sv_next (which may
     be sh_prev, sv_prev)."""
-    c = _host_coeffs(coeffs)
+    x = _WaveExtent(desc)
+    for t, name in ((mv, "mv"), (rho, "rho")):
+        _need(t, name, nbytes=x.model)
+    for t, name in ((sh_cur, "sh_cur"), (sv_cur, "sv_cur"), (sh_prev, "sh_prev"), (sv_prev, "sv_prev"),
+                    (sh_next, "sh_next"), (sv_next, "sv_next")):
+        _need(t, name, nbytes=x.field)
+    _need(src_amp, "src_amp", nbytes=x.amp)
+    _need(rec, "rec", nbytes=x.rec, required=False)
+    c = _wave_coeffs(desc, coeffs)
     check(load().mms_vti_step(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(mv), _ptr(rho),
                               _ptr(sh_cur), _ptr(sv_cur), _ptr(sh_prev), _ptr(sv_prev), _ptr(sh_next),
                               _ptr(sv_next), _ptr(src_amp), _ptr(rec), _stream(stream)))
@@ -433,6 +600,11 @@ def vti_step(desc, coeffs, mv, rho, sh_cur, sv_cur, sh_prev, sv_prev, sh_next, s
 
 def tti_model(desc, vp, vs, eps, delta, alpha, theta, phi, med, dt, h, stream=None):
     """mms_tti_model: med (8, nz, ny, nx) = [a, b, c, d, alpha, nx, ny, nz]."""
+    x = _WaveExtent(desc)
+    for t, name in ((vp, "vp"), (vs, "vs"), (eps, "eps"), (delta, "delta"), (alpha, "alpha"), (theta, "theta"),
+                    (phi, "phi")):
+        _need(t, name, nbytes=x.dense, dense=True)
+    _need(med, "med", nbytes=8 * x.dense, dense=True)
     check(load().mms_tti_model(ctypes.byref(desc), _ptr(vp), _ptr(vs), _ptr(eps), _ptr(delta), _ptr(alpha),
                                _ptr(theta), _ptr(phi), _ptr(med), float(dt), float(h), _stream(stream)))
 
@@ -441,9 +613,15 @@ def tti_step(desc, w2, w1, med, p_cur, q_cur, p_prev, q_prev, p_next, q_next, wo
              stream=None):
     """mms_tti_step: (p, q)^{n+1} into p_next, q_next (which may be p_prev,
     q_prev); work: 4*nshots*nx*ny*nz floats of scratch."""
-    a2, a1 = _host_coeffs(w2), _host_coeffs(w1)
-    if a2.size != 2 * desc.radius + 1 or a1.size != 2 * desc.radius + 1:
-        raise ValueError("w2 and w1 need 2r+1 weights each")
+    x = _WaveExtent(desc)
+    a2, a1 = _host_coeffs(w2, 2 * desc.radius + 1), _host_coeffs(w1, 2 * desc.radius + 1)
+    _need(med, "med", nbytes=8 * x.dense, dense=True)
+    for t, name in ((p_cur, "p_cur"), (q_cur, "q_cur"), (p_prev, "p_prev"), (q_prev, "q_prev"),
+                    (p_next, "p_next"), (q_next, "q_next")):
+        _need(t, name, nbytes=x.field)
+    _need(work, "work", nbytes=4 * desc.nshots * x.dense if x.ok else 0, dense=True)
+    _need(src_amp, "src_amp", nbytes=x.amp)
+    _need(rec, "rec", nbytes=x.rec, required=False)
     check(load().mms_tti_step(ctypes.byref(desc), a2.ctypes.data_as(ctypes.c_void_p),
                               a1.ctypes.data_as(ctypes.c_void_p), _ptr(med), _ptr(p_cur), _ptr(q_cur),
                               _ptr(p_prev), _ptr(q_prev), _ptr(p_next), _ptr(q_next), _ptr(work), _ptr(src_amp),
@@ -464,8 +642,13 @@ def aniso_set_variant(kind, variant):
 def sum_f64(slices, out, stream=None):
     """out = slices.sum(0) in FP64 (mms_sum_f64); slices (k, ...) contiguous,
     out a tensor of the slice shape (may be slices[0])."""
+    _need(slices, "slices", _f64())
     k = slices.shape[0]
     n = slices[0].numel()
+    if not slices[0].is_contiguous():
+        raise ArgumentError("each slice must be contiguous")
+    _need(slices, "slices", _f64(), nbytes=8 * ((k - 1) * slices.stride(0) + n))
+    _need(out, "out", _f64(), nbytes=8 * n, dense=True)
     check(load().mms_sum_f64(_ptr(slices), int(k), slices.stride(0), n, _ptr(out), _stream(stream)))
     return out
 
@@ -478,4 +661,9 @@ def selftest_timeout(limit_us, stream=None):
 
 
 def dot_f64(a, b, result, stream=None):
+    _need(a, "a", dense=True)
+    _need(b, "b", nbytes=4 * a.numel(), dense=True)
+    if b.numel() != a.numel():
+        raise ArgumentError(f"a has {a.numel()} values, b {b.numel()}")
+    _need(result, "result", _f64(), nbytes=8)
     check(load().mms_dot_f64(_ptr(a), _ptr(b), a.numel(), _ptr(result), _stream(stream)))

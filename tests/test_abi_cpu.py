@@ -247,3 +247,21 @@ def test_wave_outputs_may_not_alias_their_inputs(lib):
     refused(lib.mms_grad_to_velocity(P(gp), x, x, n, ctypes.c_float(1e-3), ctypes.c_float(10.0), None),
             b"grad_v overlaps v")
     refused(lib.mms_dot_f64(x, y, n, x, None), b"result overlaps")
+
+
+def test_tti_work_and_outputs_may_not_alias(lib):
+    P = ctypes.c_void_p
+    nx, ny, nz, r = 10, 8, 8, 1
+    d, _src = _lib.wave_desc(nx, ny, nz, r, 1)
+    n = nx * ny * nz
+    size = max((nz + 2 * r) * (ny + 2 * r) * (nx + 2 * r), 8 * n)
+    bufs = [np.zeros(size + 16, np.float32) for _ in range(8)]
+    med, pc, qc, pp, qp, pn, qn, work = [ctypes.c_void_p((b.ctypes.data + 15) & ~15) for b in bufs]
+    w = np.ones(3, np.float32).ctypes.data_as(P)
+    amp = np.zeros(1, np.float32).ctypes.data_as(P)
+    assert lib.mms_tti_step(ctypes.byref(d), w, w, med, pc, qc, pp, qp, pn, qn, pn, amp, None, None) == 1
+    assert b"work overlaps" in lib.mms_last_error()
+    assert lib.mms_tti_step(ctypes.byref(d), w, w, med, pc, qc, pp, qp, pn, pn, work, amp, None, None) == 1
+    assert b"overlap" in lib.mms_last_error()
+    assert lib.mms_tti_step(ctypes.byref(d), w, w, med, pc, qc, pp, qp, med, qn, work, amp, None, None) == 1
+    assert b"med" in lib.mms_last_error()

@@ -168,9 +168,10 @@ def test_vti_refuses_overlaps_and_bad_alignment():
         mms.vti_step(s.desc, s.cf, s.mv, s.rho, hc, vc, hp, vp, hn, hn, s.amps[0])
     with pytest.raises(mms.MMSError):
         mms.vti_step(s.desc, s.cf, s.mv, s.rho, hc, vc, hp, vp, vp, vn, s.amps[0])   # next over the other prev
-    flat = torch.zeros(hc.numel() + 4, device="cuda")
-    mis = flat[1:1 + hc.numel()].view(hc.shape)
-    with pytest.raises(mms.MMSError):
+    # a field one float off the 16-byte grid, with room for its whole geometry
+    flat = torch.zeros(hc.untyped_storage().nbytes() // 4 + 4, device="cuda")
+    mis = torch.as_strided(flat, hc.shape, hc.stride(), 1)
+    with pytest.raises(mms.MMSError, match="E_ALIGN"):
         mms.vti_step(s.desc, s.cf, s.mv, s.rho, mis, vc, hp, vp, hn, vn, s.amps[0])
 
 
