@@ -49,8 +49,7 @@ def tune(shape, r, path, nx, ny, nz, coeffs=None, reps=10, table=TABLE, write=Tr
     inp.uniform_(-1, 1, generator=torch.Generator(device=dev).manual_seed(seed))
     out = torch.empty((nz, ny, nx), device=dev)
     if coeffs is None:
-        w = 2 * r + 1
-        n = {"star": 3 * w, "box": w ** 3, "star2d": 2 * w, "box2d": w * w}[shape]
+        n = _lib.n_coeffs(shape, r)
         coeffs = np.random.default_rng(seed).normal(0, n ** -0.5, n).astype(np.float32)
     ms = time_variants(shape, r, path, inp, out, coeffs, reps=reps)
     best = int(min(range(len(ms)), key=lambda i: ms[i]))
@@ -90,7 +89,8 @@ def tune_auto(shape, r, nx, ny, nz, reps=10, table=TABLE, seed=0):
 
 def load_table(table=TABLE, n=None):
     """Register the recorded best variants for this GPU (largest grid wins
-    when several sizes were tuned, unless n = (nx, ny, nz) picks one)."""
+    when several sizes were tuned, unless n = (nx, ny, nz) picks one);
+    returns {(shape, r, path): variant} of what it registered."""
     import torch
     if not os.path.exists(table):
         return {}
@@ -108,7 +108,10 @@ def load_table(table=TABLE, n=None):
         vol = dims[0] * dims[1] * dims[2]
         if key not in chosen or vol > chosen[key][0]:
             chosen[key] = (vol, v["variant"])
+    registered = {}
     for (shape, r, path), (_, var) in chosen.items():
+        # a table written by a build with more variants than this one is skipped
         if var < _lib.num_variants(shape, r, path):
             _lib.set_variant(shape, r, path, var)
-    return {k: v[1] for k, v in chosen.items()}
+            registered[(shape, r, path)] = var
+    return registered
