@@ -230,7 +230,7 @@ mms_status mms_stencil_apply_f64(const mms_stencil_desc *desc, const double *coe
 typedef struct {
     int64_t nx, ny, nz;        /* interior */
     int32_t radius;            /* 1..4 */
-    int32_t nshots;            /* >= 1 */
+    int32_t nshots;            /* 1..64 */
     int64_t pitch_y, pitch_z;  /* padded field pitches (elements), 0 = dense */
     int64_t shot_stride;       /* elements between shots, 0 = pitch_z*(nz+2r) */
     int32_t sponge_width;      /* w >= 0 (0 = no sponge) */
