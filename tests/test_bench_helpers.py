@@ -1,6 +1,7 @@
 """bench.py's bookkeeping on CPU: the traffic of a committed ncu capture is
 used only while the kernel's code is the one captured (a comment-insensitive
-hash), and the roofline helpers count what they say."""
+hash), the roofline helpers count what they say, and the reference arm (the
+oracle on the host cores) prints the contract's JSON line on rank 0 only."""
 import json
 import os
 
@@ -59,3 +60,32 @@ def test_tensor_core_dense_work_per_point():
 def test_job_rate_and_fp32_peak():
     assert bench.job_rate(4, 1e9, 2.0) == pytest.approx(2.0)
     assert bench.fp32_alu_peak_tflops(152, 2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+
+
+@pytest.mark.parametrize("workload", ["box512", "rtm512", "vti512"])
+def test_reference_arm_prints_the_contract_line(workload):
+    # the oracle on the host cores, on tiny samples (MMS_REF_STEP_SECONDS)
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ, MMS_REF_STEP_SECONDS="0.05", OMP_NUM_THREADS="2")
+    cmd = [sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--workload", workload,
+           "--steps", "2", "--warmup", "3"]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["dtype"] == "f64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
+    assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] and "model" not in d["config"]
+    # other ranks of a torchrun launch exit quietly
+    out = subprocess.run(cmd, env=dict(env, RANK="1", WORLD_SIZE="2"), capture_output=True, text=True,
+                         timeout=120, cwd=bench.ROOT)
+    assert out.returncode == 0 and not out.stdout.strip()
