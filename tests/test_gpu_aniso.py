@@ -7,7 +7,6 @@ for one step (FP32 arithmetic over at most 2 x 17 terms per point).
 import numpy as np
 import pytest
 
-import oracle
 from oracle import aniso
 import paper_2507_11067_gb300 as mms
 import workloads
