@@ -554,7 +554,7 @@ extern "C" {
 mms_status mms_wave_step(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *p_cur,
                          float *p_prev, const float *src_amp, float *rec, void *stream)
 {
-    WaveGeo g;
+    WaveGeo g{};
     mms_status st = wave_geo(desc, coeffs, &g);
     if (st != MMS_OK) return st;
     if (!m || !p_cur || !p_prev || !src_amp) return fail(MMS_E_ARG, "null field pointer");
@@ -571,7 +571,7 @@ mms_status mms_wave_step(const mms_wave_desc *desc, const float *coeffs, const f
 mms_status mms_wave_step_to(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *p_cur,
                             const float *p_prev, float *p_next, const float *src_amp, float *rec, void *stream)
 {
-    WaveGeo g;
+    WaveGeo g{};
     mms_status st = wave_geo(desc, coeffs, &g);
     if (st != MMS_OK) return st;
     if (!m || !p_cur || !p_prev || !p_next || !src_amp) return fail(MMS_E_ARG, "null field pointer");
@@ -594,7 +594,7 @@ mms_status mms_wave_forward(const mms_wave_desc *desc, const float *coeffs, cons
                             int32_t nsteps, float *p0, float *p1, float *rec_all, float *ckpt, int32_t ckpt_every,
                             uint32_t flags, void *stream)
 {
-    WaveGeo g;
+    WaveGeo g{};
     mms_status st = wave_geo(desc, coeffs, &g);
     if (st != MMS_OK) return st;
     if (nsteps < 0) return fail(MMS_E_ARG, "negative step count");
@@ -693,7 +693,7 @@ static mms_status wave_adjoint(const mms_wave_desc *desc, const float *coeffs, c
                                float *lam_prev, const float *resid, const float *a_n, double *grad_m, void *stream,
                                bool lapin)
 {
-    WaveGeo g;
+    WaveGeo g{};
     mms_status st = wave_geo(desc, coeffs, &g);
     if (st != MMS_OK) return st;
     if (!m || !lam_cur || !lam_prev) return fail(MMS_E_ARG, "null field pointer");
@@ -733,7 +733,7 @@ mms_status mms_wave_step_lap(const mms_wave_desc *desc, const float *coeffs, con
                              const float *p_prev, float *p_next, float *lap_out, const float *src_amp, float *rec,
                              void *stream)
 {
-    WaveGeo g;
+    WaveGeo g{};
     mms_status st = wave_geo(desc, coeffs, &g);
     if (st != MMS_OK) return st;
     if (!m || !p_cur || !p_prev || !p_next || !lap_out || !src_amp) return fail(MMS_E_ARG, "null field pointer");
@@ -758,7 +758,7 @@ mms_status mms_wave_step_lap(const mms_wave_desc *desc, const float *coeffs, con
 mms_status mms_vti_model(const mms_wave_desc *desc, const float *vp, const float *eps, const float *delta,
                          float *mv, float *rho, float dt, float h, void *stream)
 {
-    WaveGeo g;
+    WaveGeo g{};
     static const float dummy[27] = {0};
     mms_status st = wave_geo(desc, dummy, &g);
     if (st != MMS_OK) return st;
@@ -778,7 +778,7 @@ mms_status mms_vti_step(const mms_wave_desc *desc, const float *coeffs, const fl
                         const float *sh_cur, const float *sv_cur, const float *sh_prev, const float *sv_prev,
                         float *sh_next, float *sv_next, const float *src_amp, float *rec, void *stream)
 {
-    WaveGeo g;
+    WaveGeo g{};
     mms_status st = wave_geo(desc, coeffs, &g);
     if (st != MMS_OK) return st;
     if (!mv || !rho || !sh_cur || !sv_cur || !sh_prev || !sv_prev || !sh_next || !sv_next || !src_amp)
@@ -813,7 +813,7 @@ mms_status mms_tti_model(const mms_wave_desc *desc, const float *vp, const float
                          const float *delta, const float *alpha, const float *theta, const float *phi,
                          float *med, float dt, float h, void *stream)
 {
-    WaveGeo g;
+    WaveGeo g{};
     static const float dummy[27] = {0};
     mms_status st = wave_geo(desc, dummy, &g);
     if (st != MMS_OK) return st;
@@ -832,7 +832,7 @@ mms_status mms_tti_step(const mms_wave_desc *desc, const float *w2, const float 
                         const float *p_cur, const float *q_cur, const float *p_prev, const float *q_prev,
                         float *p_next, float *q_next, float *work, const float *src_amp, float *rec, void *stream)
 {
-    WaveGeo g;
+    WaveGeo g{};
     static const float dummy[27] = {0};
     mms_status st = wave_geo(desc, dummy, &g);
     if (st != MMS_OK) return st;
@@ -881,7 +881,7 @@ mms_status mms_aniso_set_variant(int32_t kind, int32_t variant)
 mms_status mms_model_from_velocity(const mms_wave_desc *desc, const float *v, float *m, float dt, float h,
                                    void *stream)
 {
-    WaveGeo g;
+    WaveGeo g{};
     static const float dummy[27] = {0};
     mms_status st = wave_geo(desc, dummy, &g);
     if (st != MMS_OK) return st;
