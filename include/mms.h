@@ -28,6 +28,10 @@
  *     out(x,y,z) = sum_d c_d * in(x+r+dx, y+r+dy, z+r+dz)
  * over the stencil's offsets d.  Pitches are in elements; 0 selects the
  * dense value (in: nx+2r and (ny+2r)*pitch_y; out: nx and ny*pitch_y).
+ * Sizes are below 2^30 per axis; a pitch or stride that is negative, or
+ * that spans more than 2^46 elements (rows * pitch_y, planes * pitch_z,
+ * shots * shot_stride), is refused with MMS_E_ARG before any extent is
+ * computed from it.
  */
 #ifndef MMS_H
 #define MMS_H

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "validate.cuh"
 #include "wave.cuh"
 
 namespace mms {
@@ -153,10 +154,10 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
     if (!in || !out) return fail(MMS_E_ARG, "null grid pointer");
     // planar shapes: nz independent planes, padded in x and y only
     const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + (is_planar(shape) ? 0 : 2 * r);
-    const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
-    const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
-    const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
-    const int64_t opz = d->out_pitch_z ? d->out_pitch_z : d->ny * opy;
+    int64_t ipy, ipz, opy, opz;
+    if (!resolve_pitches(X, Y, Z, d->in_pitch_y, d->in_pitch_z, &ipy, &ipz) ||
+        !resolve_pitches(d->nx, d->ny, d->nz, d->out_pitch_y, d->out_pitch_z, &opy, &opz))
+        return fail(MMS_E_ARG, "pitches not positive or spanning more than 2^46 elements");
     if (ipy < X || ipz < Y * ipy) return fail(MMS_E_ARG, "input pitches (%lld, %lld) below the padded extents", (long long)ipy, (long long)ipz);
     if (opy < d->nx || opz < d->ny * opy) return fail(MMS_E_ARG, "output pitches (%lld, %lld) below the interior extents", (long long)opy, (long long)opz);
     const size_t in_bytes = (size_t)((Z - 1) * ipz + (Y - 1) * ipy + X) * 4;
@@ -244,10 +245,10 @@ static mms_status apply_f64(const mms_stencil_desc *d, const double *coeffs, con
     if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 8)
         return fail(MMS_E_ALIGN, "FP64 grids must be 8-byte aligned");
     const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + (is_planar(shape) ? 0 : 2 * r);
-    const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
-    const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
-    const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
-    const int64_t opz = d->out_pitch_z ? d->out_pitch_z : d->ny * opy;
+    int64_t ipy, ipz, opy, opz;
+    if (!resolve_pitches(X, Y, Z, d->in_pitch_y, d->in_pitch_z, &ipy, &ipz) ||
+        !resolve_pitches(d->nx, d->ny, d->nz, d->out_pitch_y, d->out_pitch_z, &opy, &opz))
+        return fail(MMS_E_ARG, "pitches not positive or spanning more than 2^46 elements");
     if (ipy < X || ipz < Y * ipy) return fail(MMS_E_ARG, "input pitches (%lld, %lld) below the padded extents", (long long)ipy, (long long)ipz);
     if (opy < d->nx || opz < d->ny * opy) return fail(MMS_E_ARG, "output pitches (%lld, %lld) below the interior extents", (long long)opy, (long long)opz);
     const size_t in_bytes = (size_t)((Z - 1) * ipz + (Y - 1) * ipy + X) * 8;
@@ -280,10 +281,10 @@ static mms_status apply_host(const mms_stencil_desc *d, const float *in, float *
     if (d->nx == 0 || d->ny == 0 || d->nz == 0) return MMS_OK;
     if (!in || !out) return fail(MMS_E_ARG, "null grid pointer");
     const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * rz;
-    const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
-    const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
-    const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
-    const int64_t opz = d->out_pitch_z ? d->out_pitch_z : d->ny * opy;
+    int64_t ipy, ipz, opy, opz;
+    if (!resolve_pitches(X, Y, Z, d->in_pitch_y, d->in_pitch_z, &ipy, &ipz) ||
+        !resolve_pitches(d->nx, d->ny, d->nz, d->out_pitch_y, d->out_pitch_z, &opy, &opz))
+        return fail(MMS_E_ARG, "pitches not positive or spanning more than 2^46 elements");
     if (ipy < X || ipz < Y * ipy) return fail(MMS_E_ARG, "input pitches below the padded extents");
     if (opy < d->nx || opz < d->ny * opy) return fail(MMS_E_ARG, "output pitches below the interior extents");
     if (ipy % 4 || ipz % 4) return fail(MMS_E_ALIGN, "host input pitches must be multiples of 4 floats");
@@ -480,9 +481,11 @@ static mms_status wave_geo(const mms_wave_desc *d, const float *coeffs, WaveGeo 
     const int r = d->radius;
     const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * r;
     g->nx = (int)d->nx; g->ny = (int)d->ny; g->nz = (int)d->nz; g->r = r; g->nshots = d->nshots;
-    g->py = d->pitch_y ? d->pitch_y : X;
-    g->pz = d->pitch_z ? d->pitch_z : Y * g->py;
+    if (!resolve_pitches(X, Y, Z, d->pitch_y, d->pitch_z, &g->py, &g->pz))
+        return fail(MMS_E_ARG, "field pitches not positive or spanning more than 2^46 elements");
     g->ss = d->shot_stride ? d->shot_stride : Z * g->pz;
+    if (g->ss <= 0 || g->ss > kMaxSpan / d->nshots)
+        return fail(MMS_E_ARG, "shot stride not positive or spanning more than 2^46 elements");
     if (g->py < X || g->pz < Y * g->py || g->ss < Z * g->pz) return fail(MMS_E_ARG, "field pitches below the padded extents");
     if (g->py % 4 || g->pz % 4 || g->ss % 4)
         return fail(MMS_E_ALIGN, "wave fields need pitches and shot stride that are multiples of 4 floats");
@@ -490,6 +493,8 @@ static mms_status wave_geo(const mms_wave_desc *d, const float *coeffs, WaveGeo 
     g->sponge_a = d->sponge_a;
     g->rec_z = d->rec_z;
     g->gss = d->grad_shot_stride;
+    if (g->gss > kMaxSpan / d->nshots)
+        return fail(MMS_E_ARG, "gradient shot stride spans more than 2^46 elements");
     if (g->gss != 0 && g->gss < d->nx * d->ny * d->nz)
         return fail(MMS_E_ARG, "gradient shot stride %lld below the interior size", (long long)g->gss);
     for (int s = 0; s < d->nshots; ++s) {
@@ -912,6 +917,8 @@ mms_status mms_sum_f64(const double *slices, int32_t nslices, int64_t stride, in
 {
     if (n < 0) return fail(MMS_E_ARG, "negative length");
     if (nslices < 1) return fail(MMS_E_ARG, "nslices %d below 1", nslices);
+    if (n > kMaxSpan || (nslices > 1 && stride > kMaxSpan / nslices))
+        return fail(MMS_E_ARG, "slices spanning more than 2^46 elements");
     if (nslices > 1 && stride < n) return fail(MMS_E_ARG, "slice stride %lld below the length", (long long)stride);
     if (n == 0) return MMS_OK;
     if (!slices || !out) return fail(MMS_E_ARG, "null pointer");

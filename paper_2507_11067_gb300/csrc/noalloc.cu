@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "validate.cuh"
 
 namespace mms {
 
@@ -71,18 +72,17 @@ static mms_status apply_noalloc(const mms_stencil_desc *d, const float *in, floa
         return fail(MMS_E_UNSUPPORTED, "the no-alloc sweep runs on tensor-core paths only (path %d)", d->path);
     if (d->variant < -1) return fail(MMS_E_ARG, "variant %d", d->variant);
     if (d->nx == 0 || d->ny == 0 || d->nz == 0) return MMS_OK;
-    const int64_t points = d->nx * d->ny * d->nz;
-    if (points > (int64_t)MMS_NOALLOC_MAX_POINTS)
-        return fail(MMS_E_ARG,
-                    "interior of %lld x %lld x %lld = %lld points is above the no-alloc limit of %lld points",
-                    (long long)d->nx, (long long)d->ny, (long long)d->nz, (long long)points,
-                    (long long)MMS_NOALLOC_MAX_POINTS);
+    // nx*ny*nz <= limit, compared by division (the product of sizes up to
+    // 2^30 each does not fit 64 bits)
+    if (d->nx > (int64_t)MMS_NOALLOC_MAX_POINTS / d->ny / d->nz)
+        return fail(MMS_E_ARG, "interior of %lld x %lld x %lld points is above the no-alloc limit of %lld points",
+                    (long long)d->nx, (long long)d->ny, (long long)d->nz, (long long)MMS_NOALLOC_MAX_POINTS);
     if (!in || !out) return fail(MMS_E_ARG, "null grid pointer");
     const int64_t X = d->nx + 2 * r, Y = d->ny + 2 * r, Z = d->nz + 2 * r;
-    const int64_t ipy = d->in_pitch_y ? d->in_pitch_y : X;
-    const int64_t ipz = d->in_pitch_z ? d->in_pitch_z : Y * ipy;
-    const int64_t opy = d->out_pitch_y ? d->out_pitch_y : d->nx;
-    const int64_t opz = d->out_pitch_z ? d->out_pitch_z : d->ny * opy;
+    int64_t ipy, ipz, opy, opz;
+    if (!resolve_pitches(X, Y, Z, d->in_pitch_y, d->in_pitch_z, &ipy, &ipz) ||
+        !resolve_pitches(d->nx, d->ny, d->nz, d->out_pitch_y, d->out_pitch_z, &opy, &opz))
+        return fail(MMS_E_ARG, "pitches not positive or spanning more than 2^46 elements");
     if (ipy < X || ipz < Y * ipy)
         return fail(MMS_E_ARG, "input pitches (%lld, %lld) below the padded extents", (long long)ipy, (long long)ipz);
     if (opy < d->nx || opz < d->ny * opy)

@@ -54,6 +54,9 @@ def _desc(**kw):
 @pytest.mark.parametrize("kw,status", [
     (dict(radius=0), 1), (dict(radius=5), 1), (dict(shape=9), 1), (dict(shape=-1), 1), (dict(nx=-1), 1),
     (dict(path=9), 1), (dict(ipy=3), 1), (dict(opy=2), 1), (dict(variant=-2), 1),
+    # pitches whose products would leave 64 bits, or negative ones
+    (dict(ipy=1 << 62), 1), (dict(ipz=1 << 62), 1), (dict(opy=1 << 61), 1), (dict(opz=-16), 1),
+    (dict(ipy=-12), 1), (dict(nx=(1 << 30) - 1, ny=(1 << 30) - 1, nz=(1 << 30) - 1), 1),
 ])
 def test_argument_validation(lib, kw, status):
     d, c = _desc(**kw)
@@ -265,3 +268,23 @@ def test_tti_work_and_outputs_may_not_alias(lib):
     assert b"overlap" in lib.mms_last_error()
     assert lib.mms_tti_step(ctypes.byref(d), w, w, med, pc, qc, pp, qp, med, qn, work, amp, None, None) == 1
     assert b"med" in lib.mms_last_error()
+
+
+def test_spans_beyond_any_device_are_refused(lib):
+    # every caller-given pitch and stride is bounded before a product of it
+    # is formed (2^46 elements), so no extent check can wrap around
+    c = np.zeros(27, np.float32)
+    P = ctypes.c_void_p
+    buf = ctypes.create_string_buffer(1 << 12)
+    for kw in (dict(pitch_y=1 << 62), dict(pitch_z=1 << 62), dict(shot_stride=1 << 62), dict(pitch_y=-16),
+               dict(grad_shot_stride=1 << 62)):
+        d, _s = mms.wave_desc(8, 8, 8, 4, 2, **kw)
+        assert lib.mms_wave_step(ctypes.byref(d), c.ctypes.data, buf, buf, buf, buf, None, None) == 1, kw
+        assert b"2^46" in lib.mms_last_error(), kw
+    d, _ = _desc(ipy=1 << 62)
+    assert lib.mms_stencil_apply_host(ctypes.byref(d), buf, buf, None) == 1
+    assert lib.mms_stencil_apply_f64(ctypes.byref(d), c.ctypes.data_as(P), buf, buf, None) == 1
+    assert b"2^46" in lib.mms_last_error()
+    assert lib.mms_sum_f64(buf, 4, 1 << 62, 8, buf, None) == 1
+    assert b"2^46" in lib.mms_last_error()
+    assert lib.mms_sum_f64(buf, 1, 0, 1 << 62, buf, None) == 1

@@ -33,6 +33,7 @@ def _desc(c, **kw):
 @pytest.mark.parametrize("kw,status", [
     (dict(nx=256, ny=256, nz=129), 1),      # one plane above the limit
     (dict(nx=4096, ny=4096, nz=1), 1),      # 2x the limit
+    (dict(nx=(1 << 30) - 1, ny=(1 << 30) - 1, nz=(1 << 30) - 1), 1),   # a product beyond 64 bits
     (dict(shape=1), 2),                     # box: needs no temporary grid
     (dict(path=1), 2),                      # CUDA-core path
     (dict(path=5), 2),                      # naive path
