@@ -288,3 +288,25 @@ def test_spans_beyond_any_device_are_refused(lib):
     assert lib.mms_sum_f64(buf, 4, 1 << 62, 8, buf, None) == 1
     assert b"2^46" in lib.mms_last_error()
     assert lib.mms_sum_f64(buf, 1, 0, 1 << 62, buf, None) == 1
+
+
+def test_every_declaration_is_documented():
+    # each entry point of the header sits under a comment block (a group of
+    # consecutive declarations may share one)
+    lines = open(os.path.join(ROOT, "include", "mms.h")).read().splitlines()
+    decl = re.compile(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(mms_[a-z0-9_]+)\s*\(")
+    seen = []
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        j = i - 1
+        while j >= 0 and not lines[j].strip():
+            j -= 1
+        # step back over the declarations of the same group
+        while j >= 0 and (lines[j].rstrip().endswith(");") or lines[j].startswith(" ")) \
+                and not lines[j].strip().endswith("*/"):
+            j -= 1
+        assert j >= 0 and lines[j].strip().endswith("*/"), m.group(1)
+        seen.append(m.group(1))
+    assert sorted(seen) == declared_symbols()
