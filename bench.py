@@ -183,20 +183,52 @@ def code_hash(path: str) -> str:
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
-# x outputs per tile of the tensor-core box kernel by radius; its MMA K is
-# that plus 2r, rounded up to the instruction K (16 for BF16, 8 for TF32).
-TC_TXO = {1: 40, 2: 24, 3: 16, 4: 12}
 TC_PATHS = ("tf32", "3xtf32", "bf16x3")
 
 
-def tc_dense_flop_per_pt(path: str, r: int, planar: bool = False) -> int:
+def tc_dense_flop_per_pt(path: str, r: int, planar: bool = False) -> float:
     """Dense work the banded MMAs issue per output point (band zeros
-    included): 2 K_pad per (dz, dy) pass, (2r+1)^2 passes ((2r+1) for a
-    planar stencil), times the split products (3 for 3xTF32 / BF16x3, 1 for
-    TF32)."""
-    step = 16 if path == "bf16x3" else 8
-    k_pad = -(-(TC_TXO[r] + 2 * r) // step) * step
-    return 2 * k_pad * (2 * r + 1) ** (1 if planar else 2) * (1 if path == "tf32" else 3)
+    included).  A tile of the tensor-core kernel is 4 x-subtiles of
+    TXO = 16 - 2r outputs by TY = 32 - 2r rows; per output plane it runs, for
+    each plane the stencil reaches in z ((2r+1) for the box, 1 for planar
+    stencils and the star's in-plane part), M = 128 lanes x N = (2r+1) TXO
+    (rounded up to 16) x K = 16 MMAs, times the split products (3 for
+    3xTF32 / BF16x3, 1 for TF32)."""
+    txo, ty, w = 16 - 2 * r, 32 - 2 * r, 2 * r + 1
+    n = -(-w * txo // 16) * 16
+    planes = 1 if planar else w
+    prods = 1 if path == "tf32" else 3
+    return 2.0 * 128 * n * 16 * planes * prods / (4 * txo * ty)
+
+
+def tc_roofline(shape: str, r: int, path: str, npts: int, bytes_alg: float, sec: float,
+                hbm_peak: float, bf16_peak: float, bf16_src: str) -> dict:
+    """Roofline of a tensor-core sweep on the stencil's own work: the slower
+    of its two floors, the algorithmic HBM bytes against the measured copy
+    bandwidth and its useful 2 flop per coefficient against the tensor peak
+    (BF16's; TF32 at the nominal ratio 1.1/2.25).  The banded MMAs' dense
+    work (band zeros and split products included) and its fraction of the
+    tensor peak go beside it."""
+    planar = shape in PLANAR
+    tpk = bf16_peak if path == "bf16x3" else bf16_peak * 1.1 / 2.25
+    useful = flop_per_pt(shape, r) * npts
+    dense = tc_dense_flop_per_pt(path, r, planar or shape == "star") * npts
+    t_hbm = bytes_alg / (hbm_peak * 1e9)
+    t_tc = useful / (tpk * 1e12)
+    if t_hbm >= t_tc:
+        roof = {"bound": "hbm", "achieved": bytes_alg / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": bytes_alg / sec / 1e9 / hbm_peak}
+    else:
+        roof = {"bound": "tensor", "achieved": useful / sec / 1e12, "peak": tpk, "unit": "TFLOP/s",
+                "frac": useful / sec / 1e12 / tpk}
+    roof["dense_tflops"] = dense / sec / 1e12
+    roof["tensor_pipe_frac"] = dense / sec / 1e12 / tpk
+    roof["peak_note"] = (f"bound = the slower floor of the stencil's own work: {bytes_alg / npts:.2f} B/pt over "
+                         f"MEASURED_PEAKS.json hbm_gbs, {flop_per_pt(shape, r)} flop/pt over bf16 ({bf16_src}"
+                         f"{'' if path == 'bf16x3' else ' x 1.1/2.25 (TF32)'}); dense_tflops counts the banded "
+                         f"MMAs' {tc_dense_flop_per_pt(path, r, planar or shape == 'star'):.0f} flop/pt "
+                         f"(band zeros and split products included)")
+    return roof
 
 
 def fp32_alu_peak_tflops(n_sm: int, mhz: float) -> float:
@@ -406,7 +438,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0,
-                    help="grid edge of the anisotropic workloads (0 = the workload's own 512; smaller for profiling)")
+                    help="grid edge (0 = the workload's own; smaller for profiling captures); not for rtm512 or grad256")
     ap.add_argument("--shots", type=int, default=0,
                     help="shots of the wave workloads (0 = the workload's own: 8 for rtm512, 2 for grad256)")
     args = ap.parse_args()
@@ -442,6 +474,8 @@ def main():
     from paper_2507_11067_gb300 import tune
     tune.load_table()
     plan = WORKLOADS[args.workload]
+    if args.n:   # a smaller grid of the same sweeps (profiling captures)
+        plan = [(shape, r, args.n) for shape, r, _ in plan]
     coeffs, inputs, outputs, hosts, host_out = [], [], [], [], []
     for (shape, r, n) in plan:
         coeffs.append(sweep_coeffs(shape, r))
@@ -545,19 +579,9 @@ def main():
     bytes_alg = sweep_bytes(shape, r, n)
     flops = flop_per_pt(shape, r) * npts
     resolved = mms.auto_path(shape, r) if path_used == "auto" else path_used
-    if resolved in TC_PATHS and shape != "star":
-        # tensor pipe: the banded products' dense work against the BF16 peak
-        # (TF32 at the nominal TF32/BF16 ratio 1.1/2.25)
+    if resolved in TC_PATHS:
         tpk, tsrc = bf16_sustained_peak()
-        if resolved != "bf16x3":
-            tpk, tsrc = tpk * 1.1 / 2.25, tsrc + " x 1.1/2.25 (TF32)"
-        dense = tc_dense_flop_per_pt(resolved, r, shape in PLANAR) * npts
-        roofline = {"bound": "tensor", "achieved": dense / sec / 1e12, "peak": tpk, "unit": "TFLOP/s",
-                    "frac": dense / sec / 1e12 / tpk, "traffic": None,
-                    "peak_note": f"MEASURED_PEAKS.json bf16 ({tsrc}); achieved counts the banded MMAs' "
-                                 f"dense work, {tc_dense_flop_per_pt(resolved, r, shape in PLANAR)} flop/pt (band zeros "
-                                 f"included); the stencil's own {flop_per_pt(shape, r)} flop/pt run at "
-                                 f"{flops / sec / 1e12:.1f} TFLOP/s"}
+        roofline = tc_roofline(shape, r, resolved, npts, bytes_alg, sec, hbm_peak, tpk, tsrc)
     elif flops / bytes_alg > alu_peak * 1e12 / (hbm_peak * 1e9):
         roofline = {"bound": "alu", "achieved": flops / sec / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": flops / sec / 1e12 / alu_peak, "traffic": None,
@@ -602,7 +626,8 @@ def main():
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAMES[args.workload], "path": path_used,
+        "config": {"workload": WORKLOAD_NAMES[args.workload] + (f" at grid edge {args.n}" if args.n else ""),
+                   "path": path_used,
                    "sweeps": [f"{sh} r={r} {n}^{2 if sh in PLANAR else 3}" for sh, r, n in plan],
                    "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -63,7 +63,7 @@ typedef enum {
 
 /* Computation paths of a sweep. */
 typedef enum {
-    MMS_PATH_AUTO = 0,       /* library choice (the fastest path meeting FP32-level accuracy) */
+    MMS_PATH_AUTO = 0,       /* library choice: the tuned path meeting FP32-level accuracy (mms_auto_path) */
     MMS_PATH_CUDA_CORE = 1,  /* FP32 FMA on CUDA cores, TMA-staged plane tiles */
     MMS_PATH_TF32 = 2,       /* tensor cores, one TF32 product (reduced accuracy) */
     MMS_PATH_3XTF32 = 3,     /* tensor cores, TF32 hi/lo split, 3 products, FP32 accumulate */
@@ -122,10 +122,14 @@ typedef struct {
  * multiples of 16 bytes and `in` 16-byte aligned; with MMS_PATH_AUTO an
  * input that breaks this runs on MMS_PATH_NAIVE, with a forced TMA path it
  * returns MMS_E_ALIGN.  Tensor-core paths support the box and the star of
- * radius 1..4.  The star runs in two passes: its in-plane x/y part on the
- * tensor cores into a temporary grid of nx*ny*nz floats, taken from the
- * device's stream-ordered memory pool (cudaMallocAsync on `stream`, freed on
- * it after use), then its z part on the CUDA cores.
+ * radius 1..4.  The star's variants come in two forms.  The first half
+ * (the library's choice) sweep it in one pass: the in-plane x/y part as
+ * banded tensor-core products, the 2r z terms as FP32 multiply-adds on the
+ * centre column of each staged plane, summed in the same kernel.  The
+ * second half run two passes: the x/y part on the tensor cores into a
+ * temporary grid of nx*ny*nz floats taken from the device's stream-ordered
+ * memory pool (cudaMallocAsync on `stream`, freed on it after use), then
+ * the z part on the CUDA cores.
  * Defined by: paper Sec. 1, Sec. 4.1 (banded products), Sec. 4.3 (box as
  * 2r+1 shifted 1D stencils per plane).
  */
@@ -154,7 +158,16 @@ mms_status mms_stencil_apply_host(const mms_stencil_desc *desc, const float *hos
 
 /* The path MMS_PATH_AUTO takes for (shape, radius) on an input that does
  * (tma_aligned = 1) or does not (0) meet the TMA alignment rule above;
- * -1 for an invalid shape or radius.  Host only. */
+ * -1 for an invalid shape or radius.  AUTO takes the tensor cores (BF16x3,
+ * FP32-level accuracy) where a tuned BF16x3 variant exists for (shape,
+ * radius): registered with mms_set_variant, or in the library's built-in
+ * table for the current device.  The built-in table is the autotuner's
+ * measurements compiled into the library: on a device whose name is that of
+ * the GPU the table was tuned on, it gives every (shape, radius, path) its
+ * measured best variant, and it holds a BF16x3 row only where that path beat
+ * the CUDA cores.  Elsewhere AUTO takes the TMA CUDA-core path (the naive
+ * path for unaligned input).  Host only; the first call on a device reads
+ * the device's name (cudaGetDeviceProperties). */
 int32_t mms_auto_path(int shape, int radius, int tma_aligned);
 
 /* Number of tile variants of (shape, radius, path); variant indices run
@@ -162,14 +175,18 @@ int32_t mms_auto_path(int shape, int radius, int tma_aligned);
 int32_t mms_num_variants(int shape, int radius, int path);
 
 /* Library choice of variant for (shape, radius, path, nx, ny, nz): the one
- * registered by mms_set_variant, else variant 0; -1 for an unsupported
+ * registered by mms_set_variant, else the built-in table's row for the
+ * current device (see mms_auto_path), else variant 0; -1 for an unsupported
  * combination.  The choice does not depend on the sizes at present (they are
  * in the signature so that a size-dependent table needs no ABI change).
  * Host only. */
 int32_t mms_default_variant(int shape, int radius, int path, int64_t nx, int64_t ny, int64_t nz);
 
 /* Record a tuned variant for (shape, radius, path); used by MMS_PATH_AUTO
- * and variant -1 from then on in this process.  variant -1 clears it. */
+ * and variant -1 from then on in this process, in place of the built-in
+ * table.  variant -1 clears it: (shape, radius, path) then has no tuned
+ * variant (variant 0; AUTO keeps a cleared BF16x3 path off), the built-in
+ * row included. */
 mms_status mms_set_variant(int shape, int radius, int path, int32_t variant);
 
 /* Largest interior (nx*ny*nz points) of mms_stencil_apply_noalloc: its
@@ -182,18 +199,23 @@ mms_status mms_set_variant(int shape, int radius, int path, int32_t variant);
  * allocation.  The paper has no counterpart: it is for callers that cannot
  * call cudaMalloc or a stream-ordered allocator (a host whose device memory
  * is all reserved for its own allocator, a plugin with a fixed footprint).
- * mms_stencil_apply_ex takes the star's temporary grid of nx*ny*nz floats
- * from the device's memory pool on each tensor-core call; this entry point
- * uses a file-scope device array of MMS_NOALLOC_MAX_POINTS floats instead,
- * which every GPU that loads the library holds until the process exits.
+ * It runs the star's two-pass form: where mms_stencil_apply_ex's two-pass
+ * variants take the temporary grid of nx*ny*nz floats from the device's
+ * memory pool, this entry point uses a file-scope device array of
+ * MMS_NOALLOC_MAX_POINTS floats, which every GPU that loads the library
+ * holds until the process exits.  (The single-pass variants of
+ * mms_stencil_apply_ex need no temporary grid at all.)  desc->variant picks
+ * the tile (-1 = the library's choice), always in the two-pass form.
  * Arguments, layouts and results are those of mms_stencil_apply_ex with
  * shape MMS_STAR; the caller still passes the input and output.
- * Set-up: the first call on each device (current device at the call) looks
- * the array's device address up with cudaGetSymbolAddress; make that first
- * call outside any stream capture.
- * Errors: MMS_E_ARG for nx*ny*nz above MMS_NOALLOC_MAX_POINTS (and the
- * checks of mms_stencil_apply_ex); MMS_E_UNSUPPORTED for the box shape or a
- * non-tensor-core path; MMS_E_ALIGN as for the forced TMA paths.
+ * Set-up: every call looks the array's device address up for the current
+ * device (cudaGetSymbolAddress); the first such lookup on a device loads
+ * the library's module there, so make the first call on each device
+ * outside any stream capture.
+ * Errors: MMS_E_ARG for nx*ny*nz above MMS_NOALLOC_MAX_POINTS, a path that
+ * is not an mms_path value or a variant beyond the two-pass ones (and the
+ * checks of mms_stencil_apply_ex); MMS_E_UNSUPPORTED for the box shape or
+ * a CUDA-core or naive path; MMS_E_ALIGN as for the forced TMA paths.
  * Sharing: every call on a device uses the same array and leaves its
  * contents behind; nothing in it needs to start at zero (each call writes
  * the part it reads).  Calls whose work overlaps on the GPU (other streams,

@@ -80,20 +80,88 @@ bool encode_tmap_4d(CUtensorMap *map, const float *base, int64_t X, int64_t Y, i
 }
 
 // ------------------------------------------------------- variant table
+// Registered variants (mms_set_variant): kUnset = none registered (the
+// built-in table below decides), kCleared = explicitly none, else the variant.
+constexpr int kUnset = -1, kCleared = -2;
 static std::mutex g_var_mu;
 static int g_tuned[4][kMaxR + 1][8];
 static bool g_tuned_init = false;
 
+// Built-in table: the autotuner's committed rows (tuned.json), compiled in
+// by build.py; a row applies on a device whose name is the row's GPU name.
+struct TunedRow {
+    const char *gpu;
+    int shape, r, path, variant;
+};
+#include "tuned_defaults.inc"
+
+constexpr int kMaxDevices = 64;
+static int g_dev_row_gpu[kMaxDevices];  // per device: 0 = unknown, 1 = no rows, 2 + i = rows of GPU name i
+static bool g_dev_init = false;
+
+// Index (into kTunedRows) of the first row whose GPU name is the current
+// device's, or -1 (no device, or no rows for it).  Looked up once per device.
+static int device_rows()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return -1;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_var_mu);
+        if (!g_dev_init) {
+            for (int &x : g_dev_row_gpu) x = 0;
+            g_dev_init = true;
+        }
+        if (g_dev_row_gpu[dev] != 0) return g_dev_row_gpu[dev] - 2;
+    }
+    int found = -1;
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
+        for (size_t i = 0; i < sizeof(kTunedRows) / sizeof(kTunedRows[0]); ++i)
+            if (kTunedRows[i].shape >= 0 && strcmp(kTunedRows[i].gpu, p.name) == 0) {
+                found = (int)i;
+                break;
+            }
+    } else {
+        cudaGetLastError();
+    }
+    std::lock_guard<std::mutex> lk(g_var_mu);
+    g_dev_row_gpu[dev] = found + 2;
+    return found;
+}
+
+static int builtin_variant(int shape, int r, int path)
+{
+    const int first = device_rows();
+    if (first < 0) return -1;
+    const char *gpu = kTunedRows[first].gpu;
+    for (size_t i = first; i < sizeof(kTunedRows) / sizeof(kTunedRows[0]); ++i) {
+        const TunedRow &t = kTunedRows[i];
+        if (strcmp(t.gpu, gpu) == 0 && t.shape == shape && t.r == r && t.path == path) return t.variant;
+    }
+    return -1;
+}
+
+// The tuned variant of (shape, r, path): the registered one, else the
+// built-in row for this device, else -1.
 static int tuned_variant(int shape, int r, int path)
 {
-    std::lock_guard<std::mutex> lk(g_var_mu);
-    if (!g_tuned_init) {
-        for (auto &a : g_tuned)
-            for (auto &b : a)
-                for (int &c : b) c = -1;
-        g_tuned_init = true;
+    int reg;
+    {
+        std::lock_guard<std::mutex> lk(g_var_mu);
+        if (!g_tuned_init) {
+            for (auto &a : g_tuned)
+                for (auto &b : a)
+                    for (int &c : b) c = kUnset;
+            g_tuned_init = true;
+        }
+        reg = g_tuned[shape][r][path];
     }
-    return g_tuned[shape][r][path];
+    if (reg >= 0) return reg;
+    if (reg == kCleared) return -1;
+    return builtin_variant(shape, r, path);
 }
 
 static int num_variants(int shape, int r, int path)
@@ -122,9 +190,10 @@ static bool tma_ok(const float *in, int64_t ipy, int64_t ipz)
     return (reinterpret_cast<uintptr_t>(in) % 16) == 0 && (ipy % 4) == 0 && (ipz % 4) == 0;
 }
 
-// AUTO: the tensor-core BF16x3 box path once a tuned variant for it is
-// registered (the autotuner does so only where it beats the CUDA-core path),
-// else the TMA CUDA-core path, else the naive path for unaligned pitches.
+// AUTO: the tensor-core BF16x3 path where a tuned variant for it exists
+// (the autotuner records one only where it beats the CUDA-core path; the
+// built-in table carries them for the GPUs it was tuned on), else the TMA
+// CUDA-core path, else the naive path for unaligned pitches.
 static int auto_path(int shape, int r, bool aligned)
 {
     if (!aligned) return MMS_PATH_NAIVE;
@@ -197,9 +266,10 @@ static mms_status apply(const mms_stencil_desc *d, const float *in, float *out, 
     band_tc_box(shape, r, path, v, &bx, &by, &bz, &swz);
     if (!encode_tmap_3d(&map, in, X, Y, Z, ipy, ipz, bx, by, bz, swz != 0))
         return fail(MMS_E_CUDA, "cuTensorMapEncodeTiled refused the input grid");
-    // The star's x/y partial sums go through a temporary grid (stream-ordered
-    // allocation from the device's default memory pool).
+    // The two-pass star's x/y partial sums go through a temporary grid
+    // (stream-ordered allocation from the device's default memory pool).
     float *scratch = nullptr;
+    s.variant = v;
     const size_t sb = band_tc_scratch_bytes(s);
     if (sb) {
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), sb, s.stream);
@@ -437,7 +507,7 @@ mms_status mms_set_variant(int shape, int radius, int path, int32_t variant)
         return fail(MMS_E_ARG, "variant %d out of range", variant);
     tuned_variant(shape, radius, path);  // initialises the table
     std::lock_guard<std::mutex> lk(g_var_mu);
-    g_tuned[shape][radius][path] = variant;
+    g_tuned[shape][radius][path] = variant >= 0 ? variant : kCleared;
     return MMS_OK;
 }
 

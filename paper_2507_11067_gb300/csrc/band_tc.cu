@@ -1,32 +1,48 @@
-// band_tc.cu -- box stencil sweeps on the tcgen05 tensor cores.
+// band_tc.cu -- stencil sweeps on the tcgen05 tensor cores.
 //
-// The paper (Sec. 4.1) turns a 1D stencil into an outer-product / matrix
-// product with a banded coefficient matrix, and (Sec. 4.3) a box stencil
-// into 2r+1 shifted 1D stencils.  On GB300 the contraction runs on tcgen05
-// MMAs, arranged so that the banded operand is small and sits in tensor
-// memory and the data operand is the wide one:
+// The paper (Sec. 4.1) turns the 1D stencil along x into a product with a
+// banded coefficient matrix, and (Sec. 4.3) a box stencil into 2r+1 shifted
+// 1D stencils per plane.  Here the products run on tcgen05 MMAs with the
+// grid ROWS on the 128 tensor-memory lanes:
 //
-//   D[(dy, x), line] += sum_k  Band_dz[(dy, x), k] * Data[k, line + dz*YP]
+//   D[row, (dy, x)] = sum_dz sum_k  A_{z+dz}[row, k] * B_dz[(dy, x), k]
+//   out[z][row][x]  = sum_dy D[row + dy, (dy, x)]
 //
-//  * M = 128 TMEM lanes hold (dy, x) pairs: 2r+1 row offsets dy times TXO
-//    output x positions; Band_dz[(dy, x), k] = c[dz][dy][k - x] (zero off
-//    the band), split into hi/lo parts, written to TMEM once per CTA;
-//  * K runs over TXO + 2r input x positions (the band width);
-//  * N = lines: NZ output planes x YP staged rows.  The data operand is the
-//    staged input converted to BF16 (or TF32) hi/lo parts in the K-major
-//    canonical layout; the dz shift of the box is a start-address offset of
-//    its shared-memory descriptor (whole planes), so the 2r+1 planes of the
-//    box accumulate into one TMEM accumulator without moving data;
-//  * the remaining sum over dy (2r+1 lanes, rows shifted by dy) happens in
-//    the epilogue: TMEM -> registers -> shared memory -> FP32 adds -> global.
-// Split precision (3 products hi*hi + hi*lo + lo*hi, FP32 accumulation)
+//  * A, in tensor memory: lane (q, t) = x subtile q (0..3) and input row t
+//    (0..31) of one staged plane; it holds the K = 16 input values
+//    x0 + q*TXO + k, converted to BF16 (or TF32) hi/lo parts by converter
+//    warps that write them with tcgen05.st.  A tile's staged planes form a
+//    ring in tensor memory, so the 2r+1 planes of the box are 2r+1 column
+//    offsets of the A operand and nothing moves between them;
+//  * B, in shared memory (written once per CTA): the band
+//    B_dz[(dy, x), k] = c[dz][dy][k - x], zero off the band, for the
+//    TXO = 16 - 2r output x positions of a subtile (so K = TXO + 2r = 16
+//    exactly, one BF16 MMA step) and the 2r+1 row offsets dy, split into
+//    hi/lo parts;
+//  * the sum over dy mixes lanes t .. t+2r of one lane quarter: warp
+//    shuffles in the epilogue; a quarter holds 32 rows of one subtile, so
+//    its TY = 32 - 2r output rows need no other warp's data.
+// Split precision (hi*hi + hi*lo + lo*hi into one FP32 accumulator)
 // recovers FP32-level accuracy from BF16 or TF32 operands.
 //
-// Pipeline (persistent CTAs, one per SM, warps in four roles, buffers handed
-// over by mbarriers): TMA stages the FP32 planes of later groups while
-// converter warps turn them into operand parts, two issuer warps take turns
-// with the MMAs of groups i and i+1 (one TMEM accumulator each) and the
-// epilogue warps drain the accumulator of the group before.
+// Three forms share the kernel:
+//  * BOX: the (2r+1)^3 box, 2r+1 planes per output;
+//  * PLANAR: a 2D stencil in each plane (Table I's 2D kernels, and the x/y
+//    pass of the paper's two-pass star of Sec. 4.3, which writes a
+//    temporary grid that star_zpass_kernel completes);
+//  * STAR: the 3D star in one pass: the in-plane x and y lines (and the
+//    centre) as a 2D band on the output's own plane, the z line added by
+//    the converter warps, which see every staged plane anyway and keep the
+//    z partial sums of 2r+1 output planes in registers.
+//
+// Pipeline (persistent CTAs, one per SM, buffers handed over by mbarriers):
+// warp 0 stages FP32 plane boxes by TMA; per TMEM lane quarter, one converter
+// warp fills the A ring and two epilogue warps drain the accumulators of the
+// even and odd outputs; one issuer warp issues every output's MMAs in order,
+// converged (the elected lane's MMAs predicated, not branched around), with
+// one commit per output.  The epilogue that sees an output complete releases
+// the A-ring slots no later output reads: with one issuer the MMAs complete
+// in order.
 #include <cuda_bf16.h>
 #include <stdio.h>
 
@@ -36,22 +52,40 @@
 namespace mms {
 
 #ifdef MMS_ROLE_TRACE
-// Role trace (debug builds only, -DMMS_ROLE_TRACE): cycles each role of the
-// first eight CTAs spends waiting on its barriers and in total, summed.
-//   [0] producer: wait empty staging, total
-//   [1] MMA: wait operands, total, wait accumulator, issuing
-//   [2] converter (first lane): wait staging, total, wait operand slot
-//   [3] epilogue (first lane): wait accumulator, total, group barriers
-__device__ unsigned long long g_role_trace[4][4];
+// Role trace (debug builds only, -DMMS_ROLE_TRACE): clock cycles that one
+// warp of each role in the first eight CTAs spends in its waits and its
+// work, summed.
+//   [0] producer:  wait staging slot, total
+//   [1] issuer 1:  wait planes, wait accumulator, issue, total
+//   [2] converter: wait staged plane, wait A slot, wait accumulator (star),
+//                  loads + conversion, tcgen05.st + wait, total
+//   [3] epilogue:  wait accumulator, TMEM load, reduce + store, total
+__device__ unsigned long long g_role_trace[4][6];
 #define MMS_TRACE_ADD(role, slot, v) \
     do { if (blockIdx.x < 8) atomicAdd(&g_role_trace[role][slot], (unsigned long long)(v)); } while (0)
 #define MMS_CLOCK() clock64()
+// Timeline of CTA 0 (debug builds only): clock64 stamps of events of its
+// first kTl planes / outputs.  Rows: 0 TMA issued (plane), 1 lane quarter 0
+// starts converting (plane), 2 ... has its data, 3 ... arrives, 4 issuer
+// starts waiting (output), 5 issuer starts issuing, 6 issuer done issuing, 7
+// quarter 0's epilogue has the accumulator (output), 8 ... is done, 9, 10,
+// 11: lane quarters 1, 2, 3 arrive (plane).
+constexpr int kTl = 256;
+__device__ unsigned long long g_timeline[12][kTl];
+// stamps go to shared memory (tl_smem, after the barriers) and are copied
+// out at the end, so that the trace adds no global stores to the roles
+#define MMS_TL(row, i) do { if (blockIdx.x == 0 && (i) < kTl) tl_smem[(row) * kTl + (i)] = clock64(); } while (0)
+extern "C" int mms_timeline_read(unsigned long long *host)
+{
+    if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+    return cudaMemcpyFromSymbol(host, g_timeline, sizeof(g_timeline)) != cudaSuccess;
+}
 extern "C" int mms_role_trace_read(unsigned long long *host, int reset)
 {
     if (cudaDeviceSynchronize() != cudaSuccess) return 1;
     if (cudaMemcpyFromSymbol(host, g_role_trace, sizeof(g_role_trace)) != cudaSuccess) return 1;
     if (reset) {
-        unsigned long long z[4][4] = {};
+        unsigned long long z[4][6] = {};
         cudaMemcpyToSymbol(g_role_trace, z, sizeof(z));
     }
     return 0;
@@ -59,103 +93,83 @@ extern "C" int mms_role_trace_read(unsigned long long *host, int reset)
 #else
 #define MMS_TRACE_ADD(role, slot, v) do { } while (0)
 #define MMS_CLOCK() 0ull
+#define MMS_TL(row, i) do { } while (0)
 #endif
 
 namespace {
 
 enum { P_TF32 = 0, P_3XTF32 = 1, P_BF16X3 = 2 };
+enum { M_BOX = 0, M_PLANAR = 1, M_STAR = 2 };
 
-constexpr int roundup(int a, int b) { return (a + b - 1) / b * b; }
-
-template <int R, int PREC, bool LDG = false, bool PLANAR = false>
+template <int R, int PREC, int MODE>
 struct Cfg {
-    // LDG: converter warps read the FP32 input from global memory themselves
-    // (no TMA staging ring); otherwise a producer warp stages it with TMA.
-    // PLANAR: the stencil has no z extent (2D in each plane of the padded
-    // grid, coefficients [dy][dx]): the x/y pass of the star on tensor cores.
-    static constexpr int RZ = PLANAR ? 0 : R;
-    static constexpr int WZ = 2 * RZ + 1;
-    static constexpr bool BF = PREC == P_BF16X3;
-    static constexpr int ELT = BF ? 2 : 4;           // operand bytes
-    static constexpr int KSTEP = BF ? 16 : 8;        // K of one MMA instruction
-    static constexpr int KC = 16 / ELT;              // K elements per 16-byte chunk
     static constexpr int W = 2 * R + 1;
-    static constexpr int TXO = R == 1 ? 40 : R == 2 ? 24 : R == 3 ? 16 : 12;  // x outputs per tile
-    static constexpr int LANES = W * TXO;            // used TMEM lanes (<= 128)
-    static constexpr int K = roundup(TXO + 2 * R, KSTEP);
+    static constexpr int WZ = MODE == M_BOX ? W : 1;     // planes whose bands one output multiplies
+    static constexpr int RZ = MODE == M_PLANAR ? 0 : R;  // z halo of a tile's staged planes
+    static constexpr bool BF = PREC == P_BF16X3;
+    static constexpr int K = 16;                         // contraction: input x of one subtile
+    static constexpr int TXO = K - 2 * R;                // output x per subtile (14, 12, 10, 8)
+    static constexpr int TX = 4 * TXO;                   // output x per tile (4 subtiles)
+    static constexpr int TY = 32 - 2 * R;                // output rows per tile
+    static constexpr int NB = W * TXO;                   // band rows (dy, x)
+    static constexpr int N = (NB + 15) / 16 * 16;        // MMA N
+    static constexpr int ELT = BF ? 2 : 4;               // operand bytes
+    static constexpr int KSTEP = BF ? 16 : 8;            // K of one MMA
+    static constexpr int NKS = K / KSTEP;                // MMAs per product and plane
     static constexpr int NPARTS = PREC == P_TF32 ? 1 : 2;
     static constexpr int NPROD = PREC == P_TF32 ? 1 : 3;
-    static constexpr int BANDCOLS = K * ELT / 4;     // 32-bit TMEM columns per band part
-    static constexpr int BAND_TOTAL = WZ * NPARTS * BANDCOLS;
-    // staged rows per plane: 32, or 36 at radius 2, whose 32 output rows
-    // per tile divide the usual power-of-two extents (N = 4 x 36 = 144 is
-    // a legal MMA N); elsewhere (other radii, and 3xTF32, whose larger bands
-    // leave room for 2 planes per group) N would not be a multiple of 16
-    static constexpr int YP = (R == 2 && PREC != P_3XTF32) ? 36 : 32;
-    static constexpr int TY = YP - 2 * R;            // output rows per tile
-    static constexpr int NZ = (2 * 4 * YP + BAND_TOTAL <= 512)   ? 4
-                              : (2 * 3 * YP + BAND_TOTAL <= 512) ? 3
-                              : (2 * 2 * YP + BAND_TOTAL <= 512) ? 2
-                                                                 : 1;
-    static constexpr bool FITS_TMEM = 2 * NZ * YP + BAND_TOTAL <= 512 && LANES <= 128;
-    static constexpr int N = NZ * YP;                // MMA N (lines per group)
-    // Planes are staged and converted once, in chunks of NZ planes.  Group g
-    // of a tile reads planes [g NZ, g NZ + NZ + 2R) = chunks g .. g + H; the
-    // converted chunks live in a ring of CR slots plus H duplicate slots (a
-    // chunk in slot s < H is also written to slot CR + s), so every window of
-    // H + 1 consecutive chunks is contiguous and one descriptor spans it.
-    static constexpr int H = (2 * RZ + NZ - 1) / NZ;
-    static constexpr int CR = H + 2;
-    static constexpr int CHUNK_LINES = NZ * YP;
-    static constexpr int RING_LINES = (CR + H) * CHUNK_LINES;
-    static constexpr int PART_BYTES = RING_LINES * K * ELT;  // one operand part, whole ring
-    static constexpr int CONV_BYTES = PART_BYTES * NPARTS;
-    static constexpr int STG_BYTES = CHUNK_LINES * K * 4;     // FP32 TMA staging of one chunk
-    // epilogue: one [row y + 2R][lane] float tile per epilogue warp group.
-    // A row stride of 0 mod 32 words puts lane l in bank l whatever its row,
-    // so the scattered stores are conflict-free; 2R spare rows take the
-    // values that fall outside the tile, so every store is unconditional; the
-    // reduction pads its x quads to a multiple of 8 so that 8 consecutive
-    // items read 8 different bank groups.
-    static constexpr int DSM_LD = 128;
-    static constexpr int XQ = TXO / 4, XQP = (XQ + 7) / 8 * 8;
-    static constexpr int DSM_ROWS = YP + 2 * R;
-    static constexpr int DSM_GROUP = DSM_ROWS * DSM_LD;  // floats per epilogue group
-    static constexpr int BAND_COL0 = 2 * N;          // TMEM: D0 | D1 | bands
-    static constexpr uint32_t IDESC = tc::instr_desc(BF ? 1u : 2u, 128, N);
-    // shared memory: [conv ring | dsm | staging ring | barriers, tmem slot, flags]
-    static constexpr size_t BUDGET = 227 * 1024;
-    static constexpr size_t BASE = (size_t)CONV_BYTES + 1024 + 512;
-    static constexpr size_t GRP = (size_t)DSM_GROUP * 4;
-    // epilogue warp groups (4 warps, one per TMEM lane quarter, each owns whole
-    // planes of the accumulator): as many as the planes and shared memory allow
-    static constexpr size_t STG_MIN = LDG ? 0 : 2 * (size_t)STG_BYTES;
-    static constexpr int EGF = BASE + 4 * GRP + STG_MIN <= BUDGET   ? 4
-                               : BASE + 3 * GRP + STG_MIN <= BUDGET ? 3
-                               : BASE + 2 * GRP + STG_MIN <= BUDGET ? 2
-                                                                   : 1;
-    static constexpr int EG = EGF < NZ ? EGF : NZ;
-    static constexpr int DSM_BYTES = EG * DSM_GROUP * 4;
-    static constexpr int NCONV = LDG ? 5 : 4;        // converter warps: (0,) 2, 3 and the last two
-    static constexpr int NWARPS = 4 + 4 * EG + 3;   // + the second MMA issuer (last warp)
+    static constexpr int ACOLS = K * ELT / 4;            // TMEM columns of one A part
+    static constexpr int APL = NPARTS * ACOLS;           // TMEM columns of one staged plane
+    static constexpr int ZC = MODE == M_STAR ? (TXO + 7) / 8 * 8 : 0;  // z sums of one output
+    // A-ring planes needed for progress (the box reads 2r+1 planes per
+    // output; a star output reads its centre plane and waits for the plane 2r
+    // past its first, which completes its z sum; planar reads one plane),
+    // with one more converted ahead
+    static constexpr int NEED = MODE == M_BOX ? W + 1 : MODE == M_STAR ? R + 2 : 2;
+    // Workers: three warps per TMEM lane quarter; worker 0 converts every
+    // staged plane (the star's keeps the z sums in registers), workers 1 and
+    // 2 drain the accumulators of the even and odd outputs, so the ND
+    // accumulators are an even number and each slot's laps are waited on in
+    // order by one warp.
+    static constexpr int ND = 4 * (N + ZC) + NEED * APL <= 512 ? 4 : 2;
+    // TMEM columns: ND accumulators of N | ND z-sum slots of ZC | A ring
+    static constexpr int Z0 = ND * N;
+    static constexpr int A0 = Z0 + ND * ZC;
+    static constexpr int PRF = (512 - A0) / APL < 16 ? (512 - A0) / APL : 16;
+    static constexpr int PR = PRF;                       // A ring planes
+    // FP32 staging box: TX + 2r columns (at least), 32 rows, one plane; the
+    // row pitch in 16-byte units is odd, so the converters' row reads
+    // (8 rows per quarter warp) hit 8 different bank groups
+    static constexpr int BOXW = R == 1 ? 60 : R == 2 ? 52 : R == 3 ? 52 : 44;
+    static constexpr int STG_BYTES = BOXW * 32 * 4;
+    static constexpr int STG_STRIDE = (STG_BYTES + 1023) / 1024 * 1024;
+    static constexpr int NST = 8;
+    // band: K-major canonical layout, core matrices of 8 rows x 16 bytes,
+    // the K chunks of a row group adjacent (LBO = 128 B), row groups SBO apart
+    static constexpr int KC = 16 / ELT;                  // K elements per 16-byte chunk
+    static constexpr int SBO = K * ELT * 8;
+    static constexpr int PART_BYTES = N * K * ELT;
+    static constexpr int BAND_BYTES = WZ * NPARTS * PART_BYTES;
+    static constexpr int NWARPS = 16;                    // producer, issuer, 2 idle, 12 workers
     static constexpr int NT = 32 * NWARPS;
-    static constexpr size_t FIXED = BASE + DSM_BYTES;
-    static constexpr int NST = LDG                                           ? 0
-                               : FIXED + 4 * (size_t)STG_BYTES <= BUDGET   ? 4
-                               : FIXED + 3 * (size_t)STG_BYTES <= BUDGET ? 3
-                                                                         : 2;
-    static constexpr size_t OFF_DSM = CONV_BYTES;
-    static constexpr size_t OFF_STG = OFF_DSM + DSM_BYTES;
-    static constexpr size_t OFF_BAR = OFF_STG + (size_t)NST * STG_BYTES;
-    static constexpr size_t SMEM = 1024 + OFF_BAR + 512;
-    static constexpr bool OK = FITS_TMEM && SMEM <= BUDGET && RING_LINES * 16 < (1 << 18);
-    // FP32 staging rows of exactly 128 bytes are loaded with the TMA 128-byte
-    // swizzle: 16-byte chunk q of line n sits at chunk q ^ (n & 7), so the
-    // converters' column reads across 8 lines hit 8 different bank groups.
-    static constexpr bool SWZ = K * 4 == 128;
-    static_assert(SWZ == (K * 4 == 128) && N % 16 == 0 && N <= 256, "MMA N");
-    static_assert(YP == 32 || YP == 36, "the epilogue loads 32 or 36 accumulator columns");
-    static_assert(STG_BYTES % 1024 == 0 && CONV_BYTES % 1024 == 0 && PART_BYTES % 16 == 0, "align");
+    static constexpr size_t OFF_STG = (size_t)(BAND_BYTES + 1023) / 1024 * 1024;
+    static constexpr size_t OFF_BAR = OFF_STG + (size_t)NST * STG_STRIDE;
+#ifdef MMS_ROLE_TRACE
+    static constexpr size_t TL_BYTES = 12 * 256 * 8;
+#else
+    static constexpr size_t TL_BYTES = 0;
+#endif
+    static constexpr size_t SMEM_NEED = 1024 + OFF_BAR + 1024 + TL_BYTES;
+    // at least 120 KB, so that two CTAs (each holding all 512 TMEM columns)
+    // never share an SM
+    static constexpr size_t SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
+    static constexpr bool OK = PR >= NEED && SMEM <= 227 * 1024 && A0 + PR * APL <= 512;
+    static_assert(OK, "tensor-core configuration does not fit");
+    static constexpr uint32_t IDESC = tc::instr_desc(BF ? 1u : 2u, 128, N);
+    static_assert(BOXW >= TX + 2 * R && BOXW % 4 == 0 && (BOXW / 4) % 2 == 1, "staging box");
+    static_assert(N % 16 == 0 && N <= 256 && (N == 48 || N == 64 || N == 80), "epilogue loads");
+    static_assert(2 * NST + 2 * PR + 2 * ND <= 120, "barrier area");
+    static_assert(ND % 2 == 0, "epilogue slots of two workers");
 };
 
 __device__ __forceinline__ uint32_t bf16_bits(float v)
@@ -190,71 +204,43 @@ __device__ __forceinline__ uint32_t split_part(float v, int p)
 }
 
 struct TcArgs {
-    const float *in;              // padded input (read directly by LDG converters)
-    int64_t ipy, ipz;
-    int X, Y, Z;                  // padded extents
     float *out;
     int64_t opy, opz;
     int nx, ny, nz;
-    int vec;                      // 16-byte output rows: float4 stores
-    int tiles_x, tiles_y, tiles;  // tiles = tiles_x * tiles_y * zchunks
-    int groups;                   // groups (of NZ planes) per tile
-    int zoff;                     // input plane of output plane 0 (R for a z-padded grid, 0 for planar shapes)
+    int vec;                      // output store width: 4 (float4), 2 (float2) or 1
+    int tiles_x, tiles_y, tiles;  // tiles = tiles_x * tiles_y * z chunks
+    int nzt;                      // output planes per z chunk
+    int zoff;                     // padded input plane of staged plane 0 of chunk 0
+    float cz[2 * kMaxR + 1];      // star: z weights (the centre is in the band)
 };
 
-// Warp roles: 0 = TMA producer, 1 = MMA issuer of the even groups (and TMEM
-// owner), the last warp = MMA issuer of the odd groups, 2, 3 and the two
-// warps before the last = converters (FP32 box -> operand parts),
-// 4 .. 4+4EG-1 = epilogue, EG groups of four warps (warp w reaches TMEM lane
-// quarter w % 4); group e drains planes e, e+EG, ... of each accumulator.
-// Roles hand buffers to each other through mbarriers, so TMA, conversion,
-// MMA and epilogue of different groups overlap.
-
-__device__ __forceinline__ void named_sync(int id, int nthreads)
+// Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2 and 3 =
+// idle after set-up, 4..15 = workers, three per TMEM lane quarter (warp w
+// reaches lane quarter w % 4): worker 0 converts, workers 1 and 2 drain.
+template <int R, int PREC, int MODE>
+__global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
+    band_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BoxCoef cf,
+                   const __grid_constant__ TcArgs a, unsigned *err)
 {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// 16 bytes of the padded input at (xi, yi, zi), zero outside the grid.
-__device__ __forceinline__ float4 load_in4(const TcArgs &a, int xi, int yi, int zi)
-{
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (yi >= a.Y || zi >= a.Z || xi >= a.X) return v;
-    const float *p = a.in + (int64_t)zi * a.ipz + (int64_t)yi * a.ipy + xi;
-    if (xi + 3 < a.X) return __ldg(reinterpret_cast<const float4 *>(p));
-    v.x = __ldg(p);
-    if (xi + 1 < a.X) v.y = __ldg(p + 1);
-    if (xi + 2 < a.X) v.z = __ldg(p + 2);
-    return v;
-}
-
-template <int R, int PREC, bool LDG, bool PLANAR>
-__global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
-    box_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BoxCoef cf,
-                  const __grid_constant__ TcArgs a, unsigned *err)
-{
-    using C = Cfg<R, PREC, LDG, PLANAR>;
+    using C = Cfg<R, PREC, MODE>;
     constexpr int W = C::W;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    // 1024-byte alignment: the TMA swizzle pattern repeats every 1024 bytes
     unsigned char *smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char *conv = smem;
-    float *dsm = reinterpret_cast<float *>(smem + C::OFF_DSM);
+    unsigned char *band = smem;
     float *stg = reinterpret_cast<float *>(smem + C::OFF_STG);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
     uint64_t *full_stg = bar, *empty_stg = bar + C::NST;
-    uint64_t *full_conv = bar + 2 * C::NST, *empty_conv = full_conv + C::CR;
-    uint64_t *full_d = empty_conv + C::CR, *empty_d = full_d + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty_d + 2);
+    uint64_t *full_a = empty_stg + C::NST, *empty_a = full_a + C::PR;
+    uint64_t *full_d = empty_a + C::PR, *empty_d = full_d + C::ND;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty_d + C::ND);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    volatile int *epi_fail = abort_flag + 1;  // [EG][2], by epilogue group and accumulator parity
-    constexpr int CT = C::NCONV * 32;           // converter threads
-    constexpr int NEPI = 4 * C::EG;             // epilogue warps
+#ifdef MMS_ROLE_TRACE
+    unsigned long long *tl_smem = reinterpret_cast<unsigned long long *>(smem + C::OFF_BAR + 1024);
+    for (int i = threadIdx.x; i < 12 * kTl; i += blockDim.x) tl_smem[i] = 0;
+#endif
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int my_tiles = a.tiles > (int)blockIdx.x ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int G = a.groups, CPT = a.groups + C::H;  // groups and chunks per tile
-    const int ng = my_tiles * G, nch = my_tiles * CPT;
 
     if (warp == 1) {
         tc::tmem_alloc(tmem_slot, 512);
@@ -263,393 +249,450 @@ __global__ void __launch_bounds__(Cfg<R, PREC, LDG, PLANAR>::NT, 1)
     if (tid == 0) {
         for (int b = 0; b < C::NST; ++b) {
             ptx::mbar_init(&full_stg[b], 1);
-            ptx::mbar_init(&empty_stg[b], CT);
+            ptx::mbar_init(&empty_stg[b], 4);
         }
-        for (int b = 0; b < C::CR; ++b) {
-            ptx::mbar_init(&full_conv[b], CT);
-            ptx::mbar_init(&empty_conv[b], C::H + 1);
+        for (int b = 0; b < C::PR; ++b) {
+            ptx::mbar_init(&full_a[b], 4);
+            ptx::mbar_init(&empty_a[b], 1);  // released by the epilogue
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < C::ND; ++b) {
             ptx::mbar_init(&full_d[b], 1);
-            ptx::mbar_init(&empty_d[b], NEPI);
+            ptx::mbar_init(&empty_d[b], 4);
         }
         ptx::fence_mbar_init();
         *abort_flag = 0;
-        for (int e = 0; e < 2 * C::EG; ++e) epi_fail[e] = 0;
     }
+    // The band operand: 32-bit word w of the band area holds K element(s)
+    // k0 (and k0 + 1 for BF16, high half) of band row n of part p of plane
+    // offset dz.
+    for (int w = tid; w < C::BAND_BYTES / 4; w += C::NT) {
+        const int o = 4 * w;
+        const int part = o / C::PART_BYTES, rem = o % C::PART_BYTES;
+        const int dzi = part / C::NPARTS, p = part % C::NPARTS;
+        const int g = rem / C::SBO, r2 = rem % C::SBO;
+        const int jc = r2 / 128, r3 = r2 % 128;
+        const int n = g * 8 + r3 / 16;
+        const int k0 = jc * C::KC + (r3 % 16) / C::ELT;
+        const int dyi = n / C::TXO, xo = n % C::TXO;
+        uint32_t word = 0;
+#pragma unroll
+        for (int h = 0; h < (C::BF ? 2 : 1); ++h) {
+            const int d = k0 + h - xo;
+            if (n < C::NB && d >= 0 && d <= 2 * R) {
+                const float c = MODE == M_BOX ? cf.c[(dzi * W + dyi) * W + d] : cf.c[dyi * W + d];
+                word |= split_part<PREC>(c, p) << (16 * h);
+            }
+        }
+        reinterpret_cast<uint32_t *>(band)[w] = word;
+    }
+    ptx::fence_proxy_async_smem();  // generic writes -> tensor-core reads
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *tmem_slot;
 
-    // Banded coefficient operand, written once by the first warp of each lane
-    // quarter: lane (dy, x) of part p for plane offset dz.
-    if (warp >= 4 && warp < 8) {
-        const int q = warp & 3;
-        const int l = q * 32 + lane;
-        const bool used = l < C::LANES;
-        const int dyi = used ? l / C::TXO : 0, xo = used ? l % C::TXO : 0;
-        for (int dzi = 0; dzi < C::WZ; ++dzi)
-            for (int p = 0; p < C::NPARTS; ++p)
-                for (int c0 = 0; c0 < C::BANDCOLS; c0 += 8) {
-                    uint32_t v[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        uint32_t word = 0;
-                        if constexpr (C::BF) {
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const int k = 2 * (c0 + j) + h, d = k - xo;
-                                uint32_t bits = 0;
-                                if (used && d >= 0 && d <= 2 * R)
-                                    bits = split_part<PREC>(cf.c[(dzi * W + dyi) * W + d], p);
-                                word |= bits << (16 * h);
-                            }
-                        } else {
-                            const int k = c0 + j, d = k - xo;
-                            if (used && d >= 0 && d <= 2 * R)
-                                word = split_part<PREC>(cf.c[(dzi * W + dyi) * W + d], p);
-                        }
-                        v[j] = word;
-                    }
-                    const uint32_t col = C::BAND_COL0 + (dzi * C::NPARTS + p) * C::BANDCOLS + c0;
-                    tc::tmem_st_32x32b_x8(tbase + ((uint32_t)(q * 32) << 16) + col, v);
-                }
-        tc::tmem_wait_st();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-
-    // tile (per CTA, tl-th) -> column origin and first plane of its z chunk
-    auto tile_origin = [&](int tl, int &x0, int &y0, int &zt) {
+    // tile tl of this CTA -> output column origin, first output plane and
+    // its number of output planes
+    auto tile_of = [&](int tl, int &x0, int &y0, int &z0, int &nzt) {
         const int t = (int)blockIdx.x + tl * (int)gridDim.x;
         const int xt = t % a.tiles_x, yt = (t / a.tiles_x) % a.tiles_y, zc = t / (a.tiles_x * a.tiles_y);
-        x0 = xt * C::TXO;
+        x0 = xt * C::TX;
         y0 = yt * C::TY;
-        zt = zc * G * C::NZ;
+        z0 = zc * a.nzt;
+        nzt = a.nz - z0 < a.nzt ? a.nz - z0 : a.nzt;
     };
-    // Bounded wait of the producer and MMA roles; on expiry raise the abort flag.
-    [[maybe_unused]] unsigned long long waited = 0;  // role trace only
+    // Bounded wait; on expiry (or once another role has given up) raise the
+    // abort flag and return false.
     auto wait = [&](uint64_t *b, uint32_t parity) -> bool {
         if (*abort_flag) return false;
-        const unsigned long long t0 = MMS_CLOCK();
-        const bool done = ptx::mbar_wait_bounded(b, parity, err);
-        waited += MMS_CLOCK() - t0;
-        if (done) return true;
+        if (ptx::mbar_wait_bounded(b, parity, err)) return true;
         *abort_flag = 1;
         return false;
     };
 
-    if (warp == 0 && !LDG) {
-        // ------------------------------------------- TMA producer: chunk k
-        // (whole warp waits, one elected lane issues)
+    if (warp == 0) {
+        // -------------------------------------------------- TMA producer
         const bool leader = ptx::elect_one();
-        [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
         if (leader) ptx::prefetch_tmap(&tmap);
-        for (int k = 0; k < nch; ++k) {
-            constexpr int NSTD = C::NST > 0 ? C::NST : 1;  // (this branch only runs with a ring)
-            const int st = k % NSTD;
-            const bool ok = wait(&empty_stg[st], ((uint32_t)(k / NSTD) & 1u) ^ 1u);
-            if (!__all_sync(0xffffffffu, ok)) {
-                *abort_flag = 1;
-                break;
-            }
-            if (leader) {
-                int x0, y0, zt;
-                tile_origin(k / CPT, x0, y0, zt);
-                ptx::mbar_arrive_expect_tx(&full_stg[st], C::STG_BYTES);
-                ptx::tma_load_3d(stg + (size_t)st * (C::STG_BYTES / 4), &tmap, x0, y0,
-                                 zt + (k % CPT) * C::NZ + a.zoff, &full_stg[st]);
-            }
-            __syncwarp();
-        }
-        if (lane == 0) {
-            MMS_TRACE_ADD(0, 0, waited);
-            MMS_TRACE_ADD(0, 1, MMS_CLOCK() - tstart);
-        }
-    } else if (warp == 1 || warp == C::NWARPS - 1) {
-        // ----------------------------------------------------- MMA issuers
-        // Two warps alternate groups: warp 1 issues the even groups into
-        // accumulator 0, the last warp the odd ones into accumulator 1.  A
-        // warp's barrier polls wait behind its own MMAs still queued, so a
-        // single issuer leaves the tensor pipe idle at every group boundary;
-        // with two, one warp's queued MMAs cover the other's polls.  The
-        // whole warp runs the loop and waits; one elected lane issues.
-        const int s = warp == 1 ? 0 : 1;
-        const bool leader = ptx::elect_one();
-        [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
-        [[maybe_unused]] unsigned long long wconv = 0, wacc = 0, tissue = 0;
-        int last = -1;  // last group this warp issued
-        for (int i = s; i < ng; i += 2) {
-            const int g = i % G;
-            const int kg = (i / G) * CPT + g;  // first chunk of this group's window
-            bool ok = true;
-            unsigned long long w0 = waited;
-            for (int h = 0; h <= C::H && ok; ++h)
-                ok = wait(&full_conv[(kg + h) % C::CR], (uint32_t)((kg + h) / C::CR) & 1u);
-            wconv += waited - w0;
-            w0 = waited;
-            ok = ok && wait(&empty_d[s], ((uint32_t)(i >> 1) & 1u) ^ 1u);
-            wacc += waited - w0;
-            // every lane takes the same decision
-            if (!__all_sync(0xffffffffu, ok)) {
-                *abort_flag = 1;
-                break;
-            }
-            [[maybe_unused]] const unsigned long long ti = MMS_CLOCK();
-            tc::fence_after_sync();
-            if (leader) {
-                const uint32_t dcol = tbase + (uint32_t)(s * C::N);
-                const uint32_t cbase = ptx::smem_u32(conv) + (uint32_t)((kg % C::CR) * C::CHUNK_LINES * 16);
-                // one descriptor per group; each MMA adds a constant (>> 4) to its start field
-                const uint64_t d0 = tc::smem_desc(cbase, C::RING_LINES * 16, 128);
-                const uint32_t a0 = tbase + C::BAND_COL0;
-#pragma unroll
-                for (int dzi = 0; dzi < C::WZ; ++dzi) {
-#pragma unroll
-                    for (int pr = 0; pr < C::NPROD; ++pr) {
-                        const int pa = pr == 2 ? 1 : 0;  // band part
-                        const int pb = pr == 1 ? 1 : 0;  // data part
-#pragma unroll
-                        for (int kk = 0; kk < C::K / C::KSTEP; ++kk) {
-                            const uint32_t acol = a0 + (dzi * C::NPARTS + pa) * C::BANDCOLS + kk * (C::KSTEP * C::ELT / 4);
-                            const uint64_t bdesc = d0 + (uint64_t)((pb * C::PART_BYTES + (dzi * C::YP) * 16 +
-                                                                    kk * (C::KSTEP / C::KC) * C::RING_LINES * 16) >> 4);
-                            const uint32_t acc = (dzi | pr | kk) ? 1u : 0u;
-                            if constexpr (C::BF)
-                                tc::mma_bf16_ts(dcol, acol, bdesc, C::IDESC, acc);
-                            else
-                                tc::mma_tf32_ts(dcol, acol, bdesc, C::IDESC, acc);
-                        }
-                    }
-                }
-                tc::mma_commit(&full_d[s]);  // accumulator ready for the epilogue
-                // A chunk slot is free again after H+1 arrivals: one from every
-                // group of the tile that reads the chunk, once its MMAs are
-                // done, and, for the chunks at the tile's ends that fewer
-                // groups read, the missing ones from their first reader.
-                for (int h = 0; h <= C::H; ++h) {
-                    const int c = g + h;  // tile-local chunk
-                    const int first = c - C::H > 0 ? c - C::H : 0;
-                    const int nread = (c < G - 1 ? c : G - 1) - first + 1;
-                    const int n = g == first ? C::H + 2 - nread : 1;
-                    for (int j = 0; j < n; ++j) tc::mma_commit(&empty_conv[(kg + h) % C::CR]);
-                }
-            }
-            __syncwarp();
-            last = i;
-            tissue += MMS_CLOCK() - ti;
-        }
-        // every MMA this warp issued completes before TMEM is freed at teardown
-        if (last >= 0) ptx::mbar_wait_bounded(&full_d[s], (uint32_t)(last >> 1) & 1u, err);
-        if (lane == 0) {
-            MMS_TRACE_ADD(1, 0, wconv);
-            MMS_TRACE_ADD(1, 1, MMS_CLOCK() - tstart);
-            MMS_TRACE_ADD(1, 2, wacc);
-            MMS_TRACE_ADD(1, 3, tissue);
-        }
-    } else if (warp < 4 || warp >= 4 + NEPI) {
-        // -------------------------------------------- converters: chunk k
-        const int cw = warp == 0 ? C::NCONV - 1 : warp < 4 ? warp - 2 : warp - 2 - NEPI;
-        const int ct = cw * 32 + lane;
-        constexpr int NCH = C::K / C::KC;  // 16-byte operand chunks per line
-        [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
-        [[maybe_unused]] unsigned long long wstg = 0, wslot = 0;
-        constexpr int NV4 = C::KC / 4;  // FP32 float4 per operand chunk (2 for BF16, 1 for TF32)
-        constexpr int IPT = (C::CHUNK_LINES * NCH + CT - 1) / CT;  // items per thread
-        for (int k = 0; k < nch; ++k) {
-            const int sl = k % C::CR;
-            const int st = LDG ? 0 : k % (C::NST > 0 ? C::NST : 1);
-            // operand values of this thread's items, from global memory (LDG)
-            // or from the TMA staging ring
-            float4 in4[IPT][NV4];
-            if constexpr (LDG) {
-                int x0, y0, zt;
-                tile_origin(k / CPT, x0, y0, zt);
-                const int zc = zt + (k % CPT) * C::NZ + a.zoff;
-#pragma unroll
-                for (int t = 0; t < IPT; ++t) {
-                    const int it = ct + t * CT;
-                    const int n = it % C::CHUNK_LINES, kc = it / C::CHUNK_LINES;
-#pragma unroll
-                    for (int q = 0; q < NV4; ++q)
-                        in4[t][q] = it < C::CHUNK_LINES * NCH
-                                        ? load_in4(a, x0 + kc * C::KC + 4 * q, y0 + n % C::YP, zc + n / C::YP)
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            // decisions stay warp-uniform: a failed wait in any lane stops the warp
-            [[maybe_unused]] const unsigned long long t0 = MMS_CLOCK();
-            constexpr int NSTD = C::NST > 0 ? C::NST : 1;
-            bool ok = LDG ? true : ptx::mbar_wait_bounded(&full_stg[st], (uint32_t)(k / NSTD) & 1u, err);
-            [[maybe_unused]] const unsigned long long t1 = MMS_CLOCK();
-            ok = ok && ptx::mbar_wait_bounded(&empty_conv[sl], ((uint32_t)(k / C::CR) & 1u) ^ 1u, err);
-            wstg += t1 - t0;
-            wslot += MMS_CLOCK() - t1;
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                *abort_flag = 1;
-                break;
-            }
-            const float *src = stg + (size_t)st * (C::STG_BYTES / 4);
-            const int line0 = sl * C::CHUNK_LINES;
-            const bool dup = sl < C::H;
-            // lines fastest: a warp converts one 16-byte chunk column of 32
-            // consecutive lines, so its stores are contiguous
-#pragma unroll
-            for (int t = 0; t < IPT; ++t) {
-                const int it = ct + t * CT;
-                if (it >= C::CHUNK_LINES * NCH) break;
-                const int n = it % C::CHUNK_LINES, kc = it / C::CHUNK_LINES;
-                unsigned char *d0 = conv + ((size_t)kc * C::RING_LINES + line0 + n) * 16;
-                if constexpr (!LDG) {
-                    const float *line = src + n * C::K;
-#pragma unroll
-                    for (int q = 0; q < NV4; ++q) {
-                        // swizzled staging: 16-byte chunk j of line n sits at j ^ (n & 7)
-                        const int j = kc * NV4 + q;
-                        const int pj = C::SWZ ? (j ^ (n & 7)) : j;
-                        in4[t][q] = *reinterpret_cast<const float4 *>(line + 4 * pj);
-                    }
-                }
-                uint4 o[2];
-                if constexpr (C::BF) {
-                    const float4 q0 = in4[t][0], q1 = in4[t][NV4 - 1];
-                    const float v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-                    uint32_t hi[4], lo[4];
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        // one cvt packs the pair (even k in the low half)
-                        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
-                        hi[h] = *reinterpret_cast<const uint32_t *>(&b);
-                        const float h0 = __uint_as_float(hi[h] << 16), h1 = __uint_as_float(hi[h] & 0xffff0000u);
-                        const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * h] - h0, v[2 * h + 1] - h1);
-                        lo[h] = *reinterpret_cast<const uint32_t *>(&l);
-                    }
-                    o[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    o[1] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                } else {
-                    const float4 q = in4[t][0];
-                    const uint32_t h0 = tf32_rna(q.x), h1 = tf32_rna(q.y), h2 = tf32_rna(q.z), h3 = tf32_rna(q.w);
-                    o[0] = make_uint4(h0, h1, h2, h3);
-                    if constexpr (C::NPARTS == 2)
-                        o[1] = make_uint4(tf32_rna(q.x - __uint_as_float(h0)), tf32_rna(q.y - __uint_as_float(h1)),
-                                          tf32_rna(q.z - __uint_as_float(h2)), tf32_rna(q.w - __uint_as_float(h3)));
-                }
-#pragma unroll
-                for (int part = 0; part < C::NPARTS; ++part) {
-                    *reinterpret_cast<uint4 *>(d0 + (size_t)part * C::PART_BYTES) = o[part];
-                    if (dup)
-                        *reinterpret_cast<uint4 *>(d0 + (size_t)part * C::PART_BYTES +
-                                                   (size_t)C::CR * C::CHUNK_LINES * 16) = o[part];
-                }
-            }
-            ptx::fence_proxy_async_smem();  // generic writes -> tensor-core reads
-            ptx::mbar_arrive(&full_conv[sl]);
-            if (!LDG) ptx::mbar_arrive(&empty_stg[st]);
-        }
-        if (ct == 0) {
-            MMS_TRACE_ADD(2, 0, wstg);
-            MMS_TRACE_ADD(2, 1, MMS_CLOCK() - tstart);
-            MMS_TRACE_ADD(2, 2, wslot);
-        }
-    } else {
-        // ---------------------------------------------------------- epilogue
-        // TMEM -> registers -> shared memory, the sum over the 2r+1 lanes
-        // (dy, x) with rows shifted by dy, float4 stores.  Lane (dy, x) of
-        // column c feeds output row y = c - dy, so it is stored at
-        // [y + 2R][lane] and the reduction reads four x positions per load.
-        const int eg = (warp - 4) >> 2, q = warp & 3;
-        const int my_lane = q * 32 + lane;
-        const int my_dyi = my_lane < C::LANES ? my_lane / C::TXO : 0;
-        const int et = (warp & 3) * 32 + lane;  // thread index within the group
-        float *gbuf = dsm + eg * C::DSM_GROUP;
-        float *st_base = gbuf + (2 * R - my_dyi) * C::DSM_LD + my_lane;
-        volatile int *fail = epi_fail + 2 * eg;
-        bool stop = false;
-        [[maybe_unused]] const unsigned long long tstart = MMS_CLOCK();
-        [[maybe_unused]] unsigned long long wacc = 0, wbar = 0;
-        for (int i = 0; i < ng && !stop; ++i) {
-            const int s = i & 1;
-            const unsigned long long t0 = MMS_CLOCK();
-            if (!ptx::mbar_wait_bounded(&full_d[s], (uint32_t)(i >> 1) & 1u, err)) fail[s] = 1;
-            wacc += MMS_CLOCK() - t0;
-            tc::fence_after_sync();
-            int x0, y0, zt;
-            tile_origin(i / G, x0, y0, zt);
-            const int z0 = zt + (i % G) * C::NZ;
-            for (int zl = eg; zl < C::NZ; zl += C::EG) {
-                uint32_t r[C::YP];
-                {
-                    const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * C::N + zl * C::YP);
-                    uint32_t (&r32)[32] = *reinterpret_cast<uint32_t (*)[32]>(&r[0]);
-                    tc::tmem_ld_32x32b_x32(ta, r32);
-                    if constexpr (C::YP == 36) {
-                        uint32_t (&r4)[4] = *reinterpret_cast<uint32_t (*)[4]>(&r[32]);
-                        tc::tmem_ld_32x32b_x4(ta + 32, r4);
-                    }
-                }
-                tc::tmem_wait_ld();
-                if (zl + C::EG >= C::NZ) {
-                    // this warp's last read of the accumulator: hand it back
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(&empty_d[s]);
-                }
-#pragma unroll
-                for (int c = 0; c < C::YP; ++c) st_base[c * C::DSM_LD] = __uint_as_float(r[c]);
-                [[maybe_unused]] const unsigned long long tb = MMS_CLOCK();
-                named_sync(1 + eg, 128);
-                wbar += MMS_CLOCK() - tb;
-                // a timed-out wait (any thread of the group) was recorded before
-                // the group's first barrier, in the flag of this accumulator
-                // parity, which no thread writes again before all have read it:
-                // the four warps take the same decision and stop together
-                if (zl == eg && fail[s]) {
-                    stop = true;
+        int k = 0;  // staged planes issued
+        bool ok = true;
+        [[maybe_unused]] unsigned long long tw = 0, t00 = MMS_CLOCK();
+        for (int tl = 0; tl < my_tiles && ok; ++tl) {
+            int x0, y0, z0, nzt;
+            tile_of(tl, x0, y0, z0, nzt);
+            const int np = nzt + 2 * C::RZ;
+            for (int p = 0; p < np; ++p) {
+                const int st = k % C::NST;
+                [[maybe_unused]] const unsigned long long t0 = MMS_CLOCK();
+                ok = __all_sync(0xffffffffu, wait(&empty_stg[st], ((uint32_t)(k / C::NST) & 1u) ^ 1u));
+                tw += MMS_CLOCK() - t0;
+                if (!ok) {
                     *abort_flag = 1;
                     break;
                 }
-                const int z = z0 + zl;
-                if (z < a.nz) {
-                    for (int it = et; it < C::TY * C::XQP; it += 128) {
-                        const int xq = it % C::XQP, yl = it / C::XQP;
-                        const int y = y0 + yl, x = x0 + 4 * xq;
-                        if (xq >= C::XQ || y >= a.ny || x >= a.nx) continue;
-                        const float *src = gbuf + (2 * R + yl) * C::DSM_LD + 4 * xq;
-                        float4 acc = *reinterpret_cast<const float4 *>(src);
+                if (leader) {
+                    MMS_TL(0, k);
+                    ptx::mbar_arrive_expect_tx(&full_stg[st], C::STG_BYTES);
+                    ptx::tma_load_3d(stg + (size_t)st * (C::STG_STRIDE / 4), &tmap, x0, y0, z0 + p + a.zoff,
+                                     &full_stg[st]);
+                }
+                __syncwarp();
+                ++k;
+            }
+        }
+        if (lane == 0) {
+            MMS_TRACE_ADD(0, 0, tw);
+            MMS_TRACE_ADD(0, 1, MMS_CLOCK() - t00);
+        }
+        // every copy this warp issued has landed before the CTA exits
+        if (leader)
+            for (int st = 0; st < C::NST && st < k; ++st) {
+                const int last = (k - 1 - st) / C::NST * C::NST + st;
+                ptx::mbar_wait_bounded(&full_stg[st], (uint32_t)(last / C::NST) & 1u, err);
+            }
+    } else if (warp == 1) {
+        // ------------------------------------------------------- MMA issuer
+        // One warp issues every output's MMAs in order.  It stays converged:
+        // each lane executes the MMA and commit statements, the elected lane
+        // alone with its predicate set.  A branch around a single-lane issue
+        // costs a reconvergence, and every poll or commit between batches of
+        // MMAs leaves the shallow tensor-pipe queue to drain, so the warp
+        // waits on each staged plane once, in order (which also keeps it at
+        // most one phase behind each A-ring slot), and commits once per
+        // output.  The A-ring slots are released by the epilogue, which sees
+        // an output's completion: with one issuer the MMAs complete in order.
+        const uint32_t on = ptx::elect_one() ? 1u : 0u;
+        // planes output z of a tile reads (or, for the star, waits for):
+        // up to kb + z + OFF_HI
+        constexpr int OFF_HI = MODE == M_PLANAR ? 0 : 2 * R;
+        const uint64_t bdesc0 = tc::smem_desc(ptx::smem_u32(band), 128, C::SBO);
+        int wnext = 0;      // next staged plane to wait on
+        int j = 0, kb = 0;  // global output index, global index of the tile's staged plane 0
+        int last = -1;      // last output issued
+        bool ok = true;
+        [[maybe_unused]] unsigned long long tp = 0, ta = 0, ti = 0, t00 = MMS_CLOCK();
+        for (int tl = 0; tl < my_tiles && ok; ++tl) {
+            int x0, y0, z0, nzt;
+            tile_of(tl, x0, y0, z0, nzt);
+            for (int z = 0; z < nzt; ++z, ++j) {
+                [[maybe_unused]] const unsigned long long t0 = MMS_CLOCK();
+                if (lane == 0) MMS_TL(4, j);
+                for (; ok && wnext <= kb + z + OFF_HI; ++wnext)
+                    ok = __all_sync(0xffffffffu, wait(&full_a[wnext % C::PR], (uint32_t)(wnext / C::PR) & 1u));
+                [[maybe_unused]] const unsigned long long t1 = MMS_CLOCK();
+                ok = ok && __all_sync(0xffffffffu, wait(&empty_d[j % C::ND], ((uint32_t)(j / C::ND) & 1u) ^ 1u));
+                [[maybe_unused]] const unsigned long long t2 = MMS_CLOCK();
+                tp += t1 - t0;
+                ta += t2 - t1;
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                if (lane == 0) MMS_TL(5, j);
+                // the banded product of each plane the output reads, three
+                // split products (one for TF32), into accumulator j % ND; a B
+                // descriptor differs from the band's first by a constant added
+                // to its start-address field
+                const uint32_t dcol = tbase + (uint32_t)((j % C::ND) * C::N);
 #pragma unroll
-                        for (int dyi = 1; dyi < W; ++dyi) {
-                            const float4 t = *reinterpret_cast<const float4 *>(src + dyi * C::TXO);
-                            acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
-                        }
-                        float *o = a.out + (int64_t)z * a.opz + (int64_t)y * a.opy + x;
-                        if (a.vec && x + 3 < a.nx) {
-                            *reinterpret_cast<float4 *>(o) = acc;
-                        } else {
-                            const float v4[4] = {acc.x, acc.y, acc.z, acc.w};
-                            for (int k = 0; k < 4 && x + k < a.nx; ++k) o[k] = v4[k];
+                for (int dzi = 0; dzi < C::WZ; ++dzi) {
+                    const int pl = kb + z + (MODE == M_BOX ? dzi : MODE == M_STAR ? R : 0);
+                    const uint32_t acol = tbase + (uint32_t)(C::A0 + (pl % C::PR) * C::APL);
+#pragma unroll
+                    for (int pr = 0; pr < C::NPROD; ++pr) {
+                        const int pa = pr == 2 ? 1 : 0;  // data part (A)
+                        const int pb = pr == 1 ? 1 : 0;  // band part (B)
+#pragma unroll
+                        for (int kk = 0; kk < C::NKS; ++kk) {
+                            const uint32_t aaddr = acol + (uint32_t)(pa * C::ACOLS + kk * (C::KSTEP * C::ELT / 4));
+                            const uint64_t bdesc = bdesc0 + (uint64_t)(((dzi * C::NPARTS + pb) * C::PART_BYTES +
+                                                                        kk * (C::KSTEP / C::KC) * 128) >> 4);
+                            const uint32_t acc = (dzi | pr | kk) ? 1u : 0u;
+                            if constexpr (C::BF)
+                                tc::mma_bf16_ts_if(on, dcol, aaddr, bdesc, C::IDESC, acc);
+                            else
+                                tc::mma_tf32_ts_if(on, dcol, aaddr, bdesc, C::IDESC, acc);
                         }
                     }
                 }
-                named_sync(1 + eg, 128);  // the tile is free for the next plane
+                tc::mma_commit_if(on, &full_d[j % C::ND]);  // accumulator ready for the epilogue
+                if (lane == 0) MMS_TL(6, j);
+                ti += MMS_CLOCK() - t2;
+                last = j;
+            }
+            kb += nzt + 2 * C::RZ;
+        }
+        if (lane == 0) {
+            MMS_TRACE_ADD(1, 0, tp);
+            MMS_TRACE_ADD(1, 1, ta);
+            MMS_TRACE_ADD(1, 2, ti);
+            MMS_TRACE_ADD(1, 3, MMS_CLOCK() - t00);
+        }
+        // every MMA issued completes before TMEM is freed
+        if (last >= 0) ptx::mbar_wait_bounded(&full_d[last % C::ND], (uint32_t)(last / C::ND) & 1u, err);
+    } else if (warp >= 4) {
+        // ---------------------------------------------------------- workers
+        // warp 4 + 4 wi + q: worker wi of TMEM lane quarter q; lane t holds
+        // row t of subtile q
+        const int q = warp & 3, wi = (warp - 4) >> 2, t = lane;
+        const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16);
+        bool ok = true;
+        [[maybe_unused]] unsigned long long ts = 0, ta = 0, td = 0, tc0 = 0, tf = 0, tep = 0, t00 = MMS_CLOCK();
+
+        // Conversion of staged plane k (tile-local p, the tile's outputs
+        // start at global index jb): FP32 row -> BF16 (or TF32) hi/lo parts
+        // in the A ring; the star also adds the plane's centre values to the
+        // z sums of the outputs it reaches (zq: outputs p-2R .. p).
+        auto convert = [&](int k, int p, int jb, int nzt, auto &zq) -> bool {
+            const int st = k % C::NST, as = k % C::PR;
+            [[maybe_unused]] const int zo = p - 2 * R;  // STAR: the output this plane completes
+            [[maybe_unused]] const unsigned long long t0 = MMS_CLOCK();
+            if (q == 0) MMS_TL(1, k);
+            bool good = wait(&full_stg[st], (uint32_t)(k / C::NST) & 1u);
+            [[maybe_unused]] const unsigned long long t1 = MMS_CLOCK();
+            good = good && wait(&empty_a[as], ((uint32_t)(k / C::PR) & 1u) ^ 1u);
+            [[maybe_unused]] const unsigned long long t2 = MMS_CLOCK();
+            if constexpr (MODE == M_STAR) {
+                const int jo = jb + zo;
+                if (zo >= 0 && zo < nzt)
+                    good = good && wait(&empty_d[jo % C::ND], ((uint32_t)(jo / C::ND) & 1u) ^ 1u);
+            }
+            [[maybe_unused]] const unsigned long long t3 = MMS_CLOCK();
+            ts += t1 - t0;
+            ta += t2 - t1;
+            td += t3 - t2;
+            if (!__all_sync(0xffffffffu, good)) return false;
+            tc::fence_after_sync();  // the slot's last MMAs (and epilogue loads) are ordered before our stores
+            if (q == 0) MMS_TL(2, k);
+            // the 16 input values of this lane's row
+            float v[16];
+            const float *row = stg + (size_t)st * (C::STG_STRIDE / 4) + t * C::BOXW + q * C::TXO;
+            if constexpr (C::TXO % 4 == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 f = reinterpret_cast<const float4 *>(row)[i];
+                    v[4 * i] = f.x; v[4 * i + 1] = f.y; v[4 * i + 2] = f.z; v[4 * i + 3] = f.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float2 f = reinterpret_cast<const float2 *>(row)[i];
+                    v[2 * i] = f.x; v[2 * i + 1] = f.y;
+                }
+            }
+            const uint32_t acol = lane_base + (uint32_t)(C::A0 + as * C::APL);
+            if constexpr (C::BF) {
+                uint32_t hi[8], lo[8];
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    // one cvt packs the pair (even k in the low half)
+                    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+                    hi[h] = *reinterpret_cast<const uint32_t *>(&b);
+                    const float h0 = __uint_as_float(hi[h] << 16), h1 = __uint_as_float(hi[h] & 0xffff0000u);
+                    const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * h] - h0, v[2 * h + 1] - h1);
+                    lo[h] = *reinterpret_cast<const uint32_t *>(&l);
+                }
+                tc::tmem_st_32x32b_x8(acol, hi);
+                tc::tmem_st_32x32b_x8(acol + C::ACOLS, lo);
+            } else {
+                uint32_t hi[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) hi[i] = tf32_rna(v[i]);
+                tc::tmem_st_32x32b_x16(acol, hi);
+                if constexpr (C::NPARTS == 2) {
+                    uint32_t lo[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) lo[i] = tf32_rna(v[i] - __uint_as_float(hi[i]));
+                    tc::tmem_st_32x32b_x16(acol + C::ACOLS, lo);
+                }
+            }
+            if constexpr (MODE == M_STAR) {
+                // centre values of output row t: input row t + R, from lane t + R
+                float cv[C::TXO];
+#pragma unroll
+                for (int x = 0; x < C::TXO; ++x) cv[x] = __shfl_down_sync(0xffffffffu, v[R + x], R);
+                // plane p adds cz[dz] to output p - R - dz = p - 2R + s (s = R - dz)
+#pragma unroll
+                for (int s = 0; s < W; ++s)
+                    if (s != R)
+#pragma unroll
+                        for (int x = 0; x < C::TXO; ++x) zq[s][x] = fmaf(a.cz[2 * R - s], cv[x], zq[s][x]);
+                if (zo >= 0 && zo < nzt) {
+                    // output zo is complete: its z sum goes beside its accumulator
+                    const uint32_t zcol = lane_base + (uint32_t)(C::Z0 + ((jb + zo) % C::ND) * C::ZC);
+#pragma unroll
+                    for (int c0 = 0; c0 < C::ZC; c0 += 8) {
+                        uint32_t zz[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            zz[i] = c0 + i < C::TXO ? __float_as_uint(zq[0][c0 + i < C::TXO ? c0 + i : 0]) : 0u;
+                        tc::tmem_st_32x32b_x8(zcol + c0, zz);
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < W - 1; ++s)
+#pragma unroll
+                    for (int x = 0; x < C::TXO; ++x) zq[s][x] = zq[s + 1][x];
+#pragma unroll
+                for (int x = 0; x < C::TXO; ++x) zq[W - 1][x] = 0.f;
+            }
+            tc::tmem_wait_st();
+            tc::fence_before_sync();
+            __syncwarp();
+            // The staging slot is handed back only now: its values have been
+            // consumed (converted and stored), so none of this warp's
+            // shared-memory loads can still be in flight when the next TMA
+            // copy overwrites the slot.
+            if (lane == 0) {
+                ptx::mbar_arrive(&empty_stg[st]);
+                ptx::mbar_arrive(&full_a[as]);
+                MMS_TL(q == 0 ? 3 : 8 + q, k);
+            }
+            tc0 += MMS_CLOCK() - t3;
+            return true;
+        };
+
+        // Epilogue of output z of a tile (global index j; the tile's staged
+        // plane 0 has global index kb, its column origin is x0, y0, z0).
+        auto epilogue = [&](int j, int z, int kb, int nzt, int x0, int y0, int z0) -> bool {
+            const int ds = j % C::ND;
+            [[maybe_unused]] const unsigned long long t0 = MMS_CLOCK();
+            if (!__all_sync(0xffffffffu, wait(&full_d[ds], (uint32_t)(j / C::ND) & 1u))) return false;
+            [[maybe_unused]] const unsigned long long t1 = MMS_CLOCK();
+            tf += t1 - t0;
+            if (lane == 0 && q == 0) MMS_TL(7, j);
+            tc::fence_after_sync();
+            // Output j's MMAs are done, and with them (one issuer, in order)
+            // every earlier MMA: the A-ring slots of the planes no later
+            // output reads are free again.  The box's plane z is read last
+            // by output z, the star's centre plane z+r by output z (its
+            // z-halo planes by no MMA: they go with the tile's first and last
+            // outputs), the planar plane z by output z.
+            if (q == 0 && lane == 0) {
+                constexpr int OFF = MODE == M_STAR ? R : 0;
+                ptx::mbar_arrive(&empty_a[(kb + z + OFF) % C::PR]);
+                if (MODE == M_STAR && z == 0)
+                    for (int p = 0; p < R; ++p) ptx::mbar_arrive(&empty_a[(kb + p) % C::PR]);
+                if (MODE != M_PLANAR && z == nzt - 1)
+                    for (int p = nzt + OFF; p < nzt + 2 * R; ++p) ptx::mbar_arrive(&empty_a[(kb + p) % C::PR]);
+            }
+            uint32_t d[C::N];
+            [[maybe_unused]] uint32_t zz[C::ZC > 0 ? C::ZC : 1];
+            {
+                const uint32_t dc = lane_base + (uint32_t)(ds * C::N);
+                [[maybe_unused]] const uint32_t zc = lane_base + (uint32_t)(C::Z0 + ds * C::ZC);
+                uint32_t (&d0)[32] = *reinterpret_cast<uint32_t (*)[32]>(&d[0]);
+                tc::tmem_ld_32x32b_x32(dc, d0);
+                if constexpr (C::N == 48) {
+                    uint32_t (&d1)[16] = *reinterpret_cast<uint32_t (*)[16]>(&d[32]);
+                    tc::tmem_ld_32x32b_x16(dc + 32, d1);
+                } else {
+                    uint32_t (&d1)[32] = *reinterpret_cast<uint32_t (*)[32]>(&d[32]);
+                    tc::tmem_ld_32x32b_x32(dc + 32, d1);
+                    if constexpr (C::N == 80) {
+                        uint32_t (&d2)[16] = *reinterpret_cast<uint32_t (*)[16]>(&d[64]);
+                        tc::tmem_ld_32x32b_x16(dc + 64, d2);
+                    }
+                }
+                if constexpr (C::ZC == 8) {
+                    uint32_t (&z0r)[8] = *reinterpret_cast<uint32_t (*)[8]>(&zz[0]);
+                    tc::tmem_ld_32x32b_x8(zc, z0r);
+                } else if constexpr (C::ZC == 16) {
+                    uint32_t (&z0r)[16] = *reinterpret_cast<uint32_t (*)[16]>(&zz[0]);
+                    tc::tmem_ld_32x32b_x16(zc, z0r);
+                }
+            }
+            tc::tmem_wait_ld();
+            tc::tmem_regs_ready(d);
+            if constexpr (C::ZC > 0) tc::tmem_regs_ready(zz);
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&empty_d[ds]);  // the accumulator is free again
+            // out[t][x] = sum_dy D[t + dy][(dy, x)]: lanes t .. t+2R
+            float o[C::TXO];
+#pragma unroll
+            for (int x = 0; x < C::TXO; ++x) {
+                float acc = __uint_as_float(d[x]);
+#pragma unroll
+                for (int dyi = 1; dyi < W; ++dyi)
+                    acc += __shfl_down_sync(0xffffffffu, __uint_as_float(d[dyi * C::TXO + x]), dyi);
+                if constexpr (MODE == M_STAR) acc += __uint_as_float(zz[x]);
+                o[x] = acc;
+            }
+            const int y = y0 + t, xb = x0 + q * C::TXO, zg = z0 + z;
+            if (t < C::TY && y < a.ny && xb < a.nx) {
+                float *op = a.out + (int64_t)zg * a.opz + (int64_t)y * a.opy + xb;
+                const bool full = xb + C::TXO <= a.nx;
+                if (C::TXO % 4 == 0 && full && a.vec == 4) {
+#pragma unroll
+                    for (int i = 0; i < C::TXO / 4; ++i)
+                        reinterpret_cast<float4 *>(op)[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+                } else if (full && a.vec >= 2) {
+#pragma unroll
+                    for (int i = 0; i < C::TXO / 2; ++i)
+                        reinterpret_cast<float2 *>(op)[i] = make_float2(o[2 * i], o[2 * i + 1]);
+                } else {
+#pragma unroll
+                    for (int x = 0; x < C::TXO; ++x)
+                        if (xb + x < a.nx) op[x] = o[x];
+                }
+            }
+            if (lane == 0 && q == 0) MMS_TL(8, j);
+            tep += MMS_CLOCK() - t1;
+            return true;
+        };
+
+        if (wi == 0) {
+            // every staged plane in order (the star's z sums in registers)
+            float zq[MODE == M_STAR ? W : 1][MODE == M_STAR ? C::TXO : 1];
+            int k = 0, jb = 0;
+            for (int tl = 0; tl < my_tiles && ok; ++tl) {
+                int x0, y0, z0, nzt;
+                tile_of(tl, x0, y0, z0, nzt);
+                if constexpr (MODE == M_STAR) {
+#pragma unroll
+                    for (int s2 = 0; s2 < W; ++s2)
+#pragma unroll
+                        for (int x = 0; x < C::TXO; ++x) zq[s2][x] = 0.f;
+                }
+                for (int p = 0; p < nzt + 2 * C::RZ && ok; ++p, ++k) ok = convert(k, p, jb, nzt, zq);
+                jb += nzt;
+            }
+        } else {
+            // the epilogues of the even (worker 1) or odd (worker 2) outputs
+            int j = 0, kb = 0;
+            for (int tl = 0; tl < my_tiles && ok; ++tl) {
+                int x0, y0, z0, nzt;
+                tile_of(tl, x0, y0, z0, nzt);
+                for (int z = 0; z < nzt && ok; ++z, ++j)
+                    if (j % 2 == wi - 1) ok = epilogue(j, z, kb, nzt, x0, y0, z0);
+                kb += nzt + 2 * C::RZ;
             }
         }
-        if (warp == 4 && lane == 0) {
-            MMS_TRACE_ADD(3, 0, wacc);
-            MMS_TRACE_ADD(3, 1, MMS_CLOCK() - tstart);
-            MMS_TRACE_ADD(3, 2, wbar);
+        if (!ok) *abort_flag = 1;
+        if (lane == 0 && warp == 4) {
+            MMS_TRACE_ADD(2, 0, ts);
+            MMS_TRACE_ADD(2, 1, ta);
+            MMS_TRACE_ADD(2, 2, td);
+            MMS_TRACE_ADD(2, 3, tc0);
+            MMS_TRACE_ADD(2, 4, tf);
+            MMS_TRACE_ADD(2, 5, MMS_CLOCK() - t00);
+            MMS_TRACE_ADD(3, 0, tep);
         }
     }
 
-    __syncwarp();  // the single-lane roles reconverge their warps first
+    __syncwarp();
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tbase, 512);
     }
+#ifdef MMS_ROLE_TRACE
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < 12 * kTl; i += blockDim.x) (&g_timeline[0][0])[i] = tl_smem[i];
+#endif
 }
 
 int g_num_sms = 0;
@@ -665,102 +708,66 @@ int num_sms()
     return g_num_sms;
 }
 
-template <int R, int PREC, bool LDG, bool PLANAR = false>
-cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int groups)
+// What one launch computes: the band weights (box: (2r+1)^3; planar and
+// star: the (2r+1)^2 in-plane set), the star's z weights, where the staged
+// planes start, and where the results go.
+struct Launch {
+    const float *band;
+    const float *cz;   // star only
+    int zoff;
+    float *out;
+    int64_t opy, opz;
+};
+
+template <int R, int PREC, int MODE>
+cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int nzt, const Launch &L)
 {
-    using C = Cfg<R, PREC, LDG, PLANAR>;
-    if constexpr (!C::OK) {
-        return cudaErrorNotSupported;
-    } else {
-        BoxCoef cf{};
-        for (int i = 0; i < C::WZ * C::W * C::W; ++i) cf.c[i] = s.coeffs[i];
-        TcArgs a;
-        a.in = s.in;
-        a.ipy = s.ipy;
-        a.ipz = s.ipz;
-        a.X = (int)s.nx + 2 * R;
-        a.Y = (int)s.ny + 2 * R;
-        // planar shapes (a batch of 2D grids) have no z halo; otherwise an
-        // output's centre plane is R - RZ planes into the padded grid
-        a.Z = (int)s.nz + (is_planar(s.shape) ? 0 : 2 * R);
-        a.zoff = is_planar(s.shape) ? 0 : R - C::RZ;
-        a.out = s.out;
-        a.opy = s.opy;
-        a.opz = s.opz;
-        a.nx = (int)s.nx;
-        a.ny = (int)s.ny;
-        a.nz = (int)s.nz;
-        a.vec = (s.opy % 4 == 0 && s.opz % 4 == 0 && reinterpret_cast<uintptr_t>(s.out) % 16 == 0) ? 1 : 0;
-        a.tiles_x = (int)((s.nx + C::TXO - 1) / C::TXO);
-        a.tiles_y = (int)((s.ny + C::TY - 1) / C::TY);
-        const int zgroups = (int)((s.nz + C::NZ - 1) / C::NZ);
-        a.groups = groups < zgroups ? groups : zgroups;
-        const int zchunks = (zgroups + a.groups - 1) / a.groups;
-        a.tiles = a.tiles_x * a.tiles_y * zchunks;
-        auto kern = box_tc_kernel<R, PREC, LDG, PLANAR>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        const int grid = a.tiles < num_sms() ? a.tiles : num_sms();
-        kern<<<grid, C::NT, C::SMEM, s.stream>>>(map, cf, a, device_error_word());
-        return cudaGetLastError();
-    }
+    using C = Cfg<R, PREC, MODE>;
+    static_assert(C::OK, "tensor-core configuration does not fit");
+    BoxCoef cf{};
+    const int ncoef = MODE == M_BOX ? C::W * C::W * C::W : C::W * C::W;
+    for (int i = 0; i < ncoef; ++i) cf.c[i] = L.band[i];
+    TcArgs a{};
+    a.out = L.out;
+    a.opy = L.opy;
+    a.opz = L.opz;
+    a.nx = (int)s.nx;
+    a.ny = (int)s.ny;
+    a.nz = (int)s.nz;
+    const uintptr_t ob = reinterpret_cast<uintptr_t>(L.out);
+    a.vec = (L.opy % 4 == 0 && L.opz % 4 == 0 && ob % 16 == 0) ? 4 : (L.opy % 2 == 0 && L.opz % 2 == 0 && ob % 8 == 0) ? 2 : 1;
+    const int64_t tx = (s.nx + C::TX - 1) / C::TX, ty = (s.ny + C::TY - 1) / C::TY, tz = (s.nz + nzt - 1) / nzt;
+    if (tx * ty * tz > (int64_t)1 << 30) return cudaErrorInvalidValue;
+    a.tiles_x = (int)tx;
+    a.tiles_y = (int)ty;
+    a.tiles = (int)(tx * ty * tz);
+    a.nzt = nzt;
+    a.zoff = L.zoff;
+    if (MODE == M_STAR)
+        for (int d = 0; d < C::W; ++d) a.cz[d] = L.cz[d];
+    auto kern = band_tc_kernel<R, PREC, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    const int grid = a.tiles < num_sms() ? a.tiles : num_sms();
+    kern<<<grid, C::NT, C::SMEM, s.stream>>>(map, cf, a, device_error_word());
+    return cudaGetLastError();
 }
 
-// Variants: z-groups per tile (the z extent of a tile is groups * NZ planes)
-// times the feed of the converters (TMA staging ring, or direct loads).
-constexpr int kGroups[] = {16, 8, 32, 4};
-constexpr int kNumGroups = sizeof(kGroups) / sizeof(int);
-constexpr int kNumVariants = 2 * kNumGroups;
+// Variants: output planes per z chunk of a tile; the star's variants
+// kNumTile.. run the paper's two-pass form (x/y pass into a temporary grid,
+// then the z pass).
+constexpr int kNzt[] = {64, 32, 128, 16};
+constexpr int kNumTile = sizeof(kNzt) / sizeof(int);
 
-template <int PREC, bool LDG, bool PLANAR>
-cudaError_t launch_feed(const Sweep &s, const CUtensorMap &map, int g)
+template <int PREC, int MODE>
+cudaError_t launch_mode(const Sweep &s, const CUtensorMap &map, int nzt, const Launch &L)
 {
     switch (s.r) {
-        case 1: return launch_r<1, PREC, LDG, PLANAR>(s, map, g);
-        case 2: return launch_r<2, PREC, LDG, PLANAR>(s, map, g);
-        case 3: return launch_r<3, PREC, LDG, PLANAR>(s, map, g);
-        case 4: return launch_r<4, PREC, LDG, PLANAR>(s, map, g);
+        case 1: return launch_r<1, PREC, MODE>(s, map, nzt, L);
+        case 2: return launch_r<2, PREC, MODE>(s, map, nzt, L);
+        case 3: return launch_r<3, PREC, MODE>(s, map, nzt, L);
+        case 4: return launch_r<4, PREC, MODE>(s, map, nzt, L);
         default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int PREC, bool PLANAR>
-cudaError_t launch_prec(const Sweep &s, const CUtensorMap &map, int v)
-{
-    const int g = kGroups[v % kNumGroups];
-    return v < kNumGroups ? launch_feed<PREC, false, PLANAR>(s, map, g)
-                          : launch_feed<PREC, true, PLANAR>(s, map, g);
-}
-
-template <int PREC, bool PLANAR>
-void box_dims(int r, int *bx, int *by, int *bz, int *swz)
-{
-#define MMS_DIMS(RR)                                          \
-    case RR:                                                  \
-        *bx = Cfg<RR, PREC, false, PLANAR>::K;                \
-        *by = Cfg<RR, PREC, false, PLANAR>::YP;               \
-        *bz = Cfg<RR, PREC, false, PLANAR>::NZ;               \
-        *swz = Cfg<RR, PREC, false, PLANAR>::SWZ ? 1 : 0;     \
-        return;
-    switch (r) {
-        MMS_DIMS(1)
-        MMS_DIMS(2)
-        MMS_DIMS(3)
-        MMS_DIMS(4)
-        default: *bx = *by = *bz = *swz = 0;
-    }
-#undef MMS_DIMS
-}
-
-template <int PREC, bool PLANAR>
-bool supported_r(int r)
-{
-    switch (r) {
-        case 1: return Cfg<1, PREC, false, PLANAR>::OK && Cfg<1, PREC, true, PLANAR>::OK;
-        case 2: return Cfg<2, PREC, false, PLANAR>::OK && Cfg<2, PREC, true, PLANAR>::OK;
-        case 3: return Cfg<3, PREC, false, PLANAR>::OK && Cfg<3, PREC, true, PLANAR>::OK;
-        case 4: return Cfg<4, PREC, false, PLANAR>::OK && Cfg<4, PREC, true, PLANAR>::OK;
-        default: return false;
     }
 }
 
@@ -774,29 +781,18 @@ int prec_of(int path)
     }
 }
 
-template <bool PLANAR>
-int supported(int r, int path)
+template <int MODE>
+cudaError_t launch_prec(const Sweep &s, int path, const CUtensorMap &map, int nzt, const Launch &L)
 {
     switch (prec_of(path)) {
-        case P_TF32: return supported_r<P_TF32, PLANAR>(r);
-        case P_3XTF32: return supported_r<P_3XTF32, PLANAR>(r);
-        case P_BF16X3: return supported_r<P_BF16X3, PLANAR>(r);
-        default: return 0;
-    }
-}
-
-template <bool PLANAR>
-cudaError_t launch_tc(const Sweep &s, int path, const CUtensorMap &map, int v)
-{
-    switch (prec_of(path)) {
-        case P_TF32: return launch_prec<P_TF32, PLANAR>(s, map, v);
-        case P_3XTF32: return launch_prec<P_3XTF32, PLANAR>(s, map, v);
-        case P_BF16X3: return launch_prec<P_BF16X3, PLANAR>(s, map, v);
+        case P_TF32: return launch_mode<P_TF32, MODE>(s, map, nzt, L);
+        case P_3XTF32: return launch_mode<P_3XTF32, MODE>(s, map, nzt, L);
+        case P_BF16X3: return launch_mode<P_BF16X3, MODE>(s, map, nzt, L);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// z part of the star after the tensor-core x/y pass:
+// z part of the two-pass star after the tensor-core x/y pass:
 //   out(x,y,z) = T(x,y,z) + sum_{dz != 0} cz[dz] in(x+r, y+r, z+r+dz)
 // Each thread owns four x positions of one row and marches a z range with a
 // register queue of the 2r+1 centre values.
@@ -870,72 +866,91 @@ cudaError_t launch_zpass(const Sweep &s, const float *T, int64_t tpy, int64_t tp
     return cudaGetLastError();
 }
 
+// The in-plane (2r+1)^2 weights [dy][dx] of a star (x line, y line and the
+// centre weights) or of a planar shape.
+void planar_weights(const Sweep &s, bool with_z_centre, float *c2)
+{
+    const int r = s.r, w = 2 * r + 1;
+    for (int i = 0; i < w * w; ++i) c2[i] = 0.f;
+    if (s.shape == MMS_BOX2D) {
+        for (int i = 0; i < w * w; ++i) c2[i] = s.coeffs[i];
+        return;
+    }
+    for (int d = -r; d <= r; ++d) {
+        c2[r * w + d + r] += s.coeffs[d + r];          // x line (dy = 0)
+        c2[(d + r) * w + r] += s.coeffs[w + d + r];    // y line (dx = 0)
+    }
+    if (with_z_centre) c2[r * w + r] += s.coeffs[2 * w + r];
+}
+
 }  // namespace
 
 int band_tc_supported(int shape, int r, int path)
 {
-    // the box runs the 3D kernel; the star's x/y pass and the planar shapes the planar one
-    return shape == MMS_BOX ? supported<false>(r, path) : supported<true>(r, path);
+    return shape >= MMS_STAR && shape <= MMS_BOX2D && r >= 1 && r <= kMaxR && prec_of(path) >= 0;
 }
 
-int band_tc_variants(int shape, int r, int path) { return band_tc_supported(shape, r, path) ? kNumVariants : 0; }
+int band_tc_variants(int shape, int r, int path)
+{
+    if (!band_tc_supported(shape, r, path)) return 0;
+    return shape == MMS_STAR ? 2 * kNumTile : kNumTile;
+}
+
+int band_tc_two_pass(int shape, int v) { return shape == MMS_STAR && v >= kNumTile && v < 2 * kNumTile; }
+
+int band_tc_two_pass_variant(int v) { return kNumTile + (v >= 0 ? v % kNumTile : 0); }
 
 void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz, int *swz)
 {
-    (void)v;
-    const bool planar = shape != MMS_BOX;
-    switch (prec_of(path)) {
-        case P_TF32: planar ? box_dims<P_TF32, true>(r, bx, by, bz, swz) : box_dims<P_TF32, false>(r, bx, by, bz, swz); return;
-        case P_3XTF32: planar ? box_dims<P_3XTF32, true>(r, bx, by, bz, swz) : box_dims<P_3XTF32, false>(r, bx, by, bz, swz); return;
-        case P_BF16X3: planar ? box_dims<P_BF16X3, true>(r, bx, by, bz, swz) : box_dims<P_BF16X3, false>(r, bx, by, bz, swz); return;
-        default: *bx = *by = *bz = *swz = 0;
-    }
+    (void)shape; (void)path; (void)v;
+    static const int boxw[kMaxR + 1] = {0, 60, 52, 52, 44};
+    *bx = r >= 1 && r <= kMaxR ? boxw[r] : 0;
+    *by = 32;
+    *bz = 1;
+    *swz = 0;
 }
 
-size_t band_tc_scratch_bytes(const Sweep &s) { return s.shape == MMS_STAR ? (size_t)s.nx * s.ny * s.nz * 4 : 0; }
+size_t band_tc_scratch_bytes(const Sweep &s)
+{
+    return band_tc_two_pass(s.shape, s.variant) ? (size_t)s.nx * s.ny * s.nz * 4 : 0;
+}
 
 cudaError_t launch_band_tc(const Sweep &s, int path, const CUtensorMap &map, int v, float *scratch)
 {
-    if (v < 0 || v >= kNumVariants) return cudaErrorInvalidValue;
-    if (s.shape == MMS_BOX) return launch_tc<false>(s, path, map, v);
+    if (v < 0 || v >= band_tc_variants(s.shape, s.r, path)) return cudaErrorInvalidValue;
+    const int nzt = kNzt[v % kNumTile];
     const int w = 2 * s.r + 1;
+    float c2[(2 * kMaxR + 1) * (2 * kMaxR + 1)];
+    if (s.shape == MMS_BOX) {
+        const Launch L{s.coeffs, nullptr, 0, s.out, s.opy, s.opz};
+        return launch_prec<M_BOX>(s, path, map, nzt, L);
+    }
     if (is_planar(s.shape)) {
         // Table I's 2D kernels: the planar banded pass straight into the output
-        float c2[(2 * kMaxR + 1) * (2 * kMaxR + 1)] = {};
-        if (s.shape == MMS_BOX2D) {
-            for (int i = 0; i < w * w; ++i) c2[i] = s.coeffs[i];
-        } else {
-            for (int d = -s.r; d <= s.r; ++d) {
-                c2[s.r * w + d + s.r] += s.coeffs[d + s.r];          // x line
-                c2[(d + s.r) * w + s.r] += s.coeffs[w + d + s.r];    // y line
-            }
-        }
-        Sweep p = s;
-        p.coeffs = c2;
-        return launch_tc<true>(p, path, map, v);
+        planar_weights(s, false, c2);
+        const Launch L{c2, nullptr, 0, s.out, s.opy, s.opz};
+        return launch_prec<M_PLANAR>(s, path, map, nzt, L);
     }
-    // Star: the in-plane x/y part (with the three centre weights) as a planar
-    // banded pass on tensor cores into `scratch` (the paper's temporary buffer
-    // for x/y partial results, Sec. 4.3), then the z part on CUDA cores.
-    const int r = s.r;
-    float c2[(2 * kMaxR + 1) * (2 * kMaxR + 1)] = {};
-    for (int d = -r; d <= r; ++d) {
-        c2[r * w + d + r] += s.coeffs[0 * w + d + r];  // x line (dy = 0)
-        c2[(d + r) * w + r] += s.coeffs[1 * w + d + r];  // y line (dx = 0)
+    if (!band_tc_two_pass(s.shape, v)) {
+        // the star in one pass: x/y lines and the centre on tensor cores, the
+        // z line summed by the converter warps
+        planar_weights(s, true, c2);
+        const Launch L{c2, s.coeffs + 2 * w, 0, s.out, s.opy, s.opz};
+        return launch_prec<M_STAR>(s, path, map, nzt, L);
     }
-    c2[r * w + r] += s.coeffs[2 * w + r];  // z centre
-    Sweep p = s;
-    p.coeffs = c2;
-    p.out = scratch;
-    p.opy = s.nx;
-    p.opz = s.nx * s.ny;
-    cudaError_t e = launch_tc<true>(p, path, map, v);
+    // The paper's two-pass star (Sec. 4.3): the in-plane x/y part with the
+    // three centre weights into `scratch` (its temporary buffer), then the z
+    // part on CUDA cores.
+    if (!scratch) return cudaErrorInvalidValue;
+    planar_weights(s, true, c2);
+    const Launch L{c2, nullptr, s.r, scratch, s.nx, s.nx * s.ny};
+    cudaError_t e = launch_prec<M_PLANAR>(s, path, map, nzt, L);
     if (e != cudaSuccess) return e;
-    switch (r) {
-        case 1: return launch_zpass<1>(s, scratch, p.opy, p.opz);
-        case 2: return launch_zpass<2>(s, scratch, p.opy, p.opz);
-        case 3: return launch_zpass<3>(s, scratch, p.opy, p.opz);
-        case 4: return launch_zpass<4>(s, scratch, p.opy, p.opz);
+    switch (s.r) {
+        case 1: return launch_zpass<1>(s, scratch, s.nx, s.nx * s.ny);
+        case 2: return launch_zpass<2>(s, scratch, s.nx, s.nx * s.ny);
+        case 3: return launch_zpass<3>(s, scratch, s.nx, s.nx * s.ny);
+        case 4: return launch_zpass<4>(s, scratch, s.nx, s.nx * s.ny);
         default: return cudaErrorInvalidValue;
     }
 }

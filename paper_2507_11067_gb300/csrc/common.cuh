@@ -61,8 +61,10 @@ __host__ __device__ constexpr bool is_planar(int shape) { return shape == MMS_ST
 
 // Tensor-core banded sweeps (band_tc.cu).
 int band_tc_supported(int shape, int r, int path);
-// The star runs as a planar tensor-core pass into `scratch` (nx*ny*nz floats,
-// dense) followed by a CUDA-core z pass; the box needs no scratch.
+// The star's two-pass variants run a planar tensor-core pass into `scratch`
+// (nx*ny*nz floats, dense; band_tc_scratch_bytes of the sweep with its
+// resolved variant in Sweep::variant) followed by a CUDA-core z pass; every
+// other variant needs no scratch.
 cudaError_t launch_band_tc(const Sweep &s, int path, const CUtensorMap &tmap, int variant, float *scratch);
 size_t band_tc_scratch_bytes(const Sweep &s);
 void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz, int *swz);

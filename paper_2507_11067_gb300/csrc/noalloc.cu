@@ -1,17 +1,15 @@
 // noalloc.cu -- the star sweep on tensor cores for callers that cannot
 // allocate device memory (mms_stencil_apply_noalloc in include/mms.h).
 //
-// The star's tensor-core form needs a temporary grid of nx*ny*nz floats for
-// the in-plane partial sums.  mms_stencil_apply_ex takes it from the
-// device's stream-ordered memory pool on every call; some callers cannot
-// allow that: code whose memory is budgeted up front (a host that reserves
-// all device memory for its own allocator), code that may not call
-// cudaMalloc-family routines at all (a driver or plugin with a fixed
+// The paper's two-pass form of the star (Sec. 4.3) needs a temporary grid
+// of nx*ny*nz floats for the in-plane partial sums.  mms_stencil_apply_ex
+// takes it from the device's stream-ordered memory pool on every call; some
+// callers cannot allow that: code whose memory is budgeted up front (a host
+// that reserves all device memory for its own allocator), code that may not
+// call cudaMalloc-family routines at all (a driver or plugin with a fixed
 // footprint).  Here the temporary grid is a file-scope device array of a
 // fixed size, part of the library's own module, so the call allocates
 // nothing.
-#include <mutex>
-
 #include "common.cuh"
 #include "validate.cuh"
 
@@ -19,6 +17,8 @@ namespace mms {
 
 mms_status fail(mms_status st, const char *fmt, ...);
 mms_status cuda_fail(cudaError_t e, const char *what);
+// band_tc.cu: the two-pass star variant with the tile shape of variant v
+int band_tc_two_pass_variant(int v);
 
 namespace {
 
@@ -26,26 +26,18 @@ namespace {
 // MMS_NOALLOC_MAX_POINTS floats (32 MiB) until the process exits.
 static __device__ __align__(256) float g_noalloc_scratch[MMS_NOALLOC_MAX_POINTS];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-float *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device.  In host code the array's name only stands for the symbol.
-mms_status scratch_of_current_device(float **ptr)
+// Device address of g_noalloc_scratch in the calling thread's current
+// context.  In host code the array's name only stands for the symbol.  The
+// address is looked up on every call (a host-side query): a cached one
+// would go stale when the context changes under the same device number
+// (after cudaDeviceReset the module is loaded again, possibly elsewhere; a
+// caller's own driver-API context has its own copy of the array).
+mms_status scratch_of_current_context(float **ptr)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return fail(MMS_E_UNSUPPORTED, "device %d above %d", dev, kMaxDevices - 1);
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch");
-        g_scratch_ptr[dev] = static_cast<float *>(p);
-    }
-    *ptr = g_scratch_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch");
+    *ptr = static_cast<float *>(p);
     return MMS_OK;
 }
 
@@ -67,6 +59,7 @@ static mms_status apply_noalloc(const mms_stencil_desc *d, const float *in, floa
     if (d->nx < 0 || d->ny < 0 || d->nz < 0) return fail(MMS_E_ARG, "negative size");
     if (d->nx >= (1ll << 30) || d->ny >= (1ll << 30) || d->nz >= (1ll << 30))
         return fail(MMS_E_ARG, "size above 2^30");
+    if (d->path < MMS_PATH_AUTO || d->path > MMS_PATH_NAIVE) return fail(MMS_E_ARG, "unknown path %d", d->path);
     int path = d->path == MMS_PATH_AUTO ? MMS_PATH_BF16X3 : d->path;
     if (path != MMS_PATH_TF32 && path != MMS_PATH_3XTF32 && path != MMS_PATH_BF16X3)
         return fail(MMS_E_UNSUPPORTED, "the no-alloc sweep runs on tensor-core paths only (path %d)", d->path);
@@ -95,12 +88,15 @@ static mms_status apply_noalloc(const mms_stencil_desc *d, const float *in, floa
         return fail(MMS_E_ALIGN, "TMA path needs a 16-byte aligned input and pitches that are multiples of 4 floats");
     if (!band_tc_supported(MMS_STAR, r, path))
         return fail(MMS_E_UNSUPPORTED, "path %d does not support the star of radius %d", path, r);
+    // the two-pass form with the tile shape of the requested (or the
+    // library's default) variant: the form that needs the temporary grid
     const int nvar = band_tc_variants(MMS_STAR, r, path);
-    const int v = d->variant >= 0 ? d->variant : mms_default_variant(MMS_STAR, r, path, d->nx, d->ny, d->nz);
-    if (v < 0 || v >= nvar) return fail(MMS_E_ARG, "variant %d of %d", v, nvar);
+    if (d->variant >= nvar) return fail(MMS_E_ARG, "variant %d of %d", d->variant, nvar);
+    const int v = band_tc_two_pass_variant(
+        d->variant >= 0 ? d->variant : mms_default_variant(MMS_STAR, r, path, d->nx, d->ny, d->nz));
 
     float *scratch = nullptr;
-    mms_status st = scratch_of_current_device(&scratch);
+    mms_status st = scratch_of_current_context(&scratch);
     if (st != MMS_OK) return st;
 
     Sweep s{MMS_STAR, r, d->nx, d->ny, d->nz, in, ipy, ipz, out, opy, opz, d->coeffs, v,

@@ -64,12 +64,52 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d, uint32_t a, uint64_t bde
         : "memory");
 }
 
+// The same MMAs issued by the lanes whose `on` is set, with every lane of
+// the warp executing the statement: an issuing warp that stays converged
+// (no branch around a single-lane issue) keeps the tensor pipe's queue fed
+// without a reconvergence between batches of MMAs.
+__device__ __forceinline__ void mma_bf16_ts_if(uint32_t on, uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "setp.ne.b32 q, %5, 0;\n\t"
+        "@q tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(on)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32_ts_if(uint32_t on, uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "setp.ne.b32 q, %5, 0;\n\t"
+        "@q tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(on)
+        : "memory");
+}
+
 // Arrives once on `bar` when every MMA this thread issued before it is done.
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             ptx::smem_u32(bar))
+        : "memory");
+}
+
+// mma_commit by the lanes whose `on` is set, the whole warp executing it.
+__device__ __forceinline__ void mma_commit_if(uint32_t on, uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.b32 q, %1, 0;\n\t"
+        "@q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+            ptx::smem_u32(bar)),
+        "r"(on)
         : "memory");
 }
 
@@ -123,6 +163,17 @@ __device__ __forceinline__ void tmem_wait_ld()
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Registers filled by tcgen05.ld hold their values only after
+// tcgen05.wait::ld, but the compiler sees them defined at the load.  Called
+// right after tmem_wait_ld(), this redefines them in a volatile statement
+// that stays after the wait, so no use of them is scheduled before it.
+template <int N>
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+r"(r[i]));
+}
+
 // Waits for this thread's outstanding TMEM loads; the registers are tied
 // in and out so that no use of them is scheduled before the wait.
 __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&r)[16])
@@ -140,6 +191,16 @@ __device__ __forceinline__ void tmem_st_32x32b_x8(uint32_t taddr, const uint32_t
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
         "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_32x32b_x16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
         : "memory");
 }
 

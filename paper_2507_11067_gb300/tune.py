@@ -115,3 +115,32 @@ def load_table(table=TABLE, n=None):
             _lib.set_variant(shape, r, path, var)
             registered[(shape, r, path)] = var
     return registered
+
+
+# The grids the committed table is tuned on: the 3D kernels at the sizes the
+# benchmark times (box 512^3, star 1024^3), Table I's 2D kernels on one
+# 8192^2 plane.
+STANDARD = [(shape, r, n) for r in (1, 2, 3, 4)
+            for shape, n in (("box", (512, 512, 512)), ("star", (1024, 1024, 1024)),
+                             ("star2d", (8192, 8192, 1)), ("box2d", (8192, 8192, 1)))]
+
+
+def retune(table=TABLE, reps=10):
+    """Re-measure every (shape, radius) of STANDARD on this GPU (CUDA-core
+    variants, and the BF16x3 tensor-core variants kept where faster) and
+    rewrite their rows of `table`; returns {(shape, r): results}."""
+    out = {}
+    for shape, r, n in STANDARD:
+        out[(shape, r)] = tune_auto(shape, r, *n, reps=reps, table=table)
+        best = {p: min(ms) for p, (_, ms) in out[(shape, r)].items()}
+        print(f"{shape} r={r} {n[0]}x{n[1]}x{n[2]}: " + ", ".join(f"{p} {v:.3f} ms" for p, v in best.items()),
+              flush=True)
+    return out
+
+
+if __name__ == "__main__":
+    import sys
+    from . import build
+    build()
+    _lib.load()
+    retune(table=sys.argv[1] if len(sys.argv) > 1 else TABLE)

@@ -1,7 +1,11 @@
 /* A plain C program against include/mms.h and libmms.so: the boundary needs
  * no C++, CUDA or Python types.  Only host-side calls (version, variant
- * counts, argument refusals), so it runs without a GPU. */
+ * counts, argument refusals), so it runs without a GPU.  With the arguments
+ * "gpu PATH VARIANT" (on a GPU) it also checks that AUTO and the default
+ * variant of the box of radius 2 are those of the library's built-in tuned
+ * table for the device, with nothing registered by the caller. */
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "mms.h"
@@ -16,7 +20,7 @@ static void expect(int cond, const char *what)
     }
 }
 
-int main(void)
+int main(int argc, char **argv)
 {
     float c[27] = {0};
     float buf[64] = {0};
@@ -45,6 +49,13 @@ int main(void)
     w.rec_z = -1;
     expect(mms_wave_step(&w, c, buf, buf, buf + 32, buf, NULL, NULL) == MMS_E_ARG, "65 shots refused");
     expect(strlen(mms_last_error()) > 0, "refusals leave a message");
+
+    if (argc > 3 && strcmp(argv[1], "gpu") == 0) {
+        const int want_path = atoi(argv[2]), want_variant = atoi(argv[3]);
+        expect(mms_auto_path(MMS_BOX, 2, 1) == want_path, "AUTO of the box r=2 follows the built-in table");
+        expect(mms_default_variant(MMS_BOX, 2, want_path, 512, 512, 512) == want_variant,
+               "default variant of the box r=2 follows the built-in table");
+    }
 
     if (fails == 0) printf("ok\n");
     return fails;

@@ -51,10 +51,34 @@ def test_traffic_goes_null_when_a_source_changes(tmp_path, monkeypatch):
 
 
 def test_tensor_core_dense_work_per_point():
-    # 2 * K_pad * (2r+1)^2 passes * 3 products (BF16x3), K_pad = TXO + 2r rounded to 16
-    assert bench.tc_dense_flop_per_pt("bf16x3", 2) == 4800
-    assert bench.tc_dense_flop_per_pt("bf16x3", 4) == 15552
-    assert bench.tc_dense_flop_per_pt("bf16x3", 1) == 2592
+    # per output plane a tile (4 subtiles of TXO = 16 - 2r outputs, TY = 32 - 2r
+    # rows) runs 128 x N x 16 MMAs, N = (2r+1) TXO rounded up to 16, for each
+    # plane reached in z, times 3 split products (BF16x3)
+    assert bench.tc_dense_flop_per_pt("bf16x3", 2) == pytest.approx(2 * 128 * 64 * 16 * 5 * 3 / (4 * 12 * 28))
+    assert bench.tc_dense_flop_per_pt("bf16x3", 4) == pytest.approx(2 * 128 * 80 * 16 * 9 * 3 / (4 * 8 * 24))
+    assert bench.tc_dense_flop_per_pt("tf32", 1) == pytest.approx(2 * 128 * 48 * 16 * 3 / (4 * 14 * 30))
+    assert bench.tc_dense_flop_per_pt("bf16x3", 4, planar=True) == pytest.approx(2 * 128 * 80 * 16 * 3 / (4 * 8 * 24))
+
+
+def test_tensor_core_roofline_is_the_stencils_own_floor():
+    # box r=2 512^3 in 0.4734 ms: the binding floor is HBM (4 (516^3 + 512^3)
+    # bytes at 6690.8 GB/s = 0.162 ms, far above 250 flop/pt at the BF16
+    # peak), so frac = algorithmic bytes / time / measured HBM, and the dense
+    # MMA work goes to the side fields
+    n, sec = 512 ** 3, 0.4734e-3
+    b = 4.0 * (516 ** 3 + 512 ** 3)
+    r = bench.tc_roofline("box", 2, "bf16x3", n, b, sec, 6690.8, 1714.1, "measured sustained")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6690.8
+    assert r["frac"] == pytest.approx(b / sec / 1e9 / 6690.8)
+    assert r["frac"] == pytest.approx(0.343, abs=1e-3)
+    dense = bench.tc_dense_flop_per_pt("bf16x3", 2) * n
+    assert r["dense_tflops"] == pytest.approx(dense / sec / 1e12)
+    assert r["tensor_pipe_frac"] == pytest.approx(dense / sec / 1e12 / 1714.1)
+    # a hypothetical sweep whose useful flops outrun the tensor floor reports
+    # against the tensor peak (TF32 at 1.1/2.25 of BF16)
+    r = bench.tc_roofline("box", 4, "tf32", n, 1.0, 1e-3, 6690.8, 1714.1, "x")
+    assert r["bound"] == "tensor" and r["peak"] == pytest.approx(1714.1 * 1.1 / 2.25)
+    assert r["frac"] == pytest.approx(2 * 729 * n / 1e-3 / 1e12 / (1714.1 * 1.1 / 2.25))
 
 
 def test_job_rate_and_fp32_peak():

@@ -28,7 +28,9 @@ def rel(g, o):
     return float(np.abs(np.asarray(g, np.float64) - o).max() / max(np.abs(o).max(), 1e-300))
 
 
-SIZES = [(53, 41, 19), (24, 28, 8), (7, 5, 3), (100, 70, 37)]
+# ragged tiles in x and y; z chunks of 64, 32, 128 or 16 planes (the
+# variants) leave one-plane and ragged last chunks (nz = 1, 17, 37)
+SIZES = [(53, 41, 19), (24, 28, 8), (7, 5, 3), (100, 70, 37), (40, 35, 1), (33, 29, 17)]
 
 
 @pytest.mark.parametrize("path", ["bf16x3", "3xtf32", "tf32"])
@@ -88,19 +90,21 @@ def test_every_tensor_core_combination_is_built():
                 assert mms.num_variants(shape, r, path) > 0, (shape, path, r)
 
 
-@pytest.mark.parametrize("path", ["bf16x3", "3xtf32"])
-@pytest.mark.parametrize("r", [1, 2, 4])
-def test_star_tc_two_pass_matches_oracle(path, r):
-    # Star on tensor cores: planar banded x/y pass into a temporary grid,
-    # then the z part on CUDA cores.
-    if mms.num_variants("star", r, path) == 0:
-        pytest.skip("not built for this radius")
-    for k, n in enumerate([(53, 41, 19), (30, 66, 9)]):
+@pytest.mark.parametrize("path", ["bf16x3", "3xtf32", "tf32"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_star_tc_matches_oracle(path, r):
+    # Star on tensor cores, every variant: the single-pass form (x/y lines
+    # and centre as a planar band, z line summed by the converter warps) and
+    # the paper's two-pass form (planar pass into a temporary grid, then the
+    # z part on CUDA cores).
+    nvar = mms.num_variants("star", r, path)
+    assert nvar > 0
+    for k, n in enumerate([(53, 41, 19), (30, 66, 9), (40, 35, 1), (33, 29, 17)]):
         grid = workloads.uniform_grid(*n, r, workload=3, salt=500 + 10 * r + k)
         c = workloads.star_coeffs(r) if r == 4 else workloads.normal_coeffs("star", r, workload=3, salt=k)
         ref = oracle.stencil("star", r, c, grid)
         inp = mms.to_padded_device(grid, r)
-        for v in (0, mms.num_variants("star", r, path) - 1):
+        for v in range(nvar):
             out = mms.apply("star", r, c, inp, path=path, variant=v)
             torch.cuda.synchronize()
             mms.check_device()

@@ -473,3 +473,112 @@ def test_rtm512_graph_step_sampled_full_size():
         # the records are the receiver plane of the new state, bit for bit
         rp = torch.from_numpy(plane).cuda()
         assert torch.equal(rec[0, sh][rp[:, 1], rp[:, 0]], out[sh][w.zrec + R, rp[:, 1] + R, rp[:, 0] + R])
+
+
+# ------------------------------------------- the gradient workload as stated
+# 2 shots x 256^3, 200 steps, checkpoint every 20 (the gradient workload's own
+# sizes; both checks take a few seconds at this size).
+
+def _smooth_directions(n, count, seed, amp=30.0):
+    """Seeded smooth velocity perturbations on the device: each a sum of four
+    3D sinusoids with wavelengths of at least 24 cells, scaled to max |d| =
+    amp m/s."""
+    g = np.random.default_rng(seed)
+    ax = torch.arange(n, device="cuda", dtype=torch.float32)
+    z, y, x = torch.meshgrid(ax, ax, ax, indexing="ij")
+    out = []
+    for _ in range(count):
+        d = torch.zeros((n, n, n), device="cuda")
+        for _ in range(4):
+            k = g.uniform(-2 * np.pi / 24, 2 * np.pi / 24, 3)
+            d += float(g.uniform(0.5, 1.0)) * torch.sin(float(k[0]) * x + float(k[1]) * y + float(k[2]) * z
+                                                        + float(g.uniform(0, 2 * np.pi)))
+        out.append(d * (amp / d.abs().max()))
+    return out
+
+
+def test_gradient_fd_16_directions_full_size():
+    # Central differences of J(v) = 1/2 |d(v) - d_obs|^2 along 16 seeded
+    # smooth directions against the autograd gradient (hand-written adjoint,
+    # checkpoint every 20 with recompute, FP64 accumulation), at rel 1e-2:
+    # the FP32 propagation's rounding in J limits the agreement.
+    n, ns, nsteps, every = 256, 2, 200, 20
+    w_true = workloads.WaveInputs(n, n, n, nshots=ns, nsteps=nsteps, workload=5, noise=True)
+    w0 = workloads.WaveInputs(n, n, n, nshots=ns, nsteps=nsteps, workload=5, noise=False)
+    prop = WavePropagator(n, n, n, w0.src, w0.zrec, w0.h, w_true.dt, sponge_width=w0.sponge,
+                          sponge_a=w0.sponge_a)
+    amps = torch.from_numpy(w_true.amp).cuda()
+    with torch.no_grad():
+        obs = WaveFunction.apply(torch.from_numpy(w_true.v).cuda(), prop, amps, nsteps, every)
+    v0 = torch.from_numpy(w0.v).cuda()
+    v = v0.clone().requires_grad_(True)
+    loss = 0.5 * ((WaveFunction.apply(v, prop, amps, nsteps, every) - obs) ** 2).sum()
+    loss.backward()
+    g = v.grad.double()
+    torch.cuda.synchronize()
+    mms.check_device()
+
+    def J(vv):
+        with torch.no_grad():
+            return float(0.5 * ((WaveFunction.apply(vv, prop, amps, nsteps, every) - obs).double() ** 2).sum())
+
+    worst = 0.0
+    for d in _smooth_directions(n, 16, seed=16):
+        eps = 1.0
+        fd = (J(v0 + eps * d) - J(v0 - eps * d)) / (2 * eps)
+        an = float((g * d.double()).sum())
+        worst = max(worst, abs(fd - an) / abs(an))
+        assert abs(fd - an) <= 1e-2 * abs(an), (fd, an)
+    print(f"gradient 2 x 256^3 x 200 steps: 16 central-difference directions, worst rel {worst:.2e}")
+
+
+def _segment_dot(n, ns, K, seed):
+    """<M(u, w), y> and <u, lam^1> + <w, -G^2 lam^2> for the K-step map
+    M: (a^1, a^0) = (u, w) -> a^{K+1} of the wave step without sources, its
+    transpose by K adjoint steps from lam^{K+1} = y, lam^{K+2} = 0 (FP64 inner
+    products of the FP32 fields)."""
+    w = workloads.WaveInputs(n, n, n, nshots=ns, nsteps=K, workload=5, noise=False)
+    cf = workloads.fd8_star_coeffs()
+    f = [mms.padded_empty(n, n, n, R, nshots=ns) for _ in range(7)]
+    py, pz, ss = mms.field_geometry(f[0])
+    desc, _keep = mms.wave_desc(n, n, n, R, ns, py, pz, ss, w.sponge, w.sponge_a, w.zrec, w.src)
+    m = mms.padded_empty(n, n, n, R)
+    mms.model_from_velocity(desc, torch.from_numpy(w.v).cuda(), m, w.dt, w.h)
+    u, ww, y, cur, prev, lc, lp = f
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    for t in (u, ww, y):
+        t[:, R:-R, R:-R, R:-R] = torch.rand((ns, n, n, n), device="cuda", generator=g) * 2 - 1
+    zero_amp = torch.zeros(ns, device="cuda")
+    cur.copy_(u)
+    prev.copy_(ww)
+    for _ in range(K):
+        mms.wave_step(desc, cf, m, cur, prev, zero_amp)   # prev <- a^{n+1}
+        cur, prev = prev, cur
+    lc.copy_(y)
+    lp.zero_()
+    for _ in range(K):
+        mms.wave_adjoint(desc, cf, m, lc, lp)             # lp <- lam^n
+        lc, lp = lp, lc
+    # lc = lam^1, lp = lam^2; -G^2 lam^2 is the adjoint step with lam^{n+1} = 0
+    tw = prev                                             # reuse a field buffer
+    tw.copy_(lp)
+    zero = mms.padded_empty(n, n, n, R, nshots=ns)
+    mms.wave_adjoint(desc, cf, m, zero, tw)
+    torch.cuda.synchronize()
+    mms.check_device()
+    lhs = _dot(_flat(cur), _flat(y))
+    rhs = _dot(_flat(u), _flat(lc)) + _dot(_flat(ww), _flat(tw))
+    return lhs, rhs
+
+
+def test_adjoint_dot_product_one_checkpoint_segment_full_size():
+    # The transpose test of the gradient workload's checkpoint segment: the
+    # 20-step map of 2 shots x 256^3 against 20 adjoint steps, at rel 1e-6.
+    # The 200-step map (the whole run) is printed beside it.
+    lhs, rhs = _segment_dot(256, 2, 20, seed=1)
+    rel20 = abs(lhs - rhs) / (abs(lhs) + abs(rhs))
+    lhs2, rhs2 = _segment_dot(256, 2, 200, seed=2)
+    rel200 = abs(lhs2 - rhs2) / (abs(lhs2) + abs(rhs2))
+    print(f"adjoint dot test, 2 x 256^3: 20-step segment rel {rel20:.2e}, 200-step map rel {rel200:.2e}")
+    assert rel20 <= 1e-6, (lhs, rhs)
+    assert rel200 <= 1e-4, (lhs2, rhs2)
