@@ -135,6 +135,45 @@ def flop_per_pt(shape, r):
     return 2 * workloads.n_points(shape, r)
 
 
+ERROR_NOTE = ("max |result - oracle| / max |oracle| at seeded sample points (corners and face centres "
+              "included) of the timed run's own inputs, against the FP64 oracle; wave, VTI and TTI: one step "
+              "after the timed steps, from the state they left, shot 0")
+
+
+def rel_err(got, ref) -> float:
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    return float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def sweep_error(shape, r, coeffs, host_grid, out, salt=0, npts=2000) -> float:
+    """Max-relative error of a sweep's output `out` (device or host, (nz, ny,
+    nx)) against the FP64 oracle on the padded host input `host_grid`."""
+    import oracle
+    nz, ny, nx = out.shape
+    pts = workloads.sample_points(nx, ny, nz, npts, workload=9, salt=salt)
+    if shape in PLANAR:
+        ref = oracle.stencil2d_points(shape, r, coeffs, host_grid, pts)
+    else:
+        ref = oracle.stencil_points(shape, r, coeffs, host_grid, pts)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    if not isinstance(out, np.ndarray):            # a torch tensor on the device
+        import torch
+        idx = torch.from_numpy(pts).to(out.device)
+        got = out[idx[:, 2], idx[:, 1], idx[:, 0]].double().cpu().numpy()
+    else:
+        got = np.asarray(out)[z, y, x]
+    return rel_err(got, ref)
+
+
+def at_points(pts, shape, values):
+    """A zero FP64 array of `shape` holding `values` at the points (x, y, z)
+    (np.zeros leaves untouched pages unallocated): the oracle's point-wise
+    steps read a per-point medium only at their points."""
+    a = np.zeros(shape)
+    a[pts[:, 2], pts[:, 1], pts[:, 0]] = values
+    return a
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -306,8 +345,7 @@ def oracle_sample(planes: int, salt: int = 0, plan=None):
         oracle.stencil(shape, r, c, sub)
         secs += time.perf_counter() - t0
         pts += planes * n * n
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return pts, secs, threads
+    return pts, secs, oracle_threads()
 
 
 def oracle_wave_sample(planes: int, n: int, gradient: bool, salt: int = 0):
@@ -330,8 +368,7 @@ def oracle_wave_sample(planes: int, n: int, gradient: bool, salt: int = 0):
         grad = np.zeros((planes, n, n))
         prob.adjoint_step(nxt, a_cur, None, a_prev, grad)
     secs = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return planes * n * n, secs, threads
+    return planes * n * n, secs, oracle_threads()
 
 
 def oracle_aniso_sample(planes: int, n: int, kind: str, salt: int = 0):
@@ -353,13 +390,37 @@ def oracle_aniso_sample(planes: int, n: int, kind: str, salt: int = 0):
         t0 = time.perf_counter()
         aniso.vti_step(r, workloads.fd8_star_coeffs(), mh, mv, (20, 0.015), a.src[0], 1e-3, *fields)
     secs = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return planes * n * n, secs, threads
+    return planes * n * n, secs, oracle_threads()
 
 
 def oracle_pad(f, r):
     import oracle
     return oracle.pad(f, r)
+
+
+def cpu_baseline(sample, unit, what, budget_s=5.0):
+    """The oracle timed on the host: on all cores (OpenMP), then on one core,
+    each on a slab sized for about budget_s seconds; `what` names the sample
+    ({planes} is filled in)."""
+    import oracle
+    oracle.build()
+    planes = calibrate_planes(budget_s, sample)
+    p, secs, threads = sample(planes)
+    out = {"value": p / secs / 1e9, "unit": unit, "cores": threads, "kind": "oracle",
+           "sample": what.format(planes=planes)}
+    old = oracle.set_threads(1)
+    try:
+        planes1 = calibrate_planes(budget_s, sample)
+        p, secs, _ = sample(planes1)
+    finally:
+        oracle.set_threads(old)
+    out["one_core"] = {"value": p / secs / 1e9, "unit": unit, "cores": 1, "sample": what.format(planes=planes1)}
+    return out
+
+
+def oracle_threads() -> int:
+    import oracle
+    return oracle.set_threads(0)
 
 
 def calibrate_planes(budget_s: float, sample=None) -> int:
@@ -476,10 +537,11 @@ def main():
     plan = WORKLOADS[args.workload]
     if args.n:   # a smaller grid of the same sweeps (profiling captures)
         plan = [(shape, r, args.n) for shape, r, _ in plan]
-    coeffs, inputs, outputs, hosts, host_out = [], [], [], [], []
+    coeffs, inputs, outputs, hosts, host_out, grids = [], [], [], [], [], []
     for (shape, r, n) in plan:
         coeffs.append(sweep_coeffs(shape, r))
         grid = sweep_input(shape, r, n, rank)
+        grids.append(grid)
         nx_, ny_, nz_ = sweep_dims(shape, n)
         alloc = mms.padded_empty2d if shape in PLANAR else mms.padded_empty
         # host buffer pinned with the device pitch, so each copy is one memcpy
@@ -492,7 +554,6 @@ def main():
         inputs[-1].copy_(hosts[-1])
         outputs.append(torch.empty((nz_, ny_, nx_), device=dev))
         host_out.append(torch.empty((nz_, ny_, nx_), pin_memory=True))
-        del grid
     stream = torch.cuda.current_stream(dev)
     steps = args.steps or max(20, int(2000 / max(1, sum(sweep_points(sh, n) for sh, _, n in plan) / 2.7e8)))
 
@@ -608,18 +669,20 @@ def main():
                                        "hbm_gbs": b / sec / 1e9, "hbm_frac": b / sec / 1e9 / hbm_peak,
                                        "tflops": f / sec / 1e12, "alu_frac": f / sec / 1e12 / alu_peak}
 
+    # ---- accuracy of every timed result (outside the timed regions): the
+    # device-resident sweeps and the end-to-end outputs, against the oracle
+    errors = {}
+    for i, (shape, r, n) in enumerate(plan):
+        p_i = mms.auto_path(shape, r) if args.path == "auto" else args.path
+        errors[f"{shape}_r{r}_{n}_{p_i}"] = sweep_error(shape, r, coeffs[i], grids[i], outputs[i], salt=i)
+        errors[f"{shape}_r{r}_{n}_{p_i}_e2e"] = sweep_error(shape, r, coeffs[i], grids[i],
+                                                           hout_sets[0][i].numpy(), salt=10 + i)
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        import oracle
-        oracle.build()
-
-        def sample(p, salt=0):
-            return oracle_sample(p, salt, plan)
-        planes = calibrate_planes(5.0, sample)
-        p, s, threads = sample(planes)
-        cpu = {"value": p / s / 1e9, "unit": "GPoints/s", "cores": threads, "kind": "oracle",
-               "sample": f"FP64 oracle, " + ", ".join(f"{sh} r={r}" for sh, r, _ in plan) +
-                         f", a seeded slab of {planes} output planes per sweep"}
+        cpu = cpu_baseline(lambda p, salt=0: oracle_sample(p, salt, plan), "GPoints/s",
+                           "FP64 oracle, " + ", ".join(f"{sh} r={r}" for sh, r, _ in plan) +
+                           ", a seeded slab of {planes} output planes per sweep")
 
     line = {
         "metric": METRIC, "value": value, "unit": "GPoints/s", "n_gpus": world,
@@ -639,7 +702,7 @@ def main():
                         "streams"},
         "gpu_launches": len(plan) * steps,
         "clocks": clk, "peaks": {"hbm_gbs": hbm_peak, "bf16_tflops": bf16_peak, "source": peak_src},
-        "sweeps": sweeps,
+        "sweeps": sweeps, "errors": errors, "error_note": ERROR_NOTE,
     }
     if not args.no_extras:
         line["extras"] = extras(mms, torch, dev, hbm_peak, alu_peak)
@@ -789,17 +852,10 @@ def run_wave(args):
         unit = "GPoint-steps/s"
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
         grad = args.workload == "grad256"
-
-        def sample(p, salt=0):
-            return oracle_wave_sample(p, n, grad, salt)
-        planes = calibrate_planes(5.0, sample)
-        p, s, threads = sample(planes)
-        cpu = {"value": p / s / 1e9, "unit": unit, "cores": threads, "kind": "oracle",
-               "sample": f"FP64 oracle {'forward, recompute and adjoint steps' if grad else 'forward step'} "
-                         f"of one shot on a seeded {planes} x {n} x {n} slab"}
+        cpu = cpu_baseline(lambda p, salt=0: oracle_wave_sample(p, n, grad, salt), unit,
+                           f"FP64 oracle {'forward, recompute and adjoint steps' if grad else 'forward step'} "
+                           f"of one shot on a seeded {{planes}} x {n} x {n} slab")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / (steps if args.workload == "rtm512" else reps),
@@ -922,15 +978,9 @@ def run_aniso(args):
     unit = "GPoint-steps/s"
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-
-        def sample(p, salt=0):
-            return oracle_aniso_sample(p, n, spec["kind"], salt)
-        planes = calibrate_planes(5.0, sample)
-        p, secs, threads = sample(planes)
-        cpu = {"value": p / secs / 1e9, "unit": unit, "cores": threads, "kind": "oracle",
-               "sample": f"FP64 oracle {spec['kind'].upper()} step of one shot on a seeded {planes} x {n} x {n} slab"}
+        cpu = cpu_baseline(lambda p, salt=0: oracle_aniso_sample(p, n, spec["kind"], salt), unit,
+                           f"FP64 oracle {spec['kind'].upper()} step of one shot on a seeded {{planes}} x {n} x {n} "
+                           "slab")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / steps,
@@ -1042,16 +1092,9 @@ def run_f64(args):
               for i, (sh, rr, n_) in enumerate(plan)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-
-        def sample(p, salt=0):
-            return oracle_sample(p, salt, plan)
-        planes = calibrate_planes(5.0, sample)
-        p, secs, threads = sample(planes)
-        cpu = {"value": p / secs / 1e9, "unit": "GPoints/s", "cores": threads, "kind": "oracle",
-               "sample": "FP64 oracle, " + ", ".join(f"{sh} r={rr}" for sh, rr, _ in plan) +
-                         f", on a seeded slab of {planes} output planes of each grid"}
+        cpu = cpu_baseline(lambda p, salt=0: oracle_sample(p, salt, plan), "GPoints/s",
+                           "FP64 oracle, " + ", ".join(f"{sh} r={rr}" for sh, rr, _ in plan) +
+                           ", on a seeded slab of {planes} output planes of each grid")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GPoints/s", "n_gpus": world, "steps": steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / steps, "higher_is_better": True,
@@ -1083,33 +1126,232 @@ def _time(fn, reps=5):
 
 
 def extras(mms, torch, dev, hbm_peak, alu_peak):
-    """Per-path timings outside the timed region: every sweep path on the
-    box workload, and the 1024^3 star r=4 against the HBM roofline."""
+    """Timings outside the timed region, each with its error against the
+    oracle: every sweep path on the box workload, the 1024^3 star r=4 on the
+    CUDA cores and on the tensor cores, and brief runs of the wave, gradient,
+    VTI and TTI workloads against the HBM roofline of their byte models."""
     out = {}
     for r in RADII:
         c = workloads.normal_coeffs("box", r, workload=2, salt=r)
         g = torch.Generator(device=dev).manual_seed(1000 + r)
         inp = mms.padded_empty(N, N, N, r, device=dev, zero=False)
         inp.uniform_(-1, 1, generator=g)
+        host = inp.cpu().numpy()
         o = torch.empty((N, N, N), device=dev)
         for path in ("cuda_core", "naive", "tf32", "3xtf32", "bf16x3"):
             if mms.num_variants("box", r, path) == 0:
                 continue
             ms = _time(lambda: mms.apply("box", r, c, inp, o, path=path))
-            out[f"box_r{r}_{path}"] = {"ms": ms, "gpts": N ** 3 / ms / 1e6}
-        del inp, o
+            out[f"box_r{r}_{path}"] = {"ms": ms, "gpts": N ** 3 / ms / 1e6,
+                                       "max_rel_err": sweep_error("box", r, c, host, o, salt=r)}
+        del inp, o, host
     n = 1024
     inp = mms.padded_empty(n, n, n, 4, device=dev, zero=False)
     inp.uniform_(-1, 1, generator=torch.Generator(device=dev).manual_seed(7))
+    host = inp.cpu().numpy()
     o = torch.empty((n, n, n), device=dev)
     c = workloads.fd8_star_coeffs()
-    ms = _time(lambda: mms.apply("star", 4, c, inp, o, path="cuda_core"))
     bytes_alg = 4 * ((n + 8) ** 3 + n ** 3)
-    out["star_r4_1024_cuda_core"] = {"ms": ms, "gpts": n ** 3 / ms / 1e6,
-                                     "hbm_gbs": bytes_alg / ms / 1e6,
-                                     "hbm_frac": bytes_alg / ms / 1e6 / hbm_peak}
-    del inp, o
+    for path in ("cuda_core", "bf16x3"):
+        ms = _time(lambda: mms.apply("star", 4, c, inp, o, path=path))
+        out[f"star_r4_1024_{path}"] = {"ms": ms, "gpts": n ** 3 / ms / 1e6, "hbm_gbs": bytes_alg / ms / 1e6,
+                                       "hbm_frac": bytes_alg / ms / 1e6 / hbm_peak,
+                                       "variant": mms.default_variant("star", 4, path, n, n, n),
+                                       "max_rel_err": sweep_error("star", 4, c, host, o, salt=4)}
+    del inp, o, host
+    torch.cuda.empty_cache()
+    for name, fn in (("rtm512", extra_rtm), ("grad256", extra_grad), ("vti512", extra_vti),
+                     ("tti512", extra_tti)):
+        out[name] = fn(mms, torch, dev, hbm_peak)
+        torch.cuda.empty_cache()
     return out
+
+
+def _fill_interior(fields, r, gen):
+    """Seeded U[-1, 1] in the interior of (nshots, Z, Y, X) fields, zero halo."""
+    for f in fields:
+        f.zero_()
+        f[:, r:-r, r:-r, r:-r].uniform_(-1, 1, generator=gen)
+
+
+def _roof_entry(ms_step, pts, bpp, hbm_peak, err, config):
+    return {"ms_per_step": ms_step, "gpt_steps": pts / ms_step / 1e6, "bytes_per_point_step": bpp,
+            "hbm_gbs": bpp * pts / ms_step / 1e6, "hbm_frac": bpp * pts / ms_step / 1e6 / hbm_peak,
+            "max_rel_err": err, "config": config}
+
+
+def extra_rtm(mms, torch, dev, hbm_peak, steps=20):
+    """The acoustic forward workload in brief: 8 shots x 512^3, `steps`
+    graph-launched steps (read a^n, a^{n-1}; write a^{n+1}: 16 B per
+    point-step with m shared by the shots), from seeded random states; then
+    one more step, checked at sampled points of shot 0."""
+    import oracle
+    from paper_2507_11067_gb300.wave import WavePropagator
+    n, ns, R = 512, 8, 4
+    w = workloads.WaveInputs(n, n, n, nshots=ns, nsteps=steps + 1, workload=4, noise=False)
+    prop = WavePropagator(n, n, n, w.src, w.zrec, w.h, w.dt, sponge_width=w.sponge, sponge_a=w.sponge_a,
+                          device=dev)
+    prop.set_velocity(torch.from_numpy(w.v).to(dev))
+    _fill_interior(prop.p, R, torch.Generator(device=dev).manual_seed(40))
+    amps = torch.from_numpy(w.amp).to(dev).contiguous()
+    rec = torch.empty((steps, ns, n, n), device=dev)
+    ms = _time(lambda: mms.wave_forward(prop.desc, prop.coeffs, prop.m, amps[:steps], steps, prop.p[0],
+                                        prop.p[1], rec, graph=True), reps=2) / steps
+    # 3 runs of an even step count: p[1] holds a^n, p[0] a^{n-1}
+    nxt = prop.new_fields(zero=True)
+    mms.wave_step_to(prop.desc, prop.coeffs, prop.m, prop.p[1], prop.p[0], nxt, amps[steps])
+    cur, prev = prop.p[1][0].cpu().numpy(), prop.p[0][0].cpu().numpy()
+    src = w.src[0]
+    pts = np.vstack([workloads.sample_points(n, n, n, 2000, workload=9, salt=40), [src]]).astype(np.int64)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    m = at_points(pts, (n, n, n), oracle.model_m(w.v[z, y, x], w.dt, w.h))
+    ref = oracle.wave_step_points(R, prop.coeffs, m, (w.sponge, w.sponge_a), src, float(w.amp[steps, 0]),
+                                  cur, prev, pts)
+    idx = torch.from_numpy(pts).to(dev)
+    got = nxt[0][idx[:, 2] + R, idx[:, 1] + R, idx[:, 0] + R].double().cpu().numpy()
+    return _roof_entry(ms, ns * n ** 3, 16, hbm_peak, rel_err(got, ref),
+                       f"{ns} shots x {n}^3, {steps} steps in one CUDA graph, from seeded random states")
+
+
+def extra_grad(mms, torch, dev, hbm_peak):
+    """The gradient workload (2 shots x 256^3, 200 steps, checkpoint every
+    20): one whole gradient through WaveFunction; its three step kernels
+    timed alone on seeded random fields; one adjoint step with its gradient
+    term checked at every point against the oracle."""
+    import oracle
+    from paper_2507_11067_gb300.wave import WaveFunction, WavePropagator
+    n, ns, nsteps, every, R = 256, 2, 200, 20, 4
+    wt = workloads.WaveInputs(n, n, n, nshots=ns, nsteps=nsteps, workload=5, noise=True)
+    w0 = workloads.WaveInputs(n, n, n, nshots=ns, nsteps=nsteps, workload=5, noise=False)
+    prop = WavePropagator(n, n, n, w0.src, w0.zrec, w0.h, wt.dt, sponge_width=w0.sponge, sponge_a=w0.sponge_a,
+                          device=dev)
+    amps = torch.from_numpy(wt.amp).to(dev)
+    with torch.no_grad():
+        obs = WaveFunction.apply(torch.from_numpy(wt.v).to(dev), prop, amps, nsteps, every)
+    v0 = torch.from_numpy(w0.v).to(dev)
+
+    def gradient():
+        vv = v0.clone().requires_grad_(True)
+        (0.5 * ((WaveFunction.apply(vv, prop, amps, nsteps, every) - obs) ** 2).sum()).backward()
+
+    ms = _time(gradient, reps=2)
+    pts = ns * n ** 3
+    bpp = 56.0 + 16.0 / ns
+    f = [prop.new_fields() for _ in range(5)]
+    _fill_interior(f, R, torch.Generator(device=dev).manual_seed(50))
+    resid = torch.randn((ns, n, n), device=dev, generator=torch.Generator(device=dev).manual_seed(51))
+    grad = torch.zeros((n, n, n), device=dev, dtype=torch.float64)
+    t_fwd = _time(lambda: mms.wave_step_to(prop.desc, prop.coeffs, prop.m, f[0], f[1], f[2], amps[0]), reps=20)
+    t_rec = _time(lambda: mms.wave_step_lap(prop.desc, prop.coeffs, prop.m, f[0], f[1], f[2], f[3], amps[0]),
+                  reps=20)
+    t_adj = _time(lambda: mms.wave_adjoint_lap(prop.desc, prop.coeffs, prop.m, f[0], f[4], resid, f[3], grad),
+                  reps=20)
+    # accuracy: lam^n and the gradient term of one adjoint step from seeded
+    # lam^{n+1}, lam^{n+2}, a^n (L a^n from the recompute kernel)
+    _fill_interior(f, R, torch.Generator(device=dev).manual_seed(52))
+    mms.wave_step_lap(prop.desc, prop.coeffs, prop.m, f[2], f[1], f[0], f[3], amps[0])
+    l1, l2, an = (t.cpu().numpy().astype(np.float64) for t in (f[4], f[1], f[2]))
+    grad.zero_()
+    mms.wave_adjoint_lap(prop.desc, prop.coeffs, prop.m, f[4], f[1], resid, f[3], grad)
+    prob = oracle.WaveProblem(R, prop.coeffs, oracle.model_m(w0.v, wt.dt, w0.h), (w0.sponge, w0.sponge_a),
+                              w0.src, wt.amp, w0.zrec)
+    gref = np.zeros((n, n, n))
+    rh = resid.cpu().numpy().astype(np.float64)
+    errs = [rel_err(f[1][sh].cpu().numpy(), prob.adjoint_step(l1[sh], l2[sh], rh[sh], an[sh], gref))
+            for sh in range(ns)]
+    errs.append(rel_err(grad.cpu().numpy(), gref))
+    return {"ms_per_gradient": ms, "gpt_steps": pts * nsteps / ms / 1e6, "bytes_per_point_step": bpp,
+            "hbm_gbs": bpp * pts * nsteps / ms / 1e6, "hbm_frac": bpp * pts * nsteps / ms / 1e6 / hbm_peak,
+            "forward_step_us": 1e3 * t_fwd, "recompute_step_us": 1e3 * t_rec, "adjoint_step_us": 1e3 * t_adj,
+            "max_rel_err": max(errs),
+            "config": f"{ns} shots x {n}^3, {nsteps} steps, checkpoint every {every}; byte model: forward 16, "
+                      f"recompute 20, adjoint 20 B per shot-point-step + FP64 gradient 16 B per point-step"}
+
+
+def _aniso_setup(mms, torch, dev, kind, n, ns, steps):
+    tti = kind == "tti"
+    r = 4
+    a = workloads.AnisoInputs(n, n, n, ns, steps + 1, workload=7 if tti else 6, tti=tti, noise=False)
+    f = [mms.padded_empty(n, n, n, r, device=dev, nshots=ns) for _ in range(6)]
+    py, pz, ss = mms.field_geometry(f[0])
+    desc, keep = mms.wave_desc(n, n, n, r, ns, py, pz, ss, a.wave.sponge, a.wave.sponge_a, a.zrec, a.src)
+    return a, f, desc, keep
+
+
+def extra_vti(mms, torch, dev, hbm_peak, steps=10):
+    """The VTI workload in brief: 4 shots x 512^3, `steps` fused steps from
+    seeded random states (32 B per point-step); one more step checked at
+    sampled points of shot 0."""
+    from oracle import aniso
+    n, ns, r = 512, 4, 4
+    a, f, desc, _keep = _aniso_setup(mms, torch, dev, "vti", n, ns, steps)
+    mv, rho = mms.padded_empty(n, n, n, r, device=dev), mms.padded_empty(n, n, n, r, device=dev)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    mms.vti_model(desc, d(a.vp), d(a.eps), d(a.delta), mv, rho, a.dt, a.h)
+    cf = workloads.fd8_star_coeffs()
+    amps = torch.from_numpy(a.amp).to(dev).contiguous()
+    _fill_interior(f[:4], r, torch.Generator(device=dev).manual_seed(60))
+
+    def run():
+        cur = f[:4]
+        for i in range(steps):
+            mms.vti_step(desc, cf, mv, rho, cur[0], cur[1], cur[2], cur[3], cur[2], cur[3], amps[i])
+            cur = [cur[2], cur[3], cur[0], cur[1]]
+    ms = _time(run, reps=2) / steps
+    # an even step count: f[0], f[1] hold the newest state again
+    mms.vti_step(desc, cf, mv, rho, f[0], f[1], f[2], f[3], f[4], f[5], amps[steps])
+    host = [t[0].cpu().numpy() for t in f[:4]]
+    src = a.src[0]
+    pts = np.vstack([workloads.sample_points(n, n, n, 2000, workload=9, salt=60), [src]]).astype(np.int64)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    mh_p, mv_p = aniso.vti_medium(a.vp[z, y, x], a.eps[z, y, x], a.delta[z, y, x], a.dt, a.h)
+    oh, ov = aniso.vti_step_points(r, cf, at_points(pts, (n, n, n), mh_p), at_points(pts, (n, n, n), mv_p),
+                                   (a.wave.sponge, a.wave.sponge_a), src, float(a.amp[steps, 0]), *host, pts)
+    idx = torch.from_numpy(pts).to(dev)
+    got = [t[0][idx[:, 2] + r, idx[:, 1] + r, idx[:, 0] + r].double().cpu().numpy() for t in (f[4], f[5])]
+    err = max(rel_err(got[0], oh), rel_err(got[1], ov))
+    return _roof_entry(ms, ns * n ** 3, ANISO["vti512"]["bytes_per_point_step"], hbm_peak, err,
+                       f"{ns} shots x {n}^3, {steps} steps from seeded random states")
+
+
+def extra_tti(mms, torch, dev, hbm_peak, steps=10):
+    """The TTI workload in brief: 2 shots x 512^3, `steps` steps (two launches
+    each; 88 B per point-step) from seeded random states; one more step
+    checked at sampled points of shot 0."""
+    from oracle import aniso
+    n, ns, r = 512, 2, 4
+    a, f, desc, _keep = _aniso_setup(mms, torch, dev, "tti", n, ns, steps)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    med = torch.empty((8, n, n, n), device=dev)
+    mms.tti_model(desc, d(a.vp), d(a.vs), d(a.eps), d(a.delta), d(a.alpha), d(a.theta), d(a.phi), med, a.dt, a.h)
+    work = torch.empty((4, ns, n, n, n), device=dev)
+    w2, w1 = workloads.fd8_rows()
+    amps = torch.from_numpy(a.amp).to(dev).contiguous()
+    _fill_interior(f[:4], r, torch.Generator(device=dev).manual_seed(70))
+
+    def run():
+        cur = f[:4]
+        for i in range(steps):
+            mms.tti_step(desc, w2, w1, med, cur[0], cur[1], cur[2], cur[3], cur[2], cur[3], work, amps[i])
+            cur = [cur[2], cur[3], cur[0], cur[1]]
+    ms = _time(run, reps=2) / steps
+    mms.tti_step(desc, w2, w1, med, f[0], f[1], f[2], f[3], f[4], f[5], work, amps[steps])
+    host = [t[0].cpu().numpy() for t in f[:4]]
+    src = a.src[0]
+    pts = np.vstack([workloads.sample_points(n, n, n, 1000, workload=9, salt=70), [src]]).astype(np.int64)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    sel = lambda q: q[z, y, x]
+    med_p = aniso.tti_medium(sel(a.vp), sel(a.vs), sel(a.eps), sel(a.delta), sel(a.alpha), a.dt, a.h)
+    tilt_p = aniso.tilt_axis(sel(a.theta), sel(a.phi))
+    full = lambda vals: at_points(pts, (n, n, n), vals)
+    op, oq = aniso.tti_step_points(r, [full(v) for v in med_p], [full(v) for v in tilt_p],
+                                   (a.wave.sponge, a.wave.sponge_a), src, float(a.amp[steps, 0]), *host, pts,
+                                   w2, w1)
+    idx = torch.from_numpy(pts).to(dev)
+    got = [t[0][idx[:, 2] + r, idx[:, 1] + r, idx[:, 0] + r].double().cpu().numpy() for t in (f[4], f[5])]
+    err = max(rel_err(got[0], op), rel_err(got[1], oq))
+    return _roof_entry(ms, ns * n ** 3, ANISO["tti512"]["bytes_per_point_step"], hbm_peak, err,
+                       f"{ns} shots x {n}^3, {steps} steps from seeded random states")
 
 
 if __name__ == "__main__":

@@ -70,8 +70,16 @@ def _load():
                                           P, P, i64, P, P, P, P]
     lib.orc_dot_interior.argtypes = [i32, i64, i64, i64, i64, i64, P, P]
     lib.orc_dot_interior.restype = d
+    lib.orc_set_threads.argtypes = [i32]
+    lib.orc_set_threads.restype = i32
     _lib = lib
     return lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of oracle.c's parallel loops from now on in the calling thread
+    (n = 0 leaves the count); returns the count before the call."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def _ptr(a: np.ndarray):

@@ -34,6 +34,7 @@
  * the design notes (leapfrog, Cerjan sponge, zero halo).
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -235,4 +236,14 @@ double orc_dot_interior(int r, int64_t nx, int64_t ny, int64_t nz, int64_t py,
                 s += u[p] * w[p];
             }
     return s;
+}
+
+/* Thread count of the parallel loops above (n > 0 sets it for the calling
+ * thread's later loops; n = 0 leaves it); returns the count before the call.
+ * Lets a caller time the oracle on one core as well as on all of them. */
+int orc_set_threads(int n)
+{
+    const int old = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return old;
 }

@@ -57,9 +57,10 @@ namespace mms {
 // work, summed.
 //   [0] producer:  wait staging slot, total
 //   [1] issuer 1:  wait planes, wait accumulator, issue, total
-//   [2] converter: wait staged plane, wait A slot, wait accumulator (star),
-//                  loads + conversion, tcgen05.st + wait, total
-//   [3] epilogue:  wait accumulator, TMEM load, reduce + store, total
+//   [2] converter (lane quarter 0): wait staged plane, wait A slot, wait
+//                  accumulator (star), conversion and stores, -, total
+//   [3] epilogue (quarter 0, even outputs): wait accumulator, loads, reduction
+//                  and stores, -, -, -, total
 __device__ unsigned long long g_role_trace[4][6];
 #define MMS_TRACE_ADD(role, slot, v) \
     do { if (blockIdx.x < 8) atomicAdd(&g_role_trace[role][slot], (unsigned long long)(v)); } while (0)
@@ -676,9 +677,12 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
             MMS_TRACE_ADD(2, 1, ta);
             MMS_TRACE_ADD(2, 2, td);
             MMS_TRACE_ADD(2, 3, tc0);
-            MMS_TRACE_ADD(2, 4, tf);
             MMS_TRACE_ADD(2, 5, MMS_CLOCK() - t00);
-            MMS_TRACE_ADD(3, 0, tep);
+        }
+        if (lane == 0 && warp == 8) {
+            MMS_TRACE_ADD(3, 0, tf);
+            MMS_TRACE_ADD(3, 1, tep);
+            MMS_TRACE_ADD(3, 5, MMS_CLOCK() - t00);
         }
     }
 

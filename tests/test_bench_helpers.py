@@ -113,3 +113,49 @@ def test_reference_arm_prints_the_contract_line(workload):
     out = subprocess.run(cmd, env=dict(env, RANK="1", WORLD_SIZE="2"), capture_output=True, text=True,
                          timeout=120, cwd=bench.ROOT)
     assert out.returncode == 0 and not out.stdout.strip()
+
+
+def test_sweep_error_is_the_max_relative_error_at_the_sample_points():
+    # an output equal to the oracle's sweep has error 0; one off by a known
+    # amount at one sampled point reports that amount over max |oracle|
+    import numpy as np
+    import oracle
+    import workloads
+    r, n = 2, (21, 17, 13)
+    grid = workloads.uniform_grid(*n, r, workload=2, salt=5)
+    c = workloads.normal_coeffs("box", r, workload=2, salt=5)
+    exact = oracle.stencil("box", r, c, grid)
+    assert bench.sweep_error("box", r, c, grid, exact) == 0.0
+    pts = workloads.sample_points(n[0], n[1], n[2], 2000, workload=9, salt=0)
+    bad = exact.copy()
+    x, y, z = pts[0]
+    bad[z, y, x] += 1e-3
+    ref = oracle.stencil_points("box", r, c, grid, pts)
+    assert bench.sweep_error("box", r, c, grid, bad) == pytest.approx(1e-3 / np.abs(ref).max())
+    # the planar form
+    g2 = workloads.uniform_grid2d(40, 30, 1, 3, workload=6, salt=1)
+    c2 = workloads.normal_coeffs("box2d", 3, workload=6, salt=1)
+    assert bench.sweep_error("box2d", 3, c2, g2, oracle.stencil2d("box2d", 3, c2, g2)) == 0.0
+
+
+def test_at_points_places_values_only_at_the_points():
+    import numpy as np
+    pts = np.array([[1, 2, 3], [0, 0, 0]])
+    a = bench.at_points(pts, (4, 5, 6), [7.0, 8.0])
+    assert a.shape == (4, 5, 6) and a[3, 2, 1] == 7.0 and a[0, 0, 0] == 8.0 and a.sum() == 15.0
+
+
+def test_cpu_baseline_times_all_cores_and_one_core():
+    import oracle
+    calls = []
+
+    def sample(planes, salt=0):
+        calls.append(oracle.set_threads(0))
+        return bench.oracle_sample(planes, salt, [("box", 1, 24)])
+
+    before = oracle.set_threads(0)
+    out = bench.cpu_baseline(sample, "GPoints/s", "slab of {planes} planes", budget_s=0.01)
+    assert oracle.set_threads(0) == before               # the count is restored
+    assert out["cores"] == before and out["one_core"]["cores"] == 1 and 1 in calls
+    assert out["value"] > 0 and out["one_core"]["value"] > 0
+    assert "{planes}" not in out["sample"] and "{planes}" not in out["one_core"]["sample"]
