@@ -11,7 +11,7 @@ from ._lib import (BOX, BOX2D, PATHS, STAR, STAR2D, MMSError, apply, apply_dense
                    default_variant,
                    dot_f64, field_geometry, grad_to_velocity, load, model_from_velocity,
                    num_variants, padded_empty, padded_empty2d, pitches, set_variant, sum_f64, to_padded_device, to_padded_device2d,
-                   version, vti_model, vti_step, wave_adjoint, wave_adjoint_lap, wave_desc, wave_forward, wave_step,
+                   version, vti_model, vti_step, wave_adjoint, wave_adjoint_lap, wave_adjoint_scaled, wave_desc, wave_forward, wave_step,
                    wave_step_lap, wave_step_to,
                    aniso_num_variants, aniso_set_variant, tti_model, tti_step)
 from .build import build
@@ -21,5 +21,5 @@ __all__ = ["BOX", "BOX2D", "PATHS", "STAR", "STAR2D", "MMSError", "apply", "appl
            "default_variant", "dot_f64", "field_geometry", "grad_to_velocity", "load",
            "model_from_velocity", "num_variants", "padded_empty", "padded_empty2d", "pitches", "set_variant", "sum_f64",
            "to_padded_device", "to_padded_device2d", "version", "wave_adjoint", "wave_desc", "wave_forward", "wave_step",
-           "wave_step_to", "wave_step_lap", "wave_adjoint_lap", "vti_model", "vti_step", "aniso_num_variants", "aniso_set_variant",
+           "wave_step_to", "wave_step_lap", "wave_adjoint_lap", "wave_adjoint_scaled", "vti_model", "vti_step", "aniso_num_variants", "aniso_set_variant",
            "tti_model", "tti_step"]

@@ -804,6 +804,35 @@ mms_status mms_wave_adjoint_lap(const mms_wave_desc *desc, const float *coeffs, 
     return wave_adjoint(desc, coeffs, m, lam_cur, lam_prev, resid, lap_a, grad_m, stream, true);
 }
 
+mms_status mms_wave_adjoint_scaled(const mms_wave_desc *desc, const float *coeffs, const float *m,
+                                   const float *mu_cur, float *mu_prev, const float *resid, const float *lap_a,
+                                   double *grad_m, void *stream)
+{
+    WaveGeo g{};
+    mms_status st = wave_geo(desc, coeffs, &g);
+    if (st != MMS_OK) return st;
+    if (!m || !mu_cur || !mu_prev) return fail(MMS_E_ARG, "null field pointer");
+    if (lap_a && !grad_m) return fail(MMS_E_ARG, "lap_a given without grad_m");
+    if (resid && g.rec_z < 0) return fail(MMS_E_ARG, "residual given without a receiver plane");
+    if (!al16(m) || !al16(mu_cur) || !al16(mu_prev) || (lap_a && !al16(lap_a)))
+        return fail(MMS_E_ALIGN, "wave fields must be 16-byte aligned");
+    const size_t fb = field_bytes(g);
+    if (overlaps(mu_cur, fb, mu_prev, fb)) return fail(MMS_E_ARG, "mu_cur and mu_prev overlap");
+    if (lap_a && overlaps(lap_a, fb, mu_prev, fb)) return fail(MMS_E_ARG, "lap_a and mu_prev overlap");
+    if (overlaps(mu_prev, fb, m, model_bytes(g))) return fail(MMS_E_ARG, "mu_prev overlaps m");
+    if (resid && overlaps(resid, rec_bytes(g), mu_prev, fb)) return fail(MMS_E_ARG, "resid overlaps mu_prev");
+    if (grad_m) {
+        const size_t gb = grad_bytes(g);
+        if (overlaps(grad_m, gb, m, model_bytes(g)) || overlaps(grad_m, gb, mu_cur, fb) ||
+            overlaps(grad_m, gb, mu_prev, fb) || (lap_a && overlaps(grad_m, gb, lap_a, fb)) ||
+            (resid && overlaps(grad_m, gb, resid, rec_bytes(g))))
+            return fail(MMS_E_ARG, "grad_m overlaps a field");
+    }
+    cudaError_t e = launch_wave_adj_scaled(g, coeffs, m, mu_cur, mu_prev, resid, lap_a, grad_m,
+                                           reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "scaled adjoint step launch");
+}
+
 mms_status mms_wave_step_lap(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *p_cur,
                              const float *p_prev, float *p_next, float *lap_out, const float *src_amp, float *rec,
                              void *stream)

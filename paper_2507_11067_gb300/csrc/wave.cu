@@ -12,6 +12,15 @@
 //   grad += g lam^{n+1} (L a^n)     (FP64, all shots)
 // staging lam^{n+1}, m and a^n planes with TMA; the stencil input
 // q = m g lam^{n+1} is formed plane by plane in shared memory.
+//
+// The gradient path runs the same recursion in the scaled variable
+// mu = m g lam (pointwise).  Multiplying the update by m g at the output
+// point gives
+//   mu^n = g (2 mu^{n+1} + m L mu^{n+1} - g mu^{n+2} + m R^T r^n)
+//   grad += (mu^{n+1} / m) (L a^n)
+// -- the forward step's form (the stencil on the state itself, m and g after
+// it) -- so it runs on the forward kernel with no per-plane product and
+// no barrier between forming and reading it.  It needs m > 0 everywhere.
 #include "common.cuh"
 #include "tile.cuh"
 #include "wave.cuh"
@@ -53,17 +62,23 @@ __global__ void wait_selftest_kernel(unsigned long long limit_ns, unsigned *err)
 // FP32 -> FP64 by the IEEE-754 layouts (sign kept, exponent rebased by
 // 1023 - 127, fraction shifted up 29 bits), on the integer units: GB300's
 // FP64 pipe issues about two instructions per clock per SM, which a
-// conversion per point and plane would saturate.  Exact for normal numbers,
-// zero, infinities and NaN; FP32 denormals (below 1.2e-38) become zero.
+// conversion per point and plane would saturate.  Exact for every FP32
+// value: a denormal f (fraction field F, f = F 2^-149) is normalised by the
+// position of F's leading one (FP64 reaches far below 2^-149).
 __device__ __forceinline__ double widen(float f)
 {
     const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xffu;
+    const uint32_t e = (u >> 23) & 0xffu, frac = u & 0x7fffffu;
     uint64_t d = (uint64_t)(u & 0x80000000u) << 32;
-    if (e == 0xffu)
-        d |= (uint64_t)0x7ffu << 52 | (uint64_t)(u & 0x7fffffu) << 29;
-    else if (e != 0u)
-        d |= (uint64_t)(e + 896u) << 52 | (uint64_t)(u & 0x7fffffu) << 29;
+    if (e == 0xffu) {
+        d |= (uint64_t)0x7ffu << 52 | (uint64_t)frac << 29;
+    } else if (e != 0u) {
+        d |= (uint64_t)(e + 896u) << 52 | (uint64_t)frac << 29;
+    } else if (frac != 0u) {
+        // leading one of F at bit b = 23 - s: f = 1.xxx 2^(-126 - s)
+        const uint32_t sh = (uint32_t)__clz(frac) - 8u;
+        d |= (uint64_t)(897u - sh) << 52 | (uint64_t)((frac << sh) & 0x7fffffu) << 29;
+    }
     return __longlong_as_double((long long)d);
 }
 
@@ -72,7 +87,15 @@ __device__ __forceinline__ double widen(float f)
 // values of a^n) ride in the stage of input plane j, the plane that completes
 // zo, so every operand arrives asynchronously and no register queue of
 // centre values is needed.
-template <int R, int TX, int TY, int PY, int S>
+// The kernel's three forms: the forward step; the forward step that also
+// writes L a^n; the adjoint step in the scaled variable mu = m G lam, whose
+// update has the forward step's form (the stencil acts on the state itself),
+// with the receiver residual m r^n in place of the source and the FP64
+// gradient term (mu^{n+1} / m)(L a^n) = G lam^{n+1} (L a^n) read from a
+// fifth tile.
+enum { K_FWD = 0, K_FWD_LAP = 1, K_ADJ_SCALED = 2 };
+
+template <int R, int TX, int TY, int PY, int S, int MODE = K_FWD>
 struct FwdGeom {
     using G = Geom<R, TX, TY, PY, S>;
     using I = Interior<R, TX>;
@@ -81,21 +104,31 @@ struct FwdGeom {
     static constexpr int OFF_M = (G::PLANE + 31) & ~31;
     static constexpr int OFF_P = OFF_M + ((MT + 31) & ~31);
     static constexpr int OFF_C = OFF_P + ((MT + 31) & ~31);
-    static constexpr int STAGE = OFF_C + ((MT + 31) & ~31);
+    static constexpr int OFF_L = OFF_C + ((MT + 31) & ~31);  // adjoint: L a^n
+    static constexpr int STAGE = OFF_L + (MODE == K_ADJ_SCALED ? ((MT + 31) & ~31) : 0);
     static constexpr size_t SMEM = 128 + (size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16;
 };
 
-template <int R, int TX, int TY, int PY, int S, bool LAPOUT>
+// Operands of the scaled adjoint (unused by the forward forms).
+struct AdjArgs {
+    const float *resid;  // nshots*ny*nx on the receiver plane, or null
+    double *grad;        // FP64 gradient, or null (no gradient term, tlap unused)
+    int gvec;            // rows of four doubles 32-byte aligned
+};
+
+template <int R, int TX, int TY, int PY, int S, int MODE>
 __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     wave_fwd_kernel(const __grid_constant__ CUtensorMap tcur, const __grid_constant__ CUtensorMap tm,
                     const __grid_constant__ CUtensorMap tprev, const __grid_constant__ CUtensorMap tctr,
-                    const __grid_constant__ StarCoef cf,
+                    const __grid_constant__ CUtensorMap tlap, const __grid_constant__ StarCoef cf,
                     const __grid_constant__ WaveGeo geo, float *__restrict__ pnext,
                     const float *__restrict__ amp, float *__restrict__ rec, float *__restrict__ lapout,
-                    int tz, int nzc, int vec, unsigned *err)
+                    const __grid_constant__ AdjArgs adj, int tz, int nzc, int vec, unsigned *err)
 {
+    constexpr bool LAPOUT = MODE == K_FWD_LAP;
+    constexpr bool ADJ = MODE == K_ADJ_SCALED;
     using G = Geom<R, TX, TY, PY, S>;
-    using F = FwdGeom<R, TX, TY, PY, S>;
+    using F = FwdGeom<R, TX, TY, PY, S, MODE>;
     using I = Interior<R, TX>;
     constexpr int W = G::W;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -112,12 +145,14 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     const int P = nzt + 2 * R;
     const int ry0 = ty * PY;
     const int gx = x0 + 4 * tx;
-    const int sx = geo.src[sh][0], sy = geo.src[sh][1], sz = geo.src[sh][2];
+    const int sx = ADJ ? -1 : geo.src[sh][0], sy = ADJ ? -1 : geo.src[sh][1], sz = ADJ ? -1 : geo.src[sh][2];
+    const bool has_grad = ADJ && adj.grad != nullptr;
+    const int ntiles = has_grad ? 4 : 3;
 
     auto issue = [&](int j, int s) {
         float *st = stages + (size_t)s * F::STAGE;
         const bool inner = j >= 2 * R;  // this plane completes output plane j - 2R
-        ptx::mbar_arrive_expect_tx(&full[s], (G::PLANE + (inner ? 3 * F::MT : 0)) * sizeof(float));
+        ptx::mbar_arrive_expect_tx(&full[s], (G::PLANE + (inner ? ntiles * F::MT : 0)) * sizeof(float));
         ptx::tma_load_4d(st, &tcur, x0, y0, zb + j, sh, &full[s]);
         if (inner) {
             const int zp = zb + j - R;  // padded plane of output zo = j - 2R
@@ -125,6 +160,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
             ptx::tma_load_3d(st + F::OFF_M, &tm, xs, y0 + R, zp, &full[s]);
             ptx::tma_load_4d(st + F::OFF_P, &tprev, xs, y0 + R, zp, sh, &full[s]);
             ptx::tma_load_4d(st + F::OFF_C, &tctr, xs, y0 + R, zp, sh, &full[s]);
+            if (has_grad) ptx::tma_load_4d(st + F::OFF_L, &tlap, xs, y0 + R, zp, sh, &full[s]);
         }
     };
     if (tid == 0) {
@@ -132,6 +168,7 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
         ptx::prefetch_tmap(&tm);
         ptx::prefetch_tmap(&tprev);
         ptx::prefetch_tmap(&tctr);
+        if (has_grad) ptx::prefetch_tmap(&tlap);
 #pragma unroll
         for (int s = 0; s < S; ++s) ptx::mbar_init(&full[s], 1);
         ptx::fence_mbar_init();
@@ -154,13 +191,14 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[kk][i][k] = 0.f;
 
-    const float samp = amp[sh];
+    const float samp = ADJ ? 0.f : amp[sh];
     const int64_t shot_off = (int64_t)sh * geo.ss;
     for (int j = 0; j < P; ++j) {
         const int s = j % S;
         const float *st = stages + (size_t)s * F::STAGE;
         const int zo = j - 2 * R;  // output plane completed by plane j
         float mv[PY][4], pv[PY][4], cv[PY][4];
+        [[maybe_unused]] float lv[PY][4];
         if (ptx::mbar_wait_bounded(&full[s], (uint32_t)(j / S) & 1u, err)) {
             float unused[PY][4];
             star_plane<R, PY, G::BX, G::NV>(st, cf, acc, unused, tx, ry0);
@@ -171,6 +209,8 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                     load_center<I::OFF>(st + F::OFF_M + (ry0 + i) * I::BXI + 4 * tx, mv[i]);
                     load_center<I::OFF>(st + F::OFF_P + (ry0 + i) * I::BXI + 4 * tx, pv[i]);
                     load_center<I::OFF>(st + F::OFF_C + (ry0 + i) * I::BXI + 4 * tx, cv[i]);
+                    if constexpr (ADJ)
+                        if (has_grad) load_center<I::OFF>(st + F::OFF_L + (ry0 + i) * I::BXI + 4 * tx, lv[i]);
                 }
             }
         } else {
@@ -189,11 +229,21 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                 const int64_t mp = (int64_t)(z + R) * geo.pz + (int64_t)(y + R) * geo.py + (gx + R);
                 float *pp = pnext + shot_off + mp;
                 float res[4];
+                [[maybe_unused]] double gd[4] = {0.0, 0.0, 0.0, 0.0};
+                [[maybe_unused]] const bool at_rec = ADJ && adj.resid && z == geo.rec_z;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float g = gxs[k] * gys[i] * gzv;
                     float v = 2.f * cv[i][k] + mv[i][k] * acc[0][i][k] - g * pv[i][k];
-                    if (gx + k == sx && y == sy && z == sz) v += samp;
+                    if constexpr (ADJ) {
+                        if (at_rec && gx + k < geo.nx)
+                            v += mv[i][k] * adj.resid[((int64_t)sh * geo.ny + y) * geo.nx + gx + k];
+                        // G lam^{n+1} = mu^{n+1} / m; the term in FP32 (its
+                        // operands are FP32), accumulated in FP64
+                        if (has_grad) gd[k] = widen(__fdiv_rn(cv[i][k], mv[i][k]) * lv[i][k]);
+                    } else {
+                        if (gx + k == sx && y == sy && z == sz) v += samp;
+                    }
                     res[k] = g * v;
                 }
                 if (vec && gx + 3 < geo.nx) {
@@ -218,6 +268,31 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         if (gx + k < geo.nx) rp[k] = res[k];
+                }
+                if constexpr (ADJ) {
+                    if (has_grad) {
+                        const int64_t gi = ((int64_t)z * geo.ny + y) * geo.nx + gx;
+                        if (geo.gss == 0) {
+                            // one slice for all shots: other CTAs add to the same points
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (gx + k < geo.nx) atomicAdd(adj.grad + gi + k, gd[k]);
+                        } else {
+                            // this shot's own slice: no other thread touches these points
+                            double *gp = adj.grad + (int64_t)sh * geo.gss + gi;
+                            if (adj.gvec && gx + 3 < geo.nx) {
+                                double2 *g2 = reinterpret_cast<double2 *>(gp);
+                                double2 a = g2[0], b = g2[1];
+                                a.x += gd[0]; a.y += gd[1]; b.x += gd[2]; b.y += gd[3];
+                                g2[0] = a;
+                                g2[1] = b;
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k)
+                                    if (gx + k < geo.nx) gp[k] += gd[k];
+                            }
+                        }
+                    }
                 }
             }
         }
@@ -498,29 +573,40 @@ constexpr int kAdjTX = 64, kAdjTY = 16, kAdjS = 2, kAdjTZ = 128;
 template <int R>
 cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const float *p_cur,
                   const float *p_prev, float *p_next, const float *amp, float *rec, float *lapout,
-                  cudaStream_t st)
+                  cudaStream_t st, const float *lap_in = nullptr, const AdjArgs *adj = nullptr)
 {
     using G = Geom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
-    using F = FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS>;
     using I = Interior<R, kFwdTX>;
     const int X = g.nx + 2 * R, Y = g.ny + 2 * R, Z = g.nz + 2 * R;
-    CUtensorMap mcur, mm, mprev, mctr;
+    CUtensorMap mcur, mm, mprev, mctr, mlap;
     if (!encode_tmap_4d(&mcur, p_cur, X, Y, Z, g.nshots, g.py, g.pz, g.ss, G::BX, G::BY, 1) ||
         !encode_tmap_3d(&mm, m, X, Y, Z, g.py, g.pz, I::BXI, kFwdTY, 1) ||
         !encode_tmap_4d(&mprev, p_prev, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kFwdTY, 1) ||
         !encode_tmap_4d(&mctr, p_cur, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kFwdTY, 1))
         return cudaErrorInvalidValue;
-    auto kern = lapout ? wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, true>
-                       : wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
+    if (lap_in) {
+        if (!encode_tmap_4d(&mlap, lap_in, X, Y, Z, g.nshots, g.py, g.pz, g.ss, I::BXI, kFwdTY, 1))
+            return cudaErrorInvalidValue;
+    } else {
+        mlap = mctr;  // not read
+    }
+    const int mode = adj ? K_ADJ_SCALED : lapout ? K_FWD_LAP : K_FWD;
+    auto kern = mode == K_ADJ_SCALED ? wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_ADJ_SCALED>
+                : mode == K_FWD_LAP  ? wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_FWD_LAP>
+                                     : wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_FWD>;
+    const size_t smem = mode == K_ADJ_SCALED ? FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_ADJ_SCALED>::SMEM
+                        : mode == K_FWD_LAP  ? FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_FWD_LAP>::SMEM
+                                             : FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_FWD>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int tz = kFwdTZ;
     const int nzc = (g.nz + tz - 1) / tz;
     const dim3 grid((g.nx + kFwdTX - 1) / kFwdTX, (g.ny + kFwdTY - 1) / kFwdTY, nzc * g.nshots);
     const int vec = (R % 4 == 0) && g.py % 4 == 0 && g.pz % 4 == 0 && g.ss % 4 == 0 &&
                     reinterpret_cast<uintptr_t>(p_next) % 16 == 0 && reinterpret_cast<uintptr_t>(lapout) % 16 == 0;
-    kern<<<grid, G::NT, F::SMEM, st>>>(mcur, mm, mprev, mctr, cf, g, p_next, amp, rec, lapout, tz, nzc, vec,
-                                       device_error_word());
+    const AdjArgs aa = adj ? *adj : AdjArgs{nullptr, nullptr, 0};
+    kern<<<grid, G::NT, smem, st>>>(mcur, mm, mprev, mctr, mlap, cf, g, p_next, amp, rec, lapout, aa, tz, nzc,
+                                    vec, device_error_word());
     return cudaGetLastError();
 }
 
@@ -572,6 +658,24 @@ cudaError_t launch_wave_fwd(const WaveGeo &g, const float *coeffs, const float *
         case 2: return fwd_r<2>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, lapout, st);
         case 3: return fwd_r<3>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, lapout, st);
         case 4: return fwd_r<4>(g, cf, m, p_cur, p_prev, p_next, src_amp, rec, lapout, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_wave_adj_scaled(const WaveGeo &g, const float *coeffs, const float *m, const float *mu_cur,
+                                   float *mu_prev, const float *resid, const float *lap_a, double *grad,
+                                   cudaStream_t st)
+{
+    StarCoef cf{};
+    for (int i = 0; i < 3 * (2 * g.r + 1); ++i) cf.c[i] = coeffs[i];
+    const AdjArgs adj{resid, lap_a ? grad : nullptr,
+                      g.nx % 4 == 0 && g.gss % 4 == 0 && reinterpret_cast<uintptr_t>(grad) % 32 == 0};
+    const float *lap = lap_a && grad ? lap_a : nullptr;
+    switch (g.r) {
+        case 1: return fwd_r<1>(g, cf, m, mu_cur, mu_prev, mu_prev, nullptr, nullptr, nullptr, st, lap, &adj);
+        case 2: return fwd_r<2>(g, cf, m, mu_cur, mu_prev, mu_prev, nullptr, nullptr, nullptr, st, lap, &adj);
+        case 3: return fwd_r<3>(g, cf, m, mu_cur, mu_prev, mu_prev, nullptr, nullptr, nullptr, st, lap, &adj);
+        case 4: return fwd_r<4>(g, cf, m, mu_cur, mu_prev, mu_prev, nullptr, nullptr, nullptr, st, lap, &adj);
         default: return cudaErrorInvalidValue;
     }
 }

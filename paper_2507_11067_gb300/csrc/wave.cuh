@@ -23,6 +23,11 @@ struct WaveGeo {
 cudaError_t launch_wave_fwd(const WaveGeo &g, const float *coeffs, const float *m, const float *p_cur,
                             const float *p_prev, float *p_next, const float *src_amp, float *rec,
                             cudaStream_t st, float *lapout = nullptr);
+// The adjoint step in mu = m g lam (the gradient path): mu^n into mu_prev
+// (which held mu^{n+2}); with lap_a and grad, grad += (mu^{n+1}/m)(L a^n).
+cudaError_t launch_wave_adj_scaled(const WaveGeo &g, const float *coeffs, const float *m, const float *mu_cur,
+                                   float *mu_prev, const float *resid, const float *lap_a, double *grad,
+                                   cudaStream_t st);
 // lapin: a_n holds L a^n (interior read) instead of a^n.
 cudaError_t launch_wave_adj(const WaveGeo &g, const float *coeffs, const float *m, const float *lam_cur,
                             float *lam_prev, const float *resid, const float *a_n, double *grad,

@@ -92,7 +92,7 @@ class WavePropagator:
                                 (ss, pz, py, 1), flat.storage_offset())
 
     # ------------------------------------------------------------ gradient
-    def gradient_m(self, amps, resid, ckpt, ckpt_every, deterministic=False):
+    def gradient_m(self, amps, resid, ckpt, ckpt_every, deterministic=False, scaled=False):
         """dJ/dm (FP64, (nz, ny, nx)) for records whose residual is ``resid``
         (nsteps, nshots, ny, nx), from the forward checkpoints; the velocity
         (model m) must be the one the checkpoints were made with.
@@ -103,7 +103,11 @@ class WavePropagator:
         to one FP64 gradient with atomics, whose order varies from run to
         run; ``deterministic`` gives every shot its own FP64 slice (plain
         read-modify-write, summed once at the end) for bit-reproducible
-        results, at about 15 % more adjoint time with two shots."""
+        results, at about 15 % more adjoint time with two shots.  ``scaled``
+        carries the adjoint state as mu = m G lam (mms_wave_adjoint_scaled;
+        needs m > 0 at every interior point) instead of lam; None picks mu
+        where m allows it.  The same gradient either way; lam is the faster
+        of the two on GB300 (its gradient term costs less)."""
         nsteps = resid.shape[0]
         resid = resid.to(self.device, torch.float32).contiguous()
         amps = amps.to(self.device, torch.float32).contiguous()
@@ -126,7 +130,13 @@ class WavePropagator:
         scratch = [self.new_fields(zero=True), self.new_fields(zero=True)]
         lap = [self.new_fields() for _ in range(ckpt_every)]
         carry, have_carry = self.new_fields(), False
-        lam = [self.new_fields(), self.new_fields()]   # lam^{n+2}, lam^{n+1}
+        # The adjoint states: lam, or (scaled) mu = m G lam, whose step has the
+        # forward step's form; the gradient terms are the same.
+        r = self.r
+        if scaled is None:
+            scaled = bool((self.m[r:-r, r:-r, r:-r] > 0).all())
+        adjoint = _lib.wave_adjoint_scaled if scaled else _lib.wave_adjoint_lap
+        lam = [self.new_fields(), self.new_fields()]   # lam^{n+2}, lam^{n+1} (or mu)
         nseg = self.n_checkpoints(nsteps, ckpt_every)
         for j in range(nseg - 1, -1, -1):
             k0 = j * ckpt_every
@@ -139,7 +149,7 @@ class WavePropagator:
                 old_f, cur_f = cur_f, nxt
             for n in range(k1, k0, -1):                   # lam^n, n = k1 .. k0+1
                 la = lap[n - k0] if n < k1 else (carry if have_carry else None)
-                _lib.wave_adjoint_lap(desc_g, self.coeffs, self.m, lam[1], lam[0], resid[n - 1], la, grad)
+                adjoint(desc_g, self.coeffs, self.m, lam[1], lam[0], resid[n - 1], la, grad)
                 lam[0], lam[1] = lam[1], lam[0]
             lap[0], carry = carry, lap[0]
             have_carry = True

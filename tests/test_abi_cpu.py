@@ -240,6 +240,13 @@ def test_wave_outputs_may_not_alias_their_inputs(lib):
     refused(lib.mms_wave_adjoint(ctypes.byref(d), c, m, p, m, None, None, None, None), b"lam_prev overlaps m")
     refused(lib.mms_wave_adjoint(ctypes.byref(d), c, m, p, q, None, x, p, None), b"grad_m overlaps")
     refused(lib.mms_wave_adjoint(ctypes.byref(d), c, m, p, q, q, None, None, None), b"resid overlaps")
+    refused(lib.mms_wave_adjoint_scaled(ctypes.byref(d), c, m, p, m, None, None, None, None), b"mu_prev overlaps m")
+    refused(lib.mms_wave_adjoint_scaled(ctypes.byref(d), c, m, p, p, None, None, None, None), b"overlap")
+    refused(lib.mms_wave_adjoint_scaled(ctypes.byref(d), c, m, p, q, None, x, p, None), b"grad_m overlaps")
+    refused(lib.mms_wave_adjoint_scaled(ctypes.byref(d), c, m, p, q, q, None, None, None), b"resid overlaps")
+    refused(lib.mms_wave_adjoint_scaled(ctypes.byref(d), c, m, p, q, None, x, None, None), b"without grad_m")
+    refused(lib.mms_wave_adjoint_scaled(ctypes.byref(d), c, m, p, q, None, q, P(x.value + 8 * 0), None),
+            b"overlap")
     refused(lib.mms_model_from_velocity(ctypes.byref(d), m, m, ctypes.c_float(1e-3), ctypes.c_float(10.0), None),
             b"overlaps v")
     n = nx * ny * nz

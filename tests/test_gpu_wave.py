@@ -590,3 +590,122 @@ def test_adjoint_dot_product_one_checkpoint_segment_full_size():
     print(f"adjoint dot test, 2 x 256^3: 20-step segment rel {rel20:.2e}, 200-step map rel {rel200:.2e}")
     assert rel20 <= 1e-6, (lhs, rhs)
     assert rel200 <= 1e-4, (lhs2, rhs2)
+
+
+# --------------------------------------- the scaled adjoint (mu = m G lam)
+# mms_wave_adjoint_scaled carries mu = m G lam; teacher-forced from seeded
+# mu^{n+1}, mu^{n+2}, its mu^n is checked against m G lam^n of the oracle's
+# adjoint step fed lam = mu / (m G), and its gradient term against the
+# oracle's.
+
+def _mg(s):
+    """m G on the padded grid (FP64, zero halo) of a Setup's oracle problem."""
+    p = s.prob
+    g = p.gz[:, None, None] * p.gy[None, :, None] * p.gx[None, None, :]
+    out = np.zeros_like(p.m)
+    out[R:-R, R:-R, R:-R] = p.m[R:-R, R:-R, R:-R] * g
+    return out
+
+
+def _scaled_step_check(s, seed):
+    mu1, mu2, a_n, lap = s.fields
+    prev, nxt = (mms.padded_empty(s.nx, s.ny, s.nz, R, nshots=s.ns) for _ in range(2))
+    for f, sd in ((mu1, seed), (mu2, seed + 1), (a_n, seed + 2), (prev, seed + 3)):
+        s.fill(f, sd)
+    mms.wave_step_lap(s.desc, s.cf, s.m, a_n, prev, nxt, lap, s.amps[0])      # L a^n
+    m1, m2, an = s.host(mu1), s.host(mu2), s.host(a_n)
+    g = np.random.default_rng(seed + 4)
+    resid = torch.from_numpy(g.normal(size=(s.ns, s.ny, s.nx)).astype(np.float32)).cuda()
+    grad = torch.zeros((s.nz, s.ny, s.nx), device="cuda", dtype=torch.float64)
+    mms.wave_adjoint_scaled(s.desc, s.cf, s.m, mu1, mu2, resid, lap, grad)
+    torch.cuda.synchronize()
+    mms.check_device()
+    got = mu2.cpu().numpy()
+    mg = _mg(s)
+    inner = mg > 0
+    rh = resid.cpu().numpy().astype(np.float64)
+    gref = np.zeros((s.nz, s.ny, s.nx))
+    errs = []
+    for sh in range(s.ns):
+        l1 = np.divide(m1[sh], mg, out=np.zeros_like(mg), where=inner)
+        l2 = np.divide(m2[sh], mg, out=np.zeros_like(mg), where=inner)
+        ref = mg * s.prob.adjoint_step(l1, l2, rh[sh], an[sh], gref)
+        errs.append(rel(got[sh], ref))
+    return errs, rel(grad.cpu().numpy(), gref)
+
+
+def test_scaled_adjoint_step_against_oracle():
+    s = Setup(nshots=2)
+    errs, eg = _scaled_step_check(s, 70)
+    print(f"scaled adjoint step: mu^n max-rel {max(errs):.2e}, gradient term {eg:.2e}")
+    assert max(errs) <= TOL and eg <= TOL
+
+
+def test_scaled_adjoint_step_full_size():
+    # the gradient workload's size (2 shots x 256^3, 20-cell sponge), every point
+    s = Setup(nx=256, ny=256, nz=256, nshots=2, nsteps=4, sponge=20, seed=3)
+    errs, eg = _scaled_step_check(s, 80)
+    print(f"scaled adjoint step 256^3: mu^n max-rel {max(errs):.2e}, gradient term {eg:.2e}")
+    assert max(errs) <= TOL and eg <= TOL
+
+
+@pytest.mark.parametrize("form", ["lam", "mu"])
+def test_gradient_term_widening_is_exact_for_subnormal_products(form):
+    # One shot, no sponge (G = 1): the gradient term of one adjoint step is
+    # the FP32 product lam^{n+1} (L a^n) (or (mu^{n+1} / m)(L a^n)) widened to
+    # FP64 and added to zero, so it must equal, bit for bit, numpy's IEEE
+    # FP32 arithmetic converted with a true (double) -- here on operands
+    # whose products fall among the FP32 denormals (below 1.2e-38) as well as
+    # normal ones.
+    nx, ny, nz = 40, 36, 24
+    w = workloads.WaveInputs(nx, ny, nz, nshots=1, nsteps=2, workload=5, sponge=0, salt=9)
+    m = mms.padded_empty(nx, ny, nz, R)
+    f = [mms.padded_empty(nx, ny, nz, R, nshots=1) for _ in range(3)]
+    py, pz, ss = mms.field_geometry(f[0])
+    desc, _keep = mms.wave_desc(nx, ny, nz, R, 1, py, pz, ss, 0, 0.0, -1, w.src)
+    mms.model_from_velocity(desc, torch.from_numpy(w.v).cuda(), m, w.dt, w.h)
+    g = np.random.default_rng(12)
+    n3 = (nz, ny, nx)
+    sign = lambda: np.where(g.random(n3) < 0.5, -1.0, 1.0)  # noqa: E731
+    # magnitudes 1e-24 .. 1e-14 for the state and 1e-24 .. 1e-19 for L a^n:
+    # products from 1e-48 (rounds to zero) through the denormals to 1e-33
+    x1 = (sign() * 10.0 ** g.uniform(-24, -14, n3)).astype(np.float32)
+    xl = (sign() * 10.0 ** g.uniform(-24, -19, n3)).astype(np.float32)
+    cur, prev, lap = f
+    cur[0, R:-R, R:-R, R:-R] = torch.from_numpy(x1)
+    lap[0, R:-R, R:-R, R:-R] = torch.from_numpy(xl)
+    grad = torch.zeros(n3, device="cuda", dtype=torch.float64)
+    if form == "lam":
+        mms.wave_adjoint_lap(desc, workloads.fd8_star_coeffs(), m, cur, prev, None, lap, grad)
+        term = x1 * xl
+    else:
+        mms.wave_adjoint_scaled(desc, workloads.fd8_star_coeffs(), m, cur, prev, None, lap, grad)
+        mi = m[R:-R, R:-R, R:-R].cpu().numpy()
+        term = (x1 / mi) * xl
+    torch.cuda.synchronize()
+    mms.check_device()
+    assert term.dtype == np.float32
+    tiny = np.finfo(np.float32).tiny
+    denormal = (term != 0) & (np.abs(term) < tiny)
+    assert denormal.sum() > 1000 and (np.abs(term) >= tiny).sum() > 1000
+    got = grad.cpu().numpy()
+    exact = term.astype(np.float64)
+    assert np.array_equal(got, exact), float(np.abs(got - exact).max())
+
+
+def test_gradient_scaled_and_lambda_forms_agree():
+    # the two adjoint variables give the same gradient of the 48^3 workload
+    w_true, w0 = _grad_problem()
+    n, nsteps, every = 48, 200, 20
+    prop = WavePropagator(n, n, n, w0.src, w0.zrec, w0.h, w_true.dt, sponge_width=w0.sponge,
+                          sponge_a=w0.sponge_a)
+    amps = torch.from_numpy(w_true.amp).cuda()
+    with torch.no_grad():
+        obs, _ = prop.forward(torch.from_numpy(w_true.v).cuda(), amps, nsteps)
+        rec, ckpt = prop.forward(torch.from_numpy(w0.v).cuda(), amps, nsteps, ckpt_every=every)
+    out = [prop.gradient_m(amps, rec - obs, ckpt, every, scaled=sc).cpu().numpy() for sc in (True, False)]
+    torch.cuda.synchronize()
+    mms.check_device()
+    err = rel(out[0], out[1])
+    print(f"gradient 48^3: mu form vs lam form max-rel {err:.2e}")
+    assert err <= 1e-4

@@ -267,5 +267,5 @@ class AnisoInputs:
                 pn = _smooth_noise(shape, g, sigma=8.0) / 0.05 * math.radians(30.0)
             else:
                 tn = pn = 0.0
-            self.theta = np.ascontiguousarray(dip + tn, np.float32)
+            self.theta = np.ascontiguousarray(np.broadcast_to(dip + tn, shape), np.float32)
             self.phi = np.ascontiguousarray(azi + pn + np.zeros(shape), np.float32)
