@@ -500,6 +500,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0,
                     help="grid edge (0 = the workload's own; smaller for profiling captures); not for rtm512 or grad256")
+    ap.add_argument("--adjoint", default="auto", choices=["auto", "lam", "mu"],
+                    help="grad256: the adjoint state, lam or mu = m G lam (auto: mu where m > 0 everywhere)")
     ap.add_argument("--shots", type=int, default=0,
                     help="shots of the wave workloads (0 = the workload's own: 8 for rtm512, 2 for grad256)")
     args = ap.parse_args()
@@ -738,7 +740,7 @@ def run_wave(args):
     wi = workloads.WaveInputs(n, n, n, nshots=nshots, nsteps=nsteps, workload=4 if n == 512 else 5,
                               noise=True, salt=rank)
     prop = WavePropagator(n, n, n, wi.src, wi.zrec, wi.h, wi.dt, sponge_width=wi.sponge,
-                          sponge_a=wi.sponge_a, device=dev)
+                          sponge_a=wi.sponge_a, device=dev, adjoint=args.adjoint)
     v_host = torch.from_numpy(wi.v).pin_memory()
     amps_host = torch.from_numpy(wi.amp).pin_memory()
     v = v_host.to(dev)
@@ -861,7 +863,8 @@ def run_wave(args):
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / (steps if args.workload == "rtm512" else reps),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": {"workload": WORKLOAD_NAMES[args.workload], "shots": nshots,
-                                                "n": n, "time_steps": nsteps if args.workload != "rtm512" else steps},
+                                                "n": n, "time_steps": nsteps if args.workload != "rtm512" else steps,
+                                                **({"adjoint": args.adjoint} if args.workload == "grad256" else {})},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * reps, "clocks": clk,
                 "peaks": {"hbm_gbs": hbm_peak, "source": peak_src}}

@@ -362,23 +362,32 @@ mms_status mms_wave_adjoint_lap(const mms_wave_desc *desc, const float *coeffs, 
 
 /*
  * The adjoint step of mms_wave_adjoint_lap in the scaled variable
- * mu = m G lam (pointwise), which the gradient path carries instead of lam:
+ * mu = m G lam (pointwise), which the gradient path may carry instead of lam:
  *     mu^n = G (2 mu^{n+1} + m L mu^{n+1} - G mu^{n+2} + m R^T r^n)
- *     grad_m += sum_shots (mu^{n+1} / m) (L a^n)           (FP64)
- * (lam's update multiplied by m G at the output point; G lam^{n+1} =
- * mu^{n+1} / m).  It has the forward step's form -- the stencil applied to
- * the state itself -- and runs on the forward step's kernel.  mu_cur:
- * device mu^{n+1}; mu_prev: device, in mu^{n+2}, out mu^n; resid, lap_a
- * (= L a^n, as written by mms_wave_step_lap), grad_m and the per-shot
- * gradient slices as in mms_wave_adjoint_lap; lap_a NULL = no gradient term.
- * Needs m > 0 at every interior point (v != 0): mu loses lam where m = 0,
- * and the gradient term divides by m.  Aliasing and alignment errors as
- * mms_wave_adjoint_lap.  The paper is silent on the adjoint; this is the
- * gradient path's own formulation.
+ *     grad_m += sum_shots mu^{n+1} (L a^n)                 (FP64)
+ * (lam's update multiplied by m G at the output point).  It has the forward
+ * step's form -- the stencil applied to the state itself -- and runs on the
+ * forward step's kernel.  Its gradient sum is m times mms_wave_adjoint_lap's
+ * (mu^{n+1} = m G lam^{n+1}, and m does not change with n): divide it by m
+ * once, after the last step, with mms_grad_divide_m.  mu_cur: device
+ * mu^{n+1}; mu_prev: device, in mu^{n+2}, out mu^n; resid, lap_a (= L a^n,
+ * as written by mms_wave_step_lap), grad_m and the per-shot gradient slices
+ * as in mms_wave_adjoint_lap; lap_a NULL = no gradient term.  Needs m > 0
+ * at every interior point (v != 0): mu loses lam where m = 0.  Aliasing and
+ * alignment errors as mms_wave_adjoint_lap.  The paper is silent on the
+ * adjoint; this is the gradient path's own formulation.
  */
 mms_status mms_wave_adjoint_scaled(const mms_wave_desc *desc, const float *coeffs, const float *m,
                                    const float *mu_cur, float *mu_prev, const float *resid,
                                    const float *lap_a, double *grad_m, void *stream);
+
+/*
+ * grad_m[(z*ny + y)*nx + x] /= m at interior point (x, y, z), in FP64, for the
+ * nz*ny*nx doubles of grad_m (device, dense); m: device padded field of the
+ * descriptor's geometry.  Turns mms_wave_adjoint_scaled's gradient sum into
+ * dJ/dm.  MMS_E_ARG for null pointers or grad_m overlapping m.
+ */
+mms_status mms_grad_divide_m(const mms_wave_desc *desc, const float *m, double *grad_m, void *stream);
 
 /* m = v^2 dt^2 / h^2 into a padded field (halo set to 0); v dense nz*ny*nx.
  * MMS_E_ARG for null pointers, dt or h not positive, or m overlapping v. */

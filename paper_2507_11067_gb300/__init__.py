@@ -7,7 +7,7 @@ decomposition across ranks (``distributed``).  Importing
 the package does not load the library; the first call does, and fails
 loudly if the library has not been built.
 """
-from ._lib import (BOX, BOX2D, PATHS, STAR, STAR2D, MMSError, apply, apply_dense, apply_f64, apply_host, auto_path, check_device,
+from ._lib import (BOX, BOX2D, PATHS, STAR, STAR2D, MMSError, apply, grad_divide_m, apply_dense, apply_f64, apply_host, auto_path, check_device,
                    default_variant,
                    dot_f64, field_geometry, grad_to_velocity, load, model_from_velocity,
                    num_variants, padded_empty, padded_empty2d, pitches, set_variant, sum_f64, to_padded_device, to_padded_device2d,
@@ -16,7 +16,7 @@ from ._lib import (BOX, BOX2D, PATHS, STAR, STAR2D, MMSError, apply, apply_dense
                    aniso_num_variants, aniso_set_variant, tti_model, tti_step)
 from .build import build
 
-__all__ = ["BOX", "BOX2D", "PATHS", "STAR", "STAR2D", "MMSError", "apply", "apply_dense", "apply_f64", "apply_host", "auto_path", "build",
+__all__ = ["BOX", "BOX2D", "PATHS", "STAR", "STAR2D", "MMSError", "apply", "grad_divide_m", "apply_dense", "apply_f64", "apply_host", "auto_path", "build",
            "check_device",
            "default_variant", "dot_f64", "field_geometry", "grad_to_velocity", "load",
            "model_from_velocity", "num_variants", "padded_empty", "padded_empty2d", "pitches", "set_variant", "sum_f64",

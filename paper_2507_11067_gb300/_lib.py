@@ -47,7 +47,7 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_check_device", "mms_version", "mms_stencil_apply_noalloc", "mms_wave_step_to",
            "mms_sum_f64", "mms_selftest_timeout", "mms_stencil_apply_host", "mms_vti_model", "mms_vti_step",
            "mms_aniso_num_variants", "mms_aniso_set_variant", "mms_tti_model", "mms_tti_step", "mms_stencil_apply_f64", "mms_wave_step_lap",
-           "mms_wave_adjoint_lap", "mms_wave_adjoint_scaled"]
+           "mms_wave_adjoint_lap", "mms_wave_adjoint_scaled", "mms_grad_divide_m"]
 
 
 MAX_SHOTS = 64  # largest mms_wave_desc.nshots the library takes
@@ -176,6 +176,7 @@ def load():
             "mms_wave_adjoint": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
             "mms_wave_adjoint_lap": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
             "mms_wave_adjoint_scaled": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P],
+            "mms_grad_divide_m": [ctypes.POINTER(WaveDesc), P, P, P],
             "mms_wave_step_lap": [ctypes.POINTER(WaveDesc), P, P, P, P, P, P, P, P, P],
             "mms_model_from_velocity": [ctypes.POINTER(WaveDesc), P, P, ctypes.c_float,
                                         ctypes.c_float, P],
@@ -554,7 +555,8 @@ def wave_adjoint_lap(desc, coeffs, m, lam_cur, lam_prev, resid=None, lap_a=None,
 
 
 def wave_adjoint_scaled(desc, coeffs, m, mu_cur, mu_prev, resid=None, lap_a=None, grad_m=None, stream=None):
-    """mms_wave_adjoint_scaled: the adjoint step in mu = m G lam (m > 0)."""
+    """mms_wave_adjoint_scaled: the adjoint step in mu = m G lam (m > 0); its
+    gradient sum is m dJ/dm (grad_divide_m turns it into dJ/dm)."""
     x = _WaveExtent(desc)
     _need(m, "m", nbytes=x.model)
     for t, name in ((mu_cur, "mu_cur"), (mu_prev, "mu_prev")):
@@ -566,6 +568,14 @@ def wave_adjoint_scaled(desc, coeffs, m, mu_cur, mu_prev, resid=None, lap_a=None
     check(load().mms_wave_adjoint_scaled(ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                          _ptr(mu_cur), _ptr(mu_prev), _ptr(resid), _ptr(lap_a), _ptr(grad_m),
                                          _stream(stream)))
+
+
+def grad_divide_m(desc, m, grad_m, stream=None):
+    """mms_grad_divide_m: grad_m /= m at every interior point (FP64)."""
+    x = _WaveExtent(desc)
+    _need(m, "m", nbytes=x.model)
+    _need(grad_m, "grad_m", _f64(), nbytes=x.dense * 2, dense=True)
+    check(load().mms_grad_divide_m(ctypes.byref(desc), _ptr(m), _ptr(grad_m), _stream(stream)))
 
 
 def model_from_velocity(desc, v, m, dt, h, stream=None):

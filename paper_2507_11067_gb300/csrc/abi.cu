@@ -833,6 +833,18 @@ mms_status mms_wave_adjoint_scaled(const mms_wave_desc *desc, const float *coeff
     return e == cudaSuccess ? MMS_OK : cuda_fail(e, "scaled adjoint step launch");
 }
 
+mms_status mms_grad_divide_m(const mms_wave_desc *desc, const float *m, double *grad_m, void *stream)
+{
+    WaveGeo g{};
+    static const float dummy[27] = {0};
+    mms_status st = wave_geo(desc, dummy, &g);
+    if (st != MMS_OK) return st;
+    if (!m || !grad_m) return fail(MMS_E_ARG, "null pointer");
+    if (overlaps(grad_m, (size_t)g.nx * g.ny * g.nz * 8, m, model_bytes(g))) return fail(MMS_E_ARG, "grad_m overlaps m");
+    cudaError_t e = launch_grad_divide_m(g, m, grad_m, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMS_OK : cuda_fail(e, "divide-by-m kernel launch");
+}
+
 mms_status mms_wave_step_lap(const mms_wave_desc *desc, const float *coeffs, const float *m, const float *p_cur,
                              const float *p_prev, float *p_next, float *lap_out, const float *src_amp, float *rec,
                              void *stream)

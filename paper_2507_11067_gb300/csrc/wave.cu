@@ -17,10 +17,11 @@
 // mu = m g lam (pointwise).  Multiplying the update by m g at the output
 // point gives
 //   mu^n = g (2 mu^{n+1} + m L mu^{n+1} - g mu^{n+2} + m R^T r^n)
-//   grad += (mu^{n+1} / m) (L a^n)
+//   grad += mu^{n+1} (L a^n)          (= m times the lam-form term)
 // -- the forward step's form (the stencil on the state itself, m and g after
 // it) -- so it runs on the forward kernel with no per-plane product and
-// no barrier between forming and reading it.  It needs m > 0 everywhere.
+// no barrier between forming and reading it; the accumulated gradient is
+// divided by m once at the end (divide_m_kernel).  It needs m > 0.
 #include "common.cuh"
 #include "tile.cuh"
 #include "wave.cuh"
@@ -91,7 +92,7 @@ __device__ __forceinline__ double widen(float f)
 // writes L a^n; the adjoint step in the scaled variable mu = m G lam, whose
 // update has the forward step's form (the stencil acts on the state itself),
 // with the receiver residual m r^n in place of the source and the FP64
-// gradient term (mu^{n+1} / m)(L a^n) = G lam^{n+1} (L a^n) read from a
+// gradient term mu^{n+1} (L a^n) = m G lam^{n+1} (L a^n), L a^n read from a
 // fifth tile.
 enum { K_FWD = 0, K_FWD_LAP = 1, K_ADJ_SCALED = 2 };
 
@@ -238,9 +239,11 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                     if constexpr (ADJ) {
                         if (at_rec && gx + k < geo.nx)
                             v += mv[i][k] * adj.resid[((int64_t)sh * geo.ny + y) * geo.nx + gx + k];
-                        // G lam^{n+1} = mu^{n+1} / m; the term in FP32 (its
-                        // operands are FP32), accumulated in FP64
-                        if (has_grad) gd[k] = widen(__fdiv_rn(cv[i][k], mv[i][k]) * lv[i][k]);
+                        // mu^{n+1} (L a^n) = m G lam^{n+1} (L a^n): m is the same
+                        // at every step, so the sum is divided by it once, at
+                        // the end (mms_grad_divide_m).  The term in FP32 (its
+                        // operands are FP32), accumulated in FP64.
+                        if (has_grad) gd[k] = widen(cv[i][k] * lv[i][k]);
                     } else {
                         if (gx + k == sx && y == sy && z == sz) v += samp;
                     }
@@ -531,6 +534,19 @@ __global__ void model_kernel(WaveGeo geo, const float *__restrict__ v, float *__
     }
 }
 
+// grad[z][y][x] /= m at the interior point (FP64): the scaled adjoint's sum
+// of mu^{n+1} (L a^n) turned into dJ/dm.
+__global__ void divide_m_kernel(WaveGeo geo, const float *__restrict__ m, double *__restrict__ grad)
+{
+    const int r = geo.r;
+    const int64_t n = (int64_t)geo.nx * geo.ny * geo.nz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i % geo.nx, y = (i / geo.nx) % geo.ny, z = i / ((int64_t)geo.nx * geo.ny);
+        grad[i] = grad[i] / (double)m[(z + r) * geo.pz + (y + r) * geo.py + x + r];
+    }
+}
+
 __global__ void chain_kernel(const double *__restrict__ gm, const float *__restrict__ v,
                              double *__restrict__ gv, int64_t n, double s)
 {
@@ -712,6 +728,12 @@ cudaError_t launch_grad_to_velocity(const double *gm, const float *v, double *gv
 {
     const double s = ((double)dt * dt) / ((double)h * h);
     chain_kernel<<<152 * 8, 256, 0, st>>>(gm, v, gv, n, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_divide_m(const WaveGeo &g, const float *m, double *grad, cudaStream_t st)
+{
+    divide_m_kernel<<<152 * 8, 256, 0, st>>>(g, m, grad);
     return cudaGetLastError();
 }
 

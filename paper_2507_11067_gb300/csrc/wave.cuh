@@ -24,7 +24,7 @@ cudaError_t launch_wave_fwd(const WaveGeo &g, const float *coeffs, const float *
                             const float *p_prev, float *p_next, const float *src_amp, float *rec,
                             cudaStream_t st, float *lapout = nullptr);
 // The adjoint step in mu = m g lam (the gradient path): mu^n into mu_prev
-// (which held mu^{n+2}); with lap_a and grad, grad += (mu^{n+1}/m)(L a^n).
+// (which held mu^{n+2}); with lap_a and grad, grad += mu^{n+1} (L a^n).
 cudaError_t launch_wave_adj_scaled(const WaveGeo &g, const float *coeffs, const float *m, const float *mu_cur,
                                    float *mu_prev, const float *resid, const float *lap_a, double *grad,
                                    cudaStream_t st);
@@ -34,6 +34,8 @@ cudaError_t launch_wave_adj(const WaveGeo &g, const float *coeffs, const float *
                             cudaStream_t st, bool lapin = false);
 cudaError_t launch_model_from_velocity(const WaveGeo &g, const float *v, float *m, float dt, float h,
                                        cudaStream_t st);
+// grad (dense nz*ny*nx FP64) divided by m at each interior point.
+cudaError_t launch_grad_divide_m(const WaveGeo &g, const float *m, double *grad, cudaStream_t st);
 cudaError_t launch_grad_to_velocity(const double *gm, const float *v, double *gv, int64_t n, float dt,
                                     float h, cudaStream_t st);
 cudaError_t launch_dot_f64(const float *a, const float *b, int64_t n, double *res, cudaStream_t st);

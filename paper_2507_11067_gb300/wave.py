@@ -23,11 +23,17 @@ class WavePropagator:
 
     nx, ny, nz: interior size; src: (nshots, 3) interior source points;
     rec_z: receiver plane; h: grid spacing (m); dt: time step (s);
-    coeffs: (3, 2r+1) star weights (unscaled; FD8 by default).
+    coeffs: (3, 2r+1) star weights (unscaled; FD8 by default);
+    adjoint: the adjoint state the gradient carries: "lam", "mu" (= m G lam,
+    mms_wave_adjoint_scaled; needs v != 0 everywhere; the faster on GB300),
+    or "auto" (mu where every interior m > 0, else lam).
     """
 
     def __init__(self, nx, ny, nz, src, rec_z, h, dt, sponge_width=20, sponge_a=0.015, r=4,
-                 coeffs=None, device="cuda"):
+                 coeffs=None, device="cuda", adjoint="auto"):
+        if adjoint not in ("lam", "mu", "auto"):
+            raise ValueError("adjoint is 'lam', 'mu' or 'auto'")
+        self.adjoint = adjoint
         self.nx, self.ny, self.nz, self.r = int(nx), int(ny), int(nz), int(r)
         self.src = np.asarray(src, np.int32).reshape(-1, 3)
         self.nshots = len(self.src)
@@ -92,7 +98,7 @@ class WavePropagator:
                                 (ss, pz, py, 1), flat.storage_offset())
 
     # ------------------------------------------------------------ gradient
-    def gradient_m(self, amps, resid, ckpt, ckpt_every, deterministic=False, scaled=False):
+    def gradient_m(self, amps, resid, ckpt, ckpt_every, deterministic=False, scaled=None):
         """dJ/dm (FP64, (nz, ny, nx)) for records whose residual is ``resid``
         (nsteps, nshots, ny, nx), from the forward checkpoints; the velocity
         (model m) must be the one the checkpoints were made with.
@@ -105,9 +111,8 @@ class WavePropagator:
         read-modify-write, summed once at the end) for bit-reproducible
         results, at about 15 % more adjoint time with two shots.  ``scaled``
         carries the adjoint state as mu = m G lam (mms_wave_adjoint_scaled;
-        needs m > 0 at every interior point) instead of lam; None picks mu
-        where m allows it.  The same gradient either way; lam is the faster
-        of the two on GB300 (its gradient term costs less)."""
+        needs m > 0 at every interior point) instead of lam; None takes the
+        propagator's ``adjoint`` setting.  The same gradient either way."""
         nsteps = resid.shape[0]
         resid = resid.to(self.device, torch.float32).contiguous()
         amps = amps.to(self.device, torch.float32).contiguous()
@@ -134,7 +139,8 @@ class WavePropagator:
         # forward step's form; the gradient terms are the same.
         r = self.r
         if scaled is None:
-            scaled = bool((self.m[r:-r, r:-r, r:-r] > 0).all())
+            scaled = (self.adjoint == "mu" or
+                      (self.adjoint == "auto" and bool((self.m[r:-r, r:-r, r:-r] > 0).all())))
         adjoint = _lib.wave_adjoint_scaled if scaled else _lib.wave_adjoint_lap
         lam = [self.new_fields(), self.new_fields()]   # lam^{n+2}, lam^{n+1} (or mu)
         nseg = self.n_checkpoints(nsteps, ckpt_every)
@@ -155,7 +161,9 @@ class WavePropagator:
             have_carry = True
         if per_shot:
             _lib.sum_f64(grad, grad[0])
-            return grad[0]
+            grad = grad[0]
+        if scaled:   # the sum of mu^{n+1} (L a^n) is m dJ/dm
+            _lib.grad_divide_m(self.desc, self.m, grad)
         return grad
 
     def gradient_v(self, v, grad_m):

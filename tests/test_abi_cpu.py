@@ -247,6 +247,8 @@ def test_wave_outputs_may_not_alias_their_inputs(lib):
     refused(lib.mms_wave_adjoint_scaled(ctypes.byref(d), c, m, p, q, None, x, None, None), b"without grad_m")
     refused(lib.mms_wave_adjoint_scaled(ctypes.byref(d), c, m, p, q, None, q, P(x.value + 8 * 0), None),
             b"overlap")
+    refused(lib.mms_grad_divide_m(ctypes.byref(d), m, P(m.value), None), b"grad_m overlaps m")
+    refused(lib.mms_grad_divide_m(ctypes.byref(d), None, x, None), b"null pointer")
     refused(lib.mms_model_from_velocity(ctypes.byref(d), m, m, ctypes.c_float(1e-3), ctypes.c_float(10.0), None),
             b"overlaps v")
     n = nx * ny * nz

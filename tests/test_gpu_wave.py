@@ -618,6 +618,7 @@ def _scaled_step_check(s, seed):
     resid = torch.from_numpy(g.normal(size=(s.ns, s.ny, s.nx)).astype(np.float32)).cuda()
     grad = torch.zeros((s.nz, s.ny, s.nx), device="cuda", dtype=torch.float64)
     mms.wave_adjoint_scaled(s.desc, s.cf, s.m, mu1, mu2, resid, lap, grad)
+    mms.grad_divide_m(s.desc, s.m, grad)        # the sum of mu^{n+1} (L a^n) over m
     torch.cuda.synchronize()
     mms.check_device()
     got = mu2.cpu().numpy()
@@ -652,7 +653,7 @@ def test_scaled_adjoint_step_full_size():
 @pytest.mark.parametrize("form", ["lam", "mu"])
 def test_gradient_term_widening_is_exact_for_subnormal_products(form):
     # One shot, no sponge (G = 1): the gradient term of one adjoint step is
-    # the FP32 product lam^{n+1} (L a^n) (or (mu^{n+1} / m)(L a^n)) widened to
+    # the FP32 product lam^{n+1} (L a^n) (or mu^{n+1} (L a^n)) widened to
     # FP64 and added to zero, so it must equal, bit for bit, numpy's IEEE
     # FP32 arithmetic converted with a true (double) -- here on operands
     # whose products fall among the FP32 denormals (below 1.2e-38) as well as
@@ -675,13 +676,9 @@ def test_gradient_term_widening_is_exact_for_subnormal_products(form):
     cur[0, R:-R, R:-R, R:-R] = torch.from_numpy(x1)
     lap[0, R:-R, R:-R, R:-R] = torch.from_numpy(xl)
     grad = torch.zeros(n3, device="cuda", dtype=torch.float64)
-    if form == "lam":
-        mms.wave_adjoint_lap(desc, workloads.fd8_star_coeffs(), m, cur, prev, None, lap, grad)
-        term = x1 * xl
-    else:
-        mms.wave_adjoint_scaled(desc, workloads.fd8_star_coeffs(), m, cur, prev, None, lap, grad)
-        mi = m[R:-R, R:-R, R:-R].cpu().numpy()
-        term = (x1 / mi) * xl
+    fn = mms.wave_adjoint_lap if form == "lam" else mms.wave_adjoint_scaled
+    fn(desc, workloads.fd8_star_coeffs(), m, cur, prev, None, lap, grad)
+    term = x1 * xl
     torch.cuda.synchronize()
     mms.check_device()
     assert term.dtype == np.float32
