@@ -228,12 +228,13 @@ TC_PATHS = ("tf32", "3xtf32", "bf16x3")
 def tc_dense_flop_per_pt(path: str, r: int, planar: bool = False) -> float:
     """Dense work the banded MMAs issue per output point (band zeros
     included).  A tile of the tensor-core kernel is 4 x-subtiles of
-    TXO = 16 - 2r outputs by TY = 32 - 2r rows; per output plane it runs, for
+    TXO = 16 - 2r (rounded down to a multiple of 4) outputs by TY = 32 - 2r
+    rows; per output plane it runs, for
     each plane the stencil reaches in z ((2r+1) for the box, 1 for planar
     stencils and the star's in-plane part), M = 128 lanes x N = (2r+1) TXO
     (rounded up to 16) x K = 16 MMAs, times the split products (3 for
     3xTF32 / BF16x3, 1 for TF32)."""
-    txo, ty, w = 16 - 2 * r, 32 - 2 * r, 2 * r + 1
+    txo, ty, w = (16 - 2 * r) & ~3, 32 - 2 * r, 2 * r + 1
     n = -(-w * txo // 16) * 16
     planes = 1 if planar else w
     prods = 1 if path == "tf32" else 3

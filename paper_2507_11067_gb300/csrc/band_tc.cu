@@ -109,7 +109,9 @@ struct Cfg {
     static constexpr int RZ = MODE == M_PLANAR ? 0 : R;  // z halo of a tile's staged planes
     static constexpr bool BF = PREC == P_BF16X3;
     static constexpr int K = 16;                         // contraction: input x of one subtile
-    static constexpr int TXO = K - 2 * R;                // output x per subtile (14, 12, 10, 8)
+    // output x per subtile: K - 2r rounded down to a multiple of 4 (12, 12,
+    // 8, 8), so that a subtile row of outputs is a 16-byte TMA box row
+    static constexpr int TXO = (K - 2 * R) & ~3;
     static constexpr int TX = 4 * TXO;                   // output x per tile (4 subtiles)
     static constexpr int TY = 32 - 2 * R;                // output rows per tile
     static constexpr int NB = W * TXO;                   // band rows (dy, x)
@@ -141,7 +143,7 @@ struct Cfg {
     // FP32 staging box: TX + 2r columns (at least), 32 rows, one plane; the
     // row pitch in 16-byte units is odd, so the converters' row reads
     // (8 rows per quarter warp) hit 8 different bank groups
-    static constexpr int BOXW = R == 1 ? 60 : R == 2 ? 52 : R == 3 ? 52 : 44;
+    static constexpr int BOXW = R <= 2 ? 52 : 44;
     static constexpr int STG_BYTES = BOXW * 32 * 4;
     static constexpr int STG_STRIDE = (STG_BYTES + 1023) / 1024 * 1024;
     static constexpr int NST = 8;
@@ -160,14 +162,20 @@ struct Cfg {
 #else
     static constexpr size_t TL_BYTES = 0;
 #endif
-    static constexpr size_t SMEM_NEED = 1024 + OFF_BAR + 1024 + TL_BYTES;
+    // Output subtiles staged for TMA stores (one TXO x TY box per epilogue
+    // warp and output, two buffers per warp), where a subtile row is a
+    // 16-byte multiple (r = 2, 4); other radii store from registers.
+    static constexpr bool TSTORE = (TXO * 4) % 16 == 0;
+    static constexpr int OBUF = TSTORE ? (TXO * TY * 4 + 127) / 128 * 128 : 0;
+    static constexpr size_t OFF_OBUF = OFF_BAR + 1024 + TL_BYTES;
+    static constexpr size_t SMEM_NEED = 1024 + OFF_OBUF + 16 * (size_t)OBUF;
     // at least 120 KB, so that two CTAs (each holding all 512 TMEM columns)
     // never share an SM
     static constexpr size_t SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
     static constexpr bool OK = PR >= NEED && SMEM <= 227 * 1024 && A0 + PR * APL <= 512;
     static_assert(OK, "tensor-core configuration does not fit");
     static constexpr uint32_t IDESC = tc::instr_desc(BF ? 1u : 2u, 128, N);
-    static_assert(BOXW >= TX + 2 * R && BOXW % 4 == 0 && (BOXW / 4) % 2 == 1, "staging box");
+    static_assert(BOXW >= TX - TXO + K && BOXW % 4 == 0 && (BOXW / 4) % 2 == 1, "staging box");
     static_assert(N % 16 == 0 && N <= 256 && (N == 48 || N == 64 || N == 80), "epilogue loads");
     static_assert(2 * NST + 2 * PR + 2 * ND <= 120, "barrier area");
     static_assert(ND % 2 == 0, "epilogue slots of two workers");
@@ -212,16 +220,32 @@ struct TcArgs {
     int tiles_x, tiles_y, tiles;  // tiles = tiles_x * tiles_y * z chunks
     int nzt;                      // output planes per z chunk
     int zoff;                     // padded input plane of staged plane 0 of chunk 0
+    int tstore;                   // outputs leave by TMA stores (the map is valid)
     float cz[2 * kMaxR + 1];      // star: z weights (the centre is in the band)
 };
+
+// TMA store of a shared-memory box into a tensor (bulk-group completion),
+// and the waits on this thread's bulk groups.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(ptx::smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// every committed group has finished reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed group has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2 and 3 =
 // idle after set-up, 4..15 = workers, three per TMEM lane quarter (warp w
 // reaches lane quarter w % 4): worker 0 converts, workers 1 and 2 drain.
 template <int R, int PREC, int MODE>
 __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
-    band_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BoxCoef cf,
-                   const __grid_constant__ TcArgs a, unsigned *err)
+    band_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap,
+                   const __grid_constant__ BoxCoef cf, const __grid_constant__ TcArgs a, unsigned *err)
 {
     using C = Cfg<R, PREC, MODE>;
     constexpr int W = C::W;
@@ -438,6 +462,9 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
         // row t of subtile q
         const int q = warp & 3, wi = (warp - 4) >> 2, t = lane;
         const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16);
+        [[maybe_unused]] float *obuf = reinterpret_cast<float *>(smem + C::OFF_OBUF) +
+                                       (size_t)(wi > 0 ? ((wi - 1) * 4 + q) * 2 : 0) * (C::OBUF / 4);
+        [[maybe_unused]] int nout = 0;  // outputs this epilogue warp has stored
         bool ok = true;
         [[maybe_unused]] unsigned long long ts = 0, ta = 0, td = 0, tc0 = 0, tf = 0, tep = 0, t00 = MMS_CLOCK();
 
@@ -622,6 +649,32 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
                 o[x] = acc;
             }
             const int y = y0 + t, xb = x0 + q * C::TXO, zg = z0 + z;
+            if constexpr (C::TSTORE) {
+                if (a.tstore) {
+                    // the subtile into this warp's buffer for the output's
+                    // parity, then one TMA store (clipped at the grid's edges);
+                    // the store that last read the buffer is waited for first
+                    float *ob = obuf + (size_t)(nout & 1) * (C::OBUF / 4);
+                    if (lane == 0) bulk_wait_read_all();
+                    __syncwarp();
+                    if (t < C::TY) {
+#pragma unroll
+                        for (int i = 0; i < C::TXO / 4; ++i)
+                            reinterpret_cast<float4 *>(ob + t * C::TXO)[i] =
+                                make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+                    }
+                    ptx::fence_proxy_async_smem();  // generic writes -> the TMA unit's reads
+                    __syncwarp();
+                    if (lane == 0 && xb < a.nx) {
+                        tma_store_3d(&omap, ob, xb, y0, zg);
+                        bulk_commit();
+                    }
+                    ++nout;
+                    if (lane == 0 && q == 0) MMS_TL(8, j);
+                    tep += MMS_CLOCK() - t1;
+                    return true;
+                }
+            }
             if (t < C::TY && y < a.ny && xb < a.nx) {
                 float *op = a.out + (int64_t)zg * a.opz + (int64_t)y * a.opy + xb;
                 const bool full = xb + C::TXO <= a.nx;
@@ -670,6 +723,10 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
                     if (j % 2 == wi - 1) ok = epilogue(j, z, kb, nzt, x0, y0, z0);
                 kb += nzt + 2 * C::RZ;
             }
+            // this warp's output stores are complete (and their sources
+            // read) before the CTA exits
+            if constexpr (C::TSTORE)
+                if (lane == 0) bulk_wait_all();
         }
         if (!ok) *abort_flag = 1;
         if (lane == 0 && warp == 4) {
@@ -749,11 +806,16 @@ cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int nzt, const Laun
     a.zoff = L.zoff;
     if (MODE == M_STAR)
         for (int d = 0; d < C::W; ++d) a.cz[d] = L.cz[d];
+    // outputs by TMA stores where the subtile rows and the output's pitches
+    // are 16-byte multiples (and the map encodes); else from registers
+    CUtensorMap omap{};
+    a.tstore = C::TSTORE && a.vec == 4 &&
+               encode_tmap_3d(&omap, L.out, s.nx, s.ny, s.nz, L.opy, L.opz, C::TSTORE ? C::TXO : 4, C::TY, 1);
     auto kern = band_tc_kernel<R, PREC, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     const int grid = a.tiles < num_sms() ? a.tiles : num_sms();
-    kern<<<grid, C::NT, C::SMEM, s.stream>>>(map, cf, a, device_error_word());
+    kern<<<grid, C::NT, C::SMEM, s.stream>>>(map, omap, cf, a, device_error_word());
     return cudaGetLastError();
 }
 
@@ -907,7 +969,9 @@ int band_tc_two_pass_variant(int v) { return kNumTile + (v >= 0 ? v % kNumTile :
 void band_tc_box(int shape, int r, int path, int v, int *bx, int *by, int *bz, int *swz)
 {
     (void)shape; (void)path; (void)v;
-    static const int boxw[kMaxR + 1] = {0, 60, 52, 52, 44};
+    // the kernel's own staging width (it does not depend on precision or form)
+    static const int boxw[kMaxR + 1] = {0, Cfg<1, P_BF16X3, M_BOX>::BOXW, Cfg<2, P_BF16X3, M_BOX>::BOXW,
+                                        Cfg<3, P_BF16X3, M_BOX>::BOXW, Cfg<4, P_BF16X3, M_BOX>::BOXW};
     *bx = r >= 1 && r <= kMaxR ? boxw[r] : 0;
     *by = 32;
     *bz = 1;

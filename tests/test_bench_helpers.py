@@ -51,12 +51,14 @@ def test_traffic_goes_null_when_a_source_changes(tmp_path, monkeypatch):
 
 
 def test_tensor_core_dense_work_per_point():
-    # per output plane a tile (4 subtiles of TXO = 16 - 2r outputs, TY = 32 - 2r
-    # rows) runs 128 x N x 16 MMAs, N = (2r+1) TXO rounded up to 16, for each
-    # plane reached in z, times 3 split products (BF16x3)
+    # per output plane a tile (4 subtiles of TXO = 16 - 2r rounded down to a
+    # multiple of 4 outputs, TY = 32 - 2r rows) runs 128 x N x 16 MMAs,
+    # N = (2r+1) TXO rounded up to 16, for each plane reached in z, times 3
+    # split products (BF16x3)
     assert bench.tc_dense_flop_per_pt("bf16x3", 2) == pytest.approx(2 * 128 * 64 * 16 * 5 * 3 / (4 * 12 * 28))
     assert bench.tc_dense_flop_per_pt("bf16x3", 4) == pytest.approx(2 * 128 * 80 * 16 * 9 * 3 / (4 * 8 * 24))
-    assert bench.tc_dense_flop_per_pt("tf32", 1) == pytest.approx(2 * 128 * 48 * 16 * 3 / (4 * 14 * 30))
+    assert bench.tc_dense_flop_per_pt("tf32", 1) == pytest.approx(2 * 128 * 48 * 16 * 3 / (4 * 12 * 30))
+    assert bench.tc_dense_flop_per_pt("bf16x3", 3) == pytest.approx(2 * 128 * 64 * 16 * 7 * 3 / (4 * 8 * 26))
     assert bench.tc_dense_flop_per_pt("bf16x3", 4, planar=True) == pytest.approx(2 * 128 * 80 * 16 * 3 / (4 * 8 * 24))
 
 
