@@ -35,14 +35,16 @@
 //    the converter warps, which see every staged plane anyway and keep the
 //    z partial sums of 2r+1 output planes in registers.
 //
-// Pipeline (persistent CTAs, one per SM, buffers handed over by mbarriers):
-// warp 0 stages FP32 plane boxes by TMA; per TMEM lane quarter, one converter
-// warp fills the A ring and two epilogue warps drain the accumulators of the
-// even and odd outputs; one issuer warp issues every output's MMAs in order,
-// converged (the elected lane's MMAs predicated, not branched around), with
-// one commit per output.  The epilogue that sees an output complete releases
-// the A-ring slots no later output reads: with one issuer the MMAs complete
-// in order.
+// Pipeline (persistent CTAs, buffers handed over by mbarriers): warp 0
+// stages FP32 plane boxes by TMA; per TMEM lane quarter, one converter warp
+// fills the A ring and epilogue warps drain the accumulators and write each
+// output subtile with a TMA store; one issuer warp issues every output's
+// MMAs in order, converged (the elected lane's MMAs predicated, not branched
+// around), with one commit per output.  The epilogue that sees an output
+// complete releases the A-ring slots no later output reads: with one issuer
+// the MMAs complete in order.  A box sweep whose accumulators and A ring fit
+// in half the TMEM runs two such CTAs per SM (two epilogue warps per
+// quarter and four accumulators otherwise, one CTA per SM).
 #include <cuda_bf16.h>
 #include <stdio.h>
 
@@ -129,16 +131,23 @@ struct Cfg {
     // past its first, which completes its z sum; planar reads one plane),
     // with one more converted ahead
     static constexpr int NEED = MODE == M_BOX ? W + 1 : MODE == M_STAR ? R + 2 : 2;
-    // Workers: three warps per TMEM lane quarter; worker 0 converts every
-    // staged plane (the star's keeps the z sums in registers), workers 1 and
-    // 2 drain the accumulators of the even and odd outputs, so the ND
-    // accumulators are an even number and each slot's laps are waited on in
+    // Two CTAs per SM where a box sweep fits in half the TMEM (two
+    // accumulators and the A ring in 256 columns): two independent
+    // pipelines keep the tensor pipe busier than one can.  A dual CTA has
+    // ten warps: producer, issuer, and per TMEM lane quarter one converter
+    // and one epilogue warp; a single CTA has sixteen: producer, issuer, two
+    // idle, and per quarter a converter and two epilogue warps (even and odd
+    // outputs).  Either way each accumulator slot's laps are waited on in
     // order by one warp.
-    static constexpr int ND = 4 * (N + ZC) + NEED * APL <= 512 ? 4 : 2;
+    static constexpr bool DUAL = MODE == M_BOX && 2 * N + NEED * APL <= 256;
+    static constexpr int TMEM_COLS = DUAL ? 256 : 512;
+    static constexpr int NEPI = DUAL ? 1 : 2;            // epilogue warps per lane quarter
+    static constexpr int W0 = DUAL ? 2 : 4;              // first worker warp
+    static constexpr int ND = DUAL ? 2 : 4 * (N + ZC) + NEED * APL <= 512 ? 4 : 2;
     // TMEM columns: ND accumulators of N | ND z-sum slots of ZC | A ring
     static constexpr int Z0 = ND * N;
     static constexpr int A0 = Z0 + ND * ZC;
-    static constexpr int PRF = (512 - A0) / APL < 16 ? (512 - A0) / APL : 16;
+    static constexpr int PRF = (TMEM_COLS - A0) / APL < 16 ? (TMEM_COLS - A0) / APL : 16;
     static constexpr int PR = PRF;                       // A ring planes
     // FP32 staging box: TX + 2r columns (at least), 32 rows, one plane; the
     // row pitch in 16-byte units is odd, so the converters' row reads
@@ -153,7 +162,7 @@ struct Cfg {
     static constexpr int SBO = K * ELT * 8;
     static constexpr int PART_BYTES = N * K * ELT;
     static constexpr int BAND_BYTES = WZ * NPARTS * PART_BYTES;
-    static constexpr int NWARPS = 16;                    // producer, issuer, 2 idle, 12 workers
+    static constexpr int NWARPS = DUAL ? 10 : 16;
     static constexpr int NT = 32 * NWARPS;
     static constexpr size_t OFF_STG = (size_t)(BAND_BYTES + 1023) / 1024 * 1024;
     static constexpr size_t OFF_BAR = OFF_STG + (size_t)NST * STG_STRIDE;
@@ -163,16 +172,16 @@ struct Cfg {
     static constexpr size_t TL_BYTES = 0;
 #endif
     // Output subtiles staged for TMA stores (one TXO x TY box per epilogue
-    // warp and output, two buffers per warp), where a subtile row is a
-    // 16-byte multiple (r = 2, 4); other radii store from registers.
+    // warp and output, two buffers per warp); a subtile row is a 16-byte
+    // multiple (TXO % 4 == 0).
     static constexpr bool TSTORE = (TXO * 4) % 16 == 0;
     static constexpr int OBUF = TSTORE ? (TXO * TY * 4 + 127) / 128 * 128 : 0;
     static constexpr size_t OFF_OBUF = OFF_BAR + 1024 + TL_BYTES;
-    static constexpr size_t SMEM_NEED = 1024 + OFF_OBUF + 16 * (size_t)OBUF;
-    // at least 120 KB, so that two CTAs (each holding all 512 TMEM columns)
-    // never share an SM
-    static constexpr size_t SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
-    static constexpr bool OK = PR >= NEED && SMEM <= 227 * 1024 && A0 + PR * APL <= 512;
+    static constexpr size_t SMEM_NEED = 1024 + OFF_OBUF + 8 * NEPI * (size_t)OBUF;
+    // a single CTA takes at least 120 KB, so that two CTAs holding all 512
+    // TMEM columns each never share an SM; two dual CTAs fit one SM
+    static constexpr size_t SMEM = DUAL ? SMEM_NEED : SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
+    static constexpr bool OK = PR >= NEED && SMEM <= (DUAL ? 113 : 227) * 1024 && A0 + PR * APL <= TMEM_COLS;
     static_assert(OK, "tensor-core configuration does not fit");
     static constexpr uint32_t IDESC = tc::instr_desc(BF ? 1u : 2u, 128, N);
     static_assert(BOXW >= TX - TXO + K && BOXW % 4 == 0 && (BOXW / 4) % 2 == 1, "staging box");
@@ -239,11 +248,12 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 // every committed group has completed
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2 and 3 =
-// idle after set-up, 4..15 = workers, three per TMEM lane quarter (warp w
-// reaches lane quarter w % 4): worker 0 converts, workers 1 and 2 drain.
+// Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner); then the
+// workers, per TMEM lane quarter (warp w reaches lane quarter w % 4) one
+// converter and NEPI epilogue warps: warps 4..15 of a single CTA (2 and 3
+// idle after set-up), warps 2..9 of a dual one.
 template <int R, int PREC, int MODE>
-__global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
+__global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DUAL ? 2 : 1)
     band_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap omap,
                    const __grid_constant__ BoxCoef cf, const __grid_constant__ TcArgs a, unsigned *err)
 {
@@ -268,7 +278,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
     const int my_tiles = a.tiles > (int)blockIdx.x ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, 512);
+        tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
@@ -456,11 +466,11 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
         }
         // every MMA issued completes before TMEM is freed
         if (last >= 0) ptx::mbar_wait_bounded(&full_d[last % C::ND], (uint32_t)(last / C::ND) & 1u, err);
-    } else if (warp >= 4) {
+    } else if (warp >= C::W0) {
         // ---------------------------------------------------------- workers
         // warp 4 + 4 wi + q: worker wi of TMEM lane quarter q; lane t holds
         // row t of subtile q
-        const int q = warp & 3, wi = (warp - 4) >> 2, t = lane;
+        const int q = warp & 3, wi = (warp - C::W0) >> 2, t = lane;
         const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16);
         [[maybe_unused]] float *obuf = reinterpret_cast<float *>(smem + C::OFF_OBUF) +
                                        (size_t)(wi > 0 ? ((wi - 1) * 4 + q) * 2 : 0) * (C::OBUF / 4);
@@ -720,7 +730,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
                 int x0, y0, z0, nzt;
                 tile_of(tl, x0, y0, z0, nzt);
                 for (int z = 0; z < nzt && ok; ++z, ++j)
-                    if (j % 2 == wi - 1) ok = epilogue(j, z, kb, nzt, x0, y0, z0);
+                    if (j % C::NEPI == wi - 1) ok = epilogue(j, z, kb, nzt, x0, y0, z0);
                 kb += nzt + 2 * C::RZ;
             }
             // this warp's output stores are complete (and their sources
@@ -748,7 +758,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, 1)
     __syncthreads();
     if (warp == 1) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tbase, 512);
+        tc::tmem_dealloc(tbase, C::TMEM_COLS);
     }
 #ifdef MMS_ROLE_TRACE
     if (blockIdx.x == 0)
@@ -814,7 +824,9 @@ cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int nzt, const Laun
     auto kern = band_tc_kernel<R, PREC, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
-    const int grid = a.tiles < num_sms() ? a.tiles : num_sms();
+    // persistent: one CTA per SM, two for the dual configuration
+    const int slots = num_sms() * (C::DUAL ? 2 : 1);
+    const int grid = a.tiles < slots ? a.tiles : slots;
     kern<<<grid, C::NT, C::SMEM, s.stream>>>(map, omap, cf, a, device_error_word());
     return cudaGetLastError();
 }
