@@ -139,11 +139,11 @@ struct Cfg {
     // idle, and per quarter a converter and two epilogue warps (even and odd
     // outputs).  Either way each accumulator slot's laps are waited on in
     // order by one warp.
-    static constexpr bool DUAL = MODE == M_BOX && 2 * N + NEED * APL <= 256;
+    static constexpr bool DUAL = MODE == M_BOX && N + NEED * APL <= 256;
     static constexpr int TMEM_COLS = DUAL ? 256 : 512;
     static constexpr int NEPI = DUAL ? 1 : 2;            // epilogue warps per lane quarter
     static constexpr int W0 = DUAL ? 2 : 4;              // first worker warp
-    static constexpr int ND = DUAL ? 2 : 4 * (N + ZC) + NEED * APL <= 512 ? 4 : 2;
+    static constexpr int ND = DUAL ? (2 * N + NEED * APL <= 256 ? 2 : 1) : 4 * (N + ZC) + NEED * APL <= 512 ? 4 : 2;
     // TMEM columns: ND accumulators of N | ND z-sum slots of ZC | A ring
     static constexpr int Z0 = ND * N;
     static constexpr int A0 = Z0 + ND * ZC;
@@ -187,7 +187,7 @@ struct Cfg {
     static_assert(BOXW >= TX - TXO + K && BOXW % 4 == 0 && (BOXW / 4) % 2 == 1, "staging box");
     static_assert(N % 16 == 0 && N <= 256 && (N == 48 || N == 64 || N == 80), "epilogue loads");
     static_assert(2 * NST + 2 * PR + 2 * ND <= 120, "barrier area");
-    static_assert(ND % 2 == 0, "epilogue slots of two workers");
+    static_assert(ND % NEPI == 0, "every epilogue warp owns whole accumulator slots");
 };
 
 __device__ __forceinline__ uint32_t bf16_bits(float v)
