@@ -1248,10 +1248,14 @@ def extra_grad(mms, torch, dev, hbm_peak):
     t_fwd = _time(lambda: mms.wave_step_to(prop.desc, prop.coeffs, prop.m, f[0], f[1], f[2], amps[0]), reps=20)
     t_rec = _time(lambda: mms.wave_step_lap(prop.desc, prop.coeffs, prop.m, f[0], f[1], f[2], f[3], amps[0]),
                   reps=20)
-    t_adj = _time(lambda: mms.wave_adjoint_lap(prop.desc, prop.coeffs, prop.m, f[0], f[4], resid, f[3], grad),
+    # the adjoint step in the variable the gradient carries (mu = m G lam
+    # where every m > 0), and in lam for comparison
+    t_adj = _time(lambda: mms.wave_adjoint_scaled(prop.desc, prop.coeffs, prop.m, f[0], f[4], resid, f[3], grad),
                   reps=20)
-    # accuracy: lam^n and the gradient term of one adjoint step from seeded
-    # lam^{n+1}, lam^{n+2}, a^n (L a^n from the recompute kernel)
+    t_adj_lam = _time(lambda: mms.wave_adjoint_lap(prop.desc, prop.coeffs, prop.m, f[0], f[4], resid, f[3], grad),
+                      reps=20)
+    # accuracy: lam^n (and mu^n) and the gradient term of one adjoint step
+    # from seeded lam^{n+1}, lam^{n+2}, a^n (L a^n from the recompute kernel)
     _fill_interior(f, R, torch.Generator(device=dev).manual_seed(52))
     mms.wave_step_lap(prop.desc, prop.coeffs, prop.m, f[2], f[1], f[0], f[3], amps[0])
     l1, l2, an = (t.cpu().numpy().astype(np.float64) for t in (f[4], f[1], f[2]))
@@ -1264,9 +1268,28 @@ def extra_grad(mms, torch, dev, hbm_peak):
     errs = [rel_err(f[1][sh].cpu().numpy(), prob.adjoint_step(l1[sh], l2[sh], rh[sh], an[sh], gref))
             for sh in range(ns)]
     errs.append(rel_err(grad.cpu().numpy(), gref))
+    # the same in mu = m G lam: mu^{n+1}, mu^{n+2} = m G lam of the fields above
+    mg = np.zeros_like(prob.m)
+    gg = prob.gz[:, None, None] * prob.gy[None, :, None] * prob.gx[None, None, :]
+    mg[R:-R, R:-R, R:-R] = prob.m[R:-R, R:-R, R:-R] * gg
+    mu = [prop.new_fields(), prop.new_fields()]
+    for t, lam in zip(mu, (l1, l2)):
+        t.copy_(torch.from_numpy((lam * mg[None]).astype(np.float32)))
+    m1, m2 = (t.cpu().numpy().astype(np.float64) for t in mu)
+    grad.zero_()
+    mms.wave_adjoint_scaled(prop.desc, prop.coeffs, prop.m, mu[0], mu[1], resid, f[3], grad)
+    mms.grad_divide_m(prop.desc, prop.m, grad)
+    gref = np.zeros((n, n, n))
+    inner = mg > 0
+    for sh in range(ns):
+        lam1 = np.divide(m1[sh], mg, out=np.zeros_like(mg), where=inner)
+        lam2 = np.divide(m2[sh], mg, out=np.zeros_like(mg), where=inner)
+        errs.append(rel_err(mu[1][sh].cpu().numpy(), mg * prob.adjoint_step(lam1, lam2, rh[sh], an[sh], gref)))
+    errs.append(rel_err(grad.cpu().numpy(), gref))
     return {"ms_per_gradient": ms, "gpt_steps": pts * nsteps / ms / 1e6, "bytes_per_point_step": bpp,
             "hbm_gbs": bpp * pts * nsteps / ms / 1e6, "hbm_frac": bpp * pts * nsteps / ms / 1e6 / hbm_peak,
             "forward_step_us": 1e3 * t_fwd, "recompute_step_us": 1e3 * t_rec, "adjoint_step_us": 1e3 * t_adj,
+            "adjoint_lam_step_us": 1e3 * t_adj_lam, "adjoint": prop.adjoint,
             "max_rel_err": max(errs),
             "config": f"{ns} shots x {n}^3, {nsteps} steps, checkpoint every {every}; byte model: forward 16, "
                       f"recompute 20, adjoint 20 B per shot-point-step + FP64 gradient 16 B per point-step"}

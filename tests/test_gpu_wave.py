@@ -607,7 +607,7 @@ def _mg(s):
     return out
 
 
-def _scaled_step_check(s, seed):
+def _scaled_step_check(s, seed, slices=False):
     mu1, mu2, a_n, lap = s.fields
     prev, nxt = (mms.padded_empty(s.nx, s.ny, s.nz, R, nshots=s.ns) for _ in range(2))
     for f, sd in ((mu1, seed), (mu2, seed + 1), (a_n, seed + 2), (prev, seed + 3)):
@@ -616,8 +616,18 @@ def _scaled_step_check(s, seed):
     m1, m2, an = s.host(mu1), s.host(mu2), s.host(a_n)
     g = np.random.default_rng(seed + 4)
     resid = torch.from_numpy(g.normal(size=(s.ns, s.ny, s.nx)).astype(np.float32)).cuda()
-    grad = torch.zeros((s.nz, s.ny, s.nx), device="cuda", dtype=torch.float64)
-    mms.wave_adjoint_scaled(s.desc, s.cf, s.m, mu1, mu2, resid, lap, grad)
+    n3 = (s.nz, s.ny, s.nx)
+    if slices:   # every shot its own FP64 slice, summed afterwards
+        py, pz, ss = mms.field_geometry(s.fields[0])
+        desc, _keep = mms.wave_desc(s.nx, s.ny, s.nz, R, s.ns, py, pz, ss, s.w.sponge, s.w.sponge_a, s.w.zrec,
+                                    s.w.src, grad_shot_stride=s.nx * s.ny * s.nz)
+        gs = torch.zeros((s.ns,) + n3, device="cuda", dtype=torch.float64)
+        mms.wave_adjoint_scaled(desc, s.cf, s.m, mu1, mu2, resid, lap, gs)
+        grad = torch.zeros(n3, device="cuda", dtype=torch.float64)
+        mms.sum_f64(gs, grad)
+    else:
+        grad = torch.zeros(n3, device="cuda", dtype=torch.float64)
+        mms.wave_adjoint_scaled(s.desc, s.cf, s.m, mu1, mu2, resid, lap, grad)
     mms.grad_divide_m(s.desc, s.m, grad)        # the sum of mu^{n+1} (L a^n) over m
     torch.cuda.synchronize()
     mms.check_device()
@@ -635,10 +645,14 @@ def _scaled_step_check(s, seed):
     return errs, rel(grad.cpu().numpy(), gref)
 
 
-def test_scaled_adjoint_step_against_oracle():
-    s = Setup(nshots=2)
-    errs, eg = _scaled_step_check(s, 70)
-    print(f"scaled adjoint step: mu^n max-rel {max(errs):.2e}, gradient term {eg:.2e}")
+@pytest.mark.parametrize("nshots,slices", [(1, False), (2, False), (3, False), (4, False), (2, True), (3, True)])
+def test_scaled_adjoint_step_against_oracle(nshots, slices):
+    # one shot per CTA; the shots' gradient terms meet in one shared FP64
+    # slice (atomics) or in per-shot slices summed afterwards
+    s = Setup(nshots=nshots)
+    errs, eg = _scaled_step_check(s, 70, slices=slices)
+    print(f"scaled adjoint step, {nshots} shots{' (slices)' if slices else ''}: mu^n max-rel {max(errs):.2e}, "
+          f"gradient term {eg:.2e}")
     assert max(errs) <= TOL and eg <= TOL
 
 
