@@ -125,25 +125,27 @@ struct Cfg {
     static constexpr int NPROD = PREC == P_TF32 ? 1 : 3;
     static constexpr int ACOLS = K * ELT / 4;            // TMEM columns of one A part
     static constexpr int APL = NPARTS * ACOLS;           // TMEM columns of one staged plane
-    static constexpr int ZC = MODE == M_STAR ? (TXO + 7) / 8 * 8 : 0;  // z sums of one output
-    // A-ring planes needed for progress (the box reads 2r+1 planes per
-    // output; a star output reads its centre plane and waits for the plane 2r
-    // past its first, which completes its z sum; planar reads one plane),
-    // with one more converted ahead
-    static constexpr int NEED = MODE == M_BOX ? W + 1 : MODE == M_STAR ? R + 2 : 2;
-    // Two CTAs per SM where a box sweep fits in half the TMEM (two
-    // accumulators and the A ring in 256 columns): two independent
-    // pipelines keep the tensor pipe busier than one can.  A dual CTA has
+    static constexpr int ZC = MODE == M_STAR ? (TXO + 15) / 16 * 16 : 0;  // z sums of one output (16-column blocks)
+    // A-ring planes needed for progress, with one more converted ahead: the
+    // box reads 2r+1 planes per output; a star output reads its centre plane
+    // but waits for the plane 2r past its first, which completes its z sum,
+    // and a tile's first r (halo) planes are released only with its first
+    // output, so 2r+1 planes are resident at a tile's start; planar reads one
+    static constexpr int NEED = MODE == M_PLANAR ? 2 : W + 1;
+    // Two CTAs per SM where a sweep fits in half the TMEM (its accumulators,
+    // z-sum blocks and A ring in 256 columns): two independent pipelines keep
+    // the tensor pipe busier than one can.  A dual CTA has
     // ten warps: producer, issuer, and per TMEM lane quarter one converter
     // and one epilogue warp; a single CTA has sixteen: producer, issuer, two
     // idle, and per quarter a converter and two epilogue warps (even and odd
     // outputs).  Either way each accumulator slot's laps are waited on in
     // order by one warp.
-    static constexpr bool DUAL = MODE == M_BOX && N + NEED * APL <= 256;
+    static constexpr bool DUAL = N + ZC + NEED * APL <= 256;
     static constexpr int TMEM_COLS = DUAL ? 256 : 512;
     static constexpr int NEPI = DUAL ? 1 : 2;            // epilogue warps per lane quarter
     static constexpr int W0 = DUAL ? 2 : 4;              // first worker warp
-    static constexpr int ND = DUAL ? (2 * N + NEED * APL <= 256 ? 2 : 1) : 4 * (N + ZC) + NEED * APL <= 512 ? 4 : 2;
+    static constexpr int ND = DUAL ? (2 * (N + ZC) + NEED * APL <= 256 ? 2 : 1)
+                                   : 4 * (N + ZC) + NEED * APL <= 512 ? 4 : 2;
     // TMEM columns: ND accumulators of N | ND z-sum slots of ZC | A ring
     static constexpr int Z0 = ND * N;
     static constexpr int A0 = Z0 + ND * ZC;
@@ -187,6 +189,8 @@ struct Cfg {
     static_assert(BOXW >= TX - TXO + K && BOXW % 4 == 0 && (BOXW / 4) % 2 == 1, "staging box");
     static_assert(N % 16 == 0 && N <= 256 && (N == 48 || N == 64 || N == 80), "epilogue loads");
     static_assert(2 * NST + 2 * PR + 2 * ND <= 120, "barrier area");
+    // TMEM operand and accumulator columns start on 16-column boundaries
+    static_assert(Z0 % 16 == 0 && A0 % 16 == 0 && APL % 16 == 0 && N % 16 == 0, "TMEM column alignment");
     static_assert(ND % NEPI == 0, "every epilogue warp owns whole accumulator slots");
 };
 
