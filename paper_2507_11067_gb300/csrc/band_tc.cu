@@ -40,11 +40,12 @@
 // fills the A ring and epilogue warps drain the accumulators and write each
 // output subtile with a TMA store; one issuer warp issues every output's
 // MMAs in order, converged (the elected lane's MMAs predicated, not branched
-// around), with one commit per output.  The epilogue that sees an output
-// complete releases the A-ring slots no later output reads: with one issuer
-// the MMAs complete in order.  A box sweep whose accumulators and A ring fit
-// in half the TMEM runs two such CTAs per SM (two epilogue warps per
-// quarter and four accumulators otherwise, one CTA per SM).
+// around); after an output's MMAs it commits the release of the A-ring
+// slots no later output reads, then the output's accumulator.  A sweep
+// whose accumulators and A ring fit in half the TMEM runs two such CTAs per
+// SM, whose two workers per lane quarter share converting and draining where
+// there are two accumulators (two epilogue warps per quarter and four
+// accumulators otherwise, one CTA per SM).
 #include <cuda_bf16.h>
 #include <stdio.h>
 
@@ -73,11 +74,11 @@ __device__ unsigned long long g_role_trace[4][6];
 // starts waiting (output), 5 issuer starts issuing, 6 issuer done issuing, 7
 // quarter 0's epilogue has the accumulator (output), 8 ... is done, 9, 10,
 // 11: lane quarters 1, 2, 3 arrive (plane).
-constexpr int kTl = 256;
+constexpr int kTl = 128;
 __device__ unsigned long long g_timeline[12][kTl];
 // stamps go to shared memory (tl_smem, after the barriers) and are copied
 // out at the end, so that the trace adds no global stores to the roles
-#define MMS_TL(row, i) do { if (blockIdx.x == 0 && (i) < kTl) tl_smem[(row) * kTl + (i)] = clock64(); } while (0)
+#define MMS_TL(row, i) do { if (blockIdx.x == 0 && (i) < kTl) g_timeline[row][i] = clock64(); } while (0)
 extern "C" int mms_timeline_read(unsigned long long *host)
 {
     if (cudaDeviceSynchronize() != cudaSuccess) return 1;
@@ -134,15 +135,15 @@ struct Cfg {
     static constexpr int NEED = MODE == M_PLANAR ? 2 : W + 1;
     // Two CTAs per SM where a sweep fits in half the TMEM (its accumulators,
     // z-sum blocks and A ring in 256 columns): two independent pipelines keep
-    // the tensor pipe busier than one can.  A dual CTA has
-    // ten warps: producer, issuer, and per TMEM lane quarter one converter
-    // and one epilogue warp; a single CTA has sixteen: producer, issuer, two
-    // idle, and per quarter a converter and two epilogue warps (even and odd
-    // outputs).  Either way each accumulator slot's laps are waited on in
-    // order by one warp.
+    // the tensor pipe busier than one can.  A dual CTA has ten warps:
+    // producer, issuer, and two workers per TMEM lane quarter (a converter
+    // and an epilogue warp, or, mixed, two warps that both convert and
+    // drain); a single CTA has sixteen: producer, issuer, two idle, and per
+    // quarter a converter and two epilogue warps (even and odd outputs).
+    // Either way each accumulator slot's laps are waited on in order by one
+    // warp.
     static constexpr bool DUAL = N + ZC + NEED * APL <= 256;
     static constexpr int TMEM_COLS = DUAL ? 256 : 512;
-    static constexpr int NEPI = DUAL ? 1 : 2;            // epilogue warps per lane quarter
     static constexpr int W0 = DUAL ? 2 : 4;              // first worker warp
     static constexpr int ND = DUAL ? (2 * (N + ZC) + NEED * APL <= 256 ? 2 : 1)
                                    : 4 * (N + ZC) + NEED * APL <= 512 ? 4 : 2;
@@ -150,7 +151,21 @@ struct Cfg {
     static constexpr int Z0 = ND * N;
     static constexpr int A0 = Z0 + ND * ZC;
     static constexpr int PRF = (TMEM_COLS - A0) / APL < 16 ? (TMEM_COLS - A0) / APL : 16;
-    static constexpr int PR = PRF;                       // A ring planes
+    // planes an output reads (or, for the star, waits for) past its first
+    static constexpr int OFF_HI = MODE == M_PLANAR ? 0 : 2 * R;
+    // Mixed workers (MIX): in a dual CTA with two accumulators, worker wi of
+    // a lane quarter converts the planes and drains the outputs of parity
+    // wi, so neither sits idle while the other is busy (the star keeps a
+    // converter, whose z sums queue in one warp's registers).  Before
+    // draining an output a worker converts its planes up to LOOK past the
+    // last plane that output reads; the A ring bounds LOOK (a plane's slot
+    // is freed once the last output reading the plane PR before it
+    // completes), and mixing pays only if the planes of the output two
+    // ahead are converted before a drain starts (LOOK >= 2).
+    static constexpr int LOOK = (PRF & ~1) - OFF_HI - 1;
+    static constexpr bool MIX = DUAL && MODE != M_STAR && ND % 2 == 0 && LOOK >= 2;
+    static constexpr int NEPI = DUAL && !MIX ? 1 : 2;    // warps per lane quarter that drain outputs
+    static constexpr int PR = MIX ? PRF & ~1 : PRF;      // A ring planes (even when mixed)
     // FP32 staging box: TX + 2r columns (at least), 32 rows, one plane; the
     // row pitch in 16-byte units is odd, so the converters' row reads
     // (8 rows per quarter warp) hit 8 different bank groups
@@ -168,17 +183,12 @@ struct Cfg {
     static constexpr int NT = 32 * NWARPS;
     static constexpr size_t OFF_STG = (size_t)(BAND_BYTES + 1023) / 1024 * 1024;
     static constexpr size_t OFF_BAR = OFF_STG + (size_t)NST * STG_STRIDE;
-#ifdef MMS_ROLE_TRACE
-    static constexpr size_t TL_BYTES = 12 * 256 * 8;
-#else
-    static constexpr size_t TL_BYTES = 0;
-#endif
     // Output subtiles staged for TMA stores (one TXO x TY box per epilogue
     // warp and output, two buffers per warp); a subtile row is a 16-byte
     // multiple (TXO % 4 == 0).
     static constexpr bool TSTORE = (TXO * 4) % 16 == 0;
     static constexpr int OBUF = TSTORE ? (TXO * TY * 4 + 127) / 128 * 128 : 0;
-    static constexpr size_t OFF_OBUF = OFF_BAR + 1024 + TL_BYTES;
+    static constexpr size_t OFF_OBUF = OFF_BAR + 1024;
     static constexpr size_t SMEM_NEED = 1024 + OFF_OBUF + 8 * NEPI * (size_t)OBUF;
     // a single CTA takes at least 120 KB, so that two CTAs holding all 512
     // TMEM columns each never share an SM; two dual CTAs fit one SM
@@ -192,6 +202,7 @@ struct Cfg {
     // TMEM operand and accumulator columns start on 16-column boundaries
     static_assert(Z0 % 16 == 0 && A0 % 16 == 0 && APL % 16 == 0 && N % 16 == 0, "TMEM column alignment");
     static_assert(ND % NEPI == 0, "every epilogue warp owns whole accumulator slots");
+    static_assert(!MIX || (PR % 2 == 0 && NST % 2 == 0), "a mixed worker owns the slots of its parity");
 };
 
 __device__ __forceinline__ uint32_t bf16_bits(float v)
@@ -273,10 +284,6 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
     uint64_t *full_d = empty_a + C::PR, *empty_d = full_d + C::ND;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty_d + C::ND);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-#ifdef MMS_ROLE_TRACE
-    unsigned long long *tl_smem = reinterpret_cast<unsigned long long *>(smem + C::OFF_BAR + 1024);
-    for (int i = threadIdx.x; i < 12 * kTl; i += blockDim.x) tl_smem[i] = 0;
-#endif
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int my_tiles = a.tiles > (int)blockIdx.x ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
         }
         for (int b = 0; b < C::PR; ++b) {
             ptx::mbar_init(&full_a[b], 4);
-            ptx::mbar_init(&empty_a[b], 1);  // released by the epilogue
+            ptx::mbar_init(&empty_a[b], 1);  // released by the issuer's commit
         }
         for (int b = 0; b < C::ND; ++b) {
             ptx::mbar_init(&full_d[b], 1);
@@ -398,16 +405,15 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
         // MMAs leaves the shallow tensor-pipe queue to drain, so the warp
         // waits on each staged plane once, in order (which also keeps it at
         // most one phase behind each A-ring slot), and commits once per
-        // output.  The A-ring slots are released by the epilogue, which sees
-        // an output's completion: with one issuer the MMAs complete in order.
+        // output, after the release of the A-ring slots no later output reads.
         const uint32_t on = ptx::elect_one() ? 1u : 0u;
         // planes output z of a tile reads (or, for the star, waits for):
         // up to kb + z + OFF_HI
-        constexpr int OFF_HI = MODE == M_PLANAR ? 0 : 2 * R;
         const uint64_t bdesc0 = tc::smem_desc(ptx::smem_u32(band), 128, C::SBO);
         int wnext = 0;      // next staged plane to wait on
         int j = 0, kb = 0;  // global output index, global index of the tile's staged plane 0
         int last = -1;      // last output issued
+        int rel = 0;        // planes whose A-slot release has been committed (0 .. rel-1)
         bool ok = true;
         [[maybe_unused]] unsigned long long tp = 0, ta = 0, ti = 0, t00 = MMS_CLOCK();
         for (int tl = 0; tl < my_tiles && ok; ++tl) {
@@ -416,7 +422,7 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
             for (int z = 0; z < nzt; ++z, ++j) {
                 [[maybe_unused]] const unsigned long long t0 = MMS_CLOCK();
                 if (lane == 0) MMS_TL(4, j);
-                for (; ok && wnext <= kb + z + OFF_HI; ++wnext)
+                for (; ok && wnext <= kb + z + C::OFF_HI; ++wnext)
                     ok = __all_sync(0xffffffffu, wait(&full_a[wnext % C::PR], (uint32_t)(wnext / C::PR) & 1u));
                 [[maybe_unused]] const unsigned long long t1 = MMS_CLOCK();
                 ok = ok && __all_sync(0xffffffffu, wait(&empty_d[j % C::ND], ((uint32_t)(j / C::ND) & 1u) ^ 1u));
@@ -455,6 +461,24 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
                         }
                     }
                 }
+                // The A slots of the planes no later output reads are free
+                // once these products complete, released here in plane order:
+                // the box's plane z is read last by output z, the star's
+                // centre plane z+r by output z (its z-halo planes by no
+                // product: they go with the tile's first and last outputs),
+                // the planar plane z by output z.
+                {
+                    constexpr int OFF = MODE == M_STAR ? R : 0;
+                    if constexpr (MODE == M_STAR)
+                        if (z == 0)
+                            for (int p = 0; p < R; ++p) tc::mma_commit_if(on, &empty_a[(kb + p) % C::PR]);
+                    tc::mma_commit_if(on, &empty_a[(kb + z + OFF) % C::PR]);
+                    if constexpr (MODE != M_PLANAR)
+                        if (z == nzt - 1)
+                            for (int p = nzt + OFF; p < nzt + 2 * R; ++p)
+                                tc::mma_commit_if(on, &empty_a[(kb + p) % C::PR]);
+                    rel = z == nzt - 1 ? kb + nzt + 2 * C::RZ : kb + z + OFF + 1;
+                }
                 tc::mma_commit_if(on, &full_d[j % C::ND]);  // accumulator ready for the epilogue
                 if (lane == 0) MMS_TL(6, j);
                 ti += MMS_CLOCK() - t2;
@@ -470,14 +494,19 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
         }
         // every MMA issued completes before TMEM is freed
         if (last >= 0) ptx::mbar_wait_bounded(&full_d[last % C::ND], (uint32_t)(last / C::ND) & 1u, err);
+        // and every A-slot release committed has arrived before the CTA
+        // exits: slot s has had one release per plane s, s + PR, ... < rel
+        for (int sl = 0; sl < C::PR; ++sl)
+            if (rel > sl) ptx::mbar_wait_bounded(&empty_a[sl], (uint32_t)((rel - 1 - sl) / C::PR) & 1u, err);
     } else if (warp >= C::W0) {
         // ---------------------------------------------------------- workers
         // warp 4 + 4 wi + q: worker wi of TMEM lane quarter q; lane t holds
         // row t of subtile q
         const int q = warp & 3, wi = (warp - C::W0) >> 2, t = lane;
         const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16);
+        const int ew = C::MIX ? wi : wi - 1;  // this warp's index among its quarter's draining warps
         [[maybe_unused]] float *obuf = reinterpret_cast<float *>(smem + C::OFF_OBUF) +
-                                       (size_t)(wi > 0 ? ((wi - 1) * 4 + q) * 2 : 0) * (C::OBUF / 4);
+                                       (size_t)(ew >= 0 ? (ew * 4 + q) * 2 : 0) * (C::OBUF / 4);
         [[maybe_unused]] int nout = 0;  // outputs this epilogue warp has stored
         bool ok = true;
         [[maybe_unused]] unsigned long long ts = 0, ta = 0, td = 0, tc0 = 0, tf = 0, tep = 0, t00 = MMS_CLOCK();
@@ -595,9 +624,9 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
             return true;
         };
 
-        // Epilogue of output z of a tile (global index j; the tile's staged
-        // plane 0 has global index kb, its column origin is x0, y0, z0).
-        auto epilogue = [&](int j, int z, int kb, int nzt, int x0, int y0, int z0) -> bool {
+        // Epilogue of output z of a tile (global index j; the tile's column
+        // origin is x0, y0, z0).
+        auto epilogue = [&](int j, int z, int x0, int y0, int z0) -> bool {
             const int ds = j % C::ND;
             [[maybe_unused]] const unsigned long long t0 = MMS_CLOCK();
             if (!__all_sync(0xffffffffu, wait(&full_d[ds], (uint32_t)(j / C::ND) & 1u))) return false;
@@ -605,20 +634,6 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
             tf += t1 - t0;
             if (lane == 0 && q == 0) MMS_TL(7, j);
             tc::fence_after_sync();
-            // Output j's MMAs are done, and with them (one issuer, in order)
-            // every earlier MMA: the A-ring slots of the planes no later
-            // output reads are free again.  The box's plane z is read last
-            // by output z, the star's centre plane z+r by output z (its
-            // z-halo planes by no MMA: they go with the tile's first and last
-            // outputs), the planar plane z by output z.
-            if (q == 0 && lane == 0) {
-                constexpr int OFF = MODE == M_STAR ? R : 0;
-                ptx::mbar_arrive(&empty_a[(kb + z + OFF) % C::PR]);
-                if (MODE == M_STAR && z == 0)
-                    for (int p = 0; p < R; ++p) ptx::mbar_arrive(&empty_a[(kb + p) % C::PR]);
-                if (MODE != M_PLANAR && z == nzt - 1)
-                    for (int p = nzt + OFF; p < nzt + 2 * R; ++p) ptx::mbar_arrive(&empty_a[(kb + p) % C::PR]);
-            }
             uint32_t d[C::N];
             [[maybe_unused]] uint32_t zz[C::ZC > 0 ? C::ZC : 1];
             {
@@ -711,7 +726,65 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
             return true;
         };
 
-        if (wi == 0) {
+        if constexpr (C::MIX) {
+            // Worker wi converts the planes and drains the outputs of parity
+            // wi (global indices; a tile's plane and output indices share
+            // their parity, 2r being even), interleaved: before draining an
+            // output it converts its planes up to LOOK past the last plane
+            // that output reads.  Rank the conversion of plane k at k - LOOK
+            // and the drain of output j at (the last plane j reads) + 1/2:
+            // every worker's sequence is in rank order, and every wait is on
+            // an item of lower rank -- a drain on its output's planes and on
+            // the drain of its accumulator slot's previous output, a
+            // conversion on the planes before it in the staging ring and on
+            // the products that free its A slot, which read no plane past
+            // k - PR + OFF_HI, with PR > OFF_HI + LOOK -- so no wait closes a
+            // cycle.
+            float zq[1][1];
+            // plane cursor: global plane kc of tile tp (first plane kbp,
+            // first output jbp, nzp outputs)
+            int kc = wi, tp = 0, kbp = 0, jbp = 0, nzp = 0, xd, yd, zd;
+            bool planes_left = my_tiles > 0;
+            if (planes_left) tile_of(0, xd, yd, zd, nzp);
+            auto plane_fix = [&]() {
+                while (planes_left && kc - kbp >= nzp + 2 * C::RZ) {
+                    kbp += nzp + 2 * C::RZ;
+                    jbp += nzp;
+                    if (++tp >= my_tiles) planes_left = false;
+                    else tile_of(tp, xd, yd, zd, nzp);
+                }
+            };
+            plane_fix();
+            // output cursor: global output jd of tile to (first plane kbo,
+            // first output jbo, its origin and nzo outputs)
+            int jd = wi, to = 0, kbo = 0, jbo = 0, nzo = 0, x0o = 0, y0o = 0, z0o = 0;
+            bool outs_left = my_tiles > 0;
+            if (outs_left) tile_of(0, x0o, y0o, z0o, nzo);
+            auto out_fix = [&]() {
+                while (outs_left && jd - jbo >= nzo) {
+                    kbo += nzo + 2 * C::RZ;
+                    jbo += nzo;
+                    if (++to >= my_tiles) outs_left = false;
+                    else tile_of(to, x0o, y0o, z0o, nzo);
+                }
+            };
+            out_fix();
+            while (ok && (planes_left || outs_left)) {
+                // the last plane the next output of this parity reads
+                const int need = outs_left ? kbo + (jd - jbo) + C::OFF_HI : 0;
+                if (planes_left && (!outs_left || kc <= need + C::LOOK)) {
+                    ok = convert(kc, kc - kbp, jbp, nzp, zq);
+                    kc += 2;
+                    plane_fix();
+                } else {
+                    ok = epilogue(jd, jd - jbo, x0o, y0o, z0o);
+                    jd += 2;
+                    out_fix();
+                }
+            }
+            if constexpr (C::TSTORE)
+                if (lane == 0) bulk_wait_all();
+        } else if (wi == 0) {
             // every staged plane in order (the star's z sums in registers)
             float zq[MODE == M_STAR ? W : 1][MODE == M_STAR ? C::TXO : 1];
             int k = 0, jb = 0;
@@ -729,13 +802,12 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
             }
         } else {
             // the epilogues of the even (worker 1) or odd (worker 2) outputs
-            int j = 0, kb = 0;
+            int j = 0;
             for (int tl = 0; tl < my_tiles && ok; ++tl) {
                 int x0, y0, z0, nzt;
                 tile_of(tl, x0, y0, z0, nzt);
                 for (int z = 0; z < nzt && ok; ++z, ++j)
-                    if (j % C::NEPI == wi - 1) ok = epilogue(j, z, kb, nzt, x0, y0, z0);
-                kb += nzt + 2 * C::RZ;
+                    if (j % C::NEPI == wi - 1) ok = epilogue(j, z, x0, y0, z0);
             }
             // this warp's output stores are complete (and their sources
             // read) before the CTA exits
@@ -764,10 +836,6 @@ __global__ void __launch_bounds__(Cfg<R, PREC, MODE>::NT, Cfg<R, PREC, MODE>::DU
         tc::fence_after_sync();
         tc::tmem_dealloc(tbase, C::TMEM_COLS);
     }
-#ifdef MMS_ROLE_TRACE
-    if (blockIdx.x == 0)
-        for (int i = threadIdx.x; i < 12 * kTl; i += blockDim.x) (&g_timeline[0][0])[i] = tl_smem[i];
-#endif
 }
 
 int g_num_sms = 0;
