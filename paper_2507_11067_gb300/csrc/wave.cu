@@ -107,14 +107,33 @@ struct FwdGeom {
     static constexpr int OFF_C = OFF_P + ((MT + 31) & ~31);
     static constexpr int OFF_L = OFF_C + ((MT + 31) & ~31);  // adjoint: L a^n
     static constexpr int STAGE = OFF_L + (MODE == K_ADJ_SCALED ? ((MT + 31) & ~31) : 0);
-    static constexpr size_t SMEM = 128 + (size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16;
+    // adjoint: two FP64 buffers of an output plane's gradient terms (TY x
+    // TX), 128-byte aligned after the ring's barriers and abort flag
+    static constexpr size_t OFF_GB = ((size_t)S * STAGE * 4 + S * sizeof(uint64_t) + 16 + 127) / 128 * 128;
+    static constexpr size_t GB_BYTES = MODE == K_ADJ_SCALED ? 2 * (size_t)TY * TX * sizeof(double) : 0;
+    static constexpr size_t SMEM = 128 + OFF_GB + GB_BYTES;
 };
+
+// Bulk reduction of an FP64 row from shared memory into global memory (the
+// L2 adds it), in this thread's bulk groups; addresses 16-byte aligned, size
+// a multiple of 16 bytes.
+__device__ __forceinline__ void bulk_add_f64(double *dst, const double *src, uint32_t bytes)
+{
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(dst),
+                 "r"(ptx::smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most the most recent group may still be reading its source
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Operands of the scaled adjoint (unused by the forward forms).
 struct AdjArgs {
     const float *resid;  // nshots*ny*nx on the receiver plane, or null
     double *grad;        // FP64 gradient, or null (no gradient term, tlap unused)
     int gvec;            // rows of four doubles 32-byte aligned
+    int gbulk;           // one shared slice, nx even, grad 16-byte aligned: rows added by bulk reductions
 };
 
 template <int R, int TX, int TY, int PY, int S, int MODE>
@@ -148,6 +167,11 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
     const int gx = x0 + 4 * tx;
     const int sx = ADJ ? -1 : geo.src[sh][0], sy = ADJ ? -1 : geo.src[sh][1], sz = ADJ ? -1 : geo.src[sh][2];
     const bool has_grad = ADJ && adj.grad != nullptr;
+    // The shots' terms go to one shared gradient: each output plane's terms
+    // are gathered in shared memory and each row is added by one bulk
+    // reduction (the L2 does the adds), instead of one FP64 atomic per point.
+    [[maybe_unused]] const bool gbulk = has_grad && geo.gss == 0 && adj.gbulk;
+    [[maybe_unused]] double *gbuf = reinterpret_cast<double *>(smem + F::OFF_GB);
     const int ntiles = has_grad ? 4 : 3;
 
     auto issue = [&](int j, int s) {
@@ -218,11 +242,23 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
             abort_flag = 1;
         }
         __syncthreads();
-        if (abort_flag) return;
+        if (abort_flag) {
+            if constexpr (ADJ) bulk_wait_all();  // no reduction still reads this CTA's buffers
+            return;
+        }
         if (tid == 0 && j + S < P) issue(j + S, s);
         if (zo >= 0) {
             const int z = zb + zo;
             const float gzv = sponge(z, geo.nz, geo.sponge_w, geo.sponge_a);
+            // this output plane's gradient buffer; the reductions of the plane
+            // before last, which read it, are done first
+            [[maybe_unused]] double *gb = gbuf + (size_t)(zo & 1) * (TY * TX);
+            if constexpr (ADJ) {
+                if (gbulk) {
+                    if (tx == 0) bulk_wait_read_1();
+                    __syncwarp();
+                }
+            }
 #pragma unroll
             for (int i = 0; i < PY; ++i) {
                 const int y = y0 + ry0 + i;
@@ -275,7 +311,10 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                 if constexpr (ADJ) {
                     if (has_grad) {
                         const int64_t gi = ((int64_t)z * geo.ny + y) * geo.nx + gx;
-                        if (geo.gss == 0) {
+                        if (gbulk) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) gb[(ry0 + i) * TX + 4 * tx + k] = gd[k];
+                        } else if (geo.gss == 0) {
                             // one slice for all shots: other CTAs add to the same points
 #pragma unroll
                             for (int k = 0; k < 4; ++k)
@@ -298,6 +337,27 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
                     }
                 }
             }
+            if constexpr (ADJ) {
+                if (gbulk) {
+                    // the terms reach the async proxy, then each row's first
+                    // thread adds the row's valid points (an even count: nx
+                    // and x0 are even) with one bulk reduction
+                    ptx::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (tx == 0) {
+#pragma unroll
+                        for (int i = 0; i < PY; ++i) {
+                            const int y = y0 + ry0 + i;
+                            if (y < geo.ny && x0 < geo.nx) {
+                                const int n = min(TX, geo.nx - x0);
+                                bulk_add_f64(adj.grad + ((int64_t)z * geo.ny + y) * geo.nx + x0, gb + (ry0 + i) * TX,
+                                             (uint32_t)n * 8u);
+                            }
+                        }
+                        bulk_commit();
+                    }
+                }
+            }
         }
 #pragma unroll
         for (int kk = 0; kk < W - 1; ++kk)
@@ -310,6 +370,9 @@ __global__ void __launch_bounds__(Geom<R, TX, TY, PY, S>::NT)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[W - 1][i][k] = 0.f;
     }
+    // this thread's reductions are complete before the CTA exits
+    if constexpr (ADJ)
+        if (gbulk && tx == 0) bulk_wait_all();
 }
 
 // Adjoint step.  Ring stage s holds the planes lam^{n+1}, m, a^n (with halo)
@@ -610,7 +673,10 @@ cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
     auto kern = mode == K_ADJ_SCALED ? wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_ADJ_SCALED>
                 : mode == K_FWD_LAP  ? wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_FWD_LAP>
                                      : wave_fwd_kernel<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_FWD>;
-    const size_t smem = mode == K_ADJ_SCALED ? FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_ADJ_SCALED>::SMEM
+    using FA = FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_ADJ_SCALED>;
+    // the adjoint's gradient buffers only where its bulk reductions run
+    const bool gbulk = adj && adj->grad && g.gss == 0 && adj->gbulk;
+    const size_t smem = mode == K_ADJ_SCALED ? FA::SMEM - (gbulk ? 0 : FA::GB_BYTES)
                         : mode == K_FWD_LAP  ? FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_FWD_LAP>::SMEM
                                              : FwdGeom<R, kFwdTX, kFwdTY, kFwdPY, kFwdS, K_FWD>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -620,7 +686,7 @@ cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
     const dim3 grid((g.nx + kFwdTX - 1) / kFwdTX, (g.ny + kFwdTY - 1) / kFwdTY, nzc * g.nshots);
     const int vec = (R % 4 == 0) && g.py % 4 == 0 && g.pz % 4 == 0 && g.ss % 4 == 0 &&
                     reinterpret_cast<uintptr_t>(p_next) % 16 == 0 && reinterpret_cast<uintptr_t>(lapout) % 16 == 0;
-    const AdjArgs aa = adj ? *adj : AdjArgs{nullptr, nullptr, 0};
+    const AdjArgs aa = adj ? *adj : AdjArgs{nullptr, nullptr, 0, 0};
     kern<<<grid, G::NT, smem, st>>>(mcur, mm, mprev, mctr, mlap, cf, g, p_next, amp, rec, lapout, aa, tz, nzc,
                                     vec, device_error_word());
     return cudaGetLastError();
@@ -685,7 +751,8 @@ cudaError_t launch_wave_adj_scaled(const WaveGeo &g, const float *coeffs, const 
     StarCoef cf{};
     for (int i = 0; i < 3 * (2 * g.r + 1); ++i) cf.c[i] = coeffs[i];
     const AdjArgs adj{resid, lap_a ? grad : nullptr,
-                      g.nx % 4 == 0 && g.gss % 4 == 0 && reinterpret_cast<uintptr_t>(grad) % 32 == 0};
+                      g.nx % 4 == 0 && g.gss % 4 == 0 && reinterpret_cast<uintptr_t>(grad) % 32 == 0,
+                      g.nx % 2 == 0 && reinterpret_cast<uintptr_t>(grad) % 16 == 0};
     const float *lap = lap_a && grad ? lap_a : nullptr;
     switch (g.r) {
         case 1: return fwd_r<1>(g, cf, m, mu_cur, mu_prev, mu_prev, nullptr, nullptr, nullptr, st, lap, &adj);

@@ -656,6 +656,17 @@ def test_scaled_adjoint_step_against_oracle(nshots, slices):
     assert max(errs) <= TOL and eg <= TOL
 
 
+@pytest.mark.parametrize("nshots", [1, 3])
+def test_scaled_adjoint_step_bulk_rows(nshots):
+    # an even nx: the shared slice's rows are added by bulk reductions (the
+    # odd nx above takes one atomic per point); nx = 70 leaves a last tile
+    # of 6 points, and three shots reduce into the same rows
+    s = Setup(nx=70, ny=38, nz=41, nshots=nshots)
+    errs, eg = _scaled_step_check(s, 75)
+    print(f"scaled adjoint step, nx 70, {nshots} shots: mu^n max-rel {max(errs):.2e}, gradient term {eg:.2e}")
+    assert max(errs) <= TOL and eg <= TOL
+
+
 def test_scaled_adjoint_step_full_size():
     # the gradient workload's size (2 shots x 256^3, 20-cell sponge), every point
     s = Setup(nx=256, ny=256, nz=256, nshots=2, nsteps=4, sponge=20, seed=3)
