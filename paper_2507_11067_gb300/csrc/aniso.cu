@@ -377,20 +377,20 @@ __device__ __forceinline__ void tti_arrive(const float *pl, const TtiCoef &cf, i
 #pragma unroll
         for (int k = 0; k < 4; ++k) dy[k] = fmaf(cf.w1[R + d], a[k], dy[k]);
     }
-    // D_y f into the ring row at the plane's column indices; the edge threads
-    // add the x-halo columns (R on each side) that f_xy's window reaches
+    // D_y f into the ring row at the plane's column indices; the x-halo
+    // columns that f_xy's window reaches (R on each side) take one thread
+    // each, the row's first 2R, so that a warp runs the halo sums once
+    // instead of R times on two threads
 #pragma unroll
     for (int k = 0; k < 4; ++k) dyrow[4 * tx + R + k] = dy[k];
-    if (tx == 0 || tx == NTX - 1) {
-        const int c0 = tx == 0 ? 0 : 4 * NTX + R;
+    static_assert(NTX >= 2 * R, "a thread per x-halo column");
+    if (tx < 2 * R) {
+        const int c = tx < R ? tx : 4 * NTX + tx;  // 0 .. R-1, then 4 NTX + R .. 4 NTX + 2R - 1
+        float v = 0.f;
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-            float v = 0.f;
-#pragma unroll
-            for (int d = -R; d <= R; ++d)
-                if (d != 0) v = fmaf(cf.w1[R + d], pl[(ty + R + d) * BX + c0 + c], v);
-            dyrow[c0 + c] = v;
-        }
+        for (int d = -R; d <= R; ++d)
+            if (d != 0) v = fmaf(cf.w1[R + d], pl[(ty + R + d) * BX + c], v);
+        dyrow[c] = v;
     }
 #pragma unroll
     for (int kk = 0; kk < W; ++kk)

@@ -191,12 +191,24 @@ def test_star_1024_sampled_all_radii(tuned):
         mms.check_device()
         got = out[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()
         assert rel(got, ref) <= TOL, r
-        # the per-axis banded tensor-core passes with the 3xTF32 split, same grid
-        out = mms.apply("star", r, c, inp, out, path="3xtf32")
-        torch.cuda.synchronize()
-        mms.check_device()
-        got = out[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()
-        e = rel(got, ref)
-        print(f"star r={r} 1024^3 3xTF32 two-pass: {e:.2e}")
-        assert e <= TOL, ("3xtf32", r)
-        del out, inp
+        # the tensor-core star in one pass (3xTF32 and BF16x3, first variant)
+        # and in the paper's two passes (3xTF32, first two-pass variant), same
+        # grid: sampled against the oracle, and every point against AUTO's
+        # output.  BF16x3 carries about 2^-17 of each term's magnitude
+        # (8 + 8 mantissa bits per operand), and an FD Laplacian of a smooth
+        # field cancels its terms, so its bound here is the terms' error over
+        # the output's magnitude, not TOL.
+        tc = torch.empty_like(out)
+        nv = mms.num_variants("star", r, "3xtf32")
+        for path, v, bound in (("3xtf32", 0, TOL), ("3xtf32", nv // 2, TOL), ("bf16x3", 0, 5e-5)):
+            mms.apply("star", r, c, inp, tc, path=path, variant=v)
+            torch.cuda.synchronize()
+            mms.check_device()
+            got = tc[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()
+            e = rel(got, ref)
+            full = ((tc - out).abs().max() / out.abs().max()).item()
+            form = "two passes" if v >= nv // 2 else "one pass"
+            print(f"star r={r} 1024^3 {path} ({form}): sampled {e:.2e}, every point against AUTO {full:.2e}")
+            assert e <= bound, (path, v, r, e)
+            assert full <= 2 * bound, (path, v, r, full)
+        del out, inp, tc
