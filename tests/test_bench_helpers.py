@@ -28,8 +28,8 @@ def test_committed_traffic_matches_the_committed_sources():
         assert os.path.exists(os.path.join(bench.ROOT, rec["capture"])), key
         for f in rec["sources"]:
             assert os.path.exists(os.path.join(bench.ROOT, "paper_2507_11067_gb300", "csrc", f)), (key, f)
-    assert bench.captured_traffic("bf16x3 box r=2 v1", 512 ** 3) == pytest.approx(
-        t["bf16x3 box r=2 v1"]["dram_bytes_per_point"] * 512 ** 3)
+    assert bench.captured_traffic("bf16x3 box r=2 v0", 512 ** 3) == pytest.approx(
+        t["bf16x3 box r=2 v0"]["dram_bytes_per_point"] * 512 ** 3)
     assert bench.captured_traffic("no such kernel", 10) is None
 
 
