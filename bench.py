@@ -842,15 +842,19 @@ def run_wave(args):
                "h2d_bytes_per_step": v0_host.numel() * 4 + amps_host.numel() * 4 + obs_host.numel() * 4,
                "d2h_bytes_per_step": g_host.numel() * g_host.element_size()}
         # per shot-point and step: forward 16 B, recompute 20 B (out of place,
-        # no copies; it also writes L a^n), adjoint 20 B (lam^{n+1}, lam^{n+2},
-        # m, L a^n read, lam^n written), and the FP64 gradient's
-        # read-modify-write, 16 B per point shared by the shots (their atomic
-        # adds meet in L2)
+        # no copies; it also writes L a^n), adjoint 20 B (its state at n+1
+        # and n+2, m, L a^n read, the state at n written), and the FP64
+        # gradient's read-modify-write, 16 B per point shared by the shots
+        # (their reductions meet in L2)
         bpp = 56.0 + 16.0 / nshots
         bytes_alg = bpp * pts * nsteps * steps
+        ri = prop.r
+        mu = args.adjoint == "mu" or (args.adjoint == "auto" and bool((prop.m[ri:-ri, ri:-ri, ri:-ri] > 0).all()))
         roof = {"bound": "hbm", "achieved": bytes_alg / elapsed / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": bytes_alg / elapsed / 1e9 / hbm_peak, "traffic": None,
-                "kernel": "forward + recompute + wave_adj_kernel",
+                "kernel": ("wave_fwd_kernel: forward, recompute writing L a^n, and the adjoint in mu = m G lam "
+                           "(one FP64 bulk reduction per output row)") if mu else
+                          "wave_fwd_kernel (forward, recompute writing L a^n) + wave_adj_kernel (FP64 atomics)",
                 "bytes_per_point_step": bpp}
         unit = "GPoint-steps/s"
     cpu = None
