@@ -903,10 +903,13 @@ cudaError_t launch_r(const Sweep &s, const CUtensorMap &map, int nzt, const Laun
     return cudaGetLastError();
 }
 
-// Variants: output planes per z chunk of a tile; the star's variants
-// kNumTile.. run the paper's two-pass form (x/y pass into a temporary grid,
-// then the z pass).
-constexpr int kNzt[] = {64, 32, 128, 16};
+// Variants: output planes per z chunk of a tile (52 and 40 split 512
+// planes into 10 and 13 chunks, whose tiles spread more evenly over the
+// persistent CTAs than 8 or 16 chunks; the autotuner weighs that against
+// the halo planes each chunk restages); the star's variants kNumTile.. run
+// the paper's two-pass form (x/y pass into a temporary grid, then the z
+// pass).
+constexpr int kNzt[] = {64, 32, 128, 16, 52, 40};
 constexpr int kNumTile = sizeof(kNzt) / sizeof(int);
 
 template <int PREC, int MODE>
