@@ -28,8 +28,8 @@ def rel(g, o):
     return float(np.abs(np.asarray(g, np.float64) - o).max() / max(np.abs(o).max(), 1e-300))
 
 
-# ragged tiles in x and y; z chunks of 64, 32, 128 or 16 planes (the
-# variants) leave one-plane and ragged last chunks (nz = 1, 17, 37)
+# ragged tiles in x and y; z chunks of 64, 32, 128, 16, 52 or 40 planes
+# (the variants) leave one-plane and ragged last chunks (nz = 1, 17, 37)
 SIZES = [(53, 41, 19), (24, 28, 8), (7, 5, 3), (100, 70, 37), (40, 35, 1), (33, 29, 17)]
 
 
@@ -81,6 +81,28 @@ def test_box_tc_512_sampled(path):
     torch.cuda.synchronize()
     diff = (out - cc).abs().max().item() / cc.abs().max().item()
     assert diff <= 2 * TOL[path]
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_box_tc_many_tiles_per_cta(r):
+    # More tiles than resident CTAs, so that each persistent CTA runs
+    # several tiles in a row and its two mixed workers (box r = 1, 2 on two
+    # CTAs per SM) carry their plane and output cursors across tile ends;
+    # the last z chunk has an odd number of output planes (603 = 37 x 16 +
+    # 11 = 15 x 40 + 3); 400 to 1140 tiles for 304 CTAs.  Every point
+    # against the oracle.
+    n = (200, 150, 603)
+    grid = workloads.uniform_grid(*n, r, workload=2, salt=40 + r)
+    c = workloads.normal_coeffs("box", r, workload=2, salt=40 + r)
+    ref = oracle.stencil("box", r, c, grid)
+    inp = mms.to_padded_device(grid, r)
+    for v in (3, 5):   # 16- and 40-plane z chunks
+        out = mms.apply("box", r, c, inp, path="bf16x3", variant=v)
+        torch.cuda.synchronize()
+        mms.check_device()
+        err = rel(out.cpu().numpy(), ref)
+        print(f"box r={r} bf16x3 {n} variant {v}: max-rel error {err:.3e}")
+        assert err <= TOL["bf16x3"], (v, err)
 
 
 def test_every_tensor_core_combination_is_built():
