@@ -731,12 +731,16 @@ cudaError_t fwd_r(const WaveGeo &g, const StarCoef &cf, const float *m, const fl
     const int cols = (g.nx + kFwdTX - 1) / kFwdTX * ((g.ny + kFwdTY - 1) / kFwdTY) * g.nshots;
     int tz = kFwdTZ;
     if (mode == K_ADJ_SCALED) {
-        static int slots[2] = {0, 0};  // resident CTAs on the device, without / with the gradient buffers
-        int &sl = slots[gbulk ? 1 : 0];
+        // resident CTAs of this launch on the current device (cached per
+        // device, without / with the gradient buffers)
+        constexpr int kDevs = 16;
+        static int slots[kDevs][2] = {};
+        int dev = 0, sl_local = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+        int &sl = dev >= 0 && dev < kDevs ? slots[dev][gbulk ? 1 : 0] : sl_local;
         if (sl == 0) {
-            int dev = 0, sms = 0, per_sm = 0;
-            if (cudaGetDevice(&dev) == cudaSuccess &&
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            int sms = 0, per_sm = 0;
+            if (dev >= 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, smem) == cudaSuccess)
                 sl = sms * per_sm > 0 ? sms * per_sm : -1;
             else
