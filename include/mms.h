@@ -507,6 +507,24 @@ mms_status mms_check_device(void *stream);
  */
 mms_status mms_selftest_timeout(uint32_t limit_us, void *stream);
 
+/*
+ * The pipeline constants of the tensor-core sweep of (shape, radius, path)
+ * in this build, for checking its schedule on the host (no device is
+ * touched; the producer stages planes into a ring, one issuer runs every
+ * output's products in order, workers convert planes and drain outputs).
+ * cfg receives up to ncfg of, in order: mixed (1 if the two workers of a
+ * lane quarter each convert the planes and drain the outputs of one
+ * parity), look (planes a mixed worker converts past the last plane its
+ * next output reads), a_ring (planes the tensor-memory operand ring holds),
+ * staging (planes the shared-memory staging ring holds), accumulators,
+ * reach (planes an output reads, or waits for, past its first), z_halo
+ * (halo planes a tile stages on each side in z), two_ctas (1 if two CTAs
+ * share an SM), drainers (warps per lane quarter that drain outputs).
+ * Returns the number of constants (9), or -1 for a shape, radius or path
+ * without a tensor-core sweep, or a null cfg with ncfg > 0.
+ */
+int32_t mms_tc_pipeline_config(int32_t shape, int32_t radius, int32_t path, int32_t *cfg, int32_t ncfg);
+
 /* Library version string. */
 const char *mms_version(void);
 

@@ -47,7 +47,7 @@ EXPORTS = ["mms_stencil_apply", "mms_stencil_apply_ex", "mms_auto_path", "mms_nu
            "mms_check_device", "mms_version", "mms_stencil_apply_noalloc", "mms_wave_step_to",
            "mms_sum_f64", "mms_selftest_timeout", "mms_stencil_apply_host", "mms_vti_model", "mms_vti_step",
            "mms_aniso_num_variants", "mms_aniso_set_variant", "mms_tti_model", "mms_tti_step", "mms_stencil_apply_f64", "mms_wave_step_lap",
-           "mms_wave_adjoint_lap", "mms_wave_adjoint_scaled", "mms_grad_divide_m"]
+           "mms_wave_adjoint_lap", "mms_wave_adjoint_scaled", "mms_grad_divide_m", "mms_tc_pipeline_config"]
 
 
 MAX_SHOTS = 64  # largest mms_wave_desc.nshots the library takes
@@ -164,6 +164,7 @@ def load():
             "mms_stencil_apply_host": [ctypes.POINTER(StencilDesc), P, P, P],
             "mms_stencil_apply_f64": [ctypes.POINTER(StencilDesc), P, P, P, P],
             "mms_num_variants": [i32, i32, i32],
+            "mms_tc_pipeline_config": [i32, i32, i32, P, i32],
             "mms_auto_path": [i32, i32, i32],
             "mms_default_variant": [i32, i32, i32, i64, i64, i64],
             "mms_set_variant": [i32, i32, i32, i32],
@@ -385,6 +386,22 @@ def apply_dense(shape, r, coeffs, inp, out, stream=None):
 
 def num_variants(shape, r, path) -> int:
     return load().mms_num_variants(SHAPES[shape], r, PATHS[path])
+
+
+TC_PIPELINE_KEYS = ("mixed", "look", "a_ring", "staging", "accumulators", "reach", "z_halo", "two_ctas",
+                    "drainers")
+
+
+def tc_pipeline_config(shape, r, path):
+    """The pipeline constants of the tensor-core sweep of (shape, r, path) in
+    this build (mms_tc_pipeline_config), as a dict; None where there is no
+    tensor-core sweep.  Needs no GPU."""
+    buf = (ctypes.c_int32 * len(TC_PIPELINE_KEYS))()
+    n = load().mms_tc_pipeline_config(SHAPES[shape], r, PATHS[path], ctypes.cast(buf, ctypes.c_void_p),
+                                      len(TC_PIPELINE_KEYS))
+    if n < 0:
+        return None
+    return dict(zip(TC_PIPELINE_KEYS, list(buf)[:min(n, len(TC_PIPELINE_KEYS))]))
 
 
 def auto_path(shape, r, tma_aligned=True) -> str:

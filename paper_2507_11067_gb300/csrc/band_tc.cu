@@ -1036,6 +1036,40 @@ void planar_weights(const Sweep &s, bool with_z_centre, float *c2)
     if (with_z_centre) c2[r * w + r] += s.coeffs[2 * w + r];
 }
 
+// The pipeline constants of one configuration, for mms_tc_pipeline_config.
+template <int R, int PREC, int MODE>
+int pipeline_config(int32_t *cfg, int n)
+{
+    using C = Cfg<R, PREC, MODE>;
+    const int32_t v[] = {C::MIX ? 1 : 0, C::LOOK, C::PR, C::NST, C::ND, C::OFF_HI, C::RZ, C::DUAL ? 1 : 0, C::NEPI};
+    constexpr int nv = sizeof(v) / sizeof(v[0]);
+    for (int i = 0; i < nv && i < n; ++i) cfg[i] = v[i];
+    return nv;
+}
+
+template <int PREC, int MODE>
+int pipeline_config_r(int r, int32_t *cfg, int n)
+{
+    switch (r) {
+        case 1: return pipeline_config<1, PREC, MODE>(cfg, n);
+        case 2: return pipeline_config<2, PREC, MODE>(cfg, n);
+        case 3: return pipeline_config<3, PREC, MODE>(cfg, n);
+        case 4: return pipeline_config<4, PREC, MODE>(cfg, n);
+        default: return -1;
+    }
+}
+
+template <int MODE>
+int pipeline_config_p(int prec, int r, int32_t *cfg, int n)
+{
+    switch (prec) {
+        case P_TF32: return pipeline_config_r<P_TF32, MODE>(r, cfg, n);
+        case P_3XTF32: return pipeline_config_r<P_3XTF32, MODE>(r, cfg, n);
+        case P_BF16X3: return pipeline_config_r<P_BF16X3, MODE>(r, cfg, n);
+        default: return -1;
+    }
+}
+
 }  // namespace
 
 int band_tc_supported(int shape, int r, int path)
@@ -1111,3 +1145,13 @@ cudaError_t launch_band_tc(const Sweep &s, int path, const CUtensorMap &map, int
 }
 
 }  // namespace mms
+
+extern "C" int32_t mms_tc_pipeline_config(int32_t shape, int32_t radius, int32_t path, int32_t *cfg, int32_t ncfg)
+{
+    using namespace mms;
+    if (ncfg < 0 || (ncfg > 0 && !cfg) || !band_tc_supported(shape, radius, path)) return -1;
+    const int prec = prec_of(path);
+    if (shape == MMS_BOX) return pipeline_config_p<M_BOX>(prec, radius, cfg, ncfg);
+    if (shape == MMS_STAR) return pipeline_config_p<M_STAR>(prec, radius, cfg, ncfg);
+    return pipeline_config_p<M_PLANAR>(prec, radius, cfg, ncfg);
+}
